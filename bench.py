@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Throughput of the staggered-mesh EB advance (flux + WSRD on four grids).
+
+One step = one forward-Euler pass of the whole path (Eq. basic_fv_srd):
+flux divergence and provisional update on the c, u, v, w grids, then
+weighted state redistribution of all five fields.  Workload: the 3D
+Gaussian hill, 256 x 256 x 128 cells, synthetic seeded state.  The headline
+``value`` is the mixed (FP32 state, FP64 tiny-cell geometry and weights)
+path; the FP64 path is reported beside it under ``fp64``.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank advances its own
+replica of the workload; value = all ranks' cell-updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EB cell-updates/s (flux+WSRD, 4 grids) mixed vs FP64 path, % of HBM roofline"
+UNIT = "cell-updates/s"
+FIELDS = ("rho", "rhotheta", "rhou", "rhov", "rhow")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("hill256", "grf512"), default="hill256")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2604_11959_gb300 import inputs
+    return {"hill256": inputs.HILL_256, "grf512": inputs.GRF_512}[name]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.lines = []
+        self.proc = None
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle as CPU baseline (and the reference arm)
+# ---------------------------------------------------------------------------
+def cpu_baseline(w, budget_s=15.0, window=96):
+    """The FP64 oracle timed on this host's cores on a window of the same
+    workload (window x window columns, full height), geometry untimed."""
+    from oracle import eb_oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    h = w.heights()
+    U = w.state("sheltered")
+    x0 = (w.nx - window) // 2
+    dom = O.Domain(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, h, window=(x0, x0, window, window))
+    G = O.geometry(dom)
+    T = O.wsrd_setup(dom, G)
+    Uw = {f: dom.window_of(U[f]) for f in FIELDS}
+    t0 = time.perf_counter()
+    Uw = O.step(dom, G, T, Uw, w.dt(), 1)
+    t1 = time.perf_counter() - t0
+    n = int(max(1, min(50, budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    O.step(dom, G, T, Uw, w.dt(), n)
+    el = time.perf_counter() - t0
+    cells = window * window * w.nz
+    return {"value": cells * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{window}x{window} columns x {w.nz} levels of {w.name}, {n} forward-Euler steps, "
+                      f"{el:.1f} s, geometry set-up untimed"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def traffic_record(kernel, workload_name, precision):
+    """DRAM bytes per launch of a kernel from a committed ncu summary, valid
+    only while the kernel source is unchanged (hash recorded with it)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}_{precision}.txt")
+    src = os.path.join(ROOT, "paper_2604_11959_gb300", "csrc", "eb_step.cu")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        rec = {}
+        for line in open(path):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+        if rec.get("source_sha256_16") != h:
+            return None
+        return float(rec["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist):
+    import torch
+    geom = eb.Geometry(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, torch.from_numpy(h).cuda(), precision=precision,
+                       ref_rho=torch.from_numpy(refs[0]).cuda(), ref_rhotheta=torch.from_numpy(refs[1]).cuda())
+    info = geom.info()
+    A = eb.device_state(U, precision, refs)
+    B = geom.empty_state()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    dt = w.dt()
+    for _ in range(warmup):
+        eb.step(geom, A, dt, 1, out=B)
+        A, B = B, A
+    eb.sync_status(geom)
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for q in range(steps):
+        flush.zero_()   # evict the state from L2 (untimed)
+        evs[q][0].record(stream)
+        eb.step(geom, A, dt, 1, out=B)
+        evs[q][1].record(stream)
+        A, B = B, A
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    ms = [a.elapsed_time(b) for a, b in evs]
+    eb.sync_status(geom)
+    ms_step = float(np.mean(ms))
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    # the dominant kernel alone, timed with events on its stream
+    prof = []
+    for _ in range(max(5, min(steps, 20))):
+        flush.zero_()
+        prof.append(eb.step_profile(geom, A, B, dt))
+        A, B = B, A
+    prof = np.median(np.array(prof), axis=0)
+    es = 8 if precision == "f64" else 4
+    fast_bytes = info["fast_cells"] * 10 * es
+    hbm, kind = peaks()
+    achieved = fast_bytes / (prof[0] * 1e-3) / 1e9
+    launches_per_step = 2 + sum((1 if info["small_cvs"][FG] else 0) * 2 + (1 if info["affected_cvs"][FG] else 0)
+                                for FG in (0, 0, 1, 2, 3))
+    # bytes the whole step must move: every non-covered CV read and written
+    # once, plus the band geometry records read by the near-EB kernel
+    step_bytes = sum(info["cvs"][g] * (2 if g else 4) for g in range(4)) * es + \
+        sum(info["band_records"]) * 10 * 8
+    res = {
+        "value": world * info["cells"] / (ms_step * 1e-3),
+        "ms_per_step": ms_step,
+        "wall_s": wall,
+        "geometry": info,
+        "phases_ms": {"fast": float(prof[0]), "band": float(prof[1]), "wsrd": float(prof[2]),
+                      "step": float(prof[3])},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic_record("k_fast", w.name, precision), "kernel": "k_fast",
+                     "algorithmic_bytes_per_launch": fast_bytes, "peak_kind": kind},
+        "step_gbs": step_bytes / (ms_step * 1e-3) / 1e9,
+        "step_frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm,
+        "gpu_launches": launches_per_step * steps,
+    }
+    return geom, res
+
+
+def e2e(eb, geom, w, U, refs, precision, steps):
+    """Same metric through the public API with host buffers: every step
+    copies the state from pinned host memory to the device, advances it, and
+    copies the result back."""
+    import torch
+    hostU = eb.host_state(U, precision, refs)
+    dev = geom.empty_state()
+    out = geom.empty_state()
+    hout = {f: torch.empty_like(hostU[f]).pin_memory() for f in FIELDS}
+    stream = torch.cuda.current_stream()
+    bi = sum(t.numel() * t.element_size() for t in hostU.values())
+    for _ in range(2):
+        for f in FIELDS:
+            dev[f].copy_(hostU[f], non_blocking=True)
+        eb.step(geom, dev, w.dt(), 1, out=out)
+        for f in FIELDS:
+            hout[f].copy_(out[f], non_blocking=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        for f in FIELDS:
+            dev[f].copy_(hostU[f], non_blocking=True)
+        eb.step(geom, dev, w.dt(), 1, out=out)
+        for f in FIELDS:
+            hout[f].copy_(out[f], non_blocking=True)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / steps
+    return {"value": w.cells() / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi,
+            "ms_per_step": ms}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    w = workload(args.workload)
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        cb = cpu_baseline(w)
+        print(json.dumps({"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": w.cells() / cb["value"] * 1e3,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "impl": "reference",
+                          "config": {"workload": w.name, "path": "FP64 CPU oracle"},
+                          "cpu_baseline": cb,
+                          "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return 0
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    from paper_2604_11959_gb300 import build as libbuild, eb, inputs
+    libbuild.build()
+    eb.load()
+    h = w.heights()
+    refs = inputs.cell_reference(w.nz, w.Lz)
+    U = w.state("sheltered")
+    dev_index = torch.cuda.current_device()
+    with ClockSampler(dev_index) as clk:
+        geom, mixed = run_precision(eb, w, h, U, refs, "mixed", args.steps, args.warmup, world, dist)
+    e2e_res = e2e(eb, geom, w, U, refs, "mixed", min(args.steps, 10)) if rank == 0 else None
+    geom.close()
+    geom64, f64 = run_precision(eb, w, h, U, refs, "f64", args.steps, args.warmup, world, dist)
+    geom64.close()
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb = cpu_baseline(w)
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": mixed["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": w.name, "cells": w.cells(), "precision": "mixed", "stages": 1,
+                   "state": "stratified, wind u=1 above the terrain, smooth seeded perturbations",
+                   "l2": "512 MiB buffer written before every timed step (untimed); per-step CUDA events",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "roofline": mixed["roofline"],
+        "step_hbm_frac": mixed["step_frac"],
+        "phases_ms": mixed["phases_ms"],
+        "cpu_baseline": cb,
+        "e2e": e2e_res,
+        "gpu_launches": mixed["gpu_launches"],
+        "clocks": clk.summary(),
+        "fp64": {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "roofline": f64["roofline"],
+                 "step_hbm_frac": f64["step_frac"], "phases_ms": f64["phases_ms"]},
+        "geometry": {k: mixed["geometry"][k] for k in ("cells", "fast_cells", "band_cvs", "small_cvs",
+                                                       "affected_cvs", "tiny_cvs", "min_alpha")},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

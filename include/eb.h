@@ -1,0 +1,210 @@
+/*
+ * eb.h -- C ABI of the GB300 library for the explicit embedded-boundary (EB)
+ * advance on a staggered mesh (Kang et al., "An Embedded Boundary Scheme for
+ * Three-Dimensional Flow Over Terrain on a Staggered Mesh").
+ *
+ * The library computes, on one GPU:
+ *   - the cut-cell geometry of the terrain z = h(x, y) on the cell-centred
+ *     grid and on the x-, y- and z-face grids (Sec. 3.2), once;
+ *   - the cut-cell flux divergence dU of every grid (Sec. 3.1, Eqs.
+ *     update-cc and update-fc; advective fluxes of Sec. 4.1 with zero flux
+ *     through the EB and the domain walls);
+ *   - weighted state redistribution R on every grid (Sec. 5.1);
+ *   - the step U^{n+1} = R[U^n + dt dU(U^n)] of Eq. basic_fv_srd, or the
+ *     three-stage Runge-Kutta form of Algorithm 1 (Sec. 5.2).
+ *
+ * Conventions (all entry points):
+ *   - Domain [0,Lx] x [0,Ly] x [0,Lz] with origin 0, nx x ny x nz cells,
+ *     periodic in x and y, walls at z = 0 and z = Lz.  Fluid is z > h.
+ *   - Every array pointer is a DEVICE pointer owned by the caller unless
+ *     stated otherwise; arrays are dense, x fastest: index i + nx*(j + ny*k).
+ *   - Field sizes: rho, rho*theta (cell centres), rho*u (x faces), rho*v
+ *     (y faces): nx*ny*nz.  rho*w (z faces): nx*ny*(nz+1); its levels 0 and
+ *     nz are the walls, are never updated and enter every flux as zero.
+ *   - Element type: double for EB_F64, float for EB_MIXED.  With a reference
+ *     profile (eb_geom_build), rho and rho*theta hold perturbations about it.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream).  Argument errors are found
+ *     on the host before anything is launched and return
+ *     EB_ERR_INVALID_ARG.  Errors raised inside kernels (non-finite values,
+ *     an expired wait) latch into a device status word that eb_sync_status
+ *     reports.  No C++ exception crosses this boundary.
+ *   - eb_last_error() returns a thread-local message for the last non-OK
+ *     status of the calling thread.
+ */
+#ifndef EB_H
+#define EB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EB_OK = 0,
+  EB_ERR_INVALID_ARG = 1, /* bad pointer, size, enum or handle            */
+  EB_ERR_CUDA = 2,        /* a CUDA runtime call failed                    */
+  EB_ERR_OOM = 3,         /* device allocation failed                      */
+  EB_ERR_NUMERIC = 4,     /* a kernel met a non-finite value              */
+  EB_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired            */
+  EB_ERR_STATE = 6        /* call not valid in the handle's current state  */
+} eb_status;
+
+typedef enum {
+  EB_F64 = 0,   /* state, fluxes and redistribution in double                    */
+  EB_MIXED = 1  /* float state and fluxes; double geometry moments for CVs with
+                   volume fraction below 1e-3 and double redistribution weights;
+                   compensated sums in the neighbourhood averages               */
+} eb_precision;
+
+typedef enum { EB_GRID_C = 0, EB_GRID_U = 1, EB_GRID_V = 2, EB_GRID_W = 3 } eb_grid;
+
+typedef enum { EB_RHO = 0, EB_RHOTHETA = 1, EB_RHOU = 2, EB_RHOV = 3, EB_RHOW = 4 } eb_field;
+
+typedef struct {
+  int nx, ny, nz;        /* cells, each >= 4                                      */
+  double Lx, Ly, Lz;     /* domain lengths, > 0                                    */
+  double v_target_frac;  /* small-cell threshold V_target / (dx dy dz); the paper
+                            uses 1/2 (Sec. 5.1).  Must lie in (0, 1].            */
+} eb_desc;
+
+typedef struct eb_geom_s *eb_geom; /* opaque; owns all device geometry and tables */
+
+typedef struct {
+  void *rho, *rhotheta, *rhou, *rhov, *rhow; /* caller-owned device arrays */
+} eb_state;
+
+/* Geometry exported by eb_geom_export, one dense double array of
+ * nx*ny*nz_g values (nz_g = nz+1 on the w grid).  Lengths are in cell units,
+ * offsets are relative to the CV (or face) centre; faces are the LOW face of
+ * each CV in the named direction. */
+typedef enum {
+  EB_X_ALPHA = 0,                                       /* volume fraction         */
+  EB_X_CENT_X = 1, EB_X_CENT_Y = 2, EB_X_CENT_Z = 3,    /* volume centroid offset  */
+  EB_X_BETA_X = 4, EB_X_BETA_Y = 5, EB_X_BETA_Z = 6,    /* face area fractions     */
+  EB_X_FCENT_X1 = 7, EB_X_FCENT_X2 = 8,                 /* x face centroid (y, z)  */
+  EB_X_FCENT_Y1 = 9, EB_X_FCENT_Y2 = 10,                /* y face centroid (x, z)  */
+  EB_X_FCENT_Z1 = 11, EB_X_FCENT_Z2 = 12,               /* z face centroid (x, y)  */
+  EB_X_AEB = 13,                                        /* EB area / (dx dy)       */
+  EB_X_NRM_X = 14, EB_X_NRM_Y = 15, EB_X_NRM_Z = 16,    /* unit EB normal, into fluid */
+  EB_X_EBC_X = 17, EB_X_EBC_Y = 18, EB_X_EBC_Z = 19,    /* EB centroid offset      */
+  EB_X_FLAG = 20,        /* 0 covered, 1 regular, 2 cut (nodal level-set test)    */
+  EB_X_CODE = 21,        /* merging-neighbourhood code, 0 = not a small CV        */
+  EB_X_NNB = 22,         /* N: number of neighbourhoods holding the CV            */
+  EB_X_KAPPA = 23, EB_X_OMEGA = 24, EB_X_VHAT = 25,
+  EB_X_XHAT_X = 26, EB_X_XHAT_Y = 27, EB_X_XHAT_Z = 28,
+  EB_X_COUNT = 29
+} eb_export_field;
+
+/*
+ * Neighbourhood code (EB_X_CODE) of a small CV (Sec. 5.1: merge first along
+ * the EB normal, then the next-largest normal component, then to 2x2x2):
+ *   axes a1, a2, a3 ordered by decreasing |n_d| of the unit EB normal, two
+ *   components counting as equal when they differ by at most 1e-12, ties
+ *   broken x before y before z; permutation index p over
+ *   (xyz, xzy, yxz, yzx, zxy, zyx); sign bits b_d = 1 where n_d < 0;
+ *   growth level L = 1 (two CVs), 2 (2x2), 3 (2x2x2);
+ *   code = 1 + (8 p + b_x + 2 b_y + 4 b_z) * 3 + (L - 1).
+ */
+
+/* Sizes of what a geometry handle built. */
+typedef struct {
+  int64_t cells;            /* nx*ny*nz                                      */
+  int64_t cvs[4];           /* non-covered CVs per grid                       */
+  int64_t band_records[4];  /* CVs stored with explicit geometry per grid     */
+  int64_t small_cvs[4];     /* CVs with volume fraction below the threshold   */
+  int64_t affected_cvs[4];  /* CVs the redistribution writes                  */
+  int64_t band_cvs[4];      /* CVs updated by the general (near-EB) kernel    */
+  int64_t tiny_cvs[4];      /* cut CVs with volume fraction below 1e-3        */
+  int64_t fast_cells;       /* base cells updated by the geometry-free kernel  */
+  double min_alpha;         /* smallest positive volume fraction, any grid    */
+  int64_t device_bytes;     /* device memory held by the handle               */
+} eb_geom_info_t;
+
+/*
+ * Build the geometry of all four grids and the redistribution tables
+ * (Sec. 3.2: nodal level set, cut faces, cut cells, staggered CVs from two
+ * half-cells; Sec. 5.1: merging neighbourhoods, kappa, omega, weighted
+ * volume and centroid, all fixed at set-up).
+ *   desc         grid and threshold, read during the call.
+ *   h_nodes      device, (nx+1)*(ny+1) doubles, node (i, j) at i + (nx+1) j,
+ *                heights at x = i Lx/nx, y = j Ly/ny; the last row and column
+ *                must repeat the first (periodicity).
+ *   prec         precision of every later state argument.
+ *   ref_rho, ref_rhotheta
+ *                device, nz doubles each, or both NULL: a reference profile
+ *                at cell-centre levels; rho and rho*theta states then hold
+ *                values minus ref[k].  Copied during the call.
+ *   out          receives the handle; destroy it with eb_geom_destroy.
+ * Synchronises the stream (sizes are read back).  EB_ERR_OOM when the device
+ * has no room; nothing is leaked on failure.
+ */
+eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision prec, const double *ref_rho,
+                        const double *ref_rhotheta, void *stream, eb_geom *out);
+
+/* Free everything the handle owns (synchronises the device).  NULL is OK. */
+eb_status eb_geom_destroy(eb_geom geom);
+
+/* Sizes and counts of the handle. */
+eb_status eb_geom_info(eb_geom geom, eb_geom_info_t *info);
+
+/* Write one geometry or redistribution field of one grid as a dense double
+ * array of nx*ny*nz_g values into dst (device). */
+eb_status eb_geom_export(eb_geom geom, eb_grid grid, eb_export_field field, double *dst, void *stream);
+
+/*
+ * Flux divergence of Eqs. update-cc / update-fc for every field:
+ *   dU = -(1/alpha) [ sum_d (beta_+ F_+ - beta_- F_-) / delta_d ]
+ * with third-order upwind face values (second-order centred where the far
+ * upstream CV is covered or beyond a wall), fluxes interpolated to cut-face
+ * centroids, zero flux through the EB and the walls (Sec. 4.1).  dU is zero
+ * on covered CVs and on the wall levels of rho*w.  U and dU must not overlap.
+ */
+eb_status eb_flux_div(eb_geom geom, const eb_state *U, eb_state *dU, void *stream);
+
+/*
+ * Weighted state redistribution of one field (Sec. 5.1, Eqs. qhat_omega,
+ * qrecon, final_update_omega): Unew = R[Uhat] on the field's grid.  CVs that
+ * redistribution does not touch are copied.  Uhat and Unew may be the same
+ * array (in-place) or must not overlap.
+ */
+eb_status eb_wsrd(eb_geom geom, eb_field field, const void *Uhat, void *Unew, void *stream);
+
+/*
+ * nsteps steps of Algorithm 1 with zero source.  stages = 1: forward Euler,
+ * U^{n+1} = R[U^n + dt dU(U^n)] (Eq. basic_fv_srd); stages = 3: the
+ * three-stage Runge-Kutta of Sec. 5.2 with redistribution after every stage,
+ * U1 = R[U + dt/3 dU(U)], U2 = R[U + dt/2 dU(U1)], U' = R[U + dt dU(U2)].
+ * Un is read only; the result lands in Unp1 (which must not overlap Un);
+ * intermediate states use handle-owned scratch.  Covered CVs and the rho*w
+ * wall levels of Unp1 receive Un's values.
+ */
+eb_status eb_step(eb_geom geom, const eb_state *Un, eb_state *Unp1, double dt, int nsteps, int stages, void *stream);
+
+/*
+ * One forward-Euler step exactly like eb_step(nsteps = 1, stages = 1), with
+ * CUDA events recorded on the stream between its phases.  On return (the
+ * stream is synchronised) ms[0] holds the geometry-free bulk flux/update
+ * kernel, ms[1] the near-EB flux/update kernel, ms[2] the redistribution
+ * passes of all five fields and ms[3] the whole step, in milliseconds.
+ * Used by benchmarks to time the dominant kernel on its own stream.
+ */
+eb_status eb_step_profile(eb_geom geom, const eb_state *Un, eb_state *Unp1, double dt, void *stream, float ms[4]);
+
+/* Synchronise the stream, then return (and clear) the first device-side
+ * error latched since the last call: EB_ERR_NUMERIC or EB_ERR_TIMEOUT. */
+eb_status eb_sync_status(eb_geom geom, void *stream);
+
+/* Thread-local message of the calling thread's last error ("" if none). */
+const char *eb_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int eb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EB_H */

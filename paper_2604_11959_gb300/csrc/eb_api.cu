@@ -1,0 +1,503 @@
+// eb_api.cu -- the C ABI of include/eb.h: argument checks, the geometry
+// handle, and the orchestration of the kernels on the caller's stream.
+#include "eb_step.cuh"
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#define EB_VERSION_NUM 100
+
+namespace {
+
+thread_local std::string g_last_error;
+
+eb_status fail(eb_status st, const char *fmt, const char *arg = nullptr) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), fmt, arg ? arg : "");
+  g_last_error = buf;
+  return st;
+}
+
+eb_status cuda_fail(cudaError_t e, const char *where) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  g_last_error = buf;
+  return e == cudaErrorMemoryAllocation ? EB_ERR_OOM : EB_ERR_CUDA;
+}
+
+#define CUDA_TRY(x, where)                      \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+struct eb_geom_s {
+  eb_desc desc;
+  Dims D;
+  eb_precision prec;
+  int device = 0;
+  double *h = nullptr;
+  int *kcov[4] = {}, *kreg[4] = {}, *kxt[4] = {};
+  long long *roff[4] = {};
+  int *kfast = nullptr;
+  GridDev G[4];
+  WsrdDev W[4];
+  double *ref_d[2] = {nullptr, nullptr};
+  float *ref_f[2] = {nullptr, nullptr};
+  double *zero_d = nullptr;
+  float *zero_f = nullptr;
+  unsigned *status = nullptr;
+  void *qhat = nullptr, *sig = nullptr;
+  long long max_small = 0;
+  // scratch states for eb_step: 4 x 5 fields
+  void *scr[4][5] = {};
+  std::vector<void *> allocs;
+  eb_geom_info_t info;
+
+  template <typename P>
+  cudaError_t alloc(P **p, long long count) {
+    *p = nullptr;
+    if (count < 1) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(P) * (size_t)count);
+    if (e == cudaSuccess) {
+      allocs.push_back((void *)*p);
+      info.device_bytes += (int64_t)(sizeof(P) * count);
+    }
+    return e;
+  }
+  void release() {
+    for (void *p : allocs) cudaFree(p);
+    allocs.clear();
+    for (int g = 0; g < 4; ++g) free_wsrd(W[g]);
+  }
+};
+
+namespace {
+
+bool bad_desc(const eb_desc *d, std::string &why) {
+  if (!d) { why = "desc is NULL"; return true; }
+  if (d->nx < 4 || d->ny < 4 || d->nz < 4) { why = "nx, ny, nz must be >= 4"; return true; }
+  if ((long long)d->nx * d->ny * (d->nz + 1) > (1LL << 40)) { why = "grid too large"; return true; }
+  if (!(d->Lx > 0) || !(d->Ly > 0) || !(d->Lz > 0) || !isfinite(d->Lx) || !isfinite(d->Ly) || !isfinite(d->Lz)) {
+    why = "Lx, Ly, Lz must be finite and > 0";
+    return true;
+  }
+  if (!(d->v_target_frac > 0.0) || !(d->v_target_frac <= 1.0)) { why = "v_target_frac must lie in (0, 1]"; return true; }
+  return false;
+}
+
+template <typename T>
+cudaError_t fill_ref(eb_geom g, const double *src, double **dd, float **ff, cudaStream_t s) {
+  const int nz = g->D.nz;
+  std::vector<double> hv(nz, 0.0);
+  if (src) {
+    cudaError_t e = cudaMemcpyAsync(hv.data(), src, sizeof(double) * nz, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+  }
+  std::vector<float> hf(nz);
+  for (int k = 0; k < nz; ++k) hf[k] = (float)hv[k];
+  cudaError_t e = g->alloc(dd, nz);
+  if (e != cudaSuccess) return e;
+  e = g->alloc(ff, nz);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(*dd, hv.data(), sizeof(double) * nz, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*ff, hf.data(), sizeof(float) * nz, cudaMemcpyHostToDevice);
+}
+
+eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, const double *ref_rt, cudaStream_t s) {
+  const Dims &D = g->D;
+  const long long ncol = (long long)D.nx * D.ny;
+  const long long nh = (long long)(D.nx + 1) * (D.ny + 1);
+  CUDA_TRY(g->alloc(&g->h, nh), "alloc heights");
+  CUDA_TRY(cudaMemcpyAsync(g->h, h_nodes, sizeof(double) * nh, cudaMemcpyDeviceToDevice, s), "copy heights");
+  long long *counts = nullptr;
+  long long scan_room = 2 * (ncol + 2) + 8;
+  CUDA_TRY(g->alloc(&counts, scan_room), "alloc counts");
+  long long nrec[4];
+  for (int q = 0; q < 4; ++q) {
+    CUDA_TRY(g->alloc(&g->kcov[q], ncol), "alloc kcov");
+    CUDA_TRY(g->alloc(&g->kreg[q], ncol), "alloc kreg");
+    CUDA_TRY(g->alloc(&g->kxt[q], ncol), "alloc kxt");
+    CUDA_TRY(g->alloc(&g->roff[q], ncol + 1), "alloc roff");
+    launch_band_bounds(g->h, D, q, g->kcov[q], g->kreg[q], s);
+  }
+  for (int q = 0; q < 4; ++q) {
+    const int nzg = nzg_of(D, q);
+    CUDA_TRY(cudaMemsetAsync(g->roff[q], 0, sizeof(long long) * (ncol + 1), s), "memset roff");
+    launch_band_top(D, nzg, g->kcov[q], g->kreg[q], g->kxt[q], g->roff[q], s);
+    scan_exclusive(g->roff[q], ncol + 1, counts, s);
+    CUDA_TRY(cudaMemcpyAsync(&nrec[q], counts, sizeof(long long), cudaMemcpyDeviceToHost, s), "read nrec");
+  }
+  CUDA_TRY(g->alloc(&g->kfast, ncol), "alloc kfast");
+  const int *kr[4] = {g->kreg[0], g->kreg[1], g->kreg[2], g->kreg[3]};
+  launch_fast_level(D, kr, g->kfast, s);
+  CUDA_TRY(cudaGetLastError(), "band kernels");
+  CUDA_TRY(cudaStreamSynchronize(s), "band sync");
+  long long tmp_need = 0;
+  for (int q = 0; q < 4; ++q) {
+    GridDev &G = g->G[q];
+    G.nzg = nzg_of(D, q);
+    G.kcov = g->kcov[q];
+    G.kxt = g->kxt[q];
+    G.roff = g->roff[q];
+    G.nrec = nrec[q];
+    const long long n = nrec[q];
+    g->info.band_records[q] = n;
+    CUDA_TRY(g->alloc(&G.alpha, n), "alloc geometry");
+    CUDA_TRY(g->alloc(&G.cent, 3 * n), "alloc geometry");
+    CUDA_TRY(g->alloc(&G.beta, 3 * n), "alloc geometry");
+    CUDA_TRY(g->alloc(&G.fcent, 6 * n), "alloc geometry");
+    CUDA_TRY(g->alloc(&G.nrm, 3 * n), "alloc geometry");
+    CUDA_TRY(g->alloc(&G.aeb, n), "alloc geometry");
+    CUDA_TRY(g->alloc(&G.ebc, 3 * n), "alloc geometry");
+    CUDA_TRY(g->alloc(&G.flag, n), "alloc geometry");
+    CUDA_TRY(g->alloc(&G.alpha_f, n), "alloc geometry");
+    CUDA_TRY(g->alloc(&G.beta_f, 3 * n), "alloc geometry");
+    CUDA_TRY(g->alloc(&G.fcent_f, 6 * n), "alloc geometry");
+    CUDA_TRY(g->alloc(&G.code, n), "alloc tables");
+    CUDA_TRY(g->alloc(&G.nnb, n), "alloc tables");
+    CUDA_TRY(g->alloc(&G.kappa, n), "alloc tables");
+    CUDA_TRY(g->alloc(&G.omega, n), "alloc tables");
+    CUDA_TRY(g->alloc(&G.vhat, n), "alloc tables");
+    CUDA_TRY(g->alloc(&G.xhat, 3 * n), "alloc tables");
+    launch_band_geometry(g->h, D, q, G, s);
+    tmp_need = std::max(tmp_need, 2 * (n + 1) + 1 + (n + 1) / 256 + 8);
+  }
+  CUDA_TRY(cudaGetLastError(), "geometry kernels");
+  long long *tmp = nullptr;
+  CUDA_TRY(g->alloc(&tmp, tmp_need), "alloc set-up scratch");
+  for (int q = 0; q < 4; ++q) {
+    cudaError_t e = build_wsrd(D, q, g->G[q], g->G, g->desc.v_target_frac, g->W[q], s, tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "redistribution set-up");
+    g->max_small = std::max(g->max_small, g->W[q].nsmall);
+    g->info.small_cvs[q] = g->W[q].nsmall;
+    g->info.affected_cvs[q] = g->W[q].naff;
+  }
+  CUDA_TRY(g->alloc((double **)&g->qhat, g->max_small), "alloc qhat");
+  CUDA_TRY(g->alloc((double **)&g->sig, 3 * g->max_small), "alloc sig");
+  CUDA_TRY(fill_ref<double>(g, ref_rho, &g->ref_d[0], &g->ref_f[0], s), "reference");
+  CUDA_TRY(fill_ref<double>(g, ref_rt, &g->ref_d[1], &g->ref_f[1], s), "reference");
+  CUDA_TRY(g->alloc(&g->status, 1), "alloc status");
+  CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(unsigned), s), "memset status");
+  // host-side counts for eb_geom_info
+  std::vector<int> kc(ncol), kf(ncol);
+  CUDA_TRY(cudaMemcpy(kf.data(), g->kfast, sizeof(int) * ncol, cudaMemcpyDeviceToHost), "read kfast");
+  g->info.cells = (int64_t)ncol * D.nz;
+  g->info.fast_cells = 0;
+  for (long long c = 0; c < ncol; ++c) g->info.fast_cells += D.nz - std::min(kf[c], D.nz);
+  double amin = 1.0;
+  for (int q = 0; q < 4; ++q) {
+    CUDA_TRY(cudaMemcpy(kc.data(), g->kcov[q], sizeof(int) * ncol, cudaMemcpyDeviceToHost), "read kcov");
+    const int nzg = nzg_of(D, q);
+    int64_t cvs = 0, band = 0;
+    for (long long c = 0; c < ncol; ++c) {
+      cvs += nzg - kc[c];
+      for (int k = kc[c]; k < std::min(kf[c], nzg); ++k)
+        if (!(q == 3 && (k == 0 || k == D.nz))) ++band;
+    }
+    g->info.cvs[q] = cvs;
+    g->info.band_cvs[q] = band;
+    const long long n = nrec[q];
+    std::vector<double> al(n > 0 ? n : 1);
+    std::vector<uint8_t> fl(n > 0 ? n : 1);
+    if (n > 0) {
+      CUDA_TRY(cudaMemcpy(al.data(), g->G[q].alpha, sizeof(double) * n, cudaMemcpyDeviceToHost), "read alpha");
+      CUDA_TRY(cudaMemcpy(fl.data(), g->G[q].flag, n, cudaMemcpyDeviceToHost), "read flag");
+    }
+    int64_t tiny = 0;
+    for (long long r = 0; r < n; ++r) {
+      if (fl[r] == EBK_CUT && al[r] > 0.0 && al[r] < 1e-3) ++tiny;
+      if (al[r] > 0.0 && al[r] < amin) amin = al[r];
+    }
+    g->info.tiny_cvs[q] = tiny;
+  }
+  g->info.min_alpha = amin;
+  return EB_OK;
+}
+
+bool state_ok(const eb_state *U, size_t align) {
+  if (!U) return false;
+  const void *p[5] = {U->rho, U->rhotheta, U->rhou, U->rhov, U->rhow};
+  for (const void *q : p)
+    if (!q || ((uintptr_t)q % align)) return false;
+  return true;
+}
+
+void **state_ptrs(const eb_state *U) { return (void **)&U->rho; }
+
+template <typename T>
+StepArgs<T> step_args(eb_geom g, void *const src[5], void *const base[5], void *const out[5], double dt, int copy) {
+  StepArgs<T> A;
+  A.D = g->D;
+  for (int f = 0; f < 5; ++f) {
+    A.src.f[f] = (const T *)src[f];
+    A.base[f] = base ? (const T *)base[f] : nullptr;
+    A.out[f] = (T *)out[f];
+  }
+  if (sizeof(T) == sizeof(double)) {
+    A.src.ref_rho = (const T *)g->ref_d[0];
+    A.src.ref_rt = (const T *)g->ref_d[1];
+  } else {
+    A.src.ref_rho = (const T *)g->ref_f[0];
+    A.src.ref_rt = (const T *)g->ref_f[1];
+  }
+  A.dt = dt;
+  A.dtT = (T)dt;
+  A.kfast = g->kfast;
+  for (int q = 0; q < 4; ++q) A.G[q] = g->G[q];
+  A.status = g->status;
+  A.copy_static = copy;
+  return A;
+}
+
+template <typename T>
+void wsrd_field(eb_geom g, int field, T *u, cudaStream_t s) {
+  const int grid = field <= 1 ? 0 : field - 1;
+  WsrdArgs<T> R;
+  R.D = g->D;
+  R.W = g->W[grid];
+  R.u = u;
+  R.ref = nullptr;
+  if (field <= 1) R.ref = sizeof(T) == sizeof(double) ? (const T *)g->ref_d[field] : (const T *)g->ref_f[field];
+  R.qhat = (T *)g->qhat;
+  R.sig = (T *)g->sig;
+  R.status = g->status;
+  launch_wsrd(R, s);
+}
+
+template <typename T>
+void stage(eb_geom g, void *const src[5], void *const base[5], void *const out[5], double dt, int copy,
+           cudaStream_t s) {
+  launch_flux_update(step_args<T>(g, src, base, out, dt, copy), s);
+  for (int f = 0; f < 5; ++f) wsrd_field<T>(g, f, (T *)out[f], s);
+}
+
+size_t field_count(const Dims &D, int f) { return (size_t)D.nxy * (D.nz + (f == 4 ? 1 : 0)); }
+
+}  // namespace
+
+extern "C" {
+
+eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision prec, const double *ref_rho,
+                        const double *ref_rhotheta, void *stream, eb_geom *out) {
+  std::string why;
+  if (!out) return fail(EB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (bad_desc(desc, why)) return fail(EB_ERR_INVALID_ARG, "%s", why.c_str());
+  if (!h_nodes || ((uintptr_t)h_nodes % 8)) return fail(EB_ERR_INVALID_ARG, "h_nodes is NULL or misaligned");
+  if (prec != EB_F64 && prec != EB_MIXED) return fail(EB_ERR_INVALID_ARG, "unknown precision");
+  if ((ref_rho == nullptr) != (ref_rhotheta == nullptr))
+    return fail(EB_ERR_INVALID_ARG, "ref_rho and ref_rhotheta must both be given or both be NULL");
+  eb_geom g = new eb_geom_s();
+  memset(&g->info, 0, sizeof(g->info));
+  g->desc = *desc;
+  g->prec = prec;
+  cudaGetDevice(&g->device);
+  g->D.nx = desc->nx;
+  g->D.ny = desc->ny;
+  g->D.nz = desc->nz;
+  g->D.nxy = (long long)desc->nx * desc->ny;
+  g->D.dx = desc->Lx / desc->nx;
+  g->D.dy = desc->Ly / desc->ny;
+  g->D.dz = desc->Lz / desc->nz;
+  eb_status st = build_impl(g, h_nodes, ref_rho, ref_rhotheta, as_stream(stream));
+  if (st != EB_OK) {
+    cudaStreamSynchronize(as_stream(stream));
+    g->release();
+    delete g;
+    return st;
+  }
+  *out = g;
+  g_last_error.clear();
+  return EB_OK;
+}
+
+eb_status eb_geom_destroy(eb_geom geom) {
+  if (!geom) return EB_OK;
+  cudaDeviceSynchronize();
+  geom->release();
+  delete geom;
+  return EB_OK;
+}
+
+eb_status eb_geom_info(eb_geom geom, eb_geom_info_t *info) {
+  if (!geom || !info) return fail(EB_ERR_INVALID_ARG, "NULL handle or info");
+  *info = geom->info;
+  return EB_OK;
+}
+
+eb_status eb_geom_export(eb_geom geom, eb_grid grid, eb_export_field field, double *dst, void *stream) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  if ((int)grid < 0 || (int)grid > 3) return fail(EB_ERR_INVALID_ARG, "unknown grid");
+  if ((int)field < 0 || (int)field >= EB_X_COUNT) return fail(EB_ERR_INVALID_ARG, "unknown export field");
+  if (!dst || ((uintptr_t)dst % 8)) return fail(EB_ERR_INVALID_ARG, "dst is NULL or misaligned");
+  launch_export_geometry(geom->h, geom->D, (int)grid, geom->G[grid], (int)field, dst, as_stream(stream));
+  CUDA_TRY(cudaGetLastError(), "export");
+  return EB_OK;
+}
+
+eb_status eb_flux_div(eb_geom geom, const eb_state *U, eb_state *dU, void *stream) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  const size_t al = geom->prec == EB_F64 ? 8 : 4;
+  if (!state_ok(U, al) || !state_ok(dU, al)) return fail(EB_ERR_INVALID_ARG, "state pointer NULL or misaligned");
+  void **u = state_ptrs(U), **d = state_ptrs(dU);
+  for (int f = 0; f < 5; ++f)
+    for (int e = 0; e < 5; ++e)
+      if (u[f] == d[e]) return fail(EB_ERR_INVALID_ARG, "U and dU overlap");
+  if (geom->prec == EB_F64) launch_flux_update(step_args<double>(geom, u, nullptr, d, 1.0, 1), as_stream(stream));
+  else launch_flux_update(step_args<float>(geom, u, nullptr, d, 1.0, 1), as_stream(stream));
+  CUDA_TRY(cudaGetLastError(), "flux divergence");
+  return EB_OK;
+}
+
+eb_status eb_wsrd(eb_geom geom, eb_field field, const void *Uhat, void *Unew, void *stream) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  if ((int)field < 0 || (int)field > 4) return fail(EB_ERR_INVALID_ARG, "unknown field");
+  const size_t es = geom->prec == EB_F64 ? 8 : 4;
+  if (!Uhat || !Unew || ((uintptr_t)Uhat % es) || ((uintptr_t)Unew % es))
+    return fail(EB_ERR_INVALID_ARG, "field pointer NULL or misaligned");
+  const size_t bytes = field_count(geom->D, (int)field) * es;
+  cudaStream_t s = as_stream(stream);
+  if (Uhat != Unew) {
+    const char *a = (const char *)Uhat, *b = (const char *)Unew;
+    if (a < b + bytes && b < a + bytes) return fail(EB_ERR_INVALID_ARG, "Uhat and Unew overlap");
+    CUDA_TRY(cudaMemcpyAsync(Unew, Uhat, bytes, cudaMemcpyDeviceToDevice, s), "copy field");
+  }
+  if (geom->prec == EB_F64) wsrd_field<double>(geom, (int)field, (double *)Unew, s);
+  else wsrd_field<float>(geom, (int)field, (float *)Unew, s);
+  CUDA_TRY(cudaGetLastError(), "redistribution");
+  return EB_OK;
+}
+
+eb_status eb_step(eb_geom geom, const eb_state *Un, eb_state *Unp1, double dt, int nsteps, int stages, void *stream) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  const size_t es = geom->prec == EB_F64 ? 8 : 4;
+  if (!state_ok(Un, es) || !state_ok(Unp1, es)) return fail(EB_ERR_INVALID_ARG, "state pointer NULL or misaligned");
+  if (!(dt > 0.0) || !isfinite(dt)) return fail(EB_ERR_INVALID_ARG, "dt must be finite and > 0");
+  if (nsteps < 0) return fail(EB_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (stages != 1 && stages != 3) return fail(EB_ERR_INVALID_ARG, "stages must be 1 or 3");
+  void **u0 = state_ptrs(Un), **u1 = state_ptrs(Unp1);
+  for (int f = 0; f < 5; ++f) {
+    const size_t bytes = field_count(geom->D, f) * es;
+    for (int e = 0; e < 5; ++e) {
+      const size_t b2 = field_count(geom->D, e) * es;
+      const char *a = (const char *)u0[f], *b = (const char *)u1[e];
+      if (a < b + b2 && b < a + bytes) return fail(EB_ERR_INVALID_ARG, "Un and Unp1 overlap");
+    }
+  }
+  cudaStream_t s = as_stream(stream);
+  if (nsteps == 0) {
+    for (int f = 0; f < 5; ++f)
+      CUDA_TRY(cudaMemcpyAsync(u1[f], u0[f], field_count(geom->D, f) * es, cudaMemcpyDeviceToDevice, s), "copy");
+    return EB_OK;
+  }
+  // scratch states: C, D ping-pong between steps, A, B hold Runge-Kutta stages
+  const int need = stages == 3 ? 4 : 2;
+  for (int b = 0; b < need; ++b)
+    for (int f = 0; f < 5; ++f)
+      if (!geom->scr[b][f]) {
+        cudaError_t e = cudaMalloc(&geom->scr[b][f], field_count(geom->D, f) * es);
+        if (e != cudaSuccess) return cuda_fail(e, "alloc step scratch");
+        geom->allocs.push_back(geom->scr[b][f]);
+        geom->info.device_bytes += (int64_t)(field_count(geom->D, f) * es);
+      }
+  void **C = geom->scr[0], **Dd = geom->scr[1], **A = geom->scr[2], **B = geom->scr[3];
+  bool fresh[5] = {true, true, true, true, true};   // C, D, A, B, Unp1 need their static CVs once
+  auto fresh_of = [&](void **p) -> bool & {
+    return p == C ? fresh[0] : p == Dd ? fresh[1] : p == A ? fresh[2] : p == B ? fresh[3] : fresh[4];
+  };
+  void **cur = u0;
+  for (int n = 0; n < nsteps; ++n) {
+    void **dst = (n == nsteps - 1) ? u1 : (cur == C ? Dd : C);
+    if (stages == 1) {
+      bool &fr = fresh_of(dst);
+      if (geom->prec == EB_F64) stage<double>(geom, cur, cur, dst, dt, fr, s);
+      else stage<float>(geom, cur, cur, dst, dt, fr, s);
+      fr = false;
+    } else {
+      const double c[3] = {dt / 3.0, dt / 2.0, dt};
+      void **srcs[3] = {cur, A, B};
+      void **outs[3] = {A, B, dst};
+      for (int q = 0; q < 3; ++q) {
+        bool &fr = fresh_of(outs[q]);
+        if (geom->prec == EB_F64) stage<double>(geom, srcs[q], cur, outs[q], c[q], fr, s);
+        else stage<float>(geom, srcs[q], cur, outs[q], c[q], fr, s);
+        fr = false;
+      }
+    }
+    cur = dst;
+  }
+  CUDA_TRY(cudaGetLastError(), "step");
+  return EB_OK;
+}
+
+eb_status eb_step_profile(eb_geom geom, const eb_state *Un, eb_state *Unp1, double dt, void *stream, float ms[4]) {
+  if (!geom || !ms) return fail(EB_ERR_INVALID_ARG, "NULL handle or ms");
+  const size_t es = geom->prec == EB_F64 ? 8 : 4;
+  if (!state_ok(Un, es) || !state_ok(Unp1, es)) return fail(EB_ERR_INVALID_ARG, "state pointer NULL or misaligned");
+  if (!(dt > 0.0) || !isfinite(dt)) return fail(EB_ERR_INVALID_ARG, "dt must be finite and > 0");
+  void **u0 = state_ptrs(Un), **u1 = state_ptrs(Unp1);
+  for (int f = 0; f < 5; ++f)
+    for (int e = 0; e < 5; ++e)
+      if (u0[f] == u1[e]) return fail(EB_ERR_INVALID_ARG, "Un and Unp1 overlap");
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t ev[4];
+  for (int q = 0; q < 4; ++q) CUDA_TRY(cudaEventCreate(&ev[q]), "event");
+  cudaEventRecord(ev[0], s);
+  if (geom->prec == EB_F64) {
+    StepArgs<double> A = step_args<double>(geom, u0, u0, u1, dt, 1);
+    launch_flux_fast(A, s);
+    cudaEventRecord(ev[1], s);
+    launch_flux_band(A, s);
+    cudaEventRecord(ev[2], s);
+    for (int f = 0; f < 5; ++f) wsrd_field<double>(geom, f, (double *)u1[f], s);
+  } else {
+    StepArgs<float> A = step_args<float>(geom, u0, u0, u1, dt, 1);
+    launch_flux_fast(A, s);
+    cudaEventRecord(ev[1], s);
+    launch_flux_band(A, s);
+    cudaEventRecord(ev[2], s);
+    for (int f = 0; f < 5; ++f) wsrd_field<float>(geom, f, (float *)u1[f], s);
+  }
+  cudaEventRecord(ev[3], s);
+  cudaError_t e = cudaEventSynchronize(ev[3]);
+  if (e == cudaSuccess) {
+    cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
+    cudaEventElapsedTime(&ms[1], ev[1], ev[2]);
+    cudaEventElapsedTime(&ms[2], ev[2], ev[3]);
+    cudaEventElapsedTime(&ms[3], ev[0], ev[3]);
+  }
+  for (int q = 0; q < 4; ++q) cudaEventDestroy(ev[q]);
+  CUDA_TRY(e, "profiled step");
+  return EB_OK;
+}
+
+eb_status eb_sync_status(eb_geom geom, void *stream) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  cudaStream_t s = as_stream(stream);
+  CUDA_TRY(cudaStreamSynchronize(s), "synchronise");
+  unsigned w = 0;
+  CUDA_TRY(cudaMemcpy(&w, geom->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status");
+  CUDA_TRY(cudaMemset(geom->status, 0, sizeof(unsigned)), "clear status");
+  if (w & EB_DEV_TIMEOUT) return fail(EB_ERR_TIMEOUT, "a bounded device-side wait expired");
+  if (w & EB_DEV_NUMERIC) return fail(EB_ERR_NUMERIC, "a kernel produced a non-finite value");
+  return EB_OK;
+}
+
+const char *eb_last_error(void) { return g_last_error.c_str(); }
+
+int eb_version(void) { return EB_VERSION_NUM; }
+
+}  // extern "C"

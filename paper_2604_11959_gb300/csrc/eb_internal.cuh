@@ -1,0 +1,225 @@
+// eb_internal.cuh -- device data layout and shared device code of the EB
+// library.  Not part of the ABI.
+//
+// Layout.  State fields are dense SoA arrays, x fastest.  Geometry is NOT
+// dense: per grid and per column (i, j) only the levels kcov <= k < kxt carry
+// an explicit record ("band"); levels below kcov are covered, levels at or
+// above kxt are regular (full cell, open faces).  The band covers the cut CVs
+// plus one level of the redistribution neighbourhoods above them.  A column's
+// records are contiguous from roff[col].  kfast[col] is the first level from
+// which every CV of every grid at that column and all CVs its flux stencil
+// reads are regular, so the bulk kernel needs no geometry at all there.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/eb.h"
+
+#define EBK_COVERED 0
+#define EBK_REGULAR 1
+#define EBK_CUT 2
+
+// Records of one grid.
+struct GridDev {
+  int nzg;                 // nz, or nz + 1 for w
+  int *kcov, *kxt;         // [ncol]
+  long long *roff;         // [ncol + 1]
+  long long nrec;
+  // geometry, FP64, per record
+  double *alpha, *cent, *beta, *fcent, *nrm, *aeb, *ebc;   // cent/beta/nrm/ebc: 3*nrec, fcent: 6*nrec
+  uint8_t *flag;
+  // float copies for the mixed path: alpha, beta[3], fcent[6]
+  float *alpha_f, *beta_f, *fcent_f;
+  // redistribution per record
+  uint8_t *code;
+  int *nnb;
+  double *kappa, *omega, *vhat, *xhat;   // xhat: 3*nrec
+};
+
+struct Dims {
+  int nx, ny, nz;
+  long long nxy;
+  double dx, dy, dz;
+};
+
+__host__ __device__ inline int wrapi(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+__host__ __device__ inline int nzg_of(const Dims &D, int g) { return D.nz + (g == 3 ? 1 : 0); }
+
+__device__ inline long long lin(const Dims &D, int i, int j, int k) {
+  return (long long)wrapi(i, D.nx) + (long long)D.nx * ((long long)wrapi(j, D.ny) + (long long)D.ny * k);
+}
+
+// Classification of CV (i, j, k) of a grid: flag and record id (or -1).
+struct CvInfo {
+  int flag;
+  long long rec;
+};
+
+__device__ inline CvInfo cv_info(const GridDev &G, const Dims &D, int i, int j, int k) {
+  if (k < 0 || k >= G.nzg) return {EBK_COVERED, -1};
+  int col = wrapi(i, D.nx) + D.nx * wrapi(j, D.ny);
+  int kc = G.kcov[col];
+  if (k < kc) return {EBK_COVERED, -1};
+  if (k >= G.kxt[col]) return {EBK_REGULAR, -1};
+  long long r = G.roff[col] + (k - kc);
+  return {(int)G.flag[r], r};
+}
+
+// Status word bits latched by kernels.
+#define EB_DEV_NUMERIC 1u
+#define EB_DEV_TIMEOUT 2u
+
+// ---------------------------------------------------------------------------
+// State access
+// ---------------------------------------------------------------------------
+template <typename T>
+struct StateIn {
+  const T *f[5];             // rho, rho*theta, rho*u, rho*v, rho*w
+  const T *ref_rho, *ref_rt; // per cell level, reference added back to rho and rho*theta
+};
+
+template <typename T>
+struct StateOut {
+  T *f[5];
+};
+
+// ---------------------------------------------------------------------------
+// Geometry policies of the flux code.  Fast: every CV the stencil touches is
+// a regular CV (only the z range limits what exists).  Band: full lookups.
+// ---------------------------------------------------------------------------
+struct GeoFast {
+  __device__ static inline bool exists(const Dims &D, int g, int k) {
+    return k >= 0 && k < nzg_of(D, g);
+  }
+};
+
+struct GeoBand {
+  const GridDev *G;   // four grids
+  __device__ inline double alpha(const Dims &D, int g, int i, int j, int k) const {
+    CvInfo c = cv_info(G[g], D, i, j, k);
+    if (c.flag == EBK_COVERED) return 0.0;
+    if (c.rec < 0) return 1.0;
+    return G[g].alpha[c.rec];
+  }
+  // area fraction of the low d-face of CV (i, j, k) of grid g (0 outside the grid)
+  __device__ inline double beta(const Dims &D, int g, int d, int i, int j, int k) const {
+    CvInfo c = cv_info(G[g], D, i, j, k);
+    if (k < 0 || k >= nzg_of(D, g)) return 0.0;
+    if (c.flag == EBK_COVERED) return 0.0;
+    if (c.rec < 0) return 1.0;
+    return G[g].beta[(long long)d * G[g].nrec + c.rec];
+  }
+  __device__ inline void fcent(const Dims &D, int g, int d, int i, int j, int k, double &ga, double &gb) const {
+    CvInfo c = cv_info(G[g], D, i, j, k);
+    ga = gb = 0.0;
+    if (c.rec < 0) return;
+    ga = G[g].fcent[(long long)(2 * d) * G[g].nrec + c.rec];
+    gb = G[g].fcent[(long long)(2 * d + 1) * G[g].nrec + c.rec];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Values entering the fluxes (Sec. 4.1)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ inline T rho_at(const StateIn<T> &U, const Dims &D, int i, int j, int k) {
+  return U.ref_rho[k] + U.f[0][lin(D, i, j, k)];
+}
+
+template <typename T>
+__device__ inline T theta_at(const StateIn<T> &U, const Dims &D, int i, int j, int k) {
+  long long c = lin(D, i, j, k);
+  return (U.ref_rt[k] + U.f[1][c]) / (U.ref_rho[k] + U.f[0][c]);
+}
+
+// Is CV (i,j,k) of grid g usable by a flux stencil (exists, not covered)?
+template <class Geo>
+__device__ inline bool avail(const Geo &geo, const Dims &D, int g, int i, int j, int k);
+
+template <>
+__device__ inline bool avail<GeoFast>(const GeoFast &, const Dims &D, int g, int i, int j, int k) {
+  return GeoFast::exists(D, g, k);
+}
+
+template <>
+__device__ inline bool avail<GeoBand>(const GeoBand &geo, const Dims &D, int g, int i, int j, int k) {
+  if (k < 0 || k >= nzg_of(D, g)) return false;
+  return geo.alpha(D, g, i, j, k) > 0.0;
+}
+
+// Momentum of a face-grid CV as it enters a mass flux: zero where covered,
+// absent, or on the wall levels of w.
+template <typename T, class Geo>
+__device__ inline T mom_at(const StateIn<T> &U, const Geo &geo, const Dims &D, int g, int i, int j, int k) {
+  if (g == 3 && (k <= 0 || k >= D.nz)) return T(0);
+  if (!avail(geo, D, g, i, j, k)) return T(0);
+  return U.f[g + 1][lin(D, i, j, k)];
+}
+
+// Advected value of CV (i,j,k) of grid g (caller checked availability):
+// theta on c, the velocity on u, v, w (momentum over the mean density of
+// the non-covered cells beside the face; zero on the w walls).
+template <typename T, class Geo>
+__device__ inline T advected_at(const StateIn<T> &U, const Geo &geo, const Dims &D, int g, int i, int j, int k) {
+  if (g == 0) return theta_at(U, D, i, j, k);
+  if (g == 3 && (k <= 0 || k >= D.nz)) return T(0);
+  const int di = g == 1, dj = g == 2, dk = g == 3;
+  const bool a = avail(geo, D, 0, i - di, j - dj, k - dk);
+  const bool b = avail(geo, D, 0, i, j, k);
+  T rb;
+  if (a && b) rb = T(0.5) * (rho_at(U, D, i - di, j - dj, k - dk) + rho_at(U, D, i, j, k));
+  else if (a) rb = rho_at(U, D, i - di, j - dj, k - dk);
+  else if (b) rb = rho_at(U, D, i, j, k);
+  else return T(0);
+  return U.f[g + 1][lin(D, i, j, k)] / rb;
+}
+
+// Mass flux through the low d-face of CV (i,j,k) of grid g.
+template <typename T, class Geo>
+__device__ inline T mass_flux(const StateIn<T> &U, const Geo &geo, const Dims &D, int g, int d, int i, int j, int k) {
+  const int mg = d + 1;   // momentum grid normal to direction d
+  if (g == 0) return mom_at(U, geo, D, mg, i, j, k);
+  if (mg == g) {
+    const int di = d == 0, dj = d == 1, dk = d == 2;
+    return T(0.5) * (mom_at(U, geo, D, mg, i - di, j - dj, k - dk) + mom_at(U, geo, D, mg, i, j, k));
+  }
+  const int si = g == 1, sj = g == 2, sk = g == 3;
+  return T(0.5) * (mom_at(U, geo, D, mg, i - si, j - sj, k - sk) + mom_at(U, geo, D, mg, i, j, k));
+}
+
+// Provisional flux through the low d-face of CV (i,j,k) of grid g: mass flux
+// fm and advective flux fp = m * (third-order upwind value, or the centred
+// average when the far upstream CV is covered or beyond a wall).  The caller
+// guarantees the face is open.
+template <typename T, class Geo>
+__device__ inline void face_flux(const StateIn<T> &U, const Geo &geo, const Dims &D, int g, int d, int i, int j,
+                                 int k, T &fm, T &fp) {
+  const int di = d == 0, dj = d == 1, dk = d == 2;
+  fm = mass_flux(U, geo, D, g, d, i, j, k);
+  fp = T(0);
+  if (fm == T(0)) return;
+  const T pL = advected_at(U, geo, D, g, i - di, j - dj, k - dk);
+  const T pR = advected_at(U, geo, D, g, i, j, k);
+  T val;
+  if (fm > T(0)) {
+    if (avail(geo, D, g, i - 2 * di, j - 2 * dj, k - 2 * dk)) {
+      const T pF = advected_at(U, geo, D, g, i - 2 * di, j - 2 * dj, k - 2 * dk);
+      val = (T(5) * pL + T(2) * pR - pF) * T(1.0 / 6.0);
+    } else {
+      val = T(0.5) * (pL + pR);
+    }
+  } else {
+    if (avail(geo, D, g, i + di, j + dj, k + dk)) {
+      const T pF = advected_at(U, geo, D, g, i + di, j + dj, k + dk);
+      val = (T(2) * pL + T(5) * pR - pF) * T(1.0 / 6.0);
+    } else {
+      val = T(0.5) * (pL + pR);
+    }
+  }
+  fp = fm * val;
+}

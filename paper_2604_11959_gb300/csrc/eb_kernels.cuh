@@ -1,0 +1,52 @@
+// eb_kernels.cuh -- host-side launch wrappers shared between the library's
+// translation units.  Not part of the ABI.
+#pragma once
+
+#include "eb_internal.cuh"
+
+// Compact redistribution tables of one grid (Sec. 5.1), built once.
+struct WsrdDev {
+  long long nsmall = 0, naff = 0, nlsq = 0, nw = 0;
+  int *sid = nullptr;             // [nrec] small id of a record, -1 if not small
+  // per small CV
+  long long *s_lin = nullptr;     // state index
+  long long *s_rec = nullptr;     // record
+  int *s_nmem = nullptr;          // members incl. itself (<= 8)
+  int *s_piv = nullptr;           // pivot member of the deviation form
+  long long *s_mlin = nullptr;    // [8 * nsmall] member state indices (slot 0: itself)
+  double *s_mw = nullptr;         // [8 * nsmall] Qhat weights (sum 1)
+  double *s_me = nullptr;         // [24 * nsmall] member centroid - xhat (limiter points)
+  long long *s_loff = nullptr;    // [nsmall + 1] LSQ stencil offsets
+  long long *l_lin = nullptr;     // [nlsq] stencil CV state index
+  int *l_sid = nullptr;           // [nlsq] small id of the stencil CV or -1
+  double *l_c = nullptr;          // [3 * nlsq] gradient coefficient rows
+  // per affected CV
+  long long *a_lin = nullptr;
+  int *a_sid = nullptr;           // own small id or -1
+  double *a_eself = nullptr;      // [3 * naff] own centroid - own xhat
+  long long *a_woff = nullptr;    // [naff + 1]
+  int *w_sid = nullptr;           // [nw] small CV r whose neighbourhood holds the CV
+  double *w_k = nullptr;          // [nw] kappa_r / N_i
+  double *w_e = nullptr;          // [3 * nw] x_i - xhat_r (cell units, relative to r)
+};
+
+// eb_geom.cu
+void launch_band_bounds(const double *h, const Dims &D, int g, int *kcov, int *kreg, cudaStream_t s);
+void launch_band_top(const Dims &D, int nzg, const int *kcov, const int *kreg, int *kxt, long long *count,
+                     cudaStream_t s);
+void launch_fast_level(const Dims &D, const int *const kreg[4], int *kfast, cudaStream_t s);
+void launch_band_geometry(const double *h, const Dims &D, int g, const GridDev &G, cudaStream_t s);
+void launch_export_geometry(const double *h, const Dims &D, int g, const GridDev &G, int field, double *dst,
+                            cudaStream_t s);
+
+// eb_scan.cu: in-place exclusive scan of n values; total written to *total (device)
+void scan_exclusive(long long *data, long long n, long long *total, cudaStream_t s);
+
+// eb_wsrd_setup.cu
+struct SetupScratch;
+cudaError_t build_wsrd(const Dims &D, int g, GridDev &G, const GridDev *all, double vt, WsrdDev &W,
+                       cudaStream_t s, long long *dev_tmp);
+void free_wsrd(WsrdDev &W);
+
+// device allocation helper that tracks every pointer for one release
+struct DevArena;

@@ -1,0 +1,374 @@
+// eb_step.cu -- per-step kernels of the EB advance.
+//
+//   flux + update (Eqs. update-cc / update-fc, Sec. 4.1):
+//     k_fast  : every CV at or above its column's kfast level; no geometry
+//               (all CVs the stencil reads are regular), plus the pass-through
+//               of covered CVs and of the w wall levels;
+//     k_band  : the non-covered CVs below kfast, with covered-neighbour
+//               fallbacks, open-face fractions and fluxes interpolated to the
+//               cut-face centroids.
+//   weighted state redistribution (Sec. 5.1, Eqs. qhat_omega, qrecon,
+//   final_update_omega), on compact lists built at set-up:
+//     k_qhat  : neighbourhood averages of the small CVs;
+//     k_sigma : least-squares slopes and the limiter, one warp per small CV;
+//     k_final : the final update of every CV the redistribution changes.
+//
+// Every kernel writes a disjoint set of CVs, so no atomics are needed and
+// results are deterministic.
+#include "eb_step.cuh"
+
+#include <math.h>
+
+namespace {
+
+template <typename T>
+__device__ inline bool finite_val(T v) {
+  return isfinite(v);
+}
+
+// Faces of the low side of CV (i,j,k) along d exist inside the domain?  The
+// high z face of the top c, u, v CVs is the wall.
+__device__ inline bool high_face_exists(const Dims &D, int g, int d, int k) {
+  if (d != 2) return true;
+  return g == 3 ? (k + 1 <= D.nz) : (k + 1 < D.nz);
+}
+
+// Usable neighbour face for the centroid interpolation: inside the domain
+// (w-grid x/y faces of the wall levels excluded) and open.
+__device__ inline bool face_usable(const GeoBand &geo, const Dims &D, int g, int d, int i, int j, int k) {
+  if (k < 0 || k >= nzg_of(D, g)) return false;
+  if (g == 3 && d != 2 && (k < 1 || k > D.nz - 1)) return false;
+  if (g != 3 && d == 2 && k == 0) return false;   // bottom wall faces carry no flux
+  return geo.beta(D, g, d, i, j, k) > 0.0;
+}
+
+// Flux through the centroid of the low d-face of CV (i,j,k): bilinear
+// interpolation of the provisional fluxes of the face and of the neighbour
+// faces toward which the centroid is offset (Sec. 4.1).  An offset is dropped
+// when a face it needs is closed or outside the domain.
+template <typename T>
+__device__ void centroid_flux(const StateIn<T> &U, const GeoBand &geo, const Dims &D, int g, int d, int i, int j,
+                              int k, T &fm, T &fp) {
+  double ga, gb;
+  geo.fcent(D, g, d, i, j, k, ga, gb);
+  face_flux(U, geo, D, g, d, i, j, k, fm, fp);
+  if (ga == 0.0 && gb == 0.0) return;
+  const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+  int ea[3] = {0, 0, 0}, eb[3] = {0, 0, 0};
+  ea[ta] = ga >= 0.0 ? 1 : -1;
+  eb[tb] = gb >= 0.0 ? 1 : -1;
+  const bool ua = ga != 0.0 && face_usable(geo, D, g, d, i + ea[0], j + ea[1], k + ea[2]);
+  const bool ub = gb != 0.0 && face_usable(geo, D, g, d, i + eb[0], j + eb[1], k + eb[2]);
+  const bool uab = ga != 0.0 && gb != 0.0 &&
+                   face_usable(geo, D, g, d, i + ea[0] + eb[0], j + ea[1] + eb[1], k + ea[2] + eb[2]);
+  const bool za = ga != 0.0 && (!ua || (gb != 0.0 && !uab));
+  const bool zb = gb != 0.0 && (!ub || (ga != 0.0 && !uab));
+  const T wa = za ? T(0) : T(fabs(ga));
+  const T wb = zb ? T(0) : T(fabs(gb));
+  if (wa == T(0) && wb == T(0)) return;
+  T m0 = fm, p0 = fp;
+  fm = (T(1) - wa) * (T(1) - wb) * m0;
+  fp = (T(1) - wa) * (T(1) - wb) * p0;
+  T m1, p1;
+  if (wa != T(0)) {
+    face_flux(U, geo, D, g, d, i + ea[0], j + ea[1], k + ea[2], m1, p1);
+    fm += wa * (T(1) - wb) * m1;
+    fp += wa * (T(1) - wb) * p1;
+  }
+  if (wb != T(0)) {
+    face_flux(U, geo, D, g, d, i + eb[0], j + eb[1], k + eb[2], m1, p1);
+    fm += wb * (T(1) - wa) * m1;
+    fp += wb * (T(1) - wa) * p1;
+  }
+  if (wa != T(0) && wb != T(0)) {
+    face_flux(U, geo, D, g, d, i + ea[0] + eb[0], j + ea[1] + eb[1], k + ea[2] + eb[2], m1, p1);
+    fm += wa * wb * m1;
+    fp += wa * wb * p1;
+  }
+}
+
+template <typename T>
+__device__ inline void write_out(const StepArgs<T> &A, int f, long long c, double delta) {
+  T v;
+  if (A.base[0]) v = A.base[f][c] + (T)(A.dt * delta);
+  else v = (T)delta;
+  A.out[f][c] = v;
+  if (!finite_val(v)) atomicOr(A.status, EB_DEV_NUMERIC);
+}
+
+template <typename T>
+__device__ inline void write_outT(const StepArgs<T> &A, int f, long long c, T delta) {
+  T v;
+  if (A.base[0]) v = A.base[f][c] + A.dtT * delta;
+  else v = delta;
+  A.out[f][c] = v;
+  if (!finite_val(v)) atomicOr(A.status, EB_DEV_NUMERIC);
+}
+
+template <typename T>
+__device__ inline void write_static(const StepArgs<T> &A, int f, long long c) {
+  A.out[f][c] = A.base[0] ? A.base[f][c] : T(0);
+}
+
+// dU of the CV (i,j,k) of grid g with all-regular surroundings.
+template <typename T>
+__device__ void fast_cv(const StepArgs<T> &A, int g, int i, int j, int k) {
+  const Dims &D = A.D;
+  const GeoFast geo;
+  const T inv[3] = {T(1.0 / D.dx), T(1.0 / D.dy), T(1.0 / D.dz)};
+  T sm = T(0), sp = T(0);
+  for (int d = 0; d < 3; ++d) {
+    const int di = d == 0, dj = d == 1, dk = d == 2;
+    T ml, pl, mh = T(0), ph = T(0);
+    face_flux(A.src, geo, D, g, d, i, j, k, ml, pl);
+    if (high_face_exists(D, g, d, k)) face_flux(A.src, geo, D, g, d, i + di, j + dj, k + dk, mh, ph);
+    sm += (mh - ml) * inv[d];
+    sp += (ph - pl) * inv[d];
+  }
+  const long long c = lin(D, i, j, k);
+  if (g == 0) {
+    write_outT(A, 0, c, -sm);
+    write_outT(A, 1, c, -sp);
+  } else {
+    write_outT(A, g + 1, c, -sp);
+  }
+}
+
+// dU of a non-covered CV near the EB (general geometry).
+template <typename T>
+__device__ void band_cv(const StepArgs<T> &A, int g, int i, int j, int k) {
+  const Dims &D = A.D;
+  GeoBand geo;
+  geo.G = A.G;
+  const double alpha = geo.alpha(D, g, i, j, k);
+  const double dd[3] = {D.dx, D.dy, D.dz};
+  // double accumulation for every band CV: it costs little here and keeps
+  // the tiny cut CVs (alpha < 1e-3) accurate in the float path
+  double sm = 0.0, sp = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const int di = d == 0, dj = d == 1, dk = d == 2;
+    const bool lo_wall = (g != 3 && d == 2 && k == 0);
+    const double bl = lo_wall ? 0.0 : geo.beta(D, g, d, i, j, k);
+    double bh = 0.0;
+    if (high_face_exists(D, g, d, k)) bh = geo.beta(D, g, d, i + di, j + dj, k + dk);
+    T ml = T(0), pl = T(0), mh = T(0), ph = T(0);
+    if (bl > 0.0) centroid_flux(A.src, geo, D, g, d, i, j, k, ml, pl);
+    if (bh > 0.0) centroid_flux(A.src, geo, D, g, d, i + di, j + dj, k + dk, mh, ph);
+    sm += (bh * (double)mh - bl * (double)ml) / dd[d];
+    sp += (bh * (double)ph - bl * (double)pl) / dd[d];
+  }
+  const long long c = lin(D, i, j, k);
+  if (g == 0) {
+    write_out(A, 0, c, -sm / alpha);
+    write_out(A, 1, c, -sp / alpha);
+  } else {
+    write_out(A, g + 1, c, -sp / alpha);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fast(StepArgs<T> A) {
+  const Dims &D = A.D;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= D.nx || j >= D.ny) return;
+  const int col = i + D.nx * j;
+  const int kf = A.kfast[col];
+  if (k >= kf) {
+    fast_cv(A, 0, i, j, k);
+    fast_cv(A, 1, i, j, k);
+    fast_cv(A, 2, i, j, k);
+    fast_cv(A, 3, i, j, k);
+  } else if (A.copy_static) {
+    const long long c = lin(D, i, j, k);
+    if (k < A.G[0].kcov[col]) {
+      write_static(A, 0, c);
+      write_static(A, 1, c);
+    }
+    if (k < A.G[1].kcov[col]) write_static(A, 2, c);
+    if (k < A.G[2].kcov[col]) write_static(A, 3, c);
+    if (k < A.G[3].kcov[col] || k == 0) write_static(A, 4, c);
+  }
+  if (A.copy_static && k == D.nz - 1) write_static(A, 4, lin(D, i, j, D.nz));
+}
+
+template <typename T>
+__global__ void k_band(StepArgs<T> A) {
+  const Dims &D = A.D;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y;
+  if (col >= D.nx * D.ny) return;
+  const int i = col % D.nx, j = col / D.nx;
+  const int kf = A.kfast[col];
+  const int k0 = A.G[g].kcov[col];
+  for (int k = k0; k < kf; ++k) {
+    if (g == 3 && (k == 0 || k == D.nz)) continue;
+    band_cv(A, g, i, j, k);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// redistribution
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ inline T full(const WsrdArgs<T> &R, long long c) {
+  const T v = R.u[c];
+  return R.ref ? v + R.ref[c / R.D.nxy] : v;
+}
+
+// Kahan-compensated running sum in float; plain in double.
+template <typename T>
+struct CompSum {
+  T s = T(0), c = T(0);
+  __device__ inline void add(T x) {
+    const T y = x - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+template <>
+struct CompSum<double> {
+  double s = 0.0, c = 0.0;
+  __device__ inline void add(double x) { s += x; }
+};
+
+template <typename T>
+__global__ void k_qhat(WsrdArgs<T> R) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= R.W.nsmall) return;
+  const int n = R.W.s_nmem[s], p = R.W.s_piv[s];
+  const T vp = full(R, R.W.s_mlin[8 * s + p]);
+  CompSum<T> acc;
+  for (int q = 0; q < n; ++q) {
+    if (q == p) continue;
+    acc.add((T)R.W.s_mw[8 * s + q] * (full(R, R.W.s_mlin[8 * s + q]) - vp));
+  }
+  R.qhat[s] = vp + acc.s;
+}
+
+// One warp per small CV: lanes walk the stencil, shuffles reduce the slope
+// and the stencil's Qhat range; lane 0 applies the limiter at the members'
+// centroids.
+template <typename T>
+__global__ void k_sigma(WsrdArgs<T> R) {
+  const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= R.W.nsmall) return;
+  const long long o0 = R.W.s_loff[s], o1 = R.W.s_loff[s + 1];
+  const T qr = R.qhat[s];
+  T sx = T(0), sy = T(0), sz = T(0), qmax = qr, qmin = qr;
+  for (long long o = o0 + lane; o < o1; o += 32) {
+    const int sid = R.W.l_sid[o];
+    const T qm = sid >= 0 ? R.qhat[sid] : full(R, R.W.l_lin[o]);
+    const T dq = qm - qr;
+    sx += (T)R.W.l_c[3 * o] * dq;
+    sy += (T)R.W.l_c[3 * o + 1] * dq;
+    sz += (T)R.W.l_c[3 * o + 2] * dq;
+    qmax = qm > qmax ? qm : qmax;
+    qmin = qm < qmin ? qm : qmin;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+    sy += __shfl_xor_sync(0xffffffffu, sy, off);
+    sz += __shfl_xor_sync(0xffffffffu, sz, off);
+    const T a = __shfl_xor_sync(0xffffffffu, qmax, off);
+    const T b = __shfl_xor_sync(0xffffffffu, qmin, off);
+    qmax = a > qmax ? a : qmax;
+    qmin = b < qmin ? b : qmin;
+  }
+  if (lane != 0) return;
+  T phi = T(1);
+  if (o1 > o0) {
+    const int n = R.W.s_nmem[s];
+    for (int q = 0; q < n; ++q) {
+      const double *e = R.W.s_me + 24 * s + 3 * q;
+      const T del = sx * (T)e[0] + sy * (T)e[1] + sz * (T)e[2];
+      T ph = T(1);
+      if (del > T(0)) ph = (qmax - qr) / del;
+      else if (del < T(0)) ph = (qmin - qr) / del;
+      if (ph > T(1)) ph = T(1);
+      if (ph < phi) phi = ph;
+    }
+  }
+  R.sig[3 * s] = sx * phi;
+  R.sig[3 * s + 1] = sy * phi;
+  R.sig[3 * s + 2] = sz * phi;
+}
+
+// U_i = P_i + sum_r (kappa_r / N_i) (q_r(x_i) - P_i), P_i = q_i(x_i) for a
+// small CV and U_hat_i otherwise: Eq. final_update_omega with omega_i written
+// as 1 - sum_r kappa_r / N_i.
+template <typename T>
+__global__ void k_final(WsrdArgs<T> R) {
+  const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (a >= R.W.naff) return;
+  const long long c = R.W.a_lin[a];
+  const int sid = R.W.a_sid[a];
+  const T ref = R.ref ? R.ref[c / R.D.nxy] : T(0);
+  T P, Pstore;
+  if (sid >= 0) {
+    const double *e = R.W.a_eself + 3 * a;
+    const T lin = R.sig[3 * sid] * (T)e[0] + R.sig[3 * sid + 1] * (T)e[1] + R.sig[3 * sid + 2] * (T)e[2];
+    P = R.qhat[sid] + lin;
+    Pstore = (R.qhat[sid] - ref) + lin;
+  } else {
+    Pstore = R.u[c];
+    P = Pstore + ref;
+  }
+  CompSum<T> acc;
+  for (long long o = R.W.a_woff[a]; o < R.W.a_woff[a + 1]; ++o) {
+    const int r = R.W.w_sid[o];
+    const double *e = R.W.w_e + 3 * o;
+    const T q = R.qhat[r] + R.sig[3 * r] * (T)e[0] + R.sig[3 * r + 1] * (T)e[1] + R.sig[3 * r + 2] * (T)e[2];
+    acc.add((T)R.W.w_k[o] * (q - P));
+  }
+  const T v = Pstore + acc.s;
+  R.u[c] = v;
+  if (!finite_val(v)) atomicOr(R.status, EB_DEV_NUMERIC);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host wrappers
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_flux_fast(const StepArgs<T> &A, cudaStream_t s) {
+  const Dims &D = A.D;
+  dim3 blk(32, 8, 1);
+  dim3 grd((D.nx + 31) / 32, (D.ny + 7) / 8, D.nz);
+  k_fast<T><<<grd, blk, 0, s>>>(A);
+}
+
+template <typename T>
+void launch_flux_band(const StepArgs<T> &A, cudaStream_t s) {
+  const Dims &D = A.D;
+  dim3 bb(128, 1, 1), bg((D.nx * D.ny + 127) / 128, 4, 1);
+  k_band<T><<<bg, bb, 0, s>>>(A);
+}
+
+template <typename T>
+void launch_flux_update(const StepArgs<T> &A, cudaStream_t s) {
+  launch_flux_fast(A, s);
+  launch_flux_band(A, s);
+}
+
+template <typename T>
+void launch_wsrd(const WsrdArgs<T> &R, cudaStream_t s) {
+  if (R.W.nsmall) {
+    k_qhat<T><<<(unsigned)((R.W.nsmall + 127) / 128), 128, 0, s>>>(R);
+    k_sigma<T><<<(unsigned)((R.W.nsmall * 32 + 255) / 256), 256, 0, s>>>(R);
+  }
+  if (R.W.naff) k_final<T><<<(unsigned)((R.W.naff + 127) / 128), 128, 0, s>>>(R);
+}
+
+template void launch_flux_update<double>(const StepArgs<double> &, cudaStream_t);
+template void launch_flux_fast<double>(const StepArgs<double> &, cudaStream_t);
+template void launch_flux_fast<float>(const StepArgs<float> &, cudaStream_t);
+template void launch_flux_band<double>(const StepArgs<double> &, cudaStream_t);
+template void launch_flux_band<float>(const StepArgs<float> &, cudaStream_t);
+template void launch_flux_update<float>(const StepArgs<float> &, cudaStream_t);
+template void launch_wsrd<double>(const WsrdArgs<double> &, cudaStream_t);
+template void launch_wsrd<float>(const WsrdArgs<float> &, cudaStream_t);

@@ -1,0 +1,39 @@
+// eb_step.cuh -- argument blocks of the per-step kernels.  Not part of the ABI.
+#pragma once
+
+#include "eb_kernels.cuh"
+
+template <typename T>
+struct StepArgs {
+  Dims D;
+  StateIn<T> src;      // state the fluxes are computed from
+  const T *base[5];    // state the update is added to; base[0] == nullptr: write dU itself
+  T *out[5];
+  double dt;
+  T dtT;
+  const int *kfast;
+  GridDev G[4];
+  unsigned *status;
+  int copy_static;     // also write covered CVs and the w wall levels
+};
+
+template <typename T>
+struct WsrdArgs {
+  Dims D;
+  WsrdDev W;
+  T *u;                // field on its grid, redistributed in place
+  const T *ref;        // per-level reference added to u (c-grid fields) or nullptr
+  T *qhat;             // [nsmall] neighbourhood averages
+  T *sig;              // [3 * nsmall] limited slopes
+  unsigned *status;
+};
+
+template <typename T>
+void launch_flux_update(const StepArgs<T> &A, cudaStream_t s);
+template <typename T>
+void launch_flux_fast(const StepArgs<T> &A, cudaStream_t s);
+template <typename T>
+void launch_flux_band(const StepArgs<T> &A, cudaStream_t s);
+
+template <typename T>
+void launch_wsrd(const WsrdArgs<T> &R, cudaStream_t s);

@@ -1,0 +1,242 @@
+"""Python binding of the C ABI in ``include/eb.h`` (ctypes; argument
+marshalling only).  Every step of the method runs in the CUDA library
+``libeb.so``; there is no fallback: if the library is missing or no CUDA
+device is present, the calls raise.
+
+Tensors are torch CUDA tensors (torch is used for device memory and streams
+only).  State fields are dicts with keys ``rho, rhotheta, rhou, rhov, rhow``
+shaped (nz, ny, nx) -- (nz+1, ny, nx) for ``rhow`` -- of dtype float64
+(``precision="f64"``) or float32 (``precision="mixed"``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+FIELDS = ("rho", "rhotheta", "rhou", "rhov", "rhow")
+FIELD_GRID = {"rho": 0, "rhotheta": 0, "rhou": 1, "rhov": 2, "rhow": 3}
+EXPORT_FIELDS = ("alpha", "cent_x", "cent_y", "cent_z", "beta_x", "beta_y", "beta_z", "fcent_x1", "fcent_x2",
+                 "fcent_y1", "fcent_y2", "fcent_z1", "fcent_z2", "aeb", "nrm_x", "nrm_y", "nrm_z", "ebc_x",
+                 "ebc_y", "ebc_z", "flag", "code", "nnb", "kappa", "omega", "vhat", "xhat_x", "xhat_y", "xhat_z")
+STATUS = {0: "EB_OK", 1: "EB_ERR_INVALID_ARG", 2: "EB_ERR_CUDA", 3: "EB_ERR_OOM", 4: "EB_ERR_NUMERIC",
+          5: "EB_ERR_TIMEOUT", 6: "EB_ERR_STATE"}
+EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
+                    "eb_step", "eb_step_profile", "eb_sync_status", "eb_last_error", "eb_version")
+
+
+class EbError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("Lx", ctypes.c_double),
+                ("Ly", ctypes.c_double), ("Lz", ctypes.c_double), ("v_target_frac", ctypes.c_double)]
+
+
+class _State(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in FIELDS]
+
+
+class GeomInfo(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_int64), ("cvs", ctypes.c_int64 * 4), ("band_records", ctypes.c_int64 * 4),
+                ("small_cvs", ctypes.c_int64 * 4), ("affected_cvs", ctypes.c_int64 * 4),
+                ("band_cvs", ctypes.c_int64 * 4), ("tiny_cvs", ctypes.c_int64 * 4), ("fast_cells", ctypes.c_int64),
+                ("min_alpha", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libeb.so (built by ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"{_build.LIB} is missing: run paper_2604_11959_gb300.build.build() first")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P, V, I, D = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.eb_geom_build.argtypes = [P(_Desc), V, I, V, V, V, P(V)]
+    lib.eb_geom_destroy.argtypes = [V]
+    lib.eb_geom_info.argtypes = [V, P(GeomInfo)]
+    lib.eb_geom_export.argtypes = [V, I, I, V, V]
+    lib.eb_flux_div.argtypes = [V, P(_State), P(_State), V]
+    lib.eb_wsrd.argtypes = [V, I, V, V, V]
+    lib.eb_step.argtypes = [V, P(_State), P(_State), D, I, I, V]
+    lib.eb_step_profile.argtypes = [V, P(_State), P(_State), D, V, P(ctypes.c_float)]
+    lib.eb_sync_status.argtypes = [V, V]
+    lib.eb_last_error.restype = ctypes.c_char_p
+    lib.eb_version.restype = I
+    for name in ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
+                 "eb_step", "eb_step_profile", "eb_sync_status"):
+        getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != 0:
+        raise EbError(code, load().eb_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, dtype, shape, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Geometry:
+    """Handle of the geometry of all four grids and the redistribution tables
+    (``eb_geom_build``)."""
+
+    def __init__(self, nx, ny, nz, Lx, Ly, Lz, h_nodes: torch.Tensor, precision: str = "f64", ref_rho=None,
+                 ref_rhotheta=None, v_target_frac: float = 0.5, stream=None):
+        lib = load()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.Lx, self.Ly, self.Lz = float(Lx), float(Ly), float(Lz)
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "f64" else torch.float32
+        prec = {"f64": 0, "mixed": 1}[precision]
+        _require_cuda(h_nodes, torch.float64, (self.ny + 1, self.nx + 1), "h_nodes")
+        refs = [None, None]
+        for q, r in enumerate((ref_rho, ref_rhotheta)):
+            if r is not None:
+                _require_cuda(r, torch.float64, (self.nz,), "reference profile")
+                refs[q] = r
+        self._keep = (h_nodes, refs)
+        desc = _Desc(self.nx, self.ny, self.nz, self.Lx, self.Ly, self.Lz, float(v_target_frac))
+        handle = ctypes.c_void_p()
+        _check(lib.eb_geom_build(ctypes.byref(desc), h_nodes.data_ptr(), prec,
+                                 refs[0].data_ptr() if refs[0] is not None else None,
+                                 refs[1].data_ptr() if refs[1] is not None else None, _stream(stream),
+                                 ctypes.byref(handle)))
+        self._h = handle
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().eb_geom_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("geometry handle was closed")
+        return self._h
+
+    def shape(self, field_or_grid):
+        g = FIELD_GRID[field_or_grid] if isinstance(field_or_grid, str) else int(field_or_grid)
+        return (self.nz + (1 if g == 3 else 0), self.ny, self.nx)
+
+    def info(self) -> dict:
+        inf = GeomInfo()
+        _check(load().eb_geom_info(self.handle, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def export(self, grid: int, field: str, stream=None) -> torch.Tensor:
+        out = torch.empty(self.shape(int(grid)), dtype=torch.float64, device="cuda")
+        _check(load().eb_geom_export(self.handle, int(grid), EXPORT_FIELDS.index(field), out.data_ptr(),
+                                     _stream(stream)))
+        return out
+
+    def empty_state(self) -> dict:
+        return {f: torch.empty(self.shape(f), dtype=self.dtype, device="cuda") for f in FIELDS}
+
+    def _cstate(self, U: dict) -> _State:
+        for f in FIELDS:
+            _require_cuda(U[f], self.dtype, self.shape(f), f)
+        return _State(*(U[f].data_ptr() for f in FIELDS))
+
+
+def flux_div(geom: Geometry, U: dict, out: dict | None = None, stream=None) -> dict:
+    """dU of every field (``eb_flux_div``)."""
+    out = out if out is not None else geom.empty_state()
+    _check(load().eb_flux_div(geom.handle, ctypes.byref(geom._cstate(U)), ctypes.byref(geom._cstate(out)),
+                              _stream(stream)))
+    return out
+
+
+def wsrd(geom: Geometry, field: str, Uhat: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """Redistribution of one field (``eb_wsrd``); ``out`` may be ``Uhat``."""
+    _require_cuda(Uhat, geom.dtype, geom.shape(field), field)
+    out = out if out is not None else torch.empty_like(Uhat)
+    _require_cuda(out, geom.dtype, geom.shape(field), "out")
+    _check(load().eb_wsrd(geom.handle, FIELDS.index(field), Uhat.data_ptr(), out.data_ptr(), _stream(stream)))
+    return out
+
+
+def step(geom: Geometry, Un: dict, dt: float, nsteps: int = 1, stages: int = 1, out: dict | None = None,
+         stream=None) -> dict:
+    """nsteps steps of Algorithm 1 (``eb_step``)."""
+    out = out if out is not None else geom.empty_state()
+    _check(load().eb_step(geom.handle, ctypes.byref(geom._cstate(Un)), ctypes.byref(geom._cstate(out)), float(dt),
+                          int(nsteps), int(stages), _stream(stream)))
+    return out
+
+
+def step_profile(geom: Geometry, Un: dict, out: dict, dt: float, stream=None):
+    """One forward-Euler step with per-phase event times (``eb_step_profile``):
+    returns milliseconds of (bulk flux kernel, near-EB flux kernel,
+    redistribution, whole step)."""
+    ms = (ctypes.c_float * 4)()
+    _check(load().eb_step_profile(geom.handle, ctypes.byref(geom._cstate(Un)), ctypes.byref(geom._cstate(out)),
+                                  float(dt), _stream(stream), ms))
+    return tuple(float(v) for v in ms)
+
+
+def sync_status(geom: Geometry, stream=None) -> None:
+    """Raise EbError if a kernel latched a device-side error (``eb_sync_status``)."""
+    _check(load().eb_sync_status(geom.handle, _stream(stream)))
+
+
+def host_state(U: dict, precision: str, refs=None, pin: bool = True) -> dict:
+    """CPU tensors of a state given as numpy full values: float64 or float32,
+    rho and rho*theta minus the reference profile ``refs = (rho0, rho0*theta0)``
+    (per level) when given.  Pinned for asynchronous copies."""
+    import numpy as np
+    dt = torch.float64 if precision == "f64" else torch.float32
+    out = {}
+    for f in FIELDS:
+        a = U[f]
+        if refs is not None and f in ("rho", "rhotheta"):
+            a = a - np.asarray(refs[0] if f == "rho" else refs[1])[:, None, None]
+        t = torch.from_numpy(np.ascontiguousarray(a)).to(dt)
+        out[f] = t.pin_memory() if pin else t
+    return out
+
+
+def device_state(U: dict, precision: str, refs=None) -> dict:
+    """Like host_state, on the current CUDA device."""
+    return {f: t.cuda() for f, t in host_state(U, precision, refs, pin=False).items()}

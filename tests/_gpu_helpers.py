@@ -1,0 +1,91 @@
+"""Shared helpers of the GPU tests: moving seeded states between numpy
+(oracle) and torch (CUDA library), the relative L-inf error, and oracle runs
+on column windows of large domains."""
+import numpy as np
+
+FIELDS = ("rho", "rhotheta", "rhou", "rhov", "rhow")
+FGRID = {"rho": 0, "rhotheta": 0, "rhou": 1, "rhov": 2, "rhow": 3}
+
+# Tolerances of the relative L-inf error (max |gpu - oracle| / max |oracle|
+# over the compared CVs): the double path must agree to 1e-12, the mixed
+# float path to 1e-5.
+TOL = {"f64": 1e-12, "mixed": 1e-5}
+
+
+def refs_for(nz, Lz):
+    from paper_2604_11959_gb300 import inputs
+    return inputs.cell_reference(nz, Lz)
+
+
+def to_device(U, precision, refs=None):
+    """numpy full-value state -> torch CUDA state (perturbations about refs
+    for rho and rho*theta when refs are given)."""
+    import torch
+    dt = torch.float64 if precision == "f64" else torch.float32
+    out = {}
+    for f in FIELDS:
+        a = U[f]
+        if refs is not None and f in ("rho", "rhotheta"):
+            a = a - (refs[0] if f == "rho" else refs[1])[:, None, None]
+        out[f] = torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dt)
+    return out
+
+
+def to_host(U, refs=None):
+    out = {}
+    for f in FIELDS:
+        a = U[f].double().cpu().numpy()
+        if refs is not None and f in ("rho", "rhotheta"):
+            a = a + (refs[0] if f == "rho" else refs[1])[:, None, None]
+        out[f] = a
+    return out
+
+
+def rel_linf(got, want, mask=None):
+    d = np.abs(got - want)
+    w = np.abs(want)
+    if mask is not None:
+        d, w = d[mask], w[mask]
+    if d.size == 0:
+        return 0.0
+    den = w.max()
+    return float(d.max() / den) if den > 0 else float(d.max())
+
+
+def active_masks(G, nz):
+    """Non-covered prognostic CVs per grid, from oracle geometry."""
+    m = {}
+    for g in range(4):
+        a = G[g]["alpha"] > 0
+        if g == 3:
+            a = a.copy()
+            a[0] = False
+            a[nz] = False
+        m[g] = a
+    return m
+
+
+def make_geometry(eb, w, h, precision, refs=None, vt=0.5):
+    import torch
+    ht = torch.from_numpy(h).cuda()
+    kw = {}
+    if refs is not None:
+        kw = dict(ref_rho=torch.from_numpy(refs[0]).cuda(), ref_rhotheta=torch.from_numpy(refs[1]).cuda())
+    return eb.Geometry(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, ht, precision=precision, v_target_frac=vt, **kw)
+
+
+def window_oracle(oracle, w, h, U_full, x0, y0, W, dt, nsteps=1, stages=1):
+    """Oracle run on a window of W x W columns at (x0, y0): geometry, tables
+    and nsteps steps.  Returns (domain, geometry, tables, result)."""
+    dom = oracle.Domain(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, h, window=(x0, y0, W, W))
+    G = oracle.geometry(dom)
+    T = oracle.wsrd_setup(dom, G)
+    Uw = {f: dom.window_of(U_full[f]) for f in FIELDS}
+    R = oracle.step(dom, G, T, Uw, dt, nsteps, stages) if nsteps else Uw
+    return dom, G, T, Uw, R
+
+
+def window_cut(a, x0, y0, W, nx, ny):
+    ii = (x0 + np.arange(W)) % nx
+    jj = (y0 + np.arange(W)) % ny
+    return a[..., jj[:, None], ii[None, :]]

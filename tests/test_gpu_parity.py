@@ -1,0 +1,238 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 CPU oracle.
+
+Geometry flags, redistribution codes and neighbourhood counts must match bit
+for bit; geometry moments and weights to 1e-12; state fields after N steps to
+a relative L-inf error of 1e-12 (double path) or 1e-5 (mixed path)."""
+import numpy as np
+import pytest
+
+from paper_2604_11959_gb300 import inputs
+
+from _gpu_helpers import (FGRID, FIELDS, TOL, active_masks, make_geometry, refs_for, rel_linf, to_device, to_host,
+                          window_cut, window_oracle)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+EXACT = ("flag", "code", "nnb")
+
+
+@pytest.fixture(scope="module")
+def eb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_11959_gb300 import build, eb as ebmod
+    build.build()
+    ebmod.load()
+    return ebmod
+
+
+def rough_workload():
+    return inputs.Workload("grf-48x40x24", 48, 40, 24, 5, terrain="grf", seed=5, hmax=0.2, tiny=3)
+
+
+CASES = {
+    "woa": (inputs.WOA_32, None),
+    "grf": (rough_workload(), None),
+    "hill": (inputs.Workload("hill-64x64x32", 64, 64, 32, 10, terrain="gaussian", hmax=0.15), None),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request, oracle):
+    w, _ = CASES[request.param]
+    h = w.heights()
+    dom = oracle.Domain(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, h)
+    G = oracle.geometry(dom)
+    T = oracle.wsrd_setup(dom, G)
+    return request.param, w, h, dom, G, T
+
+
+def oracle_export(G, T, g, name):
+    if name == "alpha" or name == "aeb" or name == "flag":
+        return G[g][name].astype(np.float64)
+    if name.startswith("cent_") or name.startswith("nrm_") or name.startswith("ebc_") or name.startswith("beta_"):
+        key, ax = name.split("_")
+        return G[g][key]["xyz".index(ax)]
+    if name.startswith("fcent_"):
+        ax, t = name[6], int(name[7]) - 1
+        return G[g]["fcent"][2 * "xyz".index(ax) + t]
+    if name.startswith("xhat_"):
+        return T[g]["xhat"]["xyz".index(name[5])]
+    return T[g][name].astype(np.float64)
+
+
+def test_geometry_and_tables_match(eb, case):
+    name, w, h, dom, G, T = case
+    geom = make_geometry(eb, w, h, "f64")
+    worst = {}
+    for g in range(4):
+        for f in eb.EXPORT_FIELDS:
+            got = geom.export(g, f).cpu().numpy()
+            want = oracle_export(G, T, g, f)
+            if f in EXACT:
+                bad = np.argwhere(got != want)
+                assert bad.size == 0, (name, g, f, bad[:5], got[tuple(bad[0])], want[tuple(bad[0])])
+            else:
+                err = np.max(np.abs(got - want))
+                worst[(g, f)] = err
+                assert err <= 1e-12, (name, g, f, err)
+    info = geom.info()
+    assert info["cells"] == w.nx * w.ny * w.nz
+    for g in range(4):
+        assert info["small_cvs"][g] == int((T[g]["code"] > 0).sum())
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_flux_divergence_matches(eb, case, oracle, precision):
+    name, w, h, dom, G, T = case
+    refs = refs_for(w.nz, w.Lz)
+    U = w.state("uniform", pert=1e-2, seed=11)
+    want = oracle.flux_div(dom, G, U)
+    geom = make_geometry(eb, w, h, precision, refs)
+    got = to_host(eb.flux_div(geom, to_device(U, precision, refs)))
+    act = active_masks(G, w.nz)
+    for f in FIELDS:
+        err = rel_linf(got[f], want[f], act[FGRID[f]])
+        assert err <= TOL[precision], (name, precision, f, err)
+        assert np.all(got[f][~act[FGRID[f]]] == 0.0)
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_redistribution_matches(eb, case, oracle, precision):
+    name, w, h, dom, G, T = case
+    refs = refs_for(w.nz, w.Lz)
+    rng = np.random.default_rng(3)
+    U = w.state("uniform", pert=0.05, seed=12)
+    Uhat = {f: U[f] * (1.0 + 0.3 * rng.uniform(-1, 1, U[f].shape)) for f in FIELDS}
+    geom = make_geometry(eb, w, h, precision, refs)
+    dev = to_device(Uhat, precision, refs)
+    act = active_masks(G, w.nz)
+    for f in FIELDS:
+        g = FGRID[f]
+        want = oracle.wsrd(dom, G, T, g, Uhat[f])
+        out = eb.wsrd(geom, f, dev[f])
+        got = to_host({**{k: dev[k] for k in FIELDS}, f: out}, refs)[f]
+        err = rel_linf(got, want, act[g])
+        assert err <= TOL[precision], (name, precision, f, err)
+        # CVs the redistribution does not touch are copied bit for bit
+        untouched = act[g] & (T[g]["nnb"] == 1) & (T[g]["code"] == 0)
+        assert np.array_equal(out.cpu().numpy()[untouched], dev[f].cpu().numpy()[untouched])
+
+
+@pytest.mark.parametrize("precision,stages,kind", [("f64", 1, "uniform"), ("mixed", 1, "uniform"),
+                                                   ("f64", 1, "sheltered"), ("mixed", 1, "sheltered"),
+                                                   ("f64", 3, "sheltered"), ("mixed", 3, "sheltered")])
+def test_steps_match(eb, case, oracle, precision, stages, kind):
+    name, w, h, dom, G, T = case
+    refs = refs_for(w.nz, w.Lz)
+    U = w.state(kind, pert=1e-2 if kind == "uniform" else 0.0, seed=21)
+    nsteps = w.steps if stages == 1 else 3
+    want = oracle.step(dom, G, T, U, w.dt(), nsteps, stages)
+    geom = make_geometry(eb, w, h, precision, refs)
+    got = to_host(eb.step(geom, to_device(U, precision, refs), w.dt(), nsteps, stages), refs)
+    eb.sync_status(geom)
+    act = active_masks(G, w.nz)
+    for f in FIELDS:
+        g = FGRID[f]
+        err = rel_linf(got[f], want[f], act[g])
+        assert err <= TOL[precision], (name, precision, stages, kind, f, err)
+        # covered CVs and the w wall levels pass through unchanged
+        static = ~act[g]
+        ref_in = to_host(to_device({k: U[k] for k in FIELDS}, precision, refs), refs)[f]
+        assert np.array_equal(got[f][static], ref_in[static]), (name, f)
+
+
+def test_deterministic(eb):
+    w = rough_workload()
+    h = w.heights()
+    U = w.state("uniform", pert=1e-2, seed=4)
+    geom = make_geometry(eb, w, h, "mixed", refs_for(w.nz, w.Lz))
+    a = eb.step(geom, to_device(U, "mixed", refs_for(w.nz, w.Lz)), w.dt(), 4)
+    b = eb.step(geom, to_device(U, "mixed", refs_for(w.nz, w.Lz)), w.dt(), 4)
+    for f in FIELDS:
+        assert torch.equal(a[f], b[f]), f
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads: the launch configuration the benchmark times, checked
+# on column windows that the oracle computes one by one
+# ---------------------------------------------------------------------------
+FULL = {"hill256": inputs.HILL_256, "grf512": inputs.GRF_512}
+
+
+@pytest.mark.parametrize("which", sorted(FULL))
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_full_size_windows(eb, oracle, which, precision):
+    w = FULL[which]
+    h = w.heights()
+    refs = refs_for(w.nz, w.Lz)
+    U = w.state("uniform", pert=1e-2, seed=31)
+    geom = make_geometry(eb, w, h, precision, refs)
+    got = to_host(eb.step(geom, to_device(U, precision, refs), w.dt(), 1, 1), refs)
+    eb.sync_status(geom)
+    exp_flag = {g: geom.export(g, "flag").cpu().numpy() for g in range(4)}
+    exp_code = {g: geom.export(g, "code").cpu().numpy() for g in range(4)}
+    W, M = 34, 10
+    rng = np.random.default_rng(5)
+    # windows: the highest terrain column, a planted tiny cell (if any) and two random spots
+    hj, hi = np.unravel_index(np.argmax(h[:-1, :-1]), (w.ny, w.nx))
+    spots = [(hi, hj)] + [(int(rng.integers(0, w.nx)), int(rng.integers(0, w.ny))) for _ in range(2)]
+    if w.tiny:
+        _, planted = inputs.plant_tiny_cells(inputs.grf_terrain(w.nx, w.ny, w.seed, w.hmax), w.nx, w.ny, w.nz, w.Lz,
+                                             w.tiny, w.seed + 1)
+        spots.append(planted[0][:2])
+    for (ci, cj) in spots:
+        x0, y0 = (ci - W // 2) % w.nx, (cj - W // 2) % w.ny
+        dom, G, T, Uw, R = window_oracle(oracle, w, h, U, x0, y0, W, w.dt(), 1, 1)
+        inner = (slice(None), slice(M, W - M), slice(M, W - M))
+        for g in range(4):
+            wf = window_cut(exp_flag[g], x0, y0, W, w.nx, w.ny)
+            assert np.array_equal(wf[inner], G[g]["flag"][inner].astype(np.float64)), (which, g)
+            wc = window_cut(exp_code[g], x0, y0, W, w.nx, w.ny)
+            assert np.array_equal(wc[inner], T[g]["code"][inner].astype(np.float64)), (which, g)
+        act = active_masks(G, w.nz)
+        for f in FIELDS:
+            g = FGRID[f]
+            gw = window_cut(got[f], x0, y0, W, w.nx, w.ny)
+            m = act[g].copy()
+            m[:, :M, :] = False
+            m[:, W - M:, :] = False
+            m[:, :, :M] = False
+            m[:, :, W - M:] = False
+            err = rel_linf(gw, R[f], m)
+            assert err <= TOL[precision], (which, precision, (ci, cj), f, err)
+
+
+# ---------------------------------------------------------------------------
+# error handling
+# ---------------------------------------------------------------------------
+def test_invalid_arguments(eb):
+    w = inputs.WOA_32
+    h = torch.from_numpy(w.heights()).cuda()
+    with pytest.raises(eb.EbError) as e:
+        eb.Geometry(2, w.ny, w.nz, 1.0, 1.0, 0.5, torch.zeros((w.ny + 1, 3), dtype=torch.float64, device="cuda"))
+    assert e.value.code == 1
+    geom = eb.Geometry(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, h)
+    U = to_device(w.state("uniform"), "f64")
+    with pytest.raises(eb.EbError) as e:
+        eb.step(geom, U, -1.0, 1)
+    assert e.value.code == 1
+    with pytest.raises(eb.EbError) as e:
+        eb.step(geom, U, w.dt(), 1, stages=2)
+    assert e.value.code == 1
+    with pytest.raises(eb.EbError) as e:
+        eb.step(geom, U, w.dt(), 1, out=U)
+    assert e.value.code == 1
+
+
+def test_non_finite_state_is_reported(eb):
+    w = inputs.WOA_32
+    geom = make_geometry(eb, w, w.heights(), "mixed", refs_for(w.nz, w.Lz))
+    U = to_device(w.state("uniform"), "mixed", refs_for(w.nz, w.Lz))
+    U["rhou"][12, 5, 7] = float("nan")
+    eb.step(geom, U, w.dt(), 1)
+    with pytest.raises(eb.EbError) as e:
+        eb.sync_status(geom)
+    assert e.value.code == 4
+    eb.sync_status(geom)   # cleared
