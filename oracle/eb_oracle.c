@@ -170,31 +170,35 @@ static int clip_level(const Pt *in, int n, double lev, int below, Pt *out) {
 
 /* Integrals over a convex polygon of the functions needed below, by fan
  * triangulation and the three-edge-midpoint rule (exact for quadratics).
- * H is linear on each fan triangle.  zb is subtracted from heights. */
-typedef struct { double a, x, y, h, xg, yg, hh; } PolyInt;
-/* a = area, x = int xi, y = int eta, h = int (H - zb),
- * xg = int xi*(Z1 - H), yg = int eta*(Z1 - H), hh = int (H - zb)^2 */
+ * H is linear on each fan triangle.  The fluid height g = Z1 - H is formed
+ * at the vertices and averaged to the edge midpoints, so that a thin sliver
+ * of fluid (g small everywhere) keeps its relative accuracy. */
+typedef struct { double a, x, y, g, xg, yg, zg; } PolyInt;
+/* a = area, x = int xi, y = int eta, g = int (Z1 - H),
+ * xg = int xi*g, yg = int eta*g, zg = int g*(Z1 - zb - g/2), the z-moment of
+ * the fluid column [H, Z1] measured from zb */
 
 static void poly_integrals(const Pt *p, int n, double zb, double Z1, PolyInt *s) {
   memset(s, 0, sizeof(*s));
+  const double top = Z1 - zb;
   for (int t = 1; t + 1 < n; t++) {
     const Pt *v[3] = {&p[0], &p[t], &p[t + 1]};
     double A = 0.5 * ((v[1]->x - v[0]->x) * (v[2]->y - v[0]->y) -
                       (v[2]->x - v[0]->x) * (v[1]->y - v[0]->y));
     if (!(A > 0.0)) continue;
     s->a += A;
+    /* g is linear: its integral is the area times the vertex mean */
+    s->g += A * ((Z1 - v[0]->H) + (Z1 - v[1]->H) + (Z1 - v[2]->H)) / 3.0;
     for (int e = 0; e < 3; e++) {
       const Pt *u = v[e], *w = v[(e + 1) % 3];
       double mx = 0.5 * (u->x + w->x), my = 0.5 * (u->y + w->y);
-      double mh = 0.5 * ((u->H - zb) + (w->H - zb));
-      double g = (Z1 - zb) - mh;
+      double g = 0.5 * ((Z1 - u->H) + (Z1 - w->H));
       double wq = A / 3.0;
       s->x += wq * mx;
       s->y += wq * my;
-      s->h += wq * mh;
       s->xg += wq * mx * g;
       s->yg += wq * my * g;
-      s->hh += wq * mh * mh;
+      s->zg += wq * g * (top - 0.5 * g);
     }
   }
 }
@@ -258,7 +262,8 @@ static void face_profile(const double Hq[3][3], int axis, int c2, int s0, int s1
           double g = Z1 - H;
           A += len * wt[e] * g;
           S += len * wt[e] * s * g;
-          Zm += len * wt[e] * 0.5 * ((Z1 - zb) * (Z1 - zb) - (H - zb) * (H - zb));
+          /* z-moment of the fluid column [H, Z1] about zb: g (Z1 - zb - g/2) */
+          Zm += len * wt[e] * g * ((Z1 - zb) - 0.5 * g);
         }
       }
     }
@@ -319,10 +324,10 @@ static void box_moments(const double Hq[3][3], int a0, int a1, int b0, int b1, d
     m->my += hgt * sA.y;
     m->mz += 0.5 * ((Z1 - zb) * (Z1 - zb) - (Z0 - zb) * (Z0 - zb)) * sA.a;
     /* region B: Z0 <= H < Z1, height Z1 - H */
-    m->vol += (Z1 - zb) * sB.a - sB.h;
+    m->vol += sB.g;
     m->mx += sB.xg;
     m->my += sB.yg;
-    m->mz += 0.5 * ((Z1 - zb) * (Z1 - zb) * sB.a - sB.hh);
+    m->mz += sB.zg;
     /* horizontal faces: bottom open where H < Z0, top open where H < Z1 */
     m->fa[4] += sA.a; m->f1[4] += sA.x; m->f2[4] += sA.y;
     m->fa[5] += sU.a; m->f1[5] += sU.x; m->f2[5] += sU.y;
@@ -334,7 +339,7 @@ static void box_moments(const double Hq[3][3], int a0, int a1, int b0, int b1, d
       m->eba += ar;
       m->ebx += el * sB.x;
       m->eby += el * sB.y;
-      m->ebz += el * sB.h;
+      m->ebz += el * ((Z1 - zb) * sB.a - sB.g);
       m->nv[0] += -hx * sB.a; m->nv[1] += -hy * sB.a; m->nv[2] += sB.a;
       m->rv[0] += -gx[t] * sB.a; m->rv[1] += -gy[t] * sB.a; m->rv[2] += sB.a;
     }
@@ -770,6 +775,25 @@ static int members(const OrcDomain *D, const OrcGeom *Gg, int g, int gi, int gj,
   return m;
 }
 
+/* x - xhat_r for a point x given relative to r's centre, formed as
+ * sum_m w_m (x - x_m) over the members of M_r with the weights of Eq.
+ * centroid (they sum to one): no cancellation when xhat_r lies close to one
+ * member, as it does for a tiny cell merged into one large neighbour. */
+static void from_xhat(const OrcDomain *D, int g, const OrcGeom *Gg, const OrcWsrd *W, int gi, int gj, int k, long r,
+                      const double x[3], double e[3]) {
+  long n = ncv(D, g);
+  e[0] = e[1] = e[2] = 0.0;
+  long mid[8];
+  int moff[8][3];
+  int nm = W->code[r] ? members(D, Gg, g, gi, gj, k, W->code[r], mid, moff) : 1;
+  if (!W->code[r]) { mid[0] = r; moff[0][0] = moff[0][1] = moff[0][2] = 0; }
+  for (int q = 0; q < nm; q++) {
+    double wq = q == 0 ? W->omega[r] * Gg->alpha[r] / W->vhat[r]
+                       : W->kappa[r] * Gg->alpha[mid[q]] / W->nnb[mid[q]] / W->vhat[r];
+    for (int a = 0; a < 3; a++) e[a] += wq * (x[a] - (moff[q][a] + Gg->cent[a * n + mid[q]]));
+  }
+}
+
 /* Set-up of the redistribution tables of grid g: small CVs, their merging
  * neighbourhoods M, N, kappa (Eq. kappa, clamped to 1), omega (Eq. omega),
  * the weighted volume (Eq. nbhd_vol) and centroid (Eq. centroid). */
@@ -870,26 +894,43 @@ int orc_wsrd_setup(const OrcDomain *D, int g, const OrcGeom *Gg, double vt, OrcW
   return 0;
 }
 
+/* Neighbourhood averages are kept in the pivoted deviation form
+ * Qhat_r = Uhat[piv_r] + D_r,  D_r = sum_{m != p} w_m (Uhat_m - Uhat_p),
+ * which equals Eq. qhat_omega because the weights w sum to one; the pivot p
+ * is the first member with V >= V_target, else the first largest member.
+ * Non-small CVs have piv = itself and D = 0 (their neighbourhood is
+ * themselves).  Every difference of two averages is then formed as
+ * (Uhat[piv_a] - Uhat[piv_b]) + (D_a - D_b): for a tiny cell merged with one
+ * large neighbour, Qhat_r lies within ~alpha of that neighbour's value and
+ * the difference is kept to full relative accuracy. */
+typedef struct { const double *Uh; const long *piv; const double *D; } QhatForm;
+
+static double qdiff(const QhatForm *Q, long a, long b) {
+  return (Q->Uh[Q->piv[a]] - Q->Uh[Q->piv[b]]) + (Q->D[a] - Q->D[b]);
+}
+
 /* Least-squares gradient of Qhat for small CV r (Sec. 5.1): fit over the
  * non-covered CVs of the 3x3x3 box around r, each Qhat placed at its
  * neighbourhood centroid; an axis whose centroid spread is below half a cell
  * is widened to 5; the gradient is zero when the box still lacks spread, has
  * fewer than 4 points, or the normal matrix is near singular.  Then the
- * Barth-Jespersen-style limiter over the stencil's Qhat range, checked at the
- * centroids of the neighbourhood's members.  Returns the limiter factor. */
-static double lsq_gradient(const OrcDomain *D, int g, const OrcGeom *Gg, const OrcWsrd *W, const double *Qh,
+ * Barth-Jespersen-style limiter: the reconstruction at the centroids of the
+ * neighbourhood's members may not leave [Qmin, Qmax] of the stencil and r.
+ * Returns the limiter factor. */
+static double lsq_gradient(const OrcDomain *D, int g, const OrcGeom *Gg, const OrcWsrd *W, const QhatForm *Q,
                            int gi, int gj, int k, long r, double sig[3]) {
   long n = ncv(D, g);
   double xr[3] = {W->xhat[r], W->xhat[n + r], W->xhat[2 * n + r]};
   int w[3] = {1, 1, 1};
   sig[0] = sig[1] = sig[2] = 0.0;
-  double M[3][3], b[3], qmax = Qh[r], qmin = Qh[r];
+  double M[3][3], b[3];
+  double bmax = 0.0, bmin = 0.0;   /* Qmax - Qhat_r and Qmin - Qhat_r */
   int cnt = 0;
   for (int pass = 0; pass < 2; pass++) {
     double spread[3] = {0, 0, 0};
     memset(M, 0, sizeof(M));
     b[0] = b[1] = b[2] = 0.0;
-    qmax = qmin = Qh[r];
+    bmax = bmin = 0.0;
     cnt = 0;
     for (int dk = -w[2]; dk <= w[2]; dk++)
       for (int dj = -w[1]; dj <= w[1]; dj++)
@@ -898,14 +939,14 @@ static double lsq_gradient(const OrcDomain *D, int g, const OrcGeom *Gg, const O
           long m = active(D, Gg, g, gi + di, gj + dj, k + dk);
           if (m < 0) continue;
           double dv[3] = {di + W->xhat[m] - xr[0], dj + W->xhat[n + m] - xr[1], dk + W->xhat[2 * n + m] - xr[2]};
-          double dq = Qh[m] - Qh[r];
+          double dq = qdiff(Q, m, r);
           for (int a = 0; a < 3; a++) {
             if (fabs(dv[a]) > spread[a]) spread[a] = fabs(dv[a]);
             b[a] += dv[a] * dq;
             for (int c = 0; c < 3; c++) M[a][c] += dv[a] * dv[c];
           }
-          if (Qh[m] > qmax) qmax = Qh[m];
-          if (Qh[m] < qmin) qmin = Qh[m];
+          if (dq > bmax) bmax = dq;
+          if (dq < bmin) bmin = dq;
           cnt++;
         }
     int widen = 0;
@@ -936,11 +977,13 @@ static double lsq_gradient(const OrcDomain *D, int g, const OrcGeom *Gg, const O
   int nm = members(D, Gg, g, gi, gj, k, W->code[r], mid, moff);
   double phi = 1.0;
   for (int q = 0; q < nm; q++) {
-    double del = 0.0;
-    for (int a = 0; a < 3; a++) del += sig[a] * (moff[q][a] + Gg->cent[a * n + mid[q]] - xr[a]);
+    double xq[3], e[3], del = 0.0;
+    for (int a = 0; a < 3; a++) xq[a] = moff[q][a] + Gg->cent[a * n + mid[q]];
+    from_xhat(D, g, Gg, W, gi, gj, k, r, xq, e);
+    for (int a = 0; a < 3; a++) del += sig[a] * e[a];
     double ph = 1.0;
-    if (del > 0.0) ph = (qmax - Qh[r]) / del;
-    else if (del < 0.0) ph = (qmin - Qh[r]) / del;
+    if (del > 0.0) ph = bmax / del;
+    else if (del < 0.0) ph = bmin / del;
     if (ph > 1.0) ph = 1.0;
     if (ph < phi) phi = ph;
   }
@@ -949,30 +992,47 @@ static double lsq_gradient(const OrcDomain *D, int g, const OrcGeom *Gg, const O
 }
 
 /* Redistribution of one field of grid g (Eqs. qhat_omega, qrecon,
- * final_update_omega): Uhat -> Unew.  Inactive CVs are copied.  If sigma_out /
+ * final_update_omega): Uhat -> Unew.  Inactive CVs are copied.  The final
+ * update is written as U_i = P_i + (1/N_i) sum_{r in W-_i} kappa_r
+ * (q_r(x_i) - P_i) with P_i = q_i(x_i), which is Eq. final_update_omega
+ * because omega_i = 1 - (1/N_i) sum kappa_r (Eq. omega).  If sigma_out /
  * phi_out are not NULL they receive the limited gradient (3n) and the limiter
  * factor (n, 1 where no gradient was fitted). */
 int orc_wsrd_apply(const OrcDomain *D, int g, const OrcGeom *Gg, const OrcWsrd *W, const double *Uh, double *Un,
                    double *sigma_out, double *phi_out) {
   long n = ncv(D, g);
   int nzg = nzg_of(D, g);
-  double *Qh = malloc(sizeof(double) * (size_t)n);
+  long *piv = malloc(sizeof(long) * (size_t)n);
+  double *Dv = malloc(sizeof(double) * (size_t)n);
   double *sg = calloc((size_t)n * 3, sizeof(double));
-  /* neighbourhood averages (Eq. qhat_omega) */
+  QhatForm Q = {Uh, piv, Dv};
+  /* neighbourhood averages (Eq. qhat_omega), pivoted deviation form */
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < nzg; k++)
     for (int lj = 0; lj < D->WY; lj++)
       for (int li = 0; li < D->WX; li++) {
         long id = (long)li + (long)D->WX * ((long)lj + (long)D->WY * k);
         int gi = D->x0 + li, gj = D->y0 + lj;
-        Qh[id] = Uh[id];
+        piv[id] = id;
+        Dv[id] = 0.0;
         if (active(D, Gg, g, gi, gj, k) < 0 || W->code[id] == 0) continue;
         long mid[8];
         int moff[8][3];
         int nm = members(D, Gg, g, gi, gj, k, W->code[id], mid, moff);
-        double s = W->omega[id] * Gg->alpha[id] * Uh[id];
-        for (int q = 1; q < nm; q++) s += W->kappa[id] * Gg->alpha[mid[q]] / W->nnb[mid[q]] * Uh[mid[q]];
-        Qh[id] = s / W->vhat[id];
+        double wt[8];
+        wt[0] = W->omega[id] * Gg->alpha[id] / W->vhat[id];
+        for (int q = 1; q < nm; q++) wt[q] = W->kappa[id] * Gg->alpha[mid[q]] / W->nnb[mid[q]] / W->vhat[id];
+        int p = -1, big = 0;
+        for (int q = 0; q < nm; q++) {
+          if (p < 0 && Gg->alpha[mid[q]] >= 0.5) p = q;
+          if (Gg->alpha[mid[q]] > Gg->alpha[mid[big]]) big = q;
+        }
+        if (p < 0) p = big;
+        double s = 0.0;
+        for (int q = 0; q < nm; q++)
+          if (q != p) s += wt[q] * (Uh[mid[q]] - Uh[mid[p]]);
+        piv[id] = mid[p];
+        Dv[id] = s;
       }
   /* gradients (small CVs whose neighbourhood holds at least two CVs) */
 #pragma omp parallel for schedule(static)
@@ -988,7 +1048,7 @@ int orc_wsrd_apply(const OrcDomain *D, int g, const OrcGeom *Gg, const OrcWsrd *
           int nm = members(D, Gg, g, gi, gj, k, W->code[id], mid, moff);
           if (nm >= 2) {
             double s3[3];
-            phi = lsq_gradient(D, g, Gg, W, Qh, gi, gj, k, id, s3);
+            phi = lsq_gradient(D, g, Gg, W, &Q, gi, gj, k, id, s3);
             for (int a = 0; a < 3; a++) sg[a * n + id] = s3[a];
           }
         }
@@ -1003,10 +1063,13 @@ int orc_wsrd_apply(const OrcDomain *D, int g, const OrcGeom *Gg, const OrcWsrd *
         int gi = D->x0 + li, gj = D->y0 + lj;
         if (active(D, Gg, g, gi, gj, k) < 0) { Un[id] = Uh[id]; continue; }
         double xi[3] = {Gg->cent[id], Gg->cent[n + id], Gg->cent[2 * n + id]};
-        /* own reconstruction at own centroid */
-        double q = Qh[id];
-        for (int a = 0; a < 3; a++) q += sg[a * n + id] * (xi[a] - W->xhat[a * n + id]);
-        double u = W->omega[id] * q;
+        /* own reconstruction at own centroid, as an offset from Uhat_i */
+        double si = 0.0;
+        if (W->code[id]) {
+          double ei[3];
+          from_xhat(D, g, Gg, W, gi, gj, k, id, xi, ei);
+          for (int a = 0; a < 3; a++) si += sg[a * n + id] * ei[a];
+        }
         double acc = 0.0;
         for (int dk = -1; dk <= 1; dk++)
           for (int dj = -1; dj <= 1; dj++)
@@ -1019,19 +1082,22 @@ int orc_wsrd_apply(const OrcDomain *D, int g, const OrcGeom *Gg, const OrcWsrd *
               int nm = members(D, Gg, g, gi + di, gj + dj, k + dk, W->code[r], mid, moff);
               for (int qq = 1; qq < nm; qq++)
                 if (moff[qq][0] == -di && moff[qq][1] == -dj && moff[qq][2] == -dk) {
-                  /* q_r evaluated at x_i, positions relative to r's centre */
-                  double qr = Qh[r];
-                  for (int a = 0; a < 3; a++) {
-                    double off = a == 0 ? -di : a == 1 ? -dj : -dk;
-                    qr += sg[a * n + r] * (off + xi[a] - W->xhat[a * n + r]);
-                  }
-                  acc += W->kappa[r] * qr;
+                  /* q_r(x_i) - P_i, positions relative to r's centre */
+                  double xir[3] = {-di + xi[0], -dj + xi[1], -dk + xi[2]}, er[3], sr = 0.0;
+                  from_xhat(D, g, Gg, W, gi + di, gj + dj, k + dk, r, xir, er);
+                  for (int a = 0; a < 3; a++) sr += sg[a * n + r] * er[a];
+                  acc += W->kappa[r] * (qdiff(&Q, r, id) + sr - si);
                 }
             }
-        Un[id] = u + acc / W->nnb[id];
+        /* A small CV's result is anchored at its pivot, Uhat[piv] + D + s +
+         * corrections: Uhat_i itself can be huge (a tiny cell after the flux
+         * update) and must not be added and subtracted again. */
+        if (W->code[id]) Un[id] = Uh[piv[id]] + ((Dv[id] + si) + acc / W->nnb[id]);
+        else Un[id] = Uh[id] + acc / W->nnb[id];
       }
   if (sigma_out) memcpy(sigma_out, sg, sizeof(double) * (size_t)n * 3);
-  free(Qh);
+  free(piv);
+  free(Dv);
   free(sg);
   return 0;
 }

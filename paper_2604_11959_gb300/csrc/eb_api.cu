@@ -56,7 +56,7 @@ struct eb_geom_s {
   double *zero_d = nullptr;
   float *zero_f = nullptr;
   unsigned *status = nullptr;
-  void *qhat = nullptr, *sig = nullptr;
+  void *qhat = nullptr, *sig = nullptr, *pval = nullptr;
   long long max_small = 0;
   // scratch states for eb_step: 4 x 5 fields
   void *scr[4][5] = {};
@@ -187,6 +187,7 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
   }
   CUDA_TRY(g->alloc((double **)&g->qhat, g->max_small), "alloc qhat");
   CUDA_TRY(g->alloc((double **)&g->sig, 3 * g->max_small), "alloc sig");
+  CUDA_TRY(g->alloc((double **)&g->pval, g->max_small), "alloc pivot values");
   CUDA_TRY(fill_ref<double>(g, ref_rho, &g->ref_d[0], &g->ref_f[0], s), "reference");
   CUDA_TRY(fill_ref<double>(g, ref_rt, &g->ref_d[1], &g->ref_f[1], s), "reference");
   CUDA_TRY(g->alloc(&g->status, 1), "alloc status");
@@ -269,10 +270,10 @@ void wsrd_field(eb_geom g, int field, T *u, cudaStream_t s) {
   R.D = g->D;
   R.W = g->W[grid];
   R.u = u;
-  R.ref = nullptr;
-  if (field <= 1) R.ref = sizeof(T) == sizeof(double) ? (const T *)g->ref_d[field] : (const T *)g->ref_f[field];
-  R.qhat = (T *)g->qhat;
+  R.refd = field <= 1 ? g->ref_d[field] : nullptr;
+  R.dev = (T *)g->qhat;
   R.sig = (T *)g->sig;
+  R.pval = (T *)g->pval;
   R.status = g->status;
   launch_wsrd(R, s);
 }

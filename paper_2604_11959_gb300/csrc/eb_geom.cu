@@ -95,30 +95,29 @@ __device__ void cut_level(const Poly &in, Poly &out, double lev, bool below) {
   }
 }
 
-// Area moments of a simple polygon by Green's theorem:
-// m = {A, int x, int y, int x^2, int xy, int y^2}.
-__device__ void green_moments(const Poly &p, double m[6]) {
-  for (int q = 0; q < 6; ++q) m[q] = 0.0;
+// Area and first moments of a simple polygon by Green's theorem, taken
+// about its first vertex (a small polygon far from the origin keeps its
+// centroid): m = {A, int x, int y}.
+__device__ void green_moments(const Poly &p, double m[3]) {
+  m[0] = m[1] = m[2] = 0.0;
   if (p.n < 3) return;
-  for (int e = 0; e < p.n; ++e) {
-    const int f = (e + 1 == p.n) ? 0 : e + 1;
-    const double x0 = p.x[e], y0 = p.y[e], x1 = p.x[f], y1 = p.y[f];
+  const double ox = p.x[0], oy = p.y[0];
+  for (int e = 1; e + 1 < p.n; ++e) {
+    const double x0 = p.x[e] - ox, y0 = p.y[e] - oy, x1 = p.x[e + 1] - ox, y1 = p.y[e + 1] - oy;
     const double c = x0 * y1 - x1 * y0;
     m[0] += c;
     m[1] += (x0 + x1) * c;
     m[2] += (y0 + y1) * c;
-    m[3] += (x0 * x0 + x0 * x1 + x1 * x1) * c;
-    m[4] += (x0 * y1 + 2.0 * x0 * y0 + 2.0 * x1 * y1 + x1 * y0) * c;
-    m[5] += (y0 * y0 + y0 * y1 + y1 * y1) * c;
   }
   m[0] *= 0.5;
   m[1] *= 1.0 / 6.0;
   m[2] *= 1.0 / 6.0;
-  m[3] *= 1.0 / 12.0;
-  m[4] *= 1.0 / 24.0;
-  m[5] *= 1.0 / 12.0;
-  if (!(m[0] > 0.0))
-    for (int q = 0; q < 6; ++q) m[q] = 0.0;
+  if (!(m[0] > 0.0)) {
+    m[0] = m[1] = m[2] = 0.0;
+    return;
+  }
+  m[1] += ox * m[0];
+  m[2] += oy * m[0];
 }
 
 struct BoxMoments {
@@ -172,8 +171,9 @@ __device__ void side_integrals(const double Hq[3][3], bool along_y, int c2, int 
       const double g0 = Z1 - b0, g1 = Z1 - b1;
       A += 0.5 * len * (g0 + g1);
       S += len / 6.0 * (u0 * (2.0 * g0 + g1) + u1 * (g0 + 2.0 * g1));
-      const double c0 = b0 - zb, c1 = b1 - zb, top = Z1 - zb;
-      Zm += 0.5 * len * top * top - len / 6.0 * (c0 * c0 + c0 * c1 + c1 * c1);
+      // z-moment of the column [b, Z1]: g (top - g/2), g linear on [u0, u1]
+      const double top = Z1 - zb;
+      Zm += top * 0.5 * len * (g0 + g1) - len / 6.0 * (g0 * g0 + g0 * g1 + g1 * g1);
     }
   }
 }
@@ -205,7 +205,6 @@ __device__ void box_moments(const double Hq[3][3], int a0, int a1, int b0, int b
       px = Hq[2][2] - Hq[0][2];
       py = Hq[0][2] - Hq[0][0];
     }
-    const double p0 = Hq[0][0] - zb;
     Poly a, b;
     cut_axis(tri, a, 0, 0.5 * a0, false);
     cut_axis(a, b, 0, 0.5 * a1, true);
@@ -218,37 +217,55 @@ __device__ void box_moments(const double Hq[3][3], int a0, int a1, int b0, int b
     cut_level(b, tmp, Z0, false);
     cut_level(tmp, rB, Z1, true);  // EB inside the box
     cut_level(b, rU, Z1, true);    // open part of the top face
-    double mA[6], mB[6], mU[6];
+    double mA[3], mU[3];
     green_moments(rA, mA);
-    green_moments(rB, mB);
     green_moments(rU, mU);
     const double hgt = Z1 - Z0;
     M.vol += hgt * mA[0];
     M.mx += hgt * mA[1];
     M.my += hgt * mA[2];
     M.mz += 0.5 * (top * top - (Z0 - zb) * (Z0 - zb)) * mA[0];
-    // region B: fluid height top - h'(xi, eta), h' = p0 + px xi + py eta
-    const double Ih = p0 * mB[0] + px * mB[1] + py * mB[2];
-    const double Ixh = p0 * mB[1] + px * mB[3] + py * mB[4];
-    const double Iyh = p0 * mB[2] + px * mB[4] + py * mB[5];
-    const double Ihh = p0 * p0 * mB[0] + 2.0 * p0 * px * mB[1] + 2.0 * p0 * py * mB[2] + px * px * mB[3] +
-                       2.0 * px * py * mB[4] + py * py * mB[5];
-    M.vol += top * mB[0] - Ih;
-    M.mx += top * mB[1] - Ixh;
-    M.my += top * mB[2] - Iyh;
-    M.mz += 0.5 * (top * top * mB[0] - Ihh);
+    // region B: fluid height g = Z1 - H >= 0, linear; integrate over a fan of
+    // triangles from the vertex values so that thin slivers (tiny g) keep
+    // their relative accuracy: int f g = A/12 (sum f_i g_i + sum f_i sum g_i)
+    double aB = 0.0, xB = 0.0, yB = 0.0, Ig = 0.0, Ixg = 0.0, Iyg = 0.0, Izm = 0.0;
+    for (int q = 1; q + 1 < rB.n; ++q) {
+      const int vi[3] = {0, q, q + 1};
+      const double At = 0.5 * ((rB.x[q] - rB.x[0]) * (rB.y[q + 1] - rB.y[0]) -
+                               (rB.x[q + 1] - rB.x[0]) * (rB.y[q] - rB.y[0]));
+      if (!(At > 0.0)) continue;
+      double g[3], xs[3], ys[3], zc[3];
+      for (int v = 0; v < 3; ++v) {
+        g[v] = Z1 - rB.h[vi[v]];
+        xs[v] = rB.x[vi[v]];
+        ys[v] = rB.y[vi[v]];
+        zc[v] = top - 0.5 * g[v];   // mean height of the fluid column above the point, rel. zb
+      }
+      const double sg = g[0] + g[1] + g[2];
+      aB += At;
+      xB += At * (xs[0] + xs[1] + xs[2]) / 3.0;
+      yB += At * (ys[0] + ys[1] + ys[2]) / 3.0;
+      Ig += At * sg / 3.0;
+      Ixg += At / 12.0 * (xs[0] * g[0] + xs[1] * g[1] + xs[2] * g[2] + (xs[0] + xs[1] + xs[2]) * sg);
+      Iyg += At / 12.0 * (ys[0] * g[0] + ys[1] * g[1] + ys[2] * g[2] + (ys[0] + ys[1] + ys[2]) * sg);
+      Izm += At / 12.0 * (zc[0] * g[0] + zc[1] * g[1] + zc[2] * g[2] + (zc[0] + zc[1] + zc[2]) * sg);
+    }
+    M.vol += Ig;
+    M.mx += Ixg;
+    M.my += Iyg;
+    M.mz += Izm;
     M.fa[4] += mA[0]; M.f1[4] += mA[1]; M.f2[4] += mA[2];
     M.fa[5] += mU[0]; M.f1[5] += mU[1]; M.f2[5] += mU[2];
-    if (mB[0] > 0.0) {
+    if (aB > 0.0) {
       const double gx = sx * px, gy = sy * py;
       const double el = sqrt(1.0 + gx * gx + gy * gy);
-      M.eba += el * mB[0];
-      M.ebx += el * mB[1];
-      M.eby += el * mB[2];
-      M.ebz += el * Ih;
-      M.nv[0] -= gx * mB[0];
-      M.nv[1] -= gy * mB[0];
-      M.nv[2] += mB[0];
+      M.eba += el * aB;
+      M.ebx += el * xB;
+      M.eby += el * yB;
+      M.ebz += el * (top * aB - Ig);   // EB height relative to zb: top - g
+      M.nv[0] -= gx * aB;
+      M.nv[1] -= gy * aB;
+      M.nv[2] += aB;
     }
   }
 }

@@ -210,11 +210,37 @@ __global__ void k_band(StepArgs<T> A) {
 
 // ---------------------------------------------------------------------------
 // redistribution
+//
+// A neighbourhood average is held as Qhat_r = Uhat[p_r] + D_r with its pivot
+// p_r (set-up) and the deviation sum D_r = sum_{m != p} w_m (Uhat_m - Uhat_p)
+// (Eq. qhat_omega, the weights sum to one).  Non-small CVs have p = itself,
+// D = 0.  Every difference of averages is (Uhat[p_a] - Uhat[p_b]) + (D_a - D_b),
+// so a tiny cell merged into one large neighbour (Qhat within ~alpha of that
+// neighbour) keeps full relative accuracy in the limiter, and a uniform state
+// is reproduced exactly.
 // ---------------------------------------------------------------------------
+
+// Uhat_a - Uhat_b of two CVs of the field (state indices), with the
+// reference profile difference taken in double.
 template <typename T>
-__device__ inline T full(const WsrdArgs<T> &R, long long c) {
-  const T v = R.u[c];
-  return R.ref ? v + R.ref[c / R.D.nxy] : v;
+__device__ inline T vdiff(const WsrdArgs<T> &R, long long a, long long b) {
+  T d = R.u[a] - R.u[b];
+  if (R.refd) {
+    const long long ka = a / R.D.nxy, kb = b / R.D.nxy;
+    if (ka != kb) d += (T)(R.refd[ka] - R.refd[kb]);
+  }
+  return d;
+}
+
+// The same difference from two values already read, located at a and b.
+template <typename T>
+__device__ inline T vdiff_vals(const WsrdArgs<T> &R, T va, long long a, T vb, long long b) {
+  T d = va - vb;
+  if (R.refd) {
+    const long long ka = a / R.D.nxy, kb = b / R.D.nxy;
+    if (ka != kb) d += (T)(R.refd[ka] - R.refd[kb]);
+  }
+  return d;
 }
 
 // Kahan-compensated running sum in float; plain in double.
@@ -239,44 +265,54 @@ __global__ void k_qhat(WsrdArgs<T> R) {
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= R.W.nsmall) return;
   const int n = R.W.s_nmem[s], p = R.W.s_piv[s];
-  const T vp = full(R, R.W.s_mlin[8 * s + p]);
+  const long long lp = R.W.s_mlin[8 * s + p];
   CompSum<T> acc;
   for (int q = 0; q < n; ++q) {
     if (q == p) continue;
-    acc.add((T)R.W.s_mw[8 * s + q] * (full(R, R.W.s_mlin[8 * s + q]) - vp));
+    acc.add((T)R.W.s_mw[8 * s + q] * vdiff(R, R.W.s_mlin[8 * s + q], lp));
   }
-  R.qhat[s] = vp + acc.s;
+  R.dev[s] = acc.s;
+  R.pval[s] = R.u[lp];   // snapshot: the final update overwrites the field in place
 }
 
 // One warp per small CV: lanes walk the stencil, shuffles reduce the slope
-// and the stencil's Qhat range; lane 0 applies the limiter at the members'
-// centroids.
+// and the stencil's range of Qhat - Qhat_r; lane 0 applies the limiter at the
+// members' centroids.
 template <typename T>
 __global__ void k_sigma(WsrdArgs<T> R) {
   const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (s >= R.W.nsmall) return;
   const long long o0 = R.W.s_loff[s], o1 = R.W.s_loff[s + 1];
-  const T qr = R.qhat[s];
-  T sx = T(0), sy = T(0), sz = T(0), qmax = qr, qmin = qr;
+  const long long pr = R.W.s_mlin[8 * s + R.W.s_piv[s]];
+  const T dr = R.dev[s];
+  T sx = T(0), sy = T(0), sz = T(0), bmax = T(0), bmin = T(0);
   for (long long o = o0 + lane; o < o1; o += 32) {
     const int sid = R.W.l_sid[o];
-    const T qm = sid >= 0 ? R.qhat[sid] : full(R, R.W.l_lin[o]);
-    const T dq = qm - qr;
-    sx += (T)R.W.l_c[3 * o] * dq;
-    sy += (T)R.W.l_c[3 * o + 1] * dq;
-    sz += (T)R.W.l_c[3 * o + 2] * dq;
-    qmax = qm > qmax ? qm : qmax;
-    qmin = qm < qmin ? qm : qmin;
+    long long pm;
+    T dm;
+    if (sid >= 0) {
+      pm = R.W.s_mlin[8 * (long long)sid + R.W.s_piv[sid]];
+      dm = R.dev[sid];
+    } else {
+      pm = R.W.l_lin[o];
+      dm = T(0);
+    }
+    const T b = vdiff(R, pm, pr) + (dm - dr);
+    sx += (T)R.W.l_c[3 * o] * b;
+    sy += (T)R.W.l_c[3 * o + 1] * b;
+    sz += (T)R.W.l_c[3 * o + 2] * b;
+    bmax = b > bmax ? b : bmax;
+    bmin = b < bmin ? b : bmin;
   }
   for (int off = 16; off > 0; off >>= 1) {
     sx += __shfl_xor_sync(0xffffffffu, sx, off);
     sy += __shfl_xor_sync(0xffffffffu, sy, off);
     sz += __shfl_xor_sync(0xffffffffu, sz, off);
-    const T a = __shfl_xor_sync(0xffffffffu, qmax, off);
-    const T b = __shfl_xor_sync(0xffffffffu, qmin, off);
-    qmax = a > qmax ? a : qmax;
-    qmin = b < qmin ? b : qmin;
+    const T a = __shfl_xor_sync(0xffffffffu, bmax, off);
+    const T c = __shfl_xor_sync(0xffffffffu, bmin, off);
+    bmax = a > bmax ? a : bmax;
+    bmin = c < bmin ? c : bmin;
   }
   if (lane != 0) return;
   T phi = T(1);
@@ -286,8 +322,8 @@ __global__ void k_sigma(WsrdArgs<T> R) {
       const double *e = R.W.s_me + 24 * s + 3 * q;
       const T del = sx * (T)e[0] + sy * (T)e[1] + sz * (T)e[2];
       T ph = T(1);
-      if (del > T(0)) ph = (qmax - qr) / del;
-      else if (del < T(0)) ph = (qmin - qr) / del;
+      if (del > T(0)) ph = bmax / del;
+      else if (del < T(0)) ph = bmin / del;
       if (ph > T(1)) ph = T(1);
       if (ph < phi) phi = ph;
     }
@@ -298,33 +334,49 @@ __global__ void k_sigma(WsrdArgs<T> R) {
 }
 
 // U_i = P_i + sum_r (kappa_r / N_i) (q_r(x_i) - P_i), P_i = q_i(x_i) for a
-// small CV and U_hat_i otherwise: Eq. final_update_omega with omega_i written
-// as 1 - sum_r kappa_r / N_i.
+// small CV and Uhat_i otherwise: Eq. final_update_omega with omega_i written
+// as 1 - sum_r kappa_r / N_i.  Formed as an offset added to Uhat_i.
 template <typename T>
 __global__ void k_final(WsrdArgs<T> R) {
   const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (a >= R.W.naff) return;
   const long long c = R.W.a_lin[a];
   const int sid = R.W.a_sid[a];
-  const T ref = R.ref ? R.ref[c / R.D.nxy] : T(0);
-  T P, Pstore;
+  // every value this thread reads besides its own CV comes from the
+  // snapshots of k_qhat: other threads overwrite their CVs meanwhile
+  const T ui = R.u[c];
+  T si = T(0), di = T(0), pvi = ui;
+  long long pi = c;
   if (sid >= 0) {
     const double *e = R.W.a_eself + 3 * a;
-    const T lin = R.sig[3 * sid] * (T)e[0] + R.sig[3 * sid + 1] * (T)e[1] + R.sig[3 * sid + 2] * (T)e[2];
-    P = R.qhat[sid] + lin;
-    Pstore = (R.qhat[sid] - ref) + lin;
-  } else {
-    Pstore = R.u[c];
-    P = Pstore + ref;
+    si = R.sig[3 * sid] * (T)e[0] + R.sig[3 * sid + 1] * (T)e[1] + R.sig[3 * sid + 2] * (T)e[2];
+    pi = R.W.s_mlin[8 * (long long)sid + R.W.s_piv[sid]];
+    pvi = R.pval[sid];
+    di = R.dev[sid];
   }
   CompSum<T> acc;
   for (long long o = R.W.a_woff[a]; o < R.W.a_woff[a + 1]; ++o) {
     const int r = R.W.w_sid[o];
     const double *e = R.W.w_e + 3 * o;
-    const T q = R.qhat[r] + R.sig[3 * r] * (T)e[0] + R.sig[3 * r + 1] * (T)e[1] + R.sig[3 * r + 2] * (T)e[2];
-    acc.add((T)R.W.w_k[o] * (q - P));
+    const long long pr = R.W.s_mlin[8 * (long long)r + R.W.s_piv[r]];
+    const T sr = R.sig[3 * r] * (T)e[0] + R.sig[3 * r + 1] * (T)e[1] + R.sig[3 * r + 2] * (T)e[2];
+    const T diff = vdiff_vals(R, R.pval[r], pr, pvi, pi) + (R.dev[r] - di) + (sr - si);
+    acc.add((T)R.W.w_k[o] * diff);
   }
-  const T v = Pstore + acc.s;
+  // a small CV's result is anchored at its pivot value: its own provisional
+  // value can be huge (tiny cell after the flux update) and must not be added
+  // and subtracted again
+  T v;
+  if (sid >= 0) {
+    T anchor = pvi;
+    if (R.refd) {
+      const long long kp = pi / R.D.nxy, kc = c / R.D.nxy;
+      if (kp != kc) anchor += (T)(R.refd[kp] - R.refd[kc]);
+    }
+    v = anchor + ((di + si) + acc.s);
+  } else {
+    v = ui + acc.s;
+  }
   R.u[c] = v;
   if (!finite_val(v)) atomicOr(R.status, EB_DEV_NUMERIC);
 }

@@ -22,8 +22,9 @@ struct WsrdArgs {
   Dims D;
   WsrdDev W;
   T *u;                // field on its grid, redistributed in place
-  const T *ref;        // per-level reference added to u (c-grid fields) or nullptr
-  T *qhat;             // [nsmall] neighbourhood averages
+  const double *refd;  // per-level reference added to u (c-grid fields) or nullptr
+  T *dev;              // [nsmall] deviation sums D of the neighbourhood averages
+  T *pval;             // [nsmall] field value at each neighbourhood's pivot
   T *sig;              // [3 * nsmall] limited slopes
   unsigned *status;
 };

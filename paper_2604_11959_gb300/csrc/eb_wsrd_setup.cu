@@ -297,6 +297,27 @@ __device__ int lsq_stencil(const GridDev &G, const Dims &D, int g, int i, int j,
   return cnt;
 }
 
+// x - xhat_r for a point x relative to r's centre, as sum_m w_m (x - x_m)
+// over the members of M_r (weights of Eq. centroid, summing to one): exact
+// to rounding even when xhat_r sits next to one member.
+__device__ void from_xhat(const GridDev &G, const Dims &D, int g, int i, int j, int k, long long r, const double x[3],
+                          double e[3]) {
+  const long long n = G.nrec;
+  e[0] = e[1] = e[2] = 0.0;
+  if (!G.code[r]) {
+    for (int d = 0; d < 3; ++d) e[d] = x[d] - G.cent[d * n + r];
+    return;
+  }
+  Members M;
+  members_of(G, D, g, i, j, k, G.code[r], M);
+  for (int q = 0; q < M.n; ++q) {
+    const long long m = M.v[q].rec;
+    const double w = q == 0 ? G.omega[r] * M.v[0].alpha / G.vhat[r]
+                            : G.kappa[r] * M.v[q].alpha / (m >= 0 ? G.nnb[m] : 1) / G.vhat[r];
+    for (int d = 0; d < 3; ++d) e[d] += w * (x[d] - (M.off[q][d] + rec_or(G.cent + d * n, m, 0.0)));
+  }
+}
+
 // Per small CV: members, Qhat weights, pivot, limiter points, stencil size.
 __global__ void k_small_tables(Dims D, int g, GridDev G, WsrdDev W, double vt, long long *lsq_cnt) {
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -318,7 +339,9 @@ __global__ void k_small_tables(Dims D, int g, GridDev G, WsrdDev W, double vt, l
       ml = lin(D, i + M.off[q][0], j + M.off[q][1], k + M.off[q][2]);
       if (q == 0) w = G.omega[r] * M.v[0].alpha / vh;
       else w = G.kappa[r] * M.v[q].alpha / (m >= 0 ? G.nnb[m] : 1) / vh;
-      for (int d = 0; d < 3; ++d) e[d] = M.off[q][d] + rec_or(G.cent + d * n, m, 0.0) - xr[d];
+      double xq[3];
+      for (int d = 0; d < 3; ++d) xq[d] = M.off[q][d] + rec_or(G.cent + d * n, m, 0.0);
+      from_xhat(G, D, g, i, j, k, r, xq, e);
       if (piv < 0 && M.v[q].alpha >= vt) piv = q;
       if (M.v[q].alpha > M.v[big].alpha) big = q;
     }
@@ -390,7 +413,12 @@ __global__ void k_aff_count(Dims D, int g, GridDev G, const long long *aff_id, W
     const long long a = aff_id[r];
     W.a_lin[a] = lin(D, i, j, k);
     W.a_sid[a] = W.sid[r];
-    for (int d = 0; d < 3; ++d) W.a_eself[3 * a + d] = G.code[r] ? G.cent[d * n + r] - G.xhat[d * n + r] : 0.0;
+    double ee[3] = {0.0, 0.0, 0.0};
+    if (G.code[r]) {
+      const double xi[3] = {G.cent[r], G.cent[n + r], G.cent[2 * n + r]};
+      from_xhat(G, D, g, i, j, k, r, xi, ee);
+    }
+    for (int d = 0; d < 3; ++d) W.a_eself[3 * a + d] = ee[d];
     wcnt[a] = G.nnb[r] - 1;
   }
 }
@@ -419,8 +447,10 @@ __global__ void k_aff_fill(Dims D, int g, GridDev G, const long long *aff_id, Ws
               const long long q = v.rec;
               W.w_sid[o] = W.sid[q];
               W.w_k[o] = G.kappa[q] / Ni;
-              const int rel[3] = {-di, -dj, -dk};
-              for (int d = 0; d < 3; ++d) W.w_e[3 * o + d] = rel[d] + G.cent[d * n + r] - G.xhat[d * n + q];
+              const double xi[3] = {-di + G.cent[r], -dj + G.cent[n + r], -dk + G.cent[2 * n + r]};
+              double ee[3];
+              from_xhat(G, D, g, i + di, j + dj, k + dk, q, xi, ee);
+              for (int d = 0; d < 3; ++d) W.w_e[3 * o + d] = ee[d];
               ++o;
             }
         }

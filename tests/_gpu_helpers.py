@@ -41,6 +41,13 @@ def to_host(U, refs=None):
     return out
 
 
+def worst(got, want, mask):
+    """Location and values of the largest difference (for messages)."""
+    d = np.where(mask, np.abs(got - want), -1.0)
+    loc = np.unravel_index(int(np.argmax(d)), d.shape)
+    return {"at(k,j,i)": tuple(int(v) for v in loc), "got": float(got[loc]), "want": float(want[loc])}
+
+
 def rel_linf(got, want, mask=None):
     d = np.abs(got - want)
     w = np.abs(want)
