@@ -1,7 +1,8 @@
 #!/usr/bin/env python
 """Throughput of the staggered-mesh EB advance (flux + WSRD on four grids).
 
-One step = one forward-Euler pass of the whole path (Eq. basic_fv_srd):
+One step = one forward-Euler pass of the whole path (Eq. basic_fv_srd) over
+the same seeded input state:
 flux divergence and provisional update on the c, u, v, w grids, then
 weighted state redistribution of all five fields.  Workload: the 3D
 Gaussian hill, 256 x 256 x 128 cells, synthetic seeded state.  The headline
@@ -37,11 +38,14 @@ FIELDS = ("rho", "rhotheta", "rhou", "rhov", "rhow")
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=("hill256", "grf512"), default="hill256")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--precision", choices=("both", "mixed", "f64"), default="both",
+                    help="arms to run (profiling runs pick one)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     return ap.parse_args()
 
 
@@ -75,7 +79,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                                          "-lms", "100", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                          "-lms", "20", "-i", str(self.dev)], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -172,13 +176,16 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist):
     geom = eb.Geometry(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, torch.from_numpy(h).cuda(), precision=precision,
                        ref_rho=torch.from_numpy(refs[0]).cuda(), ref_rhotheta=torch.from_numpy(refs[1]).cuda())
     info = geom.info()
+    # every step is one pass of the whole path over the same input state U0
+    # (evolving the state for hundreds of forward-Euler steps would measure a
+    # different, eventually degenerate, flow); outputs alternate between two
+    # buffers and the L2 is flushed before each timed step
     A = eb.device_state(U, precision, refs)
-    B = geom.empty_state()
+    outs = [geom.empty_state(), geom.empty_state()]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     dt = w.dt()
-    for _ in range(warmup):
-        eb.step(geom, A, dt, 1, out=B)
-        A, B = B, A
+    for q in range(warmup):
+        eb.step(geom, A, dt, 1, out=outs[q % 2])
     eb.sync_status(geom)
     stream = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -189,9 +196,8 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist):
     for q in range(steps):
         flush.zero_()   # evict the state from L2 (untimed)
         evs[q][0].record(stream)
-        eb.step(geom, A, dt, 1, out=B)
+        eb.step(geom, A, dt, 1, out=outs[q % 2])
         evs[q][1].record(stream)
-        A, B = B, A
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -205,17 +211,19 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist):
         ms_step = float(t.item())
     # the dominant kernel alone, timed with events on its stream
     prof = []
-    for _ in range(max(5, min(steps, 20))):
+    for q in range(max(5, min(steps, 20))):
         flush.zero_()
-        prof.append(eb.step_profile(geom, A, B, dt))
-        A, B = B, A
+        prof.append(eb.step_profile(geom, A, outs[q % 2], dt))
     prof = np.median(np.array(prof), axis=0)
     es = 8 if precision == "f64" else 4
     fast_bytes = info["fast_cells"] * 10 * es
     hbm, kind = peaks()
     achieved = fast_bytes / (prof[0] * 1e-3) / 1e9
-    launches_per_step = 2 + sum((1 if info["small_cvs"][FG] else 0) * 2 + (1 if info["affected_cvs"][FG] else 0)
-                                for FG in (0, 0, 1, 2, 3))
+    # per step: static pass-through (a fresh output buffer every call), the
+    # tiled bulk kernel, the near-EB kernel of each grid with CVs to update,
+    # and the three redistribution passes of each field
+    launches_per_step = 2 + sum(1 for g in range(4) if info["band_cvs"][g]) + \
+        sum((1 if info["small_cvs"][FG] else 0) * 2 + (1 if info["affected_cvs"][FG] else 0) for FG in (0, 0, 1, 2, 3))
     # bytes the whole step must move: every non-covered CV read and written
     # once, plus the band geometry records read by the near-EB kernel
     step_bytes = sum(info["cvs"][g] * (2 if g else 4) for g in range(4)) * es + \
@@ -233,6 +241,7 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist):
         "step_gbs": step_bytes / (ms_step * 1e-3) / 1e9,
         "step_frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm,
         "gpu_launches": launches_per_step * steps,
+        "steps": steps,
     }
     return geom, res
 
@@ -303,12 +312,17 @@ def main():
     refs = inputs.cell_reference(w.nz, w.Lz)
     U = w.state("sheltered")
     dev_index = torch.cuda.current_device()
-    with ClockSampler(dev_index) as clk:
-        geom, mixed = run_precision(eb, w, h, U, refs, "mixed", args.steps, args.warmup, world, dist)
-    e2e_res = e2e(eb, geom, w, U, refs, "mixed", min(args.steps, 10)) if rank == 0 else None
-    geom.close()
-    geom64, f64 = run_precision(eb, w, h, U, refs, "f64", args.steps, args.warmup, world, dist)
-    geom64.close()
+    mixed = f64 = e2e_res = None
+    clk = ClockSampler(dev_index)
+    if args.precision in ("both", "mixed"):
+        with clk:
+            geom, mixed = run_precision(eb, w, h, U, refs, "mixed", args.steps, args.warmup, world, dist)
+        if rank == 0 and not args.no_e2e:
+            e2e_res = e2e(eb, geom, w, U, refs, "mixed", min(args.steps, 10))
+        geom.close()
+    if args.precision in ("both", "f64"):
+        geom64, f64 = run_precision(eb, w, h, U, refs, "f64", max(10, args.steps // 10), args.warmup, world, dist)
+        geom64.close()
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline(w)
@@ -316,26 +330,28 @@ def main():
         dist.destroy_process_group()
     if rank != 0:
         return 0
+    head = mixed or f64
     line = {
-        "metric": METRIC, "value": mixed["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": w.name, "cells": w.cells(), "precision": "mixed", "stages": 1,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": w.name, "cells": w.cells(), "precision": "mixed" if mixed else "f64", "stages": 1,
                    "state": "stratified, wind u=1 above the terrain, smooth seeded perturbations",
                    "l2": "512 MiB buffer written before every timed step (untimed); per-step CUDA events",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
-        "roofline": mixed["roofline"],
-        "step_hbm_frac": mixed["step_frac"],
-        "phases_ms": mixed["phases_ms"],
+        "roofline": head["roofline"],
+        "step_hbm_frac": head["step_frac"],
+        "phases_ms": head["phases_ms"],
         "cpu_baseline": cb,
         "e2e": e2e_res,
-        "gpu_launches": mixed["gpu_launches"],
+        "gpu_launches": head["gpu_launches"],
         "clocks": clk.summary(),
-        "fp64": {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "roofline": f64["roofline"],
-                 "step_hbm_frac": f64["step_frac"], "phases_ms": f64["phases_ms"]},
-        "geometry": {k: mixed["geometry"][k] for k in ("cells", "fast_cells", "band_cvs", "small_cvs",
-                                                       "affected_cvs", "tiny_cvs", "min_alpha")},
+        "geometry": {k: head["geometry"][k] for k in ("cells", "fast_cells", "band_cvs", "small_cvs",
+                                                      "affected_cvs", "tiny_cvs", "min_alpha")},
     }
+    if mixed and f64:
+        line["fp64"] = {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "roofline": f64["roofline"],
+                        "step_hbm_frac": f64["step_frac"], "phases_ms": f64["phases_ms"], "steps": f64["steps"]}
     print(json.dumps(line))
     return 0
 

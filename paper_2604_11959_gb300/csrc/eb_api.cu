@@ -176,6 +176,79 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
     tmp_need = std::max(tmp_need, 2 * (n + 1) + 1 + (n + 1) / 256 + 8);
   }
   CUDA_TRY(cudaGetLastError(), "geometry kernels");
+  // dense availability bytes and the near-EB update lists
+  std::vector<int> kf_host(ncol);
+  CUDA_TRY(cudaMemcpy(kf_host.data(), g->kfast, sizeof(int) * ncol, cudaMemcpyDeviceToHost), "read kfast");
+  int kmax = 0;
+  for (long long c = 0; c < ncol; ++c) kmax = std::max(kmax, kf_host[c]);
+  if ((long long)D.nxy * (D.nz + 1) >= (1LL << 32)) return fail(EB_ERR_INVALID_ARG, "grid too large for 32-bit lists");
+  {
+    long long *mark = nullptr;
+    const long long nm = std::max(1LL, D.nxy * (long long)kmax);
+    CUDA_TRY(cudaMalloc(&mark, sizeof(long long) * (size_t)(nm + 1)), "alloc band marks");
+    long long *scan_tmp = nullptr;
+    cudaError_t e = cudaMalloc(&scan_tmp, sizeof(long long) * (size_t)(nm / 256 + 16));
+    if (e != cudaSuccess) { cudaFree(mark); return cuda_fail(e, "alloc band scan"); }
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
+      GridDev &G = g->G[q];
+      e = g->alloc(&G.dflag, D.nxy * nzg_of(D, q));
+      if (e != cudaSuccess) break;
+      launch_dense_flags(D, q, G, s);
+      long long nb = 0;
+      if (kmax > 0) {
+        e = cudaMemsetAsync(mark, 0, sizeof(long long) * (size_t)(nm + 1), s);
+        launch_band_marks(D, q, g->kcov[q], g->kfast, kmax, mark, s);
+        scan_exclusive(mark, nm + 1, scan_tmp, s);
+        e = cudaMemcpyAsync(&nb, scan_tmp, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+      }
+      G.nband = nb;
+      if (e == cudaSuccess) e = g->alloc(&G.blist, nb);
+      if (e == cudaSuccess && nb > 0) launch_band_fill(D, q, g->kcov[q], g->kfast, kmax, mark, G.blist, s);
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(mark);
+    cudaFree(scan_tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "band lists");
+  }
+  // faces whose provisional fluxes the near-EB path reads (they lie below
+  // kfast + 2), and the dense arrays those fluxes are staged in
+  {
+    const int kface = std::min(D.nz + 1, kmax + 2);
+    const long long nfa = std::max(1LL, D.nxy * (long long)kface);
+    const size_t es = g->prec == EB_F64 ? sizeof(double) : sizeof(float);
+    uint8_t *mk[3] = {nullptr, nullptr, nullptr};
+    long long *cnt = nullptr, *scan_tmp = nullptr;
+    cudaError_t e = cudaSuccess;
+    for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = cudaMalloc(&mk[d], (size_t)nfa);
+    if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(long long) * (size_t)(nfa + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&scan_tmp, sizeof(long long) * (size_t)(nfa / 256 + 16));
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
+      GridDev &G = g->G[q];
+      for (int d = 0; d < 3; ++d) e = e == cudaSuccess ? cudaMemsetAsync(mk[d], 0, (size_t)nfa, s) : e;
+      if (e != cudaSuccess) break;
+      launch_face_marks(D, q, G, mk[0], mk[1], mk[2], s);
+      for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+        e = cudaMemsetAsync(cnt, 0, sizeof(long long) * (size_t)(nfa + 1), s);
+        launch_marks_to_counts(mk[d], nfa, cnt, s);
+        scan_exclusive(cnt, nfa + 1, scan_tmp, s);
+        long long nf = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&nf, scan_tmp, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        G.nface[d] = nf;
+        if (e == cudaSuccess) e = g->alloc(&G.flist[d], nf);
+        if (e == cudaSuccess && nf > 0) launch_marks_fill(mk[d], nfa, cnt, G.flist[d], s);
+        if (e == cudaSuccess) e = g->alloc((char **)&G.fh[d], (long long)(nfa * es));
+        G.fhm[d] = nullptr;
+        if (e == cudaSuccess && q == 0) e = g->alloc((char **)&G.fhm[d], (long long)(nfa * es));
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int d = 0; d < 3; ++d) cudaFree(mk[d]);
+    cudaFree(cnt);
+    cudaFree(scan_tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "face lists");
+  }
   long long *tmp = nullptr;
   CUDA_TRY(g->alloc(&tmp, tmp_need), "alloc set-up scratch");
   for (int q = 0; q < 4; ++q) {

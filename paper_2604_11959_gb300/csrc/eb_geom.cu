@@ -484,6 +484,104 @@ __global__ void k_band_geometry(const double *h, Dims D, int g, GridDev G) {
   }
 }
 
+// Dense availability / record byte of every CV of grid g.
+__global__ void k_dense_flags(Dims D, int g, GridDev G) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= D.nx * D.ny) return;
+  const int kc = G.kcov[col], kx = G.kxt[col];
+  for (int k = 0; k < G.nzg; ++k) {
+    uint8_t f = 0;
+    if (k >= kx) {
+      f = 1 | (7 << 2);   // regular: fluid, all three low faces open
+    } else if (k >= kc) {
+      const long long r = G.roff[col] + (k - kc);
+      f = (uint8_t)(2 | (G.alpha[r] > 0.0 ? 1 : 0));
+      for (int d = 0; d < 3; ++d)
+        if (G.beta[d * G.nrec + r] > 0.0) f |= (uint8_t)(1 << (2 + d));
+    }
+    G.dflag[(long long)col + D.nxy * k] = f;
+  }
+}
+
+// Band-list marks, plane-major: 1 for the CVs the near-EB kernel updates.
+__global__ void k_band_marks(Dims D, int g, const int *kcov, const int *kfast, int kmax, long long *mark) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long ncol = D.nxy;
+  if (t >= ncol * kmax) return;
+  const int col = (int)(t % ncol), k = (int)(t / ncol);
+  const int top = min(kfast[col], nzg_of(D, g));
+  bool m = k >= kcov[col] && k < top;
+  if (g == 3 && (k == 0 || k == D.nz)) m = false;
+  mark[t] = m ? 1 : 0;
+}
+
+__global__ void k_band_fill(Dims D, int g, const int *kcov, const int *kfast, int kmax, const long long *pos,
+                            unsigned *list) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long ncol = D.nxy;
+  if (t >= ncol * kmax) return;
+  const int col = (int)(t % ncol), k = (int)(t / ncol);
+  const int top = min(kfast[col], nzg_of(D, g));
+  bool m = k >= kcov[col] && k < top;
+  if (g == 3 && (k == 0 || k == D.nz)) m = false;
+  if (m) list[pos[t]] = (unsigned)(col + ncol * k);
+}
+
+// Faces whose provisional flux the near-EB path reads: the open low and
+// high faces of every listed CV and the neighbour faces their centroid
+// interpolation may use.  Several threads may mark the same face (all write 1).
+__device__ inline bool face_open_dense(const Dims &D, const GridDev &G, int g, int d, int i, int j, int k) {
+  if (k < 0 || k >= G.nzg) return false;
+  if (g == 3 && d != 2 && (k < 1 || k > D.nz - 1)) return false;
+  if (g != 3 && d == 2 && k == 0) return false;
+  const long long c = (long long)wrapi(i, D.nx) + (long long)D.nx * wrapi(j, D.ny) + D.nxy * k;
+  return (G.dflag[c] >> (2 + d)) & 1;
+}
+
+__global__ void k_face_marks(Dims D, int g, GridDev G, uint8_t *m0, uint8_t *m1, uint8_t *m2) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= G.nband) return;
+  const long long p = G.blist[t];
+  const int i = (int)(p % D.nx), j = (int)((p / D.nx) % D.ny), k = (int)(p / D.nxy);
+  uint8_t *mk[3] = {m0, m1, m2};
+  for (int d = 0; d < 3; ++d) {
+    for (int h = 0; h < 2; ++h) {
+      const int qi = i + (h && d == 0), qj = j + (h && d == 1), qk = k + (h && d == 2);
+      if (h && d == 2 && g != 3 && qk >= D.nz) continue;   // top wall
+      if (!face_open_dense(D, G, g, d, qi, qj, qk)) continue;
+      const long long q = (long long)wrapi(qi, D.nx) + (long long)D.nx * wrapi(qj, D.ny) + D.nxy * qk;
+      mk[d][q] = 1;
+      if (!((G.dflag[q] >> 1) & 1)) continue;
+      const int col = wrapi(qi, D.nx) + D.nx * wrapi(qj, D.ny);
+      const long long r = G.roff[col] + (qk - G.kcov[col]);
+      const double ga = G.fcent[(2 * d) * G.nrec + r], gb = G.fcent[(2 * d + 1) * G.nrec + r];
+      const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+      int ea[3] = {0, 0, 0}, eb[3] = {0, 0, 0};
+      ea[ta] = ga >= 0.0 ? 1 : -1;
+      eb[tb] = gb >= 0.0 ? 1 : -1;
+      for (int n = 1; n < 4; ++n) {
+        if ((n & 1) && ga == 0.0) continue;
+        if ((n & 2) && gb == 0.0) continue;
+        const int ni = qi + ((n & 1) ? ea[0] : 0) + ((n & 2) ? eb[0] : 0);
+        const int nj = qj + ((n & 1) ? ea[1] : 0) + ((n & 2) ? eb[1] : 0);
+        const int nk = qk + ((n & 1) ? ea[2] : 0) + ((n & 2) ? eb[2] : 0);
+        if (!face_open_dense(D, G, g, d, ni, nj, nk)) continue;
+        mk[d][(long long)wrapi(ni, D.nx) + (long long)D.nx * wrapi(nj, D.ny) + D.nxy * nk] = 1;
+      }
+    }
+  }
+}
+
+__global__ void k_marks_to_counts(const uint8_t *m, long long n, long long *cnt) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) cnt[t] = m[t];
+}
+
+__global__ void k_marks_fill(const uint8_t *m, long long n, const long long *pos, unsigned *list) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n && m[t]) list[pos[t]] = (unsigned)t;
+}
+
 // Dense export of one geometry field of one grid.
 __global__ void k_export_geometry(const double *h, Dims D, int g, GridDev G, int field, double *dst) {
   const long long nzg = nzg_of(D, g);
@@ -571,4 +669,32 @@ void launch_export_geometry(const double *h, const Dims &D, int g, const GridDev
   int blocks = nblk(total, 256);
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_export_geometry<<<blocks, 256, 0, s>>>(h, D, g, G, field, dst);
+}
+
+void launch_dense_flags(const Dims &D, int g, const GridDev &G, cudaStream_t s) {
+  k_dense_flags<<<nblk((long long)D.nx * D.ny, 128), 128, 0, s>>>(D, g, G);
+}
+
+void launch_band_marks(const Dims &D, int g, const int *kcov, const int *kfast, int kmax, long long *mark,
+                       cudaStream_t s) {
+  const long long n = D.nxy * kmax;
+  k_band_marks<<<nblk(n, 256), 256, 0, s>>>(D, g, kcov, kfast, kmax, mark);
+}
+
+void launch_band_fill(const Dims &D, int g, const int *kcov, const int *kfast, int kmax, const long long *pos,
+                      unsigned *list, cudaStream_t s) {
+  const long long n = D.nxy * kmax;
+  k_band_fill<<<nblk(n, 256), 256, 0, s>>>(D, g, kcov, kfast, kmax, pos, list);
+}
+
+void launch_face_marks(const Dims &D, int g, const GridDev &G, uint8_t *m0, uint8_t *m1, uint8_t *m2, cudaStream_t s) {
+  if (G.nband) k_face_marks<<<nblk(G.nband, 128), 128, 0, s>>>(D, g, G, m0, m1, m2);
+}
+
+void launch_marks_to_counts(const uint8_t *m, long long n, long long *cnt, cudaStream_t s) {
+  k_marks_to_counts<<<nblk(n, 256), 256, 0, s>>>(m, n, cnt);
+}
+
+void launch_marks_fill(const uint8_t *m, long long n, const long long *pos, unsigned *list, cudaStream_t s) {
+  k_marks_fill<<<nblk(n, 256), 256, 0, s>>>(m, n, pos, list);
 }

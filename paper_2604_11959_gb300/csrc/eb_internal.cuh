@@ -31,6 +31,19 @@ struct GridDev {
   uint8_t *flag;
   // float copies for the mixed path: alpha, beta[3], fcent[6]
   float *alpha_f, *beta_f, *fcent_f;
+  // dense per-CV byte (nzg x ncol): bit 0 = holds fluid (alpha > 0),
+  // bit 1 = has a band record, bits 2..4 = low x / y / z face open
+  uint8_t *dflag;
+  // provisional face fluxes of the near-EB path, dense (nzg x ncol) per
+  // direction: fluxes of the advected value, and the mass flux (c grid only)
+  void *fh[3], *fhm[3];
+  // faces whose provisional flux the near-EB path needs, per direction
+  unsigned *flist[3];
+  long long nface[3];
+  // CVs the near-EB kernel updates (non-covered, prognostic, below kfast),
+  // state indices in plane-major order
+  unsigned *blist;
+  long long nband;
   // redistribution per record
   uint8_t *code;
   int *nnb;
@@ -43,7 +56,13 @@ struct Dims {
   double dx, dy, dz;
 };
 
+// Periodic index for offsets of at most n from [0, n) (every stencil here
+// reaches a few cells and n >= 4 ... the set-up code uses full modulo).
 __host__ __device__ inline int wrapi(int a, int n) {
+  return a < 0 ? a + n : (a >= n ? a - n : a);
+}
+
+__host__ __device__ inline int wrapmod(int a, int n) {
   int r = a % n;
   return r < 0 ? r + n : r;
 }
@@ -75,6 +94,31 @@ __device__ inline CvInfo cv_info(const GridDev &G, const Dims &D, int i, int j, 
 #define EB_DEV_TIMEOUT 2u
 
 // ---------------------------------------------------------------------------
+// Arithmetic shared by every kernel that evaluates a face flux, so that a
+// face computed by two kernels (the bulk and the near-EB path) gets the same
+// bits from both and the update stays exactly conservative.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ inline T eb_div(T a, T b) {
+  return a / b;
+}
+template <>
+__device__ inline float eb_div<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+
+// Third-order upwind face value (fourth-order centred plus hyperviscosity,
+// Sec. 4.1): m > 0 uses (LL, L, R), m < 0 uses (L, R, RR); the centred
+// second-order value where that far CV does not exist.
+template <typename T>
+__device__ inline T upwind_value(T m, T pLL, T pL, T pR, T pRR, bool hasLL, bool hasRR) {
+  const T c2 = T(0.5) * (pL + pR);
+  const T vp = hasLL ? fma(T(5), pL, fma(T(2), pR, -pLL)) * T(1.0 / 6.0) : c2;
+  const T vn = hasRR ? fma(T(5), pR, fma(T(2), pL, -pRR)) * T(1.0 / 6.0) : c2;
+  return m > T(0) ? vp : vn;
+}
+
+// ---------------------------------------------------------------------------
 // State access
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -100,26 +144,49 @@ struct GeoFast {
 
 struct GeoBand {
   const GridDev *G;   // four grids
+  __device__ inline uint8_t dense(const Dims &D, int g, int i, int j, int k) const {
+    return G[g].dflag[(long long)wrapi(i, D.nx) + (long long)D.nx * wrapi(j, D.ny) + D.nxy * k];
+  }
+  __device__ inline long long record(const Dims &D, int g, int i, int j, int k) const {
+    const int col = wrapi(i, D.nx) + D.nx * wrapi(j, D.ny);
+    return G[g].roff[col] + (k - G[g].kcov[col]);
+  }
+  __device__ inline bool holds_fluid(const Dims &D, int g, int i, int j, int k) const {
+    if (k < 0 || k >= nzg_of(D, g)) return false;
+    return dense(D, g, i, j, k) & 1;
+  }
   __device__ inline double alpha(const Dims &D, int g, int i, int j, int k) const {
-    CvInfo c = cv_info(G[g], D, i, j, k);
-    if (c.flag == EBK_COVERED) return 0.0;
-    if (c.rec < 0) return 1.0;
-    return G[g].alpha[c.rec];
-  }
-  // area fraction of the low d-face of CV (i, j, k) of grid g (0 outside the grid)
-  __device__ inline double beta(const Dims &D, int g, int d, int i, int j, int k) const {
-    CvInfo c = cv_info(G[g], D, i, j, k);
     if (k < 0 || k >= nzg_of(D, g)) return 0.0;
-    if (c.flag == EBK_COVERED) return 0.0;
-    if (c.rec < 0) return 1.0;
-    return G[g].beta[(long long)d * G[g].nrec + c.rec];
+    const uint8_t f = dense(D, g, i, j, k);
+    if (!(f & 1)) return 0.0;
+    if (!(f & 2)) return 1.0;
+    return G[g].alpha[record(D, g, i, j, k)];
   }
-  __device__ inline void fcent(const Dims &D, int g, int d, int i, int j, int k, double &ga, double &gb) const {
-    CvInfo c = cv_info(G[g], D, i, j, k);
-    ga = gb = 0.0;
-    if (c.rec < 0) return;
-    ga = G[g].fcent[(long long)(2 * d) * G[g].nrec + c.rec];
-    gb = G[g].fcent[(long long)(2 * d + 1) * G[g].nrec + c.rec];
+  // area fraction of the low d-face of CV (i, j, k) of grid g (0 outside the
+  // grid), from the double records or their float copies
+  template <typename R>
+  __device__ inline R beta(const Dims &D, int g, int d, int i, int j, int k) const {
+    if (k < 0 || k >= nzg_of(D, g)) return R(0);
+    const uint8_t f = dense(D, g, i, j, k);
+    if (!(f & 2)) return (f & 1) ? R(1) : R(0);
+    const long long r = (long long)d * G[g].nrec + record(D, g, i, j, k);
+    if (sizeof(R) == sizeof(double)) return (R)G[g].beta[r];
+    return (R)G[g].beta_f[r];
+  }
+  template <typename R>
+  __device__ inline void fcent(const Dims &D, int g, int d, int i, int j, int k, R &ga, R &gb) const {
+    ga = gb = R(0);
+    if (k < 0 || k >= nzg_of(D, g)) return;
+    if (!(dense(D, g, i, j, k) & 2)) return;
+    const long long r = record(D, g, i, j, k);
+    const long long a = (long long)(2 * d) * G[g].nrec + r, b = (long long)(2 * d + 1) * G[g].nrec + r;
+    if (sizeof(R) == sizeof(double)) {
+      ga = (R)G[g].fcent[a];
+      gb = (R)G[g].fcent[b];
+    } else {
+      ga = (R)G[g].fcent_f[a];
+      gb = (R)G[g].fcent_f[b];
+    }
   }
 };
 
@@ -134,7 +201,7 @@ __device__ inline T rho_at(const StateIn<T> &U, const Dims &D, int i, int j, int
 template <typename T>
 __device__ inline T theta_at(const StateIn<T> &U, const Dims &D, int i, int j, int k) {
   long long c = lin(D, i, j, k);
-  return (U.ref_rt[k] + U.f[1][c]) / (U.ref_rho[k] + U.f[0][c]);
+  return eb_div(U.ref_rt[k] + U.f[1][c], U.ref_rho[k] + U.f[0][c]);
 }
 
 // Is CV (i,j,k) of grid g usable by a flux stencil (exists, not covered)?
@@ -148,8 +215,7 @@ __device__ inline bool avail<GeoFast>(const GeoFast &, const Dims &D, int g, int
 
 template <>
 __device__ inline bool avail<GeoBand>(const GeoBand &geo, const Dims &D, int g, int i, int j, int k) {
-  if (k < 0 || k >= nzg_of(D, g)) return false;
-  return geo.alpha(D, g, i, j, k) > 0.0;
+  return geo.holds_fluid(D, g, i, j, k);
 }
 
 // Momentum of a face-grid CV as it enters a mass flux: zero where covered,
@@ -176,7 +242,7 @@ __device__ inline T advected_at(const StateIn<T> &U, const Geo &geo, const Dims 
   else if (a) rb = rho_at(U, D, i - di, j - dj, k - dk);
   else if (b) rb = rho_at(U, D, i, j, k);
   else return T(0);
-  return U.f[g + 1][lin(D, i, j, k)] / rb;
+  return eb_div(U.f[g + 1][lin(D, i, j, k)], rb);
 }
 
 // Mass flux through the low d-face of CV (i,j,k) of grid g.
@@ -207,19 +273,13 @@ __device__ inline void face_flux(const StateIn<T> &U, const Geo &geo, const Dims
   const T pR = advected_at(U, geo, D, g, i, j, k);
   T val;
   if (fm > T(0)) {
-    if (avail(geo, D, g, i - 2 * di, j - 2 * dj, k - 2 * dk)) {
-      const T pF = advected_at(U, geo, D, g, i - 2 * di, j - 2 * dj, k - 2 * dk);
-      val = (T(5) * pL + T(2) * pR - pF) * T(1.0 / 6.0);
-    } else {
-      val = T(0.5) * (pL + pR);
-    }
+    const bool has = avail(geo, D, g, i - 2 * di, j - 2 * dj, k - 2 * dk);
+    const T pF = has ? advected_at(U, geo, D, g, i - 2 * di, j - 2 * dj, k - 2 * dk) : T(0);
+    val = upwind_value(fm, pF, pL, pR, T(0), has, false);
   } else {
-    if (avail(geo, D, g, i + di, j + dj, k + dk)) {
-      const T pF = advected_at(U, geo, D, g, i + di, j + dj, k + dk);
-      val = (T(2) * pL + T(5) * pR - pF) * T(1.0 / 6.0);
-    } else {
-      val = T(0.5) * (pL + pR);
-    }
+    const bool has = avail(geo, D, g, i + di, j + dj, k + dk);
+    const T pF = has ? advected_at(U, geo, D, g, i + di, j + dj, k + dk) : T(0);
+    val = upwind_value(fm, T(0), pL, pR, pF, false, has);
   }
   fp = fm * val;
 }

@@ -36,6 +36,14 @@ void launch_band_top(const Dims &D, int nzg, const int *kcov, const int *kreg, i
                      cudaStream_t s);
 void launch_fast_level(const Dims &D, const int *const kreg[4], int *kfast, cudaStream_t s);
 void launch_band_geometry(const double *h, const Dims &D, int g, const GridDev &G, cudaStream_t s);
+void launch_dense_flags(const Dims &D, int g, const GridDev &G, cudaStream_t s);
+void launch_band_marks(const Dims &D, int g, const int *kcov, const int *kfast, int kmax, long long *mark,
+                       cudaStream_t s);
+void launch_band_fill(const Dims &D, int g, const int *kcov, const int *kfast, int kmax, const long long *pos,
+                      unsigned *list, cudaStream_t s);
+void launch_face_marks(const Dims &D, int g, const GridDev &G, uint8_t *m0, uint8_t *m1, uint8_t *m2, cudaStream_t s);
+void launch_marks_to_counts(const uint8_t *m, long long n, long long *cnt, cudaStream_t s);
+void launch_marks_fill(const uint8_t *m, long long n, const long long *pos, unsigned *list, cudaStream_t s);
 void launch_export_geometry(const double *h, const Dims &D, int g, const GridDev &G, int field, double *dst,
                             cudaStream_t s);
 

@@ -1,9 +1,8 @@
 // eb_step.cu -- per-step kernels of the EB advance.
 //
 //   flux + update (Eqs. update-cc / update-fc, Sec. 4.1):
-//     k_fast  : every CV at or above its column's kfast level; no geometry
-//               (all CVs the stencil reads are regular), plus the pass-through
-//               of covered CVs and of the w wall levels;
+//     (the geometry-free bulk above each column's kfast level is in
+//     eb_fast.cu)
 //     k_band  : the non-covered CVs below kfast, with covered-neighbour
 //               fallbacks, open-face fractions and fluxes interpolated to the
 //               cut-face centroids.
@@ -39,173 +38,188 @@ __device__ inline bool face_usable(const GeoBand &geo, const Dims &D, int g, int
   if (k < 0 || k >= nzg_of(D, g)) return false;
   if (g == 3 && d != 2 && (k < 1 || k > D.nz - 1)) return false;
   if (g != 3 && d == 2 && k == 0) return false;   // bottom wall faces carry no flux
-  return geo.beta(D, g, d, i, j, k) > 0.0;
+  return geo.beta<float>(D, g, d, i, j, k) > 0.0f;
 }
 
 // Flux through the centroid of the low d-face of CV (i,j,k): bilinear
 // interpolation of the provisional fluxes of the face and of the neighbour
-// faces toward which the centroid is offset (Sec. 4.1).  An offset is dropped
-// when a face it needs is closed or outside the domain.
+// faces toward which the centroid is offset (Sec. 4.1), read from the face
+// arrays staged by k_face_flux.  An offset is dropped when a face it needs is
+// closed or outside the domain.
+__device__ inline bool face_usable_dense(const GeoBand &geo, const Dims &D, int g, int d, int i, int j, int k) {
+  if (k < 0 || k >= nzg_of(D, g)) return false;
+  if (g == 3 && d != 2 && (k < 1 || k > D.nz - 1)) return false;
+  if (g != 3 && d == 2 && k == 0) return false;   // bottom wall faces carry no flux
+  return (geo.dense(D, g, i, j, k) >> (2 + d)) & 1;
+}
+
 template <typename T>
-__device__ void centroid_flux(const StateIn<T> &U, const GeoBand &geo, const Dims &D, int g, int d, int i, int j,
-                              int k, T &fm, T &fp) {
-  double ga, gb;
-  geo.fcent(D, g, d, i, j, k, ga, gb);
-  face_flux(U, geo, D, g, d, i, j, k, fm, fp);
-  if (ga == 0.0 && gb == 0.0) return;
+__device__ void centroid_flux(const StepArgs<T> &A, const GeoBand &geo, int g, int d, int i, int j, int k, T &fm,
+                              T &fp) {
+  const Dims &D = A.D;
+  const T *FH = (const T *)A.G[g].fh[d];
+  const T *FM = (const T *)A.G[g].fhm[d];
+  const long long c = lin(D, i, j, k);
+  fp = FH[c];
+  fm = FM ? FM[c] : T(0);
+  T ga, gb;
+  geo.fcent<T>(D, g, d, i, j, k, ga, gb);
+  if (ga == T(0) && gb == T(0)) return;
   const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
   int ea[3] = {0, 0, 0}, eb[3] = {0, 0, 0};
-  ea[ta] = ga >= 0.0 ? 1 : -1;
-  eb[tb] = gb >= 0.0 ? 1 : -1;
-  const bool ua = ga != 0.0 && face_usable(geo, D, g, d, i + ea[0], j + ea[1], k + ea[2]);
-  const bool ub = gb != 0.0 && face_usable(geo, D, g, d, i + eb[0], j + eb[1], k + eb[2]);
-  const bool uab = ga != 0.0 && gb != 0.0 &&
-                   face_usable(geo, D, g, d, i + ea[0] + eb[0], j + ea[1] + eb[1], k + ea[2] + eb[2]);
-  const bool za = ga != 0.0 && (!ua || (gb != 0.0 && !uab));
-  const bool zb = gb != 0.0 && (!ub || (ga != 0.0 && !uab));
-  const T wa = za ? T(0) : T(fabs(ga));
-  const T wb = zb ? T(0) : T(fabs(gb));
+  ea[ta] = ga >= T(0) ? 1 : -1;
+  eb[tb] = gb >= T(0) ? 1 : -1;
+  const bool ua = ga != T(0) && face_usable_dense(geo, D, g, d, i + ea[0], j + ea[1], k + ea[2]);
+  const bool ub = gb != T(0) && face_usable_dense(geo, D, g, d, i + eb[0], j + eb[1], k + eb[2]);
+  const bool uab = ga != T(0) && gb != T(0) &&
+                   face_usable_dense(geo, D, g, d, i + ea[0] + eb[0], j + ea[1] + eb[1], k + ea[2] + eb[2]);
+  const bool za = ga != T(0) && (!ua || (gb != T(0) && !uab));
+  const bool zb = gb != T(0) && (!ub || (ga != T(0) && !uab));
+  const T wa = za ? T(0) : (ga < T(0) ? -ga : ga);
+  const T wb = zb ? T(0) : (gb < T(0) ? -gb : gb);
   if (wa == T(0) && wb == T(0)) return;
-  T m0 = fm, p0 = fp;
-  fm = (T(1) - wa) * (T(1) - wb) * m0;
-  fp = (T(1) - wa) * (T(1) - wb) * p0;
-  T m1, p1;
+  const T w0 = (T(1) - wa) * (T(1) - wb);
+  fm *= w0;
+  fp *= w0;
   if (wa != T(0)) {
-    face_flux(U, geo, D, g, d, i + ea[0], j + ea[1], k + ea[2], m1, p1);
-    fm += wa * (T(1) - wb) * m1;
-    fp += wa * (T(1) - wb) * p1;
+    const long long n = lin(D, i + ea[0], j + ea[1], k + ea[2]);
+    const T w = wa * (T(1) - wb);
+    fp += w * FH[n];
+    if (FM) fm += w * FM[n];
   }
   if (wb != T(0)) {
-    face_flux(U, geo, D, g, d, i + eb[0], j + eb[1], k + eb[2], m1, p1);
-    fm += wb * (T(1) - wa) * m1;
-    fp += wb * (T(1) - wa) * p1;
+    const long long n = lin(D, i + eb[0], j + eb[1], k + eb[2]);
+    const T w = wb * (T(1) - wa);
+    fp += w * FH[n];
+    if (FM) fm += w * FM[n];
   }
   if (wa != T(0) && wb != T(0)) {
-    face_flux(U, geo, D, g, d, i + ea[0] + eb[0], j + ea[1] + eb[1], k + ea[2] + eb[2], m1, p1);
-    fm += wa * wb * m1;
-    fp += wa * wb * p1;
+    const long long n = lin(D, i + ea[0] + eb[0], j + ea[1] + eb[1], k + ea[2] + eb[2]);
+    const T w = wa * wb;
+    fp += w * FH[n];
+    if (FM) fm += w * FM[n];
   }
 }
 
 template <typename T>
-__device__ inline void write_out(const StepArgs<T> &A, int f, long long c, double delta) {
-  T v;
-  if (A.base[0]) v = A.base[f][c] + (T)(A.dt * delta);
-  else v = (T)delta;
-  A.out[f][c] = v;
-  if (!finite_val(v)) atomicOr(A.status, EB_DEV_NUMERIC);
-}
-
-template <typename T>
-__device__ inline void write_outT(const StepArgs<T> &A, int f, long long c, T delta) {
+__device__ inline void write_out(const StepArgs<T> &A, int f, long long c, T delta) {
   T v;
   if (A.base[0]) v = A.base[f][c] + A.dtT * delta;
   else v = delta;
   A.out[f][c] = v;
-  if (!finite_val(v)) atomicOr(A.status, EB_DEV_NUMERIC);
+  if (!isfinite(v)) atomicOr(A.status, EB_DEV_NUMERIC);
 }
 
 template <typename T>
-__device__ inline void write_static(const StepArgs<T> &A, int f, long long c) {
-  A.out[f][c] = A.base[0] ? A.base[f][c] : T(0);
+__device__ inline void write_out_d(const StepArgs<T> &A, int f, long long c, double delta) {
+  T v;
+  if (A.base[0]) v = A.base[f][c] + (T)(A.dt * delta);
+  else v = (T)delta;
+  A.out[f][c] = v;
+  if (!isfinite(v)) atomicOr(A.status, EB_DEV_NUMERIC);
 }
 
-// dU of the CV (i,j,k) of grid g with all-regular surroundings.
-template <typename T>
-__device__ void fast_cv(const StepArgs<T> &A, int g, int i, int j, int k) {
+// dU of a non-covered CV near the EB (general geometry): Eqs. update-cc /
+// update-fc.  The face sums run in the state's precision, except for tiny cut
+// CVs (alpha < 1e-3) of the float path, whose sums, area fractions and
+// volume fraction are taken in double.
+template <typename T, typename R>
+__device__ void band_divergence(const StepArgs<T> &A, const GeoBand &geo, int g, int i, int j, int k, R &sm,
+                                R &sp) {
   const Dims &D = A.D;
-  const GeoFast geo;
-  const T inv[3] = {T(1.0 / D.dx), T(1.0 / D.dy), T(1.0 / D.dz)};
-  T sm = T(0), sp = T(0);
+  const R inv[3] = {R(1.0 / D.dx), R(1.0 / D.dy), R(1.0 / D.dz)};
+  sm = R(0);
+  sp = R(0);
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int di = d == 0, dj = d == 1, dk = d == 2;
-    T ml, pl, mh = T(0), ph = T(0);
-    face_flux(A.src, geo, D, g, d, i, j, k, ml, pl);
-    if (high_face_exists(D, g, d, k)) face_flux(A.src, geo, D, g, d, i + di, j + dj, k + dk, mh, ph);
-    sm += (mh - ml) * inv[d];
-    sp += (ph - pl) * inv[d];
-  }
-  const long long c = lin(D, i, j, k);
-  if (g == 0) {
-    write_outT(A, 0, c, -sm);
-    write_outT(A, 1, c, -sp);
-  } else {
-    write_outT(A, g + 1, c, -sp);
+    const bool lo_wall = (g != 3 && d == 2 && k == 0);
+    const R bl = lo_wall ? R(0) : geo.beta<R>(D, g, d, i, j, k);
+    R bh = R(0);
+    if (high_face_exists(D, g, d, k)) bh = geo.beta<R>(D, g, d, i + di, j + dj, k + dk);
+    T ml = T(0), pl = T(0), mh = T(0), ph = T(0);
+    if (bl > R(0)) centroid_flux(A, geo, g, d, i, j, k, ml, pl);
+    if (bh > R(0)) centroid_flux(A, geo, g, d, i + di, j + dj, k + dk, mh, ph);
+    sm += (bh * (R)mh - bl * (R)ml) * inv[d];
+    sp += (bh * (R)ph - bl * (R)pl) * inv[d];
   }
 }
 
-// dU of a non-covered CV near the EB (general geometry).
 template <typename T>
 __device__ void band_cv(const StepArgs<T> &A, int g, int i, int j, int k) {
   const Dims &D = A.D;
   GeoBand geo;
   geo.G = A.G;
-  const double alpha = geo.alpha(D, g, i, j, k);
-  const double dd[3] = {D.dx, D.dy, D.dz};
-  // double accumulation for every band CV: it costs little here and keeps
-  // the tiny cut CVs (alpha < 1e-3) accurate in the float path
-  double sm = 0.0, sp = 0.0;
-  for (int d = 0; d < 3; ++d) {
-    const int di = d == 0, dj = d == 1, dk = d == 2;
-    const bool lo_wall = (g != 3 && d == 2 && k == 0);
-    const double bl = lo_wall ? 0.0 : geo.beta(D, g, d, i, j, k);
-    double bh = 0.0;
-    if (high_face_exists(D, g, d, k)) bh = geo.beta(D, g, d, i + di, j + dj, k + dk);
-    T ml = T(0), pl = T(0), mh = T(0), ph = T(0);
-    if (bl > 0.0) centroid_flux(A.src, geo, D, g, d, i, j, k, ml, pl);
-    if (bh > 0.0) centroid_flux(A.src, geo, D, g, d, i + di, j + dj, k + dk, mh, ph);
-    sm += (bh * (double)mh - bl * (double)ml) / dd[d];
-    sp += (bh * (double)ph - bl * (double)pl) / dd[d];
-  }
   const long long c = lin(D, i, j, k);
-  if (g == 0) {
-    write_out(A, 0, c, -sm / alpha);
-    write_out(A, 1, c, -sp / alpha);
-  } else {
-    write_out(A, g + 1, c, -sp / alpha);
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_fast(StepArgs<T> A) {
-  const Dims &D = A.D;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= D.nx || j >= D.ny) return;
-  const int col = i + D.nx * j;
-  const int kf = A.kfast[col];
-  if (k >= kf) {
-    fast_cv(A, 0, i, j, k);
-    fast_cv(A, 1, i, j, k);
-    fast_cv(A, 2, i, j, k);
-    fast_cv(A, 3, i, j, k);
-  } else if (A.copy_static) {
-    const long long c = lin(D, i, j, k);
-    if (k < A.G[0].kcov[col]) {
-      write_static(A, 0, c);
-      write_static(A, 1, c);
+  const uint8_t f = geo.dense(D, g, i, j, k);
+  const bool rec = f & 2;
+  const long long r = rec ? geo.record(D, g, i, j, k) : -1;
+  const bool tiny = rec && A.G[g].alpha[r] < 1e-3;
+  if (sizeof(T) == sizeof(double) || tiny) {
+    const double alpha = rec ? A.G[g].alpha[r] : 1.0;
+    double sm, sp;
+    band_divergence<T, double>(A, geo, g, i, j, k, sm, sp);
+    const double ia = 1.0 / alpha;
+    if (g == 0) {
+      write_out_d(A, 0, c, -sm * ia);
+      write_out_d(A, 1, c, -sp * ia);
+    } else {
+      write_out_d(A, g + 1, c, -sp * ia);
     }
-    if (k < A.G[1].kcov[col]) write_static(A, 2, c);
-    if (k < A.G[2].kcov[col]) write_static(A, 3, c);
-    if (k < A.G[3].kcov[col] || k == 0) write_static(A, 4, c);
+  } else {
+    const T ia = rec ? T(1) / (T)A.G[g].alpha_f[r] : T(1);
+    T sm, sp;
+    band_divergence<T, T>(A, geo, g, i, j, k, sm, sp);
+    if (g == 0) {
+      write_out(A, 0, c, -sm * ia);
+      write_out(A, 1, c, -sp * ia);
+    } else {
+      write_out(A, g + 1, c, -sp * ia);
+    }
   }
-  if (A.copy_static && k == D.nz - 1) write_static(A, 4, lin(D, i, j, D.nz));
 }
 
+// Phase A of the near-EB path: the provisional flux of every listed face,
+// once (general geometry: covered-neighbour fallbacks, zero momentum of
+// covered CVs).
+template <typename T>
+__global__ void k_face_flux(StepArgs<T> A) {
+  const Dims &D = A.D;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int g = 0, d = 0;
+  for (g = 0; g < 4; ++g) {
+    for (d = 0; d < 3; ++d) {
+      if (t < A.G[g].nface[d]) break;
+      t -= A.G[g].nface[d];
+    }
+    if (d < 3) break;
+  }
+  if (g >= 4) return;
+  const long long c = A.G[g].flist[d][t];
+  const int i = (int)(c % D.nx), j = (int)((c / D.nx) % D.ny), k = (int)(c / D.nxy);
+  GeoBand geo;
+  geo.G = A.G;
+  T fm, fp;
+  face_flux(A.src, geo, D, g, d, i, j, k, fm, fp);
+  ((T *)A.G[g].fh[d])[c] = fp;
+  if (A.G[g].fhm[d]) ((T *)A.G[g].fhm[d])[c] = fm;
+}
+
+// Phase B: interpolation to the cut-face centroids and the divergence of
+// every listed CV of every grid.
 template <typename T>
 __global__ void k_band(StepArgs<T> A) {
   const Dims &D = A.D;
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  const int g = blockIdx.y;
-  if (col >= D.nx * D.ny) return;
-  const int i = col % D.nx, j = col / D.nx;
-  const int kf = A.kfast[col];
-  const int k0 = A.G[g].kcov[col];
-  for (int k = k0; k < kf; ++k) {
-    if (g == 3 && (k == 0 || k == D.nz)) continue;
-    band_cv(A, g, i, j, k);
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int g = 0;
+  for (g = 0; g < 4; ++g) {
+    if (t < A.G[g].nband) break;
+    t -= A.G[g].nband;
   }
+  if (g >= 4) return;
+  const long long c = A.G[g].blist[t];
+  const int i = (int)(c % D.nx), j = (int)((c / D.nx) % D.ny), k = (int)(c / D.nxy);
+  band_cv(A, g, i, j, k);
 }
 
 // ---------------------------------------------------------------------------
@@ -387,18 +401,14 @@ __global__ void k_final(WsrdArgs<T> R) {
 // host wrappers
 // ---------------------------------------------------------------------------
 template <typename T>
-void launch_flux_fast(const StepArgs<T> &A, cudaStream_t s) {
-  const Dims &D = A.D;
-  dim3 blk(32, 8, 1);
-  dim3 grd((D.nx + 31) / 32, (D.ny + 7) / 8, D.nz);
-  k_fast<T><<<grd, blk, 0, s>>>(A);
-}
-
-template <typename T>
 void launch_flux_band(const StepArgs<T> &A, cudaStream_t s) {
-  const Dims &D = A.D;
-  dim3 bb(128, 1, 1), bg((D.nx * D.ny + 127) / 128, 4, 1);
-  k_band<T><<<bg, bb, 0, s>>>(A);
+  long long nf = 0, nb = 0;
+  for (int g = 0; g < 4; ++g) {
+    nb += A.G[g].nband;
+    for (int d = 0; d < 3; ++d) nf += A.G[g].nface[d];
+  }
+  if (nf) k_face_flux<T><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(A);
+  if (nb) k_band<T><<<(unsigned)((nb + 127) / 128), 128, 0, s>>>(A);
 }
 
 template <typename T>
@@ -417,8 +427,6 @@ void launch_wsrd(const WsrdArgs<T> &R, cudaStream_t s) {
 }
 
 template void launch_flux_update<double>(const StepArgs<double> &, cudaStream_t);
-template void launch_flux_fast<double>(const StepArgs<double> &, cudaStream_t);
-template void launch_flux_fast<float>(const StepArgs<float> &, cudaStream_t);
 template void launch_flux_band<double>(const StepArgs<double> &, cudaStream_t);
 template void launch_flux_band<float>(const StepArgs<float> &, cudaStream_t);
 template void launch_flux_update<float>(const StepArgs<float> &, cudaStream_t);

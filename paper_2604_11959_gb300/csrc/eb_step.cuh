@@ -15,6 +15,7 @@ struct StepArgs {
   GridDev G[4];
   unsigned *status;
   int copy_static;     // also write covered CVs and the w wall levels
+  int kchunk;          // levels per z slab of the tiled bulk kernel (set at launch)
 };
 
 template <typename T>
