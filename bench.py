@@ -156,7 +156,7 @@ def traffic_record(kernel, workload_name, precision):
     """DRAM bytes per launch of a kernel from a committed ncu summary, valid
     only while the kernel source is unchanged (hash recorded with it)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}_{precision}.txt")
-    src = os.path.join(ROOT, "paper_2604_11959_gb300", "csrc", "eb_step.cu")
+    src = os.path.join(ROOT, "paper_2604_11959_gb300", "csrc", "eb_fast.cu")
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         rec = {}
@@ -236,7 +236,7 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist):
         "phases_ms": {"fast": float(prof[0]), "band": float(prof[1]), "wsrd": float(prof[2]),
                       "step": float(prof[3])},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": traffic_record("k_fast", w.name, precision), "kernel": "k_fast",
+                     "traffic": traffic_record("k_fast_tiled", w.name, precision), "kernel": "k_fast_tiled",
                      "algorithmic_bytes_per_launch": fast_bytes, "peak_kind": kind},
         "step_gbs": step_bytes / (ms_step * 1e-3) / 1e9,
         "step_frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm,
