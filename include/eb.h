@@ -173,6 +173,47 @@ eb_status eb_flux_div(eb_geom geom, const eb_state *U, eb_state *dU, void *strea
 eb_status eb_wsrd(eb_geom geom, eb_field field, const void *Uhat, void *Unew, void *stream);
 
 /*
+ * Maximum scratch, in bytes, that eb_wsrd_noalloc may use per call.
+ */
+#define EB_WSRD_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/*
+ * eb_wsrd without device memory of its own: the same redistribution, same
+ * arguments and the same results as eb_wsrd.  The paper has no counterpart;
+ * this is a deployment variant.
+ *
+ * Who needs it: callers that may not allocate device memory at the moment
+ * they redistribute -- a host loop that runs under a fixed memory budget
+ * shared with other libraries, a caller that has handed all free memory to a
+ * pool allocator, or one that must not synchronise the device (cudaMalloc and
+ * cudaFree may).  eb_wsrd itself allocates nothing per call either, but its
+ * per-small-CV scratch lives in the handle; this variant keeps that scratch in
+ * one fixed block of EB_WSRD_NOALLOC_SCRATCH_BYTES bytes compiled into the
+ * library (a static __device__ array), so the handle's scratch is not touched.
+ *
+ * Scratch needed for a field: 5 values of the handle's precision per small CV
+ * of the field's grid (eb_geom_info_t.small_cvs), each of three parts rounded
+ * up to 256 bytes.  A larger need is rejected with EB_ERR_INVALID_ARG and a
+ * message giving both sizes; nothing is launched then.  Nothing in the
+ * scratch needs to start at zero: every entry is written before it is read
+ * within one call.
+ *
+ * Set-up: the first call on each device looks up the block's device address
+ * (cudaGetSymbolAddress, which may load the library's device code) with the
+ * handle's device current.  That first call therefore belongs before any
+ * stream capture and outside any section that must not touch the driver;
+ * later calls only launch kernels (and one device-to-device copy when Uhat
+ * and Unew differ).  The current device must be the handle's device
+ * (EB_ERR_INVALID_ARG otherwise).
+ *
+ * Races: there is ONE scratch block per device, shared by every handle and
+ * every thread.  Two calls whose work may overlap on the device (different
+ * streams without an ordering event, or calls from several host threads)
+ * corrupt each other's results.  Serialise them on one stream.
+ */
+eb_status eb_wsrd_noalloc(eb_geom geom, eb_field field, const void *Uhat, void *Unew, void *stream);
+
+/*
  * nsteps steps of Algorithm 1 with zero source.  stages = 1: forward Euler,
  * U^{n+1} = R[U^n + dt dU(U^n)] (Eq. basic_fv_srd); stages = 3: the
  * three-stage Runge-Kutta of Sec. 5.2 with redistribution after every stage,

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -362,6 +363,54 @@ size_t field_count(const Dims &D, int f) { return (size_t)D.nxy * (D.nz + (f == 
 
 }  // namespace
 
+// Scratch of eb_wsrd_noalloc.  It is part of the library's device image, so
+// using it allocates nothing; there is one block per device, shared by every
+// handle, which is why overlapping calls race.
+static __device__ __align__(256) unsigned char g_wsrd_noalloc_scratch[EB_WSRD_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of the fixed scratch on `device`, which must be current.
+// Looked up once per device; later calls read the cached pointer.
+eb_status noalloc_scratch(int device, void **out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (device < 0 || device >= kNoallocMaxDevices) return fail(EB_ERR_INVALID_ARG, "device index out of range");
+  if (!g_noalloc_addr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_wsrd_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "address of the fixed redistribution scratch");
+    g_noalloc_addr[device] = p;
+  }
+  *out = g_noalloc_addr[device];
+  return EB_OK;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Same launches as wsrd_field, with the three per-small-CV arrays carved out
+// of `scratch`: deviation sums, pivot values, then 3 slopes per small CV.
+template <typename T>
+void wsrd_field_scratch(eb_geom g, int field, T *u, char *scratch, cudaStream_t s) {
+  const int grid = field <= 1 ? 0 : field - 1;
+  const size_t one = round256((size_t)g->W[grid].nsmall * sizeof(T));
+  WsrdArgs<T> R;
+  R.D = g->D;
+  R.W = g->W[grid];
+  R.u = u;
+  R.refd = field <= 1 ? g->ref_d[field] : nullptr;
+  R.dev = (T *)scratch;
+  R.pval = (T *)(scratch + one);
+  R.sig = (T *)(scratch + 2 * one);
+  R.status = g->status;
+  launch_wsrd(R, s);
+}
+
+}  // namespace
+
 extern "C" {
 
 eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision prec, const double *ref_rho,
@@ -451,6 +500,40 @@ eb_status eb_wsrd(eb_geom geom, eb_field field, const void *Uhat, void *Unew, vo
   }
   if (geom->prec == EB_F64) wsrd_field<double>(geom, (int)field, (double *)Unew, s);
   else wsrd_field<float>(geom, (int)field, (float *)Unew, s);
+  CUDA_TRY(cudaGetLastError(), "redistribution");
+  return EB_OK;
+}
+
+eb_status eb_wsrd_noalloc(eb_geom geom, eb_field field, const void *Uhat, void *Unew, void *stream) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  if ((int)field < 0 || (int)field > 4) return fail(EB_ERR_INVALID_ARG, "unknown field");
+  const size_t es = geom->prec == EB_F64 ? 8 : 4;
+  if (!Uhat || !Unew || ((uintptr_t)Uhat % es) || ((uintptr_t)Unew % es))
+    return fail(EB_ERR_INVALID_ARG, "field pointer NULL or misaligned");
+  const size_t bytes = field_count(geom->D, (int)field) * es;
+  if (Uhat != Unew) {
+    const char *a = (const char *)Uhat, *b = (const char *)Unew;
+    if (a < b + bytes && b < a + bytes) return fail(EB_ERR_INVALID_ARG, "Uhat and Unew overlap");
+  }
+  int cur = -1;
+  CUDA_TRY(cudaGetDevice(&cur), "current device");
+  if (cur != geom->device) return fail(EB_ERR_INVALID_ARG, "the current device is not the handle's device");
+  const int grid = (int)field <= 1 ? 0 : (int)field - 1;
+  const size_t one = round256((size_t)geom->W[grid].nsmall * es);
+  const size_t need = 2 * one + round256(3 * (size_t)geom->W[grid].nsmall * es);
+  if (need > (size_t)EB_WSRD_NOALLOC_SCRATCH_BYTES) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "field needs %zu bytes of scratch (%lld small CVs), the fixed block holds %zu",
+             need, (long long)geom->W[grid].nsmall, (size_t)EB_WSRD_NOALLOC_SCRATCH_BYTES);
+    return fail(EB_ERR_INVALID_ARG, "%s", buf);
+  }
+  void *scratch = nullptr;
+  eb_status st = noalloc_scratch(cur, &scratch);
+  if (st != EB_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  if (Uhat != Unew) CUDA_TRY(cudaMemcpyAsync(Unew, Uhat, bytes, cudaMemcpyDeviceToDevice, s), "copy field");
+  if (geom->prec == EB_F64) wsrd_field_scratch<double>(geom, (int)field, (double *)Unew, (char *)scratch, s);
+  else wsrd_field_scratch<float>(geom, (int)field, (float *)Unew, (char *)scratch, s);
   CUDA_TRY(cudaGetLastError(), "redistribution");
   return EB_OK;
 }

@@ -25,7 +25,7 @@ EXPORT_FIELDS = ("alpha", "cent_x", "cent_y", "cent_z", "beta_x", "beta_y", "bet
 STATUS = {0: "EB_OK", 1: "EB_ERR_INVALID_ARG", 2: "EB_ERR_CUDA", 3: "EB_ERR_OOM", 4: "EB_ERR_NUMERIC",
           5: "EB_ERR_TIMEOUT", 6: "EB_ERR_STATE"}
 EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
-                    "eb_step", "eb_step_profile", "eb_sync_status", "eb_last_error", "eb_version")
+                    "eb_wsrd_noalloc", "eb_step", "eb_step_profile", "eb_sync_status", "eb_last_error", "eb_version")
 
 
 class EbError(RuntimeError):
@@ -78,13 +78,14 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_geom_export.argtypes = [V, I, I, V, V]
     lib.eb_flux_div.argtypes = [V, P(_State), P(_State), V]
     lib.eb_wsrd.argtypes = [V, I, V, V, V]
+    lib.eb_wsrd_noalloc.argtypes = [V, I, V, V, V]
     lib.eb_step.argtypes = [V, P(_State), P(_State), D, I, I, V]
     lib.eb_step_profile.argtypes = [V, P(_State), P(_State), D, V, P(ctypes.c_float)]
     lib.eb_sync_status.argtypes = [V, V]
     lib.eb_last_error.restype = ctypes.c_char_p
     lib.eb_version.restype = I
     for name in ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
-                 "eb_step", "eb_step_profile", "eb_sync_status"):
+                 "eb_wsrd_noalloc", "eb_step", "eb_step_profile", "eb_sync_status"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -194,6 +195,17 @@ def wsrd(geom: Geometry, field: str, Uhat: torch.Tensor, out: torch.Tensor | Non
     out = out if out is not None else torch.empty_like(Uhat)
     _require_cuda(out, geom.dtype, geom.shape(field), "out")
     _check(load().eb_wsrd(geom.handle, FIELDS.index(field), Uhat.data_ptr(), out.data_ptr(), _stream(stream)))
+    return out
+
+
+def wsrd_noalloc(geom: Geometry, field: str, Uhat: torch.Tensor, out: torch.Tensor, stream=None):
+    """Redistribution of one field through ``eb_wsrd_noalloc``: scratch from
+    the library's fixed device block, nothing allocated.  ``out`` is required
+    (it may be ``Uhat``) so that this call allocates nothing either."""
+    _require_cuda(Uhat, geom.dtype, geom.shape(field), field)
+    _require_cuda(out, geom.dtype, geom.shape(field), "out")
+    _check(load().eb_wsrd_noalloc(geom.handle, FIELDS.index(field), Uhat.data_ptr(), out.data_ptr(),
+                                  _stream(stream)))
     return out
 
 
