@@ -692,7 +692,8 @@ int orc_flux_div(const OrcDomain *D, const OrcGeom *G, const OrcState *U, OrcSta
  * format, which is why it is spelled out): axes a1, a2, a3 ordered by
  * decreasing |n_d| of the unit EB normal (two components count as equal when
  * they differ by at most 1e-12; ties go x before y before z), signs
- * s_d = sign(n_d) with sign(0) = +1, and the growth level L (1: two cells,
+ * s_d = sign(n_d) with sign(0) = +1, where a component within 1e-12 of zero
+ * counts as zero, and the growth level L (1: two cells,
  * 2: 2 x 2, 3: 2 x 2 x 2).  perm index p over the orderings
  * (xyz, xzy, yxz, yzx, zxy, zyx), sign bits sx | sy<<1 | sz<<2 (bit set =
  * negative);  code = 1 + (p*8 + signbits)*3 + (L-1), and 0 for CVs that are
@@ -815,7 +816,7 @@ int orc_wsrd_setup(const OrcDomain *D, int g, const OrcGeom *Gg, double vt, OrcW
         double nv[3] = {Gg->nrm[id], Gg->nrm[n + id], Gg->nrm[2 * n + id]};
         int ax[3], s[3], sb = 0;
         axis_order(nv, ax);
-        for (int d = 0; d < 3; d++) { s[d] = nv[d] < 0.0 ? -1 : 1; if (s[d] < 0) sb |= 1 << d; }
+        for (int d = 0; d < 3; d++) { s[d] = nv[d] < -1e-12 ? -1 : 1; if (s[d] < 0) sb |= 1 << d; }
         int L;
         double sum = 0.0;
         for (L = 1; L <= 3; L++) {

@@ -130,7 +130,7 @@ __global__ void k_codes(Dims D, int g, GridDev G, double vt) {
     int ax[3], s[3], sb = 0;
     order_axes(nv, ax);
     for (int d = 0; d < 3; ++d) {
-      s[d] = nv[d] < 0.0 ? -1 : 1;
+      s[d] = nv[d] < -1e-12 ? -1 : 1;   // components within 1e-12 of zero count as zero: +1
       if (s[d] < 0) sb |= 1 << d;
     }
     int L = 1;

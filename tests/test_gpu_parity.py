@@ -35,6 +35,9 @@ CASES = {
     "woa": (inputs.WOA_32, None),
     "grf": (rough_workload(), None),
     "hill": (inputs.Workload("hill-64x64x32", 64, 64, 32, 10, terrain="gaussian", hmax=0.15), None),
+    # odd nx and ny: rows not 16-byte aligned (element-wise copies in the bulk
+    # kernel) and ragged tiles in both directions
+    "odd": (inputs.Workload("grf-45x38x20", 45, 38, 20, 5, terrain="grf", seed=9, hmax=0.2, tiny=2), None),
 }
 
 
