@@ -50,6 +50,9 @@ struct eb_geom_s {
   int *kcov[4] = {}, *kreg[4] = {}, *kxt[4] = {};
   long long *roff[4] = {};
   int *kfast = nullptr;
+  int4 *bseg = nullptr;   // bulk kernel work split
+  int *boff = nullptr;
+  int bctas = 0;
   GridDev G[4];
   WsrdDev W[4];
   double *ref_d[2] = {nullptr, nullptr};
@@ -269,6 +272,16 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
   // host-side counts for eb_geom_info
   std::vector<int> kc(ncol), kf(ncol);
   CUDA_TRY(cudaMemcpy(kf.data(), g->kfast, sizeof(int) * ncol, cudaMemcpyDeviceToHost), "read kfast");
+  {
+    std::vector<int> seg, off;
+    CUDA_TRY(bulk_plan(D, kf.data(), g->prec == EB_F64, seg, off), "bulk work split");
+    g->bctas = (int)off.size() - 1;
+    CUDA_TRY(g->alloc(&g->bseg, std::max<long long>(1, (long long)seg.size() / 4)), "alloc bulk split");
+    CUDA_TRY(g->alloc(&g->boff, (long long)off.size()), "alloc bulk split");
+    if (!seg.empty())
+      CUDA_TRY(cudaMemcpy(g->bseg, seg.data(), sizeof(int) * seg.size(), cudaMemcpyHostToDevice), "copy bulk split");
+    CUDA_TRY(cudaMemcpy(g->boff, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice), "copy bulk split");
+  }
   g->info.cells = (int64_t)ncol * D.nz;
   g->info.fast_cells = 0;
   for (long long c = 0; c < ncol; ++c) g->info.fast_cells += D.nz - std::min(kf[c], D.nz);
@@ -331,6 +344,9 @@ StepArgs<T> step_args(eb_geom g, void *const src[5], void *const base[5], void *
   A.dt = dt;
   A.dtT = (T)dt;
   A.kfast = g->kfast;
+  A.bseg = g->bseg;
+  A.boff = g->boff;
+  A.bctas = g->bctas;
   for (int q = 0; q < 4; ++q) A.G[q] = g->G[q];
   A.status = g->status;
   A.copy_static = copy;
@@ -435,6 +451,9 @@ eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision
   g->D.dx = desc->Lx / desc->nx;
   g->D.dy = desc->Ly / desc->ny;
   g->D.dz = desc->Lz / desc->nz;
+  g->D.idx = 1.0 / g->D.dx;
+  g->D.idy = 1.0 / g->D.dy;
+  g->D.idz = 1.0 / g->D.dz;
   eb_status st = build_impl(g, h_nodes, ref_rho, ref_rhotheta, as_stream(stream));
   if (st != EB_OK) {
     cudaStreamSynchronize(as_stream(stream));

@@ -3,288 +3,438 @@
 // above its column's kfast level, where every CV any flux stencil reads is a
 // regular CV.
 //
-// Tiling.  A CTA owns a TX x TY tile of columns and marches up in z from the
-// lowest kfast of its tile.  Shared memory holds a ring of four raw planes
-// (k-1 .. k+2) of the five fields over the tile plus a halo (3 cells on the
-// low sides, 2 on the high sides: the face velocity at the halo edge needs
-// the density one cell further), and the primitive plane of level k
-// (theta, u, v, w, halo 2) that the x and y upwind stencils read.  Each
-// thread owns one column: its z stencils (levels k-2 .. k+2) live in
-// registers, and the flux through the face above it is carried to the next
-// level.  Every field is read from HBM once per level; halo reuse comes from
-// shared memory and L2.
+// Work split.  The domain is cut into tiles of TX x TY columns; a tile's work
+// is the levels from its lowest kfast to the top, cut into slabs at the same
+// levels for every tile.  One CTA marches one (tile, slab) piece; the pieces
+// are launched slab by slab so that neighbouring tiles march the same levels
+// at the same time and their halo reads hit L2 (built once per geometry on
+// the host).
+//
+// One march over levels [kb, ke) of a tile.  Each thread owns two adjacent
+// columns (x = 2t, 2t + 1 of the tile) and processes them as a pair: float2
+// shared-memory and global accesses and, on the float path, the packed
+// FP32x2 arithmetic of sm_100+ (__ffma2_rn / __fadd2_rn / __fmul2_rn).  Per
+// level p of the march (the level whose primitives are formed):
+//   phase 1: the primitive plane of level p (theta, u, v, w; halo 2) from
+//            raw planes p and p - 1 (shared ring of five raw levels, filled
+//            by asynchronous 16-byte copies two levels ahead);
+//   barrier; the raw plane of level p + 2 is requested;
+//   phase 2a: the x / y face fluxes of level p of the four advected
+//            quantities, once per face, into shared face planes;
+//   barrier;
+//   phase 2b: the x / y part of each CV's divergence at level p (kept in
+//            registers for two levels), the z flux through the top of level
+//            k = p - 2 from a register window of the thread's own columns,
+//            and the update of level k.
+// Every field is read from HBM once per level (halo re-reads hit L2) and
+// written once.  Advective face fluxes carry a factor 6 that the divergence
+// removes with 1/(6 dx).
 #include "eb_step.cuh"
 
 #include <algorithm>
+#include <vector>
 
 namespace {
 
-template <typename T>
-__device__ inline T divide(T a, T b) {
-  return eb_div(a, b);
+// ---- asynchronous global -> shared copies ---------------------------------
+__device__ inline unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+template <int BYTES>
+__device__ inline void copy_async(void *dst, const void *src) {
+  const size_t g = __cvta_generic_to_global(src);
+  if constexpr (BYTES == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(g) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(dst)), "l"(g), "n"(BYTES)
+                 : "memory");
+  }
+}
+__device__ inline void copy_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ inline void copy_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// ---- pairs of adjacent columns ----------------------------------------------
 template <typename T>
-__device__ inline T upwind_flux(T m, T pLL, T pL, T pR, T pRR, bool hasLL, bool hasRR) {
-  return m * upwind_value(m, pLL, pL, pR, pRR, hasLL, hasRR);
-}
-
-template <typename T, int TX, int TY>
-struct Tile {
-  static constexpr int PX = TX + 5, PY = TY + 5, NP = PX * PY;   // raw planes
-  static constexpr int QX = TX + 4, QY = TY + 4, NQ = QX * QY;   // primitive plane
-  static constexpr int NT = TX * TY;
-  static constexpr int RAW = 4 * 5 * NP;                           // ring of 4 planes x 5 fields
-  static constexpr size_t BYTES = sizeof(T) * (size_t)(RAW + 4 * NQ);
-  static constexpr int LOADS = (NP + NT - 1) / NT;
-  static constexpr int PRIMS = (NQ + NT - 1) / NT;
+struct PairOf;
+template <>
+struct PairOf<float> {
+  using type = float2;
+};
+template <>
+struct PairOf<double> {
+  using type = double2;
 };
 
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) k_fast_tiled(StepArgs<T> A) {
-  using TL = Tile<T, TX, TY>;
+__device__ inline float2 mk(float a, float b) { return make_float2(a, b); }
+__device__ inline double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename T>
+__device__ inline typename PairOf<T>::type splat(T a) {
+  return mk(a, a);
+}
+
+// correctly rounded elementwise operations (packed on the float path)
+__device__ inline float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ inline double2 padd(double2 a, double2 b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
+__device__ inline float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ inline double2 pmul(double2 a, double2 b) { return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)); }
+__device__ inline float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ inline double2 pfma(double2 a, double2 b, double2 c) {
+  return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+// a - b, rounded once (the product -1 * b is exact)
+__device__ inline float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ inline double2 psub(double2 a, double2 b) { return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)); }
+// elementwise reciprocal: the fast approximate one on the float path
+__device__ inline float2 prcp(float2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
+__device__ inline double2 prcp(double2 a) { return make_double2(1.0 / a.x, 1.0 / a.y); }
+template <typename P>
+__device__ inline P psel_pos(P m, P a, P b) {   // a where m > 0, else b
+  return mk(m.x > 0 ? a.x : b.x, m.y > 0 ? a.y : b.y);
+}
+
+__device__ inline float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ inline double2 ld2(const double *p) { return *reinterpret_cast<const double2 *>(p); }
+__device__ inline void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+__device__ inline void st2(double *p, double2 v) { *reinterpret_cast<double2 *>(p) = v; }
+
+// 6 * m * (third-order upwind face value) for two faces, each between b and
+// c with far values a (low side) and d (high side): m > 0 takes
+// (5b + 2c - a), m < 0 takes (5c + 2b - d), or the centred 3(b + c) when the
+// far high CV does not exist (Sec. 4.1).
+template <typename P>
+__device__ inline P flux6(P m, P a, P b, P c, P d, bool has_d = true) {
+  using T = decltype(m.x);
+  const P two = splat(T(2)), five = splat(T(5)), mone = splat(T(-1));
+  const P vp = pfma(b, five, pfma(a, mone, pmul(c, two)));
+  const P vn = has_d ? pfma(c, five, pfma(d, mone, pmul(b, two))) : pmul(padd(b, c), splat(T(3)));
+  return pmul(m, psel_pos(m, vp, vn));
+}
+
+template <typename T>
+struct BulkTile {
+  static constexpr int TX = 32, TY = 16;     // columns and rows of a tile
+  static constexpr int NPX = TX / 2;         // column pairs per row (threads per row)
+  static constexpr int NT = NPX * TY;        // threads
+  static constexpr int HX = 4;               // raw halo in x on both sides (16-byte aligned rows)
+  static constexpr int PX = TX + 2 * HX;     // raw row: x = -4 .. TX + 3
+  static constexpr int PY = TY + 5;          // raw rows: y = -3 .. TY + 1
+  static constexpr int NP = PX * PY;         // one raw plane of one field
+  static constexpr int SLOTS = 5;            // raw levels p - 2 .. p + 2
+  static constexpr int QX = TX + 4;          // primitive row: x = -2 .. TX + 1
+  static constexpr int QY = TY + 4;          // primitive rows: y = -2 .. TY + 1
+  static constexpr int NQ = QX * QY;
+  static constexpr int NQP = NQ / 2;         // primitive pairs
+  static constexpr int FXW = NPX + 1;        // x faces at even x = 0, 2, .., TX of a row
+  static constexpr int NFX = FXW * TY, NFY = TX * (TY + 1);
+  static constexpr int RAW = SLOTS * 5 * NP;
+  static constexpr int PRIM = 4 * NQ;
+  static constexpr size_t BYTES = sizeof(T) * (size_t)(RAW + PRIM + 4 * NFX + 4 * NFY);
+  static constexpr int QR = (NQP + NT - 1) / NT;   // primitive pairs per thread
+  __device__ static constexpr int ri(int x, int y) { return (y + 3) * PX + (x + HX); }
+  __device__ static constexpr int qi(int x, int y) { return (y + 2) * QX + (x + 2); }
+};
+
+// V elements per asynchronous copy: 16 bytes when every row of every field
+// starts on a 16-byte boundary (then pairs are also stored as one access),
+// else one element.
+template <typename T, int V>
+__global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_fast_tiled(StepArgs<T> A) {
+  using TL = BulkTile<T>;
+  using P = typename PairOf<T>::type;
+  constexpr int TX = TL::TX, TY = TL::TY, NPX = TL::NPX, NT = TL::NT, PX = TL::PX, NP = TL::NP, QX = TL::QX,
+                NQ = TL::NQ;
+  constexpr int GX = PX / V, NPOS = GX * TL::PY, CR = (NPOS + NT - 1) / NT;
+  constexpr int CB = (int)(V * sizeof(T));
+  constexpr bool PAIRIO = V > 1;
+  static_assert(PX % V == 0, "raw rows must split into whole copies");
+  static_assert(NPX >= TY, "one row of threads computes the faces on the high x edge");
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   T *raw = reinterpret_cast<T *>(smem_bytes);
   T *prim = raw + TL::RAW;
-  __shared__ int s_k0;
+  T *FX = prim + TL::PRIM;
+  T *FY = FX + 4 * TL::NFX;
+
   const Dims &D = A.D;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int i = i0 + tx, j = j0 + ty;
-  const bool inside = i < D.nx && j < D.ny;
-  const int kf = inside ? A.kfast[i + D.nx * j] : D.nz;
-  if (tid == 0) s_k0 = D.nz;
-  __syncthreads();
-  atomicMin(&s_k0, kf);
-  __syncthreads();
-  // this CTA's slab of levels: [max(tile's lowest kfast, chunk start), chunk end)
-  const int k0 = max(s_k0, (int)blockIdx.z * A.kchunk);
-  const int kend = min(D.nz, ((int)blockIdx.z + 1) * A.kchunk);
-  if (k0 >= kend) return;
-
-  // column offsets of the points this thread loads (fixed for the whole march)
-  long long lcol[TL::LOADS];
-  int lslot[TL::LOADS];
-#pragma unroll
-  for (int r = 0; r < TL::LOADS; ++r) {
-    const int q = tid + r * TL::NT;
-    lslot[r] = q < TL::NP ? q : -1;
-    const int x = q % TL::PX - 3, y = q / TL::PX - 3;
-    lcol[r] = (long long)wrapmod(i0 + x, D.nx) + (long long)D.nx * wrapmod(j0 + y, D.ny);
-  }
-  auto load_plane = [&](int L) {
-    T *P = raw + (L & 3) * 5 * TL::NP;
-    const bool live = L >= 0 && L < D.nz;
-    const T rr = live ? A.src.ref_rho[L] : T(0);
-    const T rt = live ? A.src.ref_rt[L] : T(0);
-#pragma unroll
-    for (int r = 0; r < TL::LOADS; ++r) {
-      if (lslot[r] < 0) continue;
-      T v0 = T(1), v1 = T(0), v2 = T(0), v3 = T(0), v4 = T(0);
-      if (live) {
-        const long long c = lcol[r] + D.nxy * L;
-        v0 = rr + A.src.f[0][c];
-        v1 = rt + A.src.f[1][c];
-        v2 = A.src.f[2][c];
-        v3 = A.src.f[3][c];
-        v4 = L >= 1 ? A.src.f[4][c] : T(0);   // rho*w on the wall level 0 enters as zero
-      }
-      const int q = lslot[r];
-      P[q] = v0;
-      P[TL::NP + q] = v1;
-      P[2 * TL::NP + q] = v2;
-      P[3 * TL::NP + q] = v3;
-      P[4 * TL::NP + q] = v4;
-    }
-  };
-  // raw index of tile point (x, y)
-  auto ri = [&](int x, int y) { return (y + 3) * TL::PX + (x + 3); };
-  auto qi = [&](int x, int y) { return (y + 2) * TL::QX + (x + 2); };
-  auto RAWV = [&](int L, int f, int x, int y) -> T { return raw[(L & 3) * 5 * TL::NP + f * TL::NP + ri(x, y)]; };
-
-  // column primitives of plane L (theta, u, v, w), from the ring
-  auto column_prims = [&](int L, T &th, T &u, T &v, T &w) {
-    if (L < 0 || L >= D.nz) {
-      th = u = v = T(0);
-      w = T(0);   // w wall level nz (and beyond, where it is never used)
-      return;
-    }
-    const T *P = raw + (L & 3) * 5 * TL::NP;
-    const int p = ri(tx, ty);
-    const T r = P[p];
-    th = divide(P[TL::NP + p], r);
-    u = divide(P[2 * TL::NP + p], T(0.5) * (P[p - 1] + r));
-    v = divide(P[3 * TL::NP + p], T(0.5) * (P[p - TL::PX] + r));
-    if (L == 0) {
-      w = T(0);
-    } else {
-      const T *Pm = raw + ((L - 1) & 3) * 5 * TL::NP;
-      w = divide(P[4 * TL::NP + p], T(0.5) * (Pm[p] + r));
-    }
-  };
-
-  // ---- prologue: ring planes k0-3 .. k0+1, column window k0-2 .. k0+1
-  T th[5], uu[5], vv[5], ww[5];
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    load_plane(k0 - 3 + q);
-    __syncthreads();
-    if (q >= 1) column_prims(k0 - 3 + q, th[q - 1], uu[q - 1], vv[q - 1], ww[q - 1]);
-    __syncthreads();
-  }
-  const T idx = T(1.0 / D.dx), idy = T(1.0 / D.dy), idz = T(1.0 / D.dz);
   const int nz = D.nz;
-  // lower z face fluxes of level k0: c (mass, theta), u, v, w
-  T zc_m, zc_t, zu, zv, zw;
-  {
-    const int k = k0;
-    const T m = RAWV(k, 4, tx, ty);
-    zc_m = m;
-    zc_t = upwind_flux(m, th[0], th[1], th[2], th[3], true, k + 1 <= nz - 1);
-    const T mu = T(0.5) * (RAWV(k, 4, tx - 1, ty) + m);
-    zu = upwind_flux(mu, uu[0], uu[1], uu[2], uu[3], true, k + 1 <= nz - 1);
-    const T mv = T(0.5) * (RAWV(k, 4, tx, ty - 1) + m);
-    zv = upwind_flux(mv, vv[0], vv[1], vv[2], vv[3], true, k + 1 <= nz - 1);
-    const T mw = T(0.5) * (RAWV(k - 1, 4, tx, ty) + m);
-    zw = upwind_flux(mw, ww[0], ww[1], ww[2], ww[3], true, true);
-  }
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * NPX + tx;
+  const int tiles_x = (D.nx + TX - 1) / TX;
+  const T idx = T(D.idx), idy = T(D.idy), idz = T(D.idz);
+  const T idx6 = T(D.idx / 6.0), idy6 = T(D.idy / 6.0), idz6 = T(D.idz / 6.0);
+  const P half = splat(T(0.5)), zero = splat(T(0));
+  const bool same_base = A.base[0] != nullptr && A.base[0] == A.src.f[0] && A.base[1] == A.src.f[1] &&
+                         A.base[2] == A.src.f[2] && A.base[3] == A.src.f[3] && A.base[4] == A.src.f[4];
+  const int self = TL::ri(2 * tx, ty);
+  P bad = zero;   // becomes NaN once any written value is not finite
 
-  for (int k = k0; k < kend; ++k) {
-    // ---- stage plane k+2 and the primitive plane of level k
-    __syncthreads();
-    load_plane(k + 2);
-    __syncthreads();
-    column_prims(k + 2, th[4], uu[4], vv[4], ww[4]);
-    if (k + 2 == nz) ww[4] = T(0);   // w wall level
-    {
-      const T *P = raw + (k & 3) * 5 * TL::NP;
-      const T *Pm = raw + ((k - 1) & 3) * 5 * TL::NP;
+  auto RAWP = [&](int L) -> const T * { return raw + (L % TL::SLOTS) * 5 * NP; };
+
+  for (int sgi = A.boff[blockIdx.x]; sgi < A.boff[blockIdx.x + 1]; ++sgi) {
+    const int4 sg = A.bseg[sgi];
+    const int tile = sg.x, kbeg = sg.y, kend = sg.z;   // kbeg >= 3 (kfast >= 3)
+    const int i0 = (tile % tiles_x) * TX, j0 = (tile / tiles_x) * TY;
+    const int i = i0 + 2 * tx, j = j0 + ty;
+    const bool jin = j < D.ny;
+    const int kfx = (jin && i < D.nx) ? A.kfast[i + D.nx * j] : nz;
+    const int kfy = (jin && i + 1 < D.nx) ? A.kfast[i + 1 + D.nx * j] : nz;
+
+    // copy plan: raw-plane positions this thread requests every level
+    int cpos_s[CR], cpos_g[CR];
 #pragma unroll
-      for (int r = 0; r < TL::PRIMS; ++r) {
-        const int q = tid + r * TL::NT;
-        if (q >= TL::NQ) continue;
-        const int x = q % TL::QX - 2, y = q / TL::QX - 2;
-        const int p = ri(x, y);
-        const T rho = P[p];
-        prim[q] = divide(P[TL::NP + p], rho);
-        prim[TL::NQ + q] = divide(P[2 * TL::NP + p], T(0.5) * (P[p - 1] + rho));
-        prim[2 * TL::NQ + q] = divide(P[3 * TL::NP + p], T(0.5) * (P[p - TL::PX] + rho));
-        prim[3 * TL::NQ + q] = divide(P[4 * TL::NP + p], T(0.5) * (Pm[p] + rho));
+    for (int r = 0; r < CR; ++r) {
+      const int q = tid + r * NT;
+      cpos_s[r] = -1;
+      cpos_g[r] = 0;
+      if (q < NPOS) {
+        const int row = q / GX, gx = q % GX;
+        const int x = wrapmod(i0 - TL::HX + gx * V, D.nx), y = wrapmod(j0 - 3 + row, D.ny);
+        cpos_s[r] = row * PX + gx * V;
+        cpos_g[r] = x + D.nx * y;
       }
     }
-    __syncthreads();
-    const bool has1 = k + 1 <= nz - 1, has2 = k + 2 <= nz - 1;   // c, u, v levels above
-    const T *TH = prim, *UP = prim + TL::NQ, *VP = prim + 2 * TL::NQ, *WP = prim + 3 * TL::NQ;
-    if (inside && k >= kf) {
-      const long long c = (long long)i + D.nx * ((long long)j + (long long)D.ny * k);
-      // ---------------- c grid: rho and rho*theta
-      {
-        const T mxl = RAWV(k, 2, tx, ty), mxh = RAWV(k, 2, tx + 1, ty);
-        const T fxl = upwind_flux(mxl, TH[qi(tx - 2, ty)], TH[qi(tx - 1, ty)], TH[qi(tx, ty)], TH[qi(tx + 1, ty)],
-                                  true, true);
-        const T fxh = upwind_flux(mxh, TH[qi(tx - 1, ty)], TH[qi(tx, ty)], TH[qi(tx + 1, ty)], TH[qi(tx + 2, ty)],
-                                  true, true);
-        const T myl = RAWV(k, 3, tx, ty), myh = RAWV(k, 3, tx, ty + 1);
-        const T fyl = upwind_flux(myl, TH[qi(tx, ty - 2)], TH[qi(tx, ty - 1)], TH[qi(tx, ty)], TH[qi(tx, ty + 1)],
-                                  true, true);
-        const T fyh = upwind_flux(myh, TH[qi(tx, ty - 1)], TH[qi(tx, ty)], TH[qi(tx, ty + 1)], TH[qi(tx, ty + 2)],
-                                  true, true);
-        const T mzh = has1 ? RAWV(k + 1, 4, tx, ty) : T(0);
-        const T fzh = upwind_flux(mzh, th[1], th[2], th[3], th[4], true, has2);
-        const T dr = -((mxh - mxl) * idx + (myh - myl) * idy + (mzh - zc_m) * idz);
-        const T dt_ = -((fxh - fxl) * idx + (fyh - fyl) * idy + (fzh - zc_t) * idz);
-        const T o0 = A.base[0] ? A.base[0][c] + A.dtT * dr : dr;
-        const T o1 = A.base[0] ? A.base[1][c] + A.dtT * dt_ : dt_;
-        A.out[0][c] = o0;
-        A.out[1][c] = o1;
-        if (!(isfinite(o0) && isfinite(o1))) atomicOr(A.status, EB_DEV_NUMERIC);
-        zc_m = mzh;
-        zc_t = fzh;
-      }
-      // ---------------- u grid (x faces at cell centres, y and z faces on edges)
-      {
-        const T ul = RAWV(k, 2, tx - 1, ty), u0 = RAWV(k, 2, tx, ty), ur = RAWV(k, 2, tx + 1, ty);
-        const T fxl = upwind_flux(T(0.5) * (ul + u0), UP[qi(tx - 2, ty)], UP[qi(tx - 1, ty)], UP[qi(tx, ty)],
-                                  UP[qi(tx + 1, ty)], true, true);
-        const T fxh = upwind_flux(T(0.5) * (u0 + ur), UP[qi(tx - 1, ty)], UP[qi(tx, ty)], UP[qi(tx + 1, ty)],
-                                  UP[qi(tx + 2, ty)], true, true);
-        const T myl = T(0.5) * (RAWV(k, 3, tx - 1, ty) + RAWV(k, 3, tx, ty));
-        const T myh = T(0.5) * (RAWV(k, 3, tx - 1, ty + 1) + RAWV(k, 3, tx, ty + 1));
-        const T fyl = upwind_flux(myl, UP[qi(tx, ty - 2)], UP[qi(tx, ty - 1)], UP[qi(tx, ty)], UP[qi(tx, ty + 1)],
-                                  true, true);
-        const T fyh = upwind_flux(myh, UP[qi(tx, ty - 1)], UP[qi(tx, ty)], UP[qi(tx, ty + 1)], UP[qi(tx, ty + 2)],
-                                  true, true);
-        const T mzh = has1 ? T(0.5) * (RAWV(k + 1, 4, tx - 1, ty) + RAWV(k + 1, 4, tx, ty)) : T(0);
-        const T fzh = upwind_flux(mzh, uu[1], uu[2], uu[3], uu[4], true, has2);
-        const T d = -((fxh - fxl) * idx + (fyh - fyl) * idy + (fzh - zu) * idz);
-        const T o = A.base[0] ? A.base[2][c] + A.dtT * d : d;
-        A.out[2][c] = o;
-        if (!isfinite(o)) atomicOr(A.status, EB_DEV_NUMERIC);
-        zu = fzh;
-      }
-      // ---------------- v grid
-      {
-        const T vl = RAWV(k, 3, tx, ty - 1), v0 = RAWV(k, 3, tx, ty), vr = RAWV(k, 3, tx, ty + 1);
-        const T mxl = T(0.5) * (RAWV(k, 2, tx, ty - 1) + RAWV(k, 2, tx, ty));
-        const T mxh = T(0.5) * (RAWV(k, 2, tx + 1, ty - 1) + RAWV(k, 2, tx + 1, ty));
-        const T fxl = upwind_flux(mxl, VP[qi(tx - 2, ty)], VP[qi(tx - 1, ty)], VP[qi(tx, ty)], VP[qi(tx + 1, ty)],
-                                  true, true);
-        const T fxh = upwind_flux(mxh, VP[qi(tx - 1, ty)], VP[qi(tx, ty)], VP[qi(tx + 1, ty)], VP[qi(tx + 2, ty)],
-                                  true, true);
-        const T fyl = upwind_flux(T(0.5) * (vl + v0), VP[qi(tx, ty - 2)], VP[qi(tx, ty - 1)], VP[qi(tx, ty)],
-                                  VP[qi(tx, ty + 1)], true, true);
-        const T fyh = upwind_flux(T(0.5) * (v0 + vr), VP[qi(tx, ty - 1)], VP[qi(tx, ty)], VP[qi(tx, ty + 1)],
-                                  VP[qi(tx, ty + 2)], true, true);
-        const T mzh = has1 ? T(0.5) * (RAWV(k + 1, 4, tx, ty - 1) + RAWV(k + 1, 4, tx, ty)) : T(0);
-        const T fzh = upwind_flux(mzh, vv[1], vv[2], vv[3], vv[4], true, has2);
-        const T d = -((fxh - fxl) * idx + (fyh - fyl) * idy + (fzh - zv) * idz);
-        const T o = A.base[0] ? A.base[3][c] + A.dtT * d : d;
-        A.out[3][c] = o;
-        if (!isfinite(o)) atomicOr(A.status, EB_DEV_NUMERIC);
-        zv = fzh;
-      }
-      // ---------------- w grid (x and y faces on edges, z faces at cell centres)
-      {
-        const T mxl = T(0.5) * (RAWV(k - 1, 2, tx, ty) + RAWV(k, 2, tx, ty));
-        const T mxh = T(0.5) * (RAWV(k - 1, 2, tx + 1, ty) + RAWV(k, 2, tx + 1, ty));
-        const T fxl = upwind_flux(mxl, WP[qi(tx - 2, ty)], WP[qi(tx - 1, ty)], WP[qi(tx, ty)], WP[qi(tx + 1, ty)],
-                                  true, true);
-        const T fxh = upwind_flux(mxh, WP[qi(tx - 1, ty)], WP[qi(tx, ty)], WP[qi(tx + 1, ty)], WP[qi(tx + 2, ty)],
-                                  true, true);
-        const T myl = T(0.5) * (RAWV(k - 1, 3, tx, ty) + RAWV(k, 3, tx, ty));
-        const T myh = T(0.5) * (RAWV(k - 1, 3, tx, ty + 1) + RAWV(k, 3, tx, ty + 1));
-        const T fyl = upwind_flux(myl, WP[qi(tx, ty - 2)], WP[qi(tx, ty - 1)], WP[qi(tx, ty)], WP[qi(tx, ty + 1)],
-                                  true, true);
-        const T fyh = upwind_flux(myh, WP[qi(tx, ty - 1)], WP[qi(tx, ty)], WP[qi(tx, ty + 1)], WP[qi(tx, ty + 2)],
-                                  true, true);
-        const T w0 = RAWV(k, 4, tx, ty), w1 = has1 ? RAWV(k + 1, 4, tx, ty) : T(0);
-        const T fzh = upwind_flux(T(0.5) * (w0 + w1), ww[1], ww[2], ww[3], ww[4], true, k + 2 <= nz);
-        const T d = -((fxh - fxl) * idx + (fyh - fyl) * idy + (fzh - zw) * idz);
-        const T o = A.base[0] ? A.base[4][c] + A.dtT * d : d;
-        A.out[4][c] = o;
-        if (!isfinite(o)) atomicOr(A.status, EB_DEV_NUMERIC);
-        zw = fzh;
-      }
-    } else {
-      // not yet at this column's fast level: keep the carried z fluxes current
-      // (the c, u, v lower fluxes of level k+1 are the upper ones of level k)
-      const T m = has1 ? RAWV(k + 1, 4, tx, ty) : T(0);
-      zc_m = m;
-      zc_t = upwind_flux(m, th[1], th[2], th[3], th[4], true, has2);
-      zu = upwind_flux(has1 ? T(0.5) * (RAWV(k + 1, 4, tx - 1, ty) + m) : T(0), uu[1], uu[2], uu[3], uu[4], true,
-                       has2);
-      zv = upwind_flux(has1 ? T(0.5) * (RAWV(k + 1, 4, tx, ty - 1) + m) : T(0), vv[1], vv[2], vv[3], vv[4], true,
-                       has2);
-      zw = upwind_flux(T(0.5) * (RAWV(k, 4, tx, ty) + m), ww[1], ww[2], ww[3], ww[4], true, k + 2 <= nz);
-    }
+    auto request = [&](int L) {
+      if (L >= 0 && L < nz) {
+        T *Pl = raw + (L % TL::SLOTS) * 5 * NP;
+        const long long off = D.nxy * L;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      th[q] = th[q + 1];
-      uu[q] = uu[q + 1];
-      vv[q] = vv[q + 1];
-      ww[q] = ww[q + 1];
+        for (int r = 0; r < CR; ++r) {
+          if (cpos_s[r] < 0) continue;
+#pragma unroll
+          for (int f = 0; f < 5; ++f) copy_async<CB>(Pl + f * NP + cpos_s[r], A.src.f[f] + off + cpos_g[r]);
+        }
+      }
+      copy_commit();
+    };
+    // primitive pairs of this thread: raw index (the pair's shared index is 2q)
+    int qraw[TL::QR];
+#pragma unroll
+    for (int r = 0; r < TL::QR; ++r) {
+      const int q = tid + r * NT;
+      qraw[r] = q < TL::NQP ? TL::ri(2 * (q % (QX / 2)) - 2, q / (QX / 2) - 2) : -1;
     }
+
+    // face fluxes (x 6) through the low x and y faces of the column pair at
+    // even tile x, row y of level p, all four grids: each momentum and
+    // primitive value is read from shared memory once
+    auto faces = [&](const T *Rk, const T *Rkm, int x, int y, P fxo[4], P fyo[4]) {
+      const int c = TL::ri(x, y);
+      const T *U = Rk + 2 * NP, *Vv = Rk + 3 * NP;
+      const P uc = ld2(U + c), ul = ld2(U + c - 2), ud = ld2(U + c - PX), ub = ld2(Rkm + 2 * NP + c);
+      const P vc = ld2(Vv + c), vl = ld2(Vv + c - 2), vd = ld2(Vv + c - PX), vkm = ld2(Rkm + 3 * NP + c);
+      const P mx[4] = {uc, pmul(padd(mk(ul.y, uc.x), uc), half), pmul(padd(ud, uc), half), pmul(padd(ub, uc), half)};
+      const P my[4] = {vc, pmul(padd(mk(vl.y, vc.x), vc), half), pmul(padd(vd, vc), half), pmul(padd(vkm, vc), half)};
+#pragma unroll
+      for (int G = 0; G < 4; ++G) {
+        const T *Q = prim + G * NQ + TL::qi(x, y);
+        const P pc = ld2(Q), pl = ld2(Q - 2), pr = ld2(Q + 2);
+        fxo[G] = flux6(mx[G], pl, mk(pl.y, pc.x), pc, mk(pc.y, pr.x));
+        fyo[G] = flux6(my[G], ld2(Q - 2 * QX), ld2(Q - QX), pc, ld2(Q + QX));
+      }
+    };
+    // y faces of the column pair at even tile x on row y (the high y edge)
+    auto yfaces = [&](const T *Rk, const T *Rkm, int x, int y, P fyo[4]) {
+      const int c = TL::ri(x, y);
+      const T *Vv = Rk + 3 * NP;
+      const P vc = ld2(Vv + c), vl = ld2(Vv + c - 2), vd = ld2(Vv + c - PX), vkm = ld2(Rkm + 3 * NP + c);
+      const P my[4] = {vc, pmul(padd(mk(vl.y, vc.x), vc), half), pmul(padd(vd, vc), half), pmul(padd(vkm, vc), half)};
+#pragma unroll
+      for (int G = 0; G < 4; ++G) {
+        const T *Q = prim + G * NQ + TL::qi(x, y);
+        fyo[G] = flux6(my[G], ld2(Q - 2 * QX), ld2(Q - QX), ld2(Q), ld2(Q + QX));
+      }
+    };
+    // x face at tile x = TX (the high x edge) on row y, all four grids
+    auto xedge = [&](const T *Rk, const T *Rkm, int y, T fxo[4]) {
+      const int c = TL::ri(TX, y);
+      const T *U = Rk + 2 * NP;
+      const T u0 = U[c];
+      const T mx[4] = {u0, T(0.5) * (U[c - 1] + u0), T(0.5) * (U[c - PX] + u0), T(0.5) * (Rkm[2 * NP + c] + u0)};
+#pragma unroll
+      for (int G = 0; G < 4; ++G) {
+        const T *Q = prim + G * NQ + TL::qi(TX, y);
+        fxo[G] = flux6(splat(mx[G]), splat(Q[-2]), splat(Q[-1]), splat(Q[0]), splat(Q[1])).x;
+      }
+    };
+
+    auto ref_r = [&](int L) -> T { return (L >= 0 && L < nz) ? A.src.ref_rho[L] : T(0); };
+    auto ref_t = [&](int L) -> T { return (L >= 0 && L < nz) ? A.src.ref_rt[L] : T(0); };
+    const int p0 = kbeg - 2, p1 = kend + 1;
+    T rr_m = ref_r(p0 - 1), rr_p = ref_r(p0), rt_p = ref_t(p0);
+
+    // prologue: raw levels p0 - 1, p0 landed, p0 + 1 in flight
+    request(p0 - 1);
+    request(p0);
+    request(p0 + 1);
+    copy_wait<1>();
+    __syncthreads();
+
+    // own-column primitive window (levels p - 3 .. p), carried bottom fluxes,
+    // and the x / y divergence parts of levels p - 2, p - 1
+    P th[4], uu[4], vv[4], ww[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) th[q] = uu[q] = vv[q] = ww[q] = zero;
+    P zc_m = zero, zc_t = zero, zu = zero, zv = zero, zw = zero;
+    P q0[4], q1[4];
+#pragma unroll
+    for (int G = 0; G < 4; ++G) q0[G] = q1[G] = zero;
+    long long cidx = (long long)i + (long long)D.nx * ((long long)j + (long long)D.ny * (p0 - 2));
+
+    for (int p = p0; p <= p1; ++p, cidx += D.nxy) {
+      const int k = p - 2;
+      const T rr_n = ref_r(p + 1), rt_n = ref_t(p + 1);
+      // ---- phase 1: primitive plane of level p
+      if (p < nz) {
+        const T *R = RAWP(p), *Rm = RAWP(p - 1);
+        const P rrp = splat(rr_p);
+#pragma unroll
+        for (int r = 0; r < TL::QR; ++r) {
+          const int c = qraw[r];
+          if (c < 0) continue;
+          T *Q = prim + 2 * (tid + r * NT);
+          const P rho = padd(ld2(R + c), rrp);
+          const P rhol = mk(rr_p + R[c - 1], rho.x);
+          const P rhod = padd(ld2(R + c - PX), rrp);
+          const P rhob = padd(ld2(Rm + c), splat(rr_m));
+          st2(Q, pmul(padd(ld2(R + NP + c), splat(rt_p)), prcp(rho)));
+          st2(Q + NQ, pmul(ld2(R + 2 * NP + c), prcp(pmul(padd(rhol, rho), half))));
+          st2(Q + 2 * NQ, pmul(ld2(R + 3 * NP + c), prcp(pmul(padd(rhod, rho), half))));
+          st2(Q + 3 * NQ, pmul(ld2(R + 4 * NP + c), prcp(pmul(padd(rhob, rho), half))));
+        }
+      }
+      __syncthreads();
+      request(p + 2 <= p1 ? p + 2 : -1);
+
+      // ---- phase 2a: own window; x / y faces of level p
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        th[q] = th[q + 1];
+        uu[q] = uu[q + 1];
+        vv[q] = vv[q + 1];
+        ww[q] = ww[q + 1];
+      }
+      if (p < nz) {
+        const T *Q = prim + TL::qi(2 * tx, ty);
+        th[3] = ld2(Q);
+        uu[3] = ld2(Q + NQ);
+        vv[3] = ld2(Q + 2 * NQ);
+        ww[3] = ld2(Q + 3 * NQ);
+      } else {
+        th[3] = uu[3] = vv[3] = ww[3] = zero;   // above the top; w wall level nz
+      }
+      const bool face_level = p >= kbeg && p < kend;
+      P fx[4], fy[4];
+      if (face_level) {
+        const T *Rk = RAWP(p), *Rkm = RAWP(p - 1);
+        faces(Rk, Rkm, 2 * tx, ty, fx, fy);
+#pragma unroll
+        for (int G = 0; G < 4; ++G) {
+          FX[G * TL::NFX + ty * TL::FXW + tx] = fx[G].x;
+          st2(FY + G * TL::NFY + ty * TX + 2 * tx, fy[G]);
+        }
+        if (ty == 0) {   // faces on the high y edge of the tile
+          P e[4];
+          yfaces(Rk, Rkm, 2 * tx, TY, e);
+#pragma unroll
+          for (int G = 0; G < 4; ++G) st2(FY + G * TL::NFY + TY * TX + 2 * tx, e[G]);
+        } else if (ty == TY - 1) {   // faces on the high x edge of the tile (row tx)
+          T e[4];
+          xedge(Rk, Rkm, tx, e);
+#pragma unroll
+          for (int G = 0; G < 4; ++G) FX[G * TL::NFX + tx * TL::FXW + NPX] = e[G];
+        }
+      }
+      copy_wait<1>();   // raw p + 1 landed (this thread's copies)
+      __syncthreads();
+
+      // ---- phase 2b: x / y divergence of level p; z flux and update of level k
+      P sxy[4];
+      if (face_level) {
+        const P ix = splat(idx6), iy = splat(idy6);
+#pragma unroll
+        for (int G = 0; G < 4; ++G) {
+          const P dfx = psub(mk(fx[G].y, FX[G * TL::NFX + ty * TL::FXW + tx + 1]), fx[G]);
+          const P dfy = psub(ld2(FY + G * TL::NFY + (ty + 1) * TX + 2 * tx), fy[G]);
+          sxy[G] = pfma(dfx, ix, pmul(dfy, iy));
+        }
+      } else {
+#pragma unroll
+        for (int G = 0; G < 4; ++G) sxy[G] = zero;
+      }
+      if (k >= kbeg - 1) {
+        // flux through the top of level k: masses from rho*w of levels k, k + 1
+        const bool has1 = k + 1 <= nz - 1, has2 = k + 2 <= nz - 1;
+        const T *Rk = RAWP(k);
+        const T *W1 = RAWP(k + 1) + 4 * NP;
+        const P m = has1 ? ld2(W1 + self) : zero;
+        const P mu = has1 ? pmul(padd(mk(W1[self - 1], m.x), m), half) : zero;
+        const P mv = has1 ? pmul(padd(ld2(W1 + self - PX), m), half) : zero;
+        const P mw = pmul(padd(ld2(Rk + 4 * NP + self), m), half);
+        const P fzc = flux6(m, th[0], th[1], th[2], th[3], has2);
+        const P fzu = flux6(mu, uu[0], uu[1], uu[2], uu[3], has2);
+        const P fzv = flux6(mv, vv[0], vv[1], vv[2], vv[3], has2);
+        const P fzw = flux6(mw, ww[0], ww[1], ww[2], ww[3], k + 2 <= nz);
+        if (k >= kbeg && (k >= kfx || k >= kfy)) {
+          const T *U = Rk + 2 * NP, *Vv = Rk + 3 * NP;
+          const P uc = ld2(U + self);
+          const P dmx = psub(mk(uc.y, U[self + 2]), uc);
+          const P dmy = psub(ld2(Vv + self + PX), ld2(Vv + self));
+          const P iz6 = splat(-idz6);
+          P d[5];
+          d[0] = pfma(dmx, splat(-idx), pfma(dmy, splat(-idy), pmul(psub(m, zc_m), splat(-idz))));
+          d[1] = pfma(psub(fzc, zc_t), iz6, pmul(q0[0], splat(T(-1))));
+          d[2] = pfma(psub(fzu, zu), iz6, pmul(q0[1], splat(T(-1))));
+          d[3] = pfma(psub(fzv, zv), iz6, pmul(q0[2], splat(T(-1))));
+          d[4] = pfma(psub(fzw, zw), iz6, pmul(q0[3], splat(T(-1))));
+          const bool both = k >= kfx && k >= kfy;
+          const P dtp = splat(A.dtT);
+#pragma unroll
+          for (int f = 0; f < 5; ++f) {
+            P o;
+            if (same_base) {
+              o = pfma(d[f], dtp, ld2(Rk + f * NP + self));
+            } else if (A.base[0]) {
+              const T *b = A.base[f] + cidx;   // element-wise: the pair may end past the last column
+              o = pfma(d[f], dtp, PAIRIO ? ld2(b) : mk(k >= kfx ? b[0] : T(0), k >= kfy ? b[1] : T(0)));
+            } else {
+              o = d[f];
+            }
+            T *dst = A.out[f] + cidx;
+            if (both) {
+              if (PAIRIO) st2(dst, o);
+              else {
+                dst[0] = o.x;
+                dst[1] = o.y;
+              }
+              bad = pfma(o, zero, bad);
+            } else if (k >= kfx) {
+              dst[0] = o.x;
+              bad.x = fma(o.x, T(0), bad.x);
+            } else {
+              dst[1] = o.y;
+              bad.y = fma(o.y, T(0), bad.y);
+            }
+          }
+        }
+        zc_m = m;
+        zc_t = fzc;
+        zu = fzu;
+        zv = fzv;
+        zw = fzw;
+      }
+#pragma unroll
+      for (int G = 0; G < 4; ++G) {
+        q0[G] = q1[G];
+        q1[G] = sxy[G];
+      }
+      rr_m = rr_p;
+      rr_p = rr_n;
+      rt_p = rt_n;
+    }
+    copy_wait<0>();
+    __syncthreads();   // the next march reuses the shared ring
   }
+  if (!(isfinite(bad.x) && isfinite(bad.y))) atomicOr(A.status, EB_DEV_NUMERIC);
 }
 
 // Pass-through of the CVs no kernel updates: covered CVs and the two wall
@@ -309,9 +459,81 @@ __global__ void k_static(StepArgs<T> A) {
   if (k == D.nz - 1) put(4, lin(D, i, j, D.nz));
 }
 
-constexpr int FTX = 32, FTY = 8;
+template <typename T, int V>
+void set_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_fast_tiled<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)BulkTile<T>::BYTES);
+    done = true;
+  }
+}
+
+template <typename T, int V>
+void launch_bulk(const StepArgs<T> &A, cudaStream_t s) {
+  using TL = BulkTile<T>;
+  if (A.bctas < 1) return;
+  set_smem_attr<T, V>();
+  k_fast_tiled<T, V><<<A.bctas, dim3(TL::NPX, TL::TY, 1), TL::BYTES, s>>>(A);
+}
+
+template <typename T>
+int resident_ctas_per_sm() {
+  constexpr int V = 16 / sizeof(T);
+  set_smem_attr<T, V>();
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast_tiled<T, V>, BulkTile<T>::NT, BulkTile<T>::BYTES) !=
+          cudaSuccess ||
+      n < 1)
+    n = 1;
+  return n;
+}
 
 }  // namespace
+
+cudaError_t bulk_plan(const Dims &D, const int *kfast_host, bool f64, std::vector<int> &seg, std::vector<int> &off) {
+  const int TX = BulkTile<float>::TX, TY = BulkTile<float>::TY;
+  const int tx = (D.nx + TX - 1) / TX, ty = (D.ny + TY - 1) / TY;
+  const long long ntile = (long long)tx * ty;
+  std::vector<int> kb(ntile, D.nz);
+  for (int j = 0; j < D.ny; ++j)
+    for (int i = 0; i < D.nx; ++i) {
+      int &v = kb[(i / TX) + (long long)tx * (j / TY)];
+      v = std::min(v, kfast_host[i + (long long)D.nx * j]);
+    }
+  long long W = 0;
+  for (long long t = 0; t < ntile; ++t) W += std::max(0, D.nz - kb[t]);
+  seg.clear();
+  off.assign(1, 0);
+  if (W == 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long slots = (long long)std::max(sms, 1) * (f64 ? resident_ctas_per_sm<double>()
+                                                              : resident_ctas_per_sm<float>());
+  // Lockstep slabs: every tile is cut at the same levels, and the pieces are
+  // launched slab by slab from the top, so CTAs of neighbouring tiles march
+  // the same levels at the same time and read each other's halo from L2.
+  // Slabs of at least 16 levels, sized for about three waves of CTAs; the
+  // short pieces of the lowest slabs come last.
+  const long long Lc = std::max(16LL, (W + 3 * slots - 1) / (3 * slots));
+  const int nslab = (int)((D.nz + Lc - 1) / Lc);
+  for (int sl = nslab - 1; sl >= 0; --sl) {
+    const int za = (int)(sl * Lc), zb = (int)std::min<long long>(D.nz, (sl + 1) * Lc);
+    for (long long t = 0; t < ntile; ++t) {
+      const int a = std::max(za, kb[t]);
+      if (a >= zb) continue;
+      seg.push_back((int)t);
+      seg.push_back(a);
+      seg.push_back(zb);
+      seg.push_back(0);
+      off.push_back((int)(seg.size() / 4));
+    }
+  }
+  return cudaGetLastError();
+}
 
 template <typename T>
 void launch_flux_fast(const StepArgs<T> &A, cudaStream_t s) {
@@ -320,25 +542,16 @@ void launch_flux_fast(const StepArgs<T> &A, cudaStream_t s) {
     dim3 blk(32, 8, 1), grd((D.nx + 31) / 32, (D.ny + 7) / 8, D.nz);
     k_static<T><<<grd, blk, 0, s>>>(A);
   }
-  using TL = Tile<T, FTX, FTY>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_fast_tiled<T, FTX, FTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::BYTES);
-    attr_set = true;
+  // 16-byte copies and pair stores need every row of every field to start on
+  // a 16-byte boundary: nx a multiple of the copy width and aligned pointers
+  constexpr int V = 16 / sizeof(T);
+  bool vec = D.nx % V == 0;
+  for (int f = 0; f < 5; ++f) {
+    vec = vec && ((uintptr_t)A.src.f[f] % 16 == 0) && ((uintptr_t)A.out[f] % 16 == 0);
+    if (A.base[0]) vec = vec && ((uintptr_t)A.base[f] % 16 == 0);
   }
-  // split the z march into slabs so that the grid fills the GPU for about
-  // three waves of resident CTAs (slabs of at least 16 levels)
-  const long long tiles = (long long)((D.nx + FTX - 1) / FTX) * ((D.ny + FTY - 1) / FTY);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long slots = (long long)(sms > 0 ? sms : 148) * 4;
-  int nch = (int)((3 * slots + tiles - 1) / tiles);
-  nch = std::max(1, std::min(nch, D.nz / 16));
-  StepArgs<T> B = A;
-  B.kchunk = (D.nz + nch - 1) / nch;
-  dim3 blk(FTX, FTY, 1), grd((D.nx + FTX - 1) / FTX, (D.ny + FTY - 1) / FTY, nch);
-  k_fast_tiled<T, FTX, FTY><<<grd, blk, TL::BYTES, s>>>(B);
+  if (vec) launch_bulk<T, V>(A, s);
+  else launch_bulk<T, 1>(A, s);
 }
 
 template void launch_flux_fast<double>(const StepArgs<double> &, cudaStream_t);

@@ -54,6 +54,7 @@ struct Dims {
   int nx, ny, nz;
   long long nxy;
   double dx, dy, dz;
+  double idx, idy, idz;   // 1/dx, 1/dy, 1/dz (set on the host with the spacings)
 };
 
 // Periodic index for offsets of at most n from [0, n) (every stencil here

@@ -4,6 +4,8 @@
 
 #include "eb_internal.cuh"
 
+#include <vector>
+
 // Compact redistribution tables of one grid (Sec. 5.1), built once.
 struct WsrdDev {
   long long nsmall = 0, naff = 0, nlsq = 0, nw = 0;
@@ -46,6 +48,11 @@ void launch_marks_to_counts(const uint8_t *m, long long n, long long *cnt, cudaS
 void launch_marks_fill(const uint8_t *m, long long n, const long long *pos, unsigned *list, cudaStream_t s);
 void launch_export_geometry(const double *h, const Dims &D, int g, const GridDev &G, int field, double *dst,
                             cudaStream_t s);
+
+// eb_fast.cu: split of the bulk kernel's (tile, level) work into equal pieces,
+// one per resident CTA; seg holds (tile, first level, end level, 0) per
+// piece, off[b] .. off[b+1] the pieces of CTA b
+cudaError_t bulk_plan(const Dims &D, const int *kfast_host, bool f64, std::vector<int> &seg, std::vector<int> &off);
 
 // eb_scan.cu: in-place exclusive scan of n values; total written to *total (device)
 void scan_exclusive(long long *data, long long n, long long *total, cudaStream_t s);

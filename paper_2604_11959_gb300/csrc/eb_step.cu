@@ -127,7 +127,7 @@ template <typename T, typename R>
 __device__ void band_divergence(const StepArgs<T> &A, const GeoBand &geo, int g, int i, int j, int k, R &sm,
                                 R &sp) {
   const Dims &D = A.D;
-  const R inv[3] = {R(1.0 / D.dx), R(1.0 / D.dy), R(1.0 / D.dz)};
+  const R inv[3] = {R(D.idx), R(D.idy), R(D.idz)};
   sm = R(0);
   sp = R(0);
 #pragma unroll

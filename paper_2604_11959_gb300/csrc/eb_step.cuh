@@ -15,7 +15,11 @@ struct StepArgs {
   GridDev G[4];
   unsigned *status;
   int copy_static;     // also write covered CVs and the w wall levels
-  int kchunk;          // levels per z slab of the tiled bulk kernel (set at launch)
+  // work split of the bulk kernel: CTA b marches the pieces boff[b] .. boff[b+1]-1
+  // of bseg, each (tile, first level, end level, 0)
+  const int4 *bseg;
+  const int *boff;
+  int bctas;
 };
 
 template <typename T>
