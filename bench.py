@@ -220,10 +220,10 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist):
     hbm, kind = peaks()
     achieved = fast_bytes / (prof[0] * 1e-3) / 1e9
     # per step: static pass-through (a fresh output buffer every call), the
-    # tiled bulk kernel, the near-EB kernel of each grid with CVs to update,
-    # and the three redistribution passes of each field
-    launches_per_step = 2 + sum(1 for g in range(4) if info["band_cvs"][g]) + \
-        sum((1 if info["small_cvs"][FG] else 0) * 2 + (1 if info["affected_cvs"][FG] else 0) for FG in (0, 0, 1, 2, 3))
+    # tiled bulk kernel, the three near-EB kernels (face fluxes, CVs with a
+    # record, regular CVs) and the three fused redistribution passes
+    launches_per_step = 2 + (3 if sum(info["band_cvs"]) else 0) + (2 if sum(info["small_cvs"]) else 0) + \
+        (1 if sum(info["affected_cvs"]) else 0)
     # bytes the whole step must move: every non-covered CV read and written
     # once, plus the band geometry records read by the near-EB kernel
     step_bytes = sum(info["cvs"][g] * (2 if g else 4) for g in range(4)) * es + \

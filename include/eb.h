@@ -64,7 +64,7 @@ typedef enum { EB_GRID_C = 0, EB_GRID_U = 1, EB_GRID_V = 2, EB_GRID_W = 3 } eb_g
 typedef enum { EB_RHO = 0, EB_RHOTHETA = 1, EB_RHOU = 2, EB_RHOV = 3, EB_RHOW = 4 } eb_field;
 
 typedef struct {
-  int nx, ny, nz;        /* cells, each >= 4                                      */
+  int nx, ny, nz;        /* cells, each >= 4; nx*ny*(nz+1) < 2^32                 */
   double Lx, Ly, Lz;     /* domain lengths, > 0                                    */
   double v_target_frac;  /* small-cell threshold V_target / (dx dy dz); the paper
                             uses 1/2 (Sec. 5.1).  Must lie in (0, 1].            */
@@ -104,7 +104,7 @@ typedef enum {
  *   axes a1, a2, a3 ordered by decreasing |n_d| of the unit EB normal, two
  *   components counting as equal when they differ by at most 1e-12, ties
  *   broken x before y before z; permutation index p over
- *   (xyz, xzy, yxz, yzx, zxy, zyx); sign bits b_d = 1 where n_d < 0;
+ *   (xyz, xzy, yxz, yzx, zxy, zyx); sign bits b_d = 1 where n_d < -1e-12;
  *   growth level L = 1 (two CVs), 2 (2x2), 3 (2x2x2);
  *   code = 1 + (8 p + b_x + 2 b_y + 4 b_z) * 3 + (L - 1).
  */
@@ -117,6 +117,7 @@ typedef struct {
   int64_t small_cvs[4];     /* CVs with volume fraction below the threshold   */
   int64_t affected_cvs[4];  /* CVs the redistribution writes                  */
   int64_t band_cvs[4];      /* CVs updated by the general (near-EB) kernel    */
+  int64_t band_faces[4];    /* near-EB faces whose provisional flux is staged */
   int64_t tiny_cvs[4];      /* cut CVs with volume fraction below 1e-3        */
   int64_t fast_cells;       /* base cells updated by the geometry-free kernel  */
   double min_alpha;         /* smallest positive volume fraction, any grid    */

@@ -53,6 +53,7 @@ struct eb_geom_s {
   int4 *bseg = nullptr;   // bulk kernel work split
   int *boff = nullptr;
   int bctas = 0;
+  int kcov_max = 0;
   GridDev G[4];
   WsrdDev W[4];
   double *ref_d[2] = {nullptr, nullptr};
@@ -62,6 +63,13 @@ struct eb_geom_s {
   unsigned *status = nullptr;
   void *qhat = nullptr, *sig = nullptr, *pval = nullptr;
   long long max_small = 0;
+  // scratch of the five-field redistribution pass (small CVs of all fields)
+  void *qhat5 = nullptr, *sig5 = nullptr, *pval5 = nullptr;
+  long long sum_small = 0;
+  // the near-EB kernels run on this stream, forked from and joined to the
+  // caller's stream around the bulk kernel
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // scratch states for eb_step: 4 x 5 fields
   void *scr[4][5] = {};
   std::vector<void *> allocs;
@@ -79,6 +87,11 @@ struct eb_geom_s {
     return e;
   }
   void release() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
+    ev_fork = ev_join = nullptr;
+    side = nullptr;
     for (void *p : allocs) cudaFree(p);
     allocs.clear();
     for (int g = 0; g < 4; ++g) free_wsrd(W[g]);
@@ -90,7 +103,10 @@ namespace {
 bool bad_desc(const eb_desc *d, std::string &why) {
   if (!d) { why = "desc is NULL"; return true; }
   if (d->nx < 4 || d->ny < 4 || d->nz < 4) { why = "nx, ny, nz must be >= 4"; return true; }
-  if ((long long)d->nx * d->ny * (d->nz + 1) > (1LL << 40)) { why = "grid too large"; return true; }
+  if ((long long)d->nx * d->ny * (d->nz + 1) >= (1LL << 32)) {
+    why = "grid too large: nx*ny*(nz+1) must be below 2^32";
+    return true;
+  }
   if (!(d->Lx > 0) || !(d->Ly > 0) || !(d->Lz > 0) || !isfinite(d->Lx) || !isfinite(d->Ly) || !isfinite(d->Lz)) {
     why = "Lx, Ly, Lz must be finite and > 0";
     return true;
@@ -215,6 +231,31 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
     cudaFree(scan_tmp);
     if (e != cudaSuccess) return cuda_fail(e, "band lists");
   }
+  // each band list: CVs with a geometry record first, then the regular ones
+  // (levels at or above kxt), which take a shorter kernel; plane order kept
+  {
+    std::vector<int> kx(ncol);
+    std::vector<unsigned> bl, ord;
+    for (int q = 0; q < 4; ++q) {
+      GridDev &G = g->G[q];
+      G.nband_rec = 0;
+      if (G.nband == 0) continue;
+      bl.resize(G.nband);
+      CUDA_TRY(cudaMemcpy(bl.data(), G.blist, sizeof(unsigned) * G.nband, cudaMemcpyDeviceToHost), "read band list");
+      CUDA_TRY(cudaMemcpy(kx.data(), g->kxt[q], sizeof(int) * ncol, cudaMemcpyDeviceToHost), "read kxt");
+      ord.clear();
+      for (int pass = 0; pass < 2; ++pass)
+        for (unsigned c : bl) {
+          const long long k = c / D.nxy, col = c % D.nxy;
+          if ((k < kx[col]) == (pass == 0)) ord.push_back(c);
+        }
+      for (unsigned c : bl) {
+        const long long k = c / D.nxy, col = c % D.nxy;
+        if (k < kx[col]) ++G.nband_rec;
+      }
+      CUDA_TRY(cudaMemcpy(G.blist, ord.data(), sizeof(unsigned) * G.nband, cudaMemcpyHostToDevice), "write band list");
+    }
+  }
   // faces whose provisional fluxes the near-EB path reads (they lie below
   // kfast + 2), and the dense arrays those fluxes are staged in
   {
@@ -265,6 +306,13 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
   CUDA_TRY(g->alloc((double **)&g->qhat, g->max_small), "alloc qhat");
   CUDA_TRY(g->alloc((double **)&g->sig, 3 * g->max_small), "alloc sig");
   CUDA_TRY(g->alloc((double **)&g->pval, g->max_small), "alloc pivot values");
+  g->sum_small = 2 * g->W[0].nsmall + g->W[1].nsmall + g->W[2].nsmall + g->W[3].nsmall;
+  CUDA_TRY(g->alloc((double **)&g->qhat5, g->sum_small), "alloc qhat");
+  CUDA_TRY(g->alloc((double **)&g->sig5, 3 * g->sum_small), "alloc sig");
+  CUDA_TRY(g->alloc((double **)&g->pval5, g->sum_small), "alloc pivot values");
+  CUDA_TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking), "side stream");
+  CUDA_TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming), "event");
+  CUDA_TRY(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming), "event");
   CUDA_TRY(fill_ref<double>(g, ref_rho, &g->ref_d[0], &g->ref_f[0], s), "reference");
   CUDA_TRY(fill_ref<double>(g, ref_rt, &g->ref_d[1], &g->ref_f[1], s), "reference");
   CUDA_TRY(g->alloc(&g->status, 1), "alloc status");
@@ -297,6 +345,8 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
     }
     g->info.cvs[q] = cvs;
     g->info.band_cvs[q] = band;
+    g->info.band_faces[q] = g->G[q].nface[0] + g->G[q].nface[1] + g->G[q].nface[2];
+    for (long long c = 0; c < ncol; ++c) g->kcov_max = std::max(g->kcov_max, kc[c]);
     const long long n = nrec[q];
     std::vector<double> al(n > 0 ? n : 1);
     std::vector<uint8_t> fl(n > 0 ? n : 1);
@@ -350,6 +400,7 @@ StepArgs<T> step_args(eb_geom g, void *const src[5], void *const base[5], void *
   for (int q = 0; q < 4; ++q) A.G[q] = g->G[q];
   A.status = g->status;
   A.copy_static = copy;
+  A.kcov_max = g->kcov_max;
   return A;
 }
 
@@ -368,11 +419,50 @@ void wsrd_field(eb_geom g, int field, T *u, cudaStream_t s) {
   launch_wsrd(R, s);
 }
 
+// Flux divergence and provisional update.  The near-EB kernels and the bulk
+// read the same input and write disjoint CVs, so the near-EB kernels run on
+// the handle's side stream alongside the bulk kernel.
+template <typename T>
+void flux_update(eb_geom g, const StepArgs<T> &A, cudaStream_t s) {
+  cudaEventRecord(g->ev_fork, s);
+  cudaStreamWaitEvent(g->side, g->ev_fork, 0);
+  launch_flux_band(A, g->side);
+  launch_flux_fast(A, s);
+  cudaEventRecord(g->ev_join, g->side);
+  cudaStreamWaitEvent(s, g->ev_join, 0);
+}
+
+// Redistribution of all five fields of a state in one pass of three kernels.
+template <typename T>
+void wsrd_all(eb_geom g, void *const out[5], cudaStream_t s) {
+  WsrdSet<T> S;
+  long long os = 0, oa = 0;
+  for (int f = 0; f < 5; ++f) {
+    const int grid = f <= 1 ? 0 : f - 1;
+    WsrdArgs<T> &R = S.f[f];
+    R.D = g->D;
+    R.W = g->W[grid];
+    R.u = (T *)out[f];
+    R.refd = f <= 1 ? g->ref_d[f] : nullptr;
+    R.dev = (T *)g->qhat5 + os;
+    R.pval = (T *)g->pval5 + os;
+    R.sig = (T *)g->sig5 + 3 * os;
+    R.status = g->status;
+    S.off_small[f] = os;
+    S.off_aff[f] = oa;
+    os += g->W[grid].nsmall;
+    oa += g->W[grid].naff;
+  }
+  S.off_small[5] = os;
+  S.off_aff[5] = oa;
+  launch_wsrd5(S, s);
+}
+
 template <typename T>
 void stage(eb_geom g, void *const src[5], void *const base[5], void *const out[5], double dt, int copy,
            cudaStream_t s) {
-  launch_flux_update(step_args<T>(g, src, base, out, dt, copy), s);
-  for (int f = 0; f < 5; ++f) wsrd_field<T>(g, f, (T *)out[f], s);
+  flux_update(g, step_args<T>(g, src, base, out, dt, copy), s);
+  wsrd_all<T>(g, out, s);
 }
 
 size_t field_count(const Dims &D, int f) { return (size_t)D.nxy * (D.nz + (f == 4 ? 1 : 0)); }
@@ -451,6 +541,17 @@ eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision
   g->D.dx = desc->Lx / desc->nx;
   g->D.dy = desc->Ly / desc->ny;
   g->D.dz = desc->Lz / desc->nz;
+  g->D.fnx.init((unsigned)desc->nx);
+  g->D.fny.init((unsigned)desc->ny);
+  g->D.fnxy.init((unsigned)g->D.nxy);
+  for (const FastDiv *f : {&g->D.fnx, &g->D.fny, &g->D.fnxy}) {   // spot check of the multipliers
+    const unsigned probe[6] = {0u, f->d - 1, f->d, 2 * f->d + 1, 0x7fffffffu, 0xffffffffu};
+    for (unsigned n : probe)
+      if (f->div(n) != n / f->d) {
+        delete g;
+        return fail(EB_ERR_INVALID_ARG, "internal: fixed-divisor multiplier check failed");
+      }
+  }
   g->D.idx = 1.0 / g->D.dx;
   g->D.idy = 1.0 / g->D.dy;
   g->D.idz = 1.0 / g->D.dz;
@@ -498,8 +599,8 @@ eb_status eb_flux_div(eb_geom geom, const eb_state *U, eb_state *dU, void *strea
   for (int f = 0; f < 5; ++f)
     for (int e = 0; e < 5; ++e)
       if (u[f] == d[e]) return fail(EB_ERR_INVALID_ARG, "U and dU overlap");
-  if (geom->prec == EB_F64) launch_flux_update(step_args<double>(geom, u, nullptr, d, 1.0, 1), as_stream(stream));
-  else launch_flux_update(step_args<float>(geom, u, nullptr, d, 1.0, 1), as_stream(stream));
+  if (geom->prec == EB_F64) flux_update(geom, step_args<double>(geom, u, nullptr, d, 1.0, 1), as_stream(stream));
+  else flux_update(geom, step_args<float>(geom, u, nullptr, d, 1.0, 1), as_stream(stream));
   CUDA_TRY(cudaGetLastError(), "flux divergence");
   return EB_OK;
 }
@@ -638,14 +739,14 @@ eb_status eb_step_profile(eb_geom geom, const eb_state *Un, eb_state *Unp1, doub
     cudaEventRecord(ev[1], s);
     launch_flux_band(A, s);
     cudaEventRecord(ev[2], s);
-    for (int f = 0; f < 5; ++f) wsrd_field<double>(geom, f, (double *)u1[f], s);
+    wsrd_all<double>(geom, u1, s);
   } else {
     StepArgs<float> A = step_args<float>(geom, u0, u0, u1, dt, 1);
     launch_flux_fast(A, s);
     cudaEventRecord(ev[1], s);
     launch_flux_band(A, s);
     cudaEventRecord(ev[2], s);
-    for (int f = 0; f < 5; ++f) wsrd_field<float>(geom, f, (float *)u1[f], s);
+    wsrd_all<float>(geom, u1, s);
   }
   cudaEventRecord(ev[3], s);
   cudaError_t e = cudaEventSynchronize(ev[3]);

@@ -437,8 +437,9 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
   if (!(isfinite(bad.x) && isfinite(bad.y))) atomicOr(A.status, EB_DEV_NUMERIC);
 }
 
-// Pass-through of the CVs no kernel updates: covered CVs and the two wall
-// levels of rho*w (or zeros when dU itself is written).
+// Pass-through of the CVs no kernel updates: covered CVs (levels below
+// kcov_max) and the two wall levels of rho*w (or zeros when dU itself is
+// written).
 template <typename T>
 __global__ void k_static(StepArgs<T> A) {
   const Dims &D = A.D;
@@ -456,7 +457,7 @@ __global__ void k_static(StepArgs<T> A) {
   if (k < A.G[1].kcov[col]) put(2, c);
   if (k < A.G[2].kcov[col]) put(3, c);
   if (k < A.G[3].kcov[col] || k == 0) put(4, c);
-  if (k == D.nz - 1) put(4, lin(D, i, j, D.nz));
+  if (k == 0) put(4, lin(D, i, j, D.nz));
 }
 
 template <typename T, int V>
@@ -539,7 +540,7 @@ template <typename T>
 void launch_flux_fast(const StepArgs<T> &A, cudaStream_t s) {
   const Dims &D = A.D;
   if (A.copy_static) {
-    dim3 blk(32, 8, 1), grd((D.nx + 31) / 32, (D.ny + 7) / 8, D.nz);
+    dim3 blk(32, 8, 1), grd((D.nx + 31) / 32, (D.ny + 7) / 8, std::max(1, std::min(D.nz, A.kcov_max)));
     k_static<T><<<grd, blk, 0, s>>>(A);
   }
   // 16-byte copies and pair stores need every row of every field to start on

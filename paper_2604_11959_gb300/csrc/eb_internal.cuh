@@ -44,10 +44,34 @@ struct GridDev {
   // state indices in plane-major order
   unsigned *blist;
   long long nband;
+  long long nband_rec;   // blist[0, nband_rec): CVs with a record; the rest are regular
   // redistribution per record
   uint8_t *code;
   int *nnb;
   double *kappa, *omega, *vhat, *xhat;   // xhat: 3*nrec
+};
+
+// Quotient of a 32-bit unsigned n by a divisor d fixed on the host, with one
+// high multiply: q = (umulhi(n, m) + n) >> s, where s = ceil(log2 d) and
+// m = floor(2^32 (2^s - d) / d) + 1 (the round-up multiplier of Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994);
+// exact for every n < 2^32 with the 33-bit sum taken in 64 bits.
+struct FastDiv {
+  unsigned d = 1, m = 1, s = 0;
+  __host__ void init(unsigned dd) {
+    d = dd;
+    s = 0;
+    while ((1ull << s) < (unsigned long long)dd) ++s;
+    m = (unsigned)((((1ull << s) - dd) << 32) / dd + 1);
+  }
+  __host__ __device__ inline unsigned div(unsigned n) const {
+#ifdef __CUDA_ARCH__
+    const unsigned hi = __umulhi(n, m);
+#else
+    const unsigned hi = (unsigned)(((unsigned long long)n * m) >> 32);
+#endif
+    return (unsigned)(((unsigned long long)hi + n) >> s);
+  }
 };
 
 struct Dims {
@@ -55,7 +79,17 @@ struct Dims {
   long long nxy;
   double dx, dy, dz;
   double idx, idy, idz;   // 1/dx, 1/dy, 1/dz (set on the host with the spacings)
+  FastDiv fnx, fny, fnxy; // division by nx, ny, nx*ny (state indices are < 2^32)
 };
+
+// (i, j, k) of a state index c of any grid
+__device__ inline void split_index(const Dims &D, unsigned c, int &i, int &j, int &k) {
+  const unsigned kk = D.fnxy.div(c), col = c - kk * (unsigned)D.nxy;
+  const unsigned jj = D.fnx.div(col);
+  i = (int)(col - jj * (unsigned)D.nx);
+  j = (int)jj;
+  k = (int)kk;
+}
 
 // Periodic index for offsets of at most n from [0, n) (every stencil here
 // reaches a few cells and n >= 4 ... the set-up code uses full modulo).

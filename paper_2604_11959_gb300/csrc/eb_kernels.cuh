@@ -30,6 +30,9 @@ struct WsrdDev {
   int *w_sid = nullptr;           // [nw] small CV r whose neighbourhood holds the CV
   double *w_k = nullptr;          // [nw] kappa_r / N_i
   double *w_e = nullptr;          // [3 * nw] x_i - xhat_r (cell units, relative to r)
+  // float copies of the weight tables for the mixed-precision path
+  float *s_mw_f = nullptr, *s_me_f = nullptr, *l_c_f = nullptr, *a_eself_f = nullptr, *w_k_f = nullptr,
+        *w_e_f = nullptr;
 };
 
 // eb_geom.cu

@@ -195,12 +195,28 @@ __global__ void k_face_flux(StepArgs<T> A) {
     if (d < 3) break;
   }
   if (g >= 4) return;
-  const long long c = A.G[g].flist[d][t];
-  const int i = (int)(c % D.nx), j = (int)((c / D.nx) % D.ny), k = (int)(c / D.nxy);
+  const unsigned c = A.G[g].flist[d][t];
+  int i, j, k;
+  split_index(D, c, i, j, k);
   GeoBand geo;
   geo.G = A.G;
   T fm, fp;
-  face_flux(A.src, geo, D, g, d, i, j, k, fm, fp);
+  // one compiled copy per (grid, direction): the generic flux code folds
+  // to the staggering of that pair
+  switch (g * 3 + d) {
+    case 0: face_flux(A.src, geo, D, 0, 0, i, j, k, fm, fp); break;
+    case 1: face_flux(A.src, geo, D, 0, 1, i, j, k, fm, fp); break;
+    case 2: face_flux(A.src, geo, D, 0, 2, i, j, k, fm, fp); break;
+    case 3: face_flux(A.src, geo, D, 1, 0, i, j, k, fm, fp); break;
+    case 4: face_flux(A.src, geo, D, 1, 1, i, j, k, fm, fp); break;
+    case 5: face_flux(A.src, geo, D, 1, 2, i, j, k, fm, fp); break;
+    case 6: face_flux(A.src, geo, D, 2, 0, i, j, k, fm, fp); break;
+    case 7: face_flux(A.src, geo, D, 2, 1, i, j, k, fm, fp); break;
+    case 8: face_flux(A.src, geo, D, 2, 2, i, j, k, fm, fp); break;
+    case 9: face_flux(A.src, geo, D, 3, 0, i, j, k, fm, fp); break;
+    case 10: face_flux(A.src, geo, D, 3, 1, i, j, k, fm, fp); break;
+    default: face_flux(A.src, geo, D, 3, 2, i, j, k, fm, fp); break;
+  }
   ((T *)A.G[g].fh[d])[c] = fp;
   if (A.G[g].fhm[d]) ((T *)A.G[g].fhm[d])[c] = fm;
 }
@@ -213,13 +229,66 @@ __global__ void k_band(StepArgs<T> A) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int g = 0;
   for (g = 0; g < 4; ++g) {
-    if (t < A.G[g].nband) break;
-    t -= A.G[g].nband;
+    if (t < A.G[g].nband_rec) break;
+    t -= A.G[g].nband_rec;
   }
   if (g >= 4) return;
-  const long long c = A.G[g].blist[t];
-  const int i = (int)(c % D.nx), j = (int)((c / D.nx) % D.ny), k = (int)(c / D.nxy);
-  band_cv(A, g, i, j, k);
+  const unsigned c = A.G[g].blist[t];
+  int i, j, k;
+  split_index(D, c, i, j, k);
+  switch (g) {   // one compiled copy per grid
+    case 0: band_cv(A, 0, i, j, k); break;
+    case 1: band_cv(A, 1, i, j, k); break;
+    case 2: band_cv(A, 2, i, j, k); break;
+    default: band_cv(A, 3, i, j, k); break;
+  }
+}
+
+// Near-EB CVs without a geometry record are regular: every face is open
+// with its centroid at the face centre, so the divergence is the difference
+// of the staged face fluxes (the sums of band_divergence with beta = 1).
+template <typename T>
+__global__ void k_band_regular(StepArgs<T> A) {
+  const Dims &D = A.D;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int g = 0;
+  for (g = 0; g < 4; ++g) {
+    const long long n = A.G[g].nband - A.G[g].nband_rec;
+    if (t < n) break;
+    t -= n;
+  }
+  if (g >= 4) return;
+  const unsigned c = A.G[g].blist[A.G[g].nband_rec + t];
+  int i, j, k;
+  split_index(D, c, i, j, k);
+  const T inv[3] = {T(D.idx), T(D.idy), T(D.idz)};
+  T sm = T(0), sp = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int di = d == 0, dj = d == 1, dk = d == 2;
+    const T *FH = (const T *)A.G[g].fh[d];
+    const T *FM = (const T *)A.G[g].fhm[d];
+    const T bl = (g != 3 && d == 2 && k == 0) ? T(0) : T(1);
+    const T bh = high_face_exists(D, g, d, k) ? T(1) : T(0);
+    T ml = T(0), pl = T(0), mh = T(0), ph = T(0);
+    if (bl > T(0)) {
+      pl = FH[c];
+      if (FM) ml = FM[c];
+    }
+    if (bh > T(0)) {
+      const long long n = lin(D, i + di, j + dj, k + dk);
+      ph = FH[n];
+      if (FM) mh = FM[n];
+    }
+    sm += (bh * mh - bl * ml) * inv[d];
+    sp += (bh * ph - bl * pl) * inv[d];
+  }
+  if (g == 0) {
+    write_out(A, 0, c, -sm);
+    write_out(A, 1, c, -sp);
+  } else {
+    write_out(A, g + 1, c, -sp);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -240,7 +309,7 @@ template <typename T>
 __device__ inline T vdiff(const WsrdArgs<T> &R, long long a, long long b) {
   T d = R.u[a] - R.u[b];
   if (R.refd) {
-    const long long ka = a / R.D.nxy, kb = b / R.D.nxy;
+    const unsigned ka = R.D.fnxy.div((unsigned)a), kb = R.D.fnxy.div((unsigned)b);
     if (ka != kb) d += (T)(R.refd[ka] - R.refd[kb]);
   }
   return d;
@@ -251,10 +320,22 @@ template <typename T>
 __device__ inline T vdiff_vals(const WsrdArgs<T> &R, T va, long long a, T vb, long long b) {
   T d = va - vb;
   if (R.refd) {
-    const long long ka = a / R.D.nxy, kb = b / R.D.nxy;
+    const unsigned ka = R.D.fnxy.div((unsigned)a), kb = R.D.fnxy.div((unsigned)b);
     if (ka != kb) d += (T)(R.refd[ka] - R.refd[kb]);
   }
   return d;
+}
+
+// A weight table in the state's precision (float copies on the mixed path).
+template <typename T>
+__device__ inline const T *tab(const double *d, const float *f);
+template <>
+__device__ inline const double *tab<double>(const double *d, const float *) {
+  return d;
+}
+template <>
+__device__ inline const float *tab<float>(const double *, const float *f) {
+  return f;
 }
 
 // Kahan-compensated running sum in float; plain in double.
@@ -275,15 +356,13 @@ struct CompSum<double> {
 };
 
 template <typename T>
-__global__ void k_qhat(WsrdArgs<T> R) {
-  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (s >= R.W.nsmall) return;
+__device__ inline void qhat_one(const WsrdArgs<T> &R, long long s) {
   const int n = R.W.s_nmem[s], p = R.W.s_piv[s];
   const long long lp = R.W.s_mlin[8 * s + p];
   CompSum<T> acc;
   for (int q = 0; q < n; ++q) {
     if (q == p) continue;
-    acc.add((T)R.W.s_mw[8 * s + q] * vdiff(R, R.W.s_mlin[8 * s + q], lp));
+    acc.add(tab<T>(R.W.s_mw, R.W.s_mw_f)[8 * s + q] * vdiff(R, R.W.s_mlin[8 * s + q], lp));
   }
   R.dev[s] = acc.s;
   R.pval[s] = R.u[lp];   // snapshot: the final update overwrites the field in place
@@ -293,10 +372,7 @@ __global__ void k_qhat(WsrdArgs<T> R) {
 // and the stencil's range of Qhat - Qhat_r; lane 0 applies the limiter at the
 // members' centroids.
 template <typename T>
-__global__ void k_sigma(WsrdArgs<T> R) {
-  const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (s >= R.W.nsmall) return;
+__device__ inline void sigma_one(const WsrdArgs<T> &R, long long s, int lane) {
   const long long o0 = R.W.s_loff[s], o1 = R.W.s_loff[s + 1];
   const long long pr = R.W.s_mlin[8 * s + R.W.s_piv[s]];
   const T dr = R.dev[s];
@@ -313,9 +389,10 @@ __global__ void k_sigma(WsrdArgs<T> R) {
       dm = T(0);
     }
     const T b = vdiff(R, pm, pr) + (dm - dr);
-    sx += (T)R.W.l_c[3 * o] * b;
-    sy += (T)R.W.l_c[3 * o + 1] * b;
-    sz += (T)R.W.l_c[3 * o + 2] * b;
+    const T *lc = tab<T>(R.W.l_c, R.W.l_c_f) + 3 * o;
+    sx += lc[0] * b;
+    sy += lc[1] * b;
+    sz += lc[2] * b;
     bmax = b > bmax ? b : bmax;
     bmin = b < bmin ? b : bmin;
   }
@@ -333,8 +410,8 @@ __global__ void k_sigma(WsrdArgs<T> R) {
   if (o1 > o0) {
     const int n = R.W.s_nmem[s];
     for (int q = 0; q < n; ++q) {
-      const double *e = R.W.s_me + 24 * s + 3 * q;
-      const T del = sx * (T)e[0] + sy * (T)e[1] + sz * (T)e[2];
+      const T *e = tab<T>(R.W.s_me, R.W.s_me_f) + 24 * s + 3 * q;
+      const T del = sx * e[0] + sy * e[1] + sz * e[2];
       T ph = T(1);
       if (del > T(0)) ph = bmax / del;
       else if (del < T(0)) ph = bmin / del;
@@ -351,9 +428,7 @@ __global__ void k_sigma(WsrdArgs<T> R) {
 // small CV and Uhat_i otherwise: Eq. final_update_omega with omega_i written
 // as 1 - sum_r kappa_r / N_i.  Formed as an offset added to Uhat_i.
 template <typename T>
-__global__ void k_final(WsrdArgs<T> R) {
-  const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (a >= R.W.naff) return;
+__device__ inline void final_one(const WsrdArgs<T> &R, long long a) {
   const long long c = R.W.a_lin[a];
   const int sid = R.W.a_sid[a];
   // every value this thread reads besides its own CV comes from the
@@ -362,8 +437,8 @@ __global__ void k_final(WsrdArgs<T> R) {
   T si = T(0), di = T(0), pvi = ui;
   long long pi = c;
   if (sid >= 0) {
-    const double *e = R.W.a_eself + 3 * a;
-    si = R.sig[3 * sid] * (T)e[0] + R.sig[3 * sid + 1] * (T)e[1] + R.sig[3 * sid + 2] * (T)e[2];
+    const T *e = tab<T>(R.W.a_eself, R.W.a_eself_f) + 3 * a;
+    si = R.sig[3 * sid] * e[0] + R.sig[3 * sid + 1] * e[1] + R.sig[3 * sid + 2] * e[2];
     pi = R.W.s_mlin[8 * (long long)sid + R.W.s_piv[sid]];
     pvi = R.pval[sid];
     di = R.dev[sid];
@@ -371,11 +446,11 @@ __global__ void k_final(WsrdArgs<T> R) {
   CompSum<T> acc;
   for (long long o = R.W.a_woff[a]; o < R.W.a_woff[a + 1]; ++o) {
     const int r = R.W.w_sid[o];
-    const double *e = R.W.w_e + 3 * o;
+    const T *e = tab<T>(R.W.w_e, R.W.w_e_f) + 3 * o;
     const long long pr = R.W.s_mlin[8 * (long long)r + R.W.s_piv[r]];
-    const T sr = R.sig[3 * r] * (T)e[0] + R.sig[3 * r + 1] * (T)e[1] + R.sig[3 * r + 2] * (T)e[2];
+    const T sr = R.sig[3 * r] * e[0] + R.sig[3 * r + 1] * e[1] + R.sig[3 * r + 2] * e[2];
     const T diff = vdiff_vals(R, R.pval[r], pr, pvi, pi) + (R.dev[r] - di) + (sr - si);
-    acc.add((T)R.W.w_k[o] * diff);
+    acc.add(tab<T>(R.W.w_k, R.W.w_k_f)[o] * diff);
   }
   // a small CV's result is anchored at its pivot value: its own provisional
   // value can be huge (tiny cell after the flux update) and must not be added
@@ -384,7 +459,7 @@ __global__ void k_final(WsrdArgs<T> R) {
   if (sid >= 0) {
     T anchor = pvi;
     if (R.refd) {
-      const long long kp = pi / R.D.nxy, kc = c / R.D.nxy;
+      const unsigned kp = R.D.fnxy.div((unsigned)pi), kc = R.D.fnxy.div((unsigned)c);
       if (kp != kc) anchor += (T)(R.refd[kp] - R.refd[kc]);
     }
     v = anchor + ((di + si) + acc.s);
@@ -395,6 +470,52 @@ __global__ void k_final(WsrdArgs<T> R) {
   if (!finite_val(v)) atomicOr(R.status, EB_DEV_NUMERIC);
 }
 
+// one field
+template <typename T>
+__global__ void k_qhat(WsrdArgs<T> R) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s < R.W.nsmall) qhat_one(R, s);
+}
+template <typename T>
+__global__ void k_sigma(WsrdArgs<T> R) {
+  const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (s < R.W.nsmall) sigma_one(R, s, threadIdx.x & 31);
+}
+template <typename T>
+__global__ void k_final(WsrdArgs<T> R) {
+  const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (a < R.W.naff) final_one(R, a);
+}
+
+// all five fields in one launch: work item t belongs to the field f with
+// off[f] <= t < off[f + 1]
+__device__ inline int field_of(const long long off[6], long long t) {
+  int f = 0;
+  while (f < 4 && t >= off[f + 1]) ++f;
+  return f;
+}
+template <typename T>
+__global__ void k_qhat5(const __grid_constant__ WsrdSet<T> S) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= S.off_small[5]) return;
+  const int f = field_of(S.off_small, t);
+  qhat_one(S.f[f], t - S.off_small[f]);
+}
+template <typename T>
+__global__ void k_sigma5(const __grid_constant__ WsrdSet<T> S) {
+  const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (t >= S.off_small[5]) return;
+  const int f = field_of(S.off_small, t);
+  sigma_one(S.f[f], t - S.off_small[f], threadIdx.x & 31);
+}
+template <typename T>
+__global__ void k_final5(const __grid_constant__ WsrdSet<T> S) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= S.off_aff[5]) return;
+  const int f = field_of(S.off_aff, t);
+  final_one(S.f[f], t - S.off_aff[f]);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -402,13 +523,15 @@ __global__ void k_final(WsrdArgs<T> R) {
 // ---------------------------------------------------------------------------
 template <typename T>
 void launch_flux_band(const StepArgs<T> &A, cudaStream_t s) {
-  long long nf = 0, nb = 0;
+  long long nf = 0, nb = 0, nr = 0;
   for (int g = 0; g < 4; ++g) {
-    nb += A.G[g].nband;
+    nb += A.G[g].nband_rec;
+    nr += A.G[g].nband - A.G[g].nband_rec;
     for (int d = 0; d < 3; ++d) nf += A.G[g].nface[d];
   }
   if (nf) k_face_flux<T><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(A);
   if (nb) k_band<T><<<(unsigned)((nb + 127) / 128), 128, 0, s>>>(A);
+  if (nr) k_band_regular<T><<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(A);
 }
 
 template <typename T>
@@ -426,7 +549,18 @@ void launch_wsrd(const WsrdArgs<T> &R, cudaStream_t s) {
   if (R.W.naff) k_final<T><<<(unsigned)((R.W.naff + 127) / 128), 128, 0, s>>>(R);
 }
 
+template <typename T>
+void launch_wsrd5(const WsrdSet<T> &S, cudaStream_t s) {
+  if (S.off_small[5]) {
+    k_qhat5<T><<<(unsigned)((S.off_small[5] + 127) / 128), 128, 0, s>>>(S);
+    k_sigma5<T><<<(unsigned)((S.off_small[5] * 32 + 255) / 256), 256, 0, s>>>(S);
+  }
+  if (S.off_aff[5]) k_final5<T><<<(unsigned)((S.off_aff[5] + 127) / 128), 128, 0, s>>>(S);
+}
+
 template void launch_flux_update<double>(const StepArgs<double> &, cudaStream_t);
+template void launch_wsrd5<double>(const WsrdSet<double> &, cudaStream_t);
+template void launch_wsrd5<float>(const WsrdSet<float> &, cudaStream_t);
 template void launch_flux_band<double>(const StepArgs<double> &, cudaStream_t);
 template void launch_flux_band<float>(const StepArgs<float> &, cudaStream_t);
 template void launch_flux_update<float>(const StepArgs<float> &, cudaStream_t);

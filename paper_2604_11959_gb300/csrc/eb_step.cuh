@@ -15,6 +15,7 @@ struct StepArgs {
   GridDev G[4];
   unsigned *status;
   int copy_static;     // also write covered CVs and the w wall levels
+  int kcov_max;        // highest covered level + 1 over every grid and column
   // work split of the bulk kernel: CTA b marches the pieces boff[b] .. boff[b+1]-1
   // of bseg, each (tile, first level, end level, 0)
   const int4 *bseg;
@@ -34,6 +35,16 @@ struct WsrdArgs {
   unsigned *status;
 };
 
+// the redistribution of all five fields in one pass: f[q] is field q, and
+// its small CVs (affected CVs) are the work items off_small[q] .. off_small[q+1]-1
+// (off_aff[q] ..) of each fused launch
+template <typename T>
+struct WsrdSet {
+  WsrdArgs<T> f[5];
+  long long off_small[6];
+  long long off_aff[6];
+};
+
 template <typename T>
 void launch_flux_update(const StepArgs<T> &A, cudaStream_t s);
 template <typename T>
@@ -43,3 +54,5 @@ void launch_flux_band(const StepArgs<T> &A, cudaStream_t s);
 
 template <typename T>
 void launch_wsrd(const WsrdArgs<T> &R, cudaStream_t s);
+template <typename T>
+void launch_wsrd5(const WsrdSet<T> &S, cudaStream_t s);

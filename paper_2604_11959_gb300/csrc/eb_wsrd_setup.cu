@@ -457,6 +457,11 @@ __global__ void k_aff_fill(Dims D, int g, GridDev G, const long long *aff_id, Ws
   }
 }
 
+__global__ void k_to_float(const double *src, float *dst, long long n) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) dst[t] = (float)src[t];
+}
+
 inline int cols_blocks(const Dims &D) { return (D.nx * D.ny + 127) / 128; }
 inline int lin_blocks(long long n) { return (int)((n + 127) / 128); }
 
@@ -534,6 +539,18 @@ cudaError_t build_wsrd(const Dims &D, int g, GridDev &G, const GridDev *all, dou
   CK(dalloc(&W.w_k, W.nw));
   CK(dalloc(&W.w_e, 3 * W.nw));
   k_aff_fill<<<cb, 128, 0, s>>>(D, g, G, aff_id, W);
+  // float copies of the weight tables (mixed-precision path)
+  const struct {
+    const double *src;
+    float **dst;
+    long long n;
+  } tabs[6] = {{W.s_mw, &W.s_mw_f, 8 * W.nsmall}, {W.s_me, &W.s_me_f, 24 * W.nsmall},
+               {W.l_c, &W.l_c_f, 3 * W.nlsq},     {W.a_eself, &W.a_eself_f, 3 * W.naff},
+               {W.w_k, &W.w_k_f, W.nw},           {W.w_e, &W.w_e_f, 3 * W.nw}};
+  for (const auto &t : tabs) {
+    CK(dalloc(t.dst, t.n));
+    if (t.n > 0) k_to_float<<<lin_blocks(t.n), 128, 0, s>>>(t.src, *t.dst, t.n);
+  }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   return cudaSuccess;
@@ -541,7 +558,8 @@ cudaError_t build_wsrd(const Dims &D, int g, GridDev &G, const GridDev *all, dou
 
 void free_wsrd(WsrdDev &W) {
   void *ptrs[] = {W.sid, W.s_lin, W.s_rec, W.s_nmem, W.s_piv, W.s_mlin, W.s_mw, W.s_me, W.s_loff, W.l_lin,
-                  W.l_sid, W.l_c, W.a_lin, W.a_sid, W.a_eself, W.a_woff, W.w_sid, W.w_k, W.w_e};
+                  W.l_sid, W.l_c, W.a_lin, W.a_sid, W.a_eself, W.a_woff, W.w_sid, W.w_k, W.w_e,
+                  W.s_mw_f, W.s_me_f, W.l_c_f, W.a_eself_f, W.w_k_f, W.w_e_f};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   W = WsrdDev();

@@ -46,7 +46,8 @@ class _State(ctypes.Structure):
 class GeomInfo(ctypes.Structure):
     _fields_ = [("cells", ctypes.c_int64), ("cvs", ctypes.c_int64 * 4), ("band_records", ctypes.c_int64 * 4),
                 ("small_cvs", ctypes.c_int64 * 4), ("affected_cvs", ctypes.c_int64 * 4),
-                ("band_cvs", ctypes.c_int64 * 4), ("tiny_cvs", ctypes.c_int64 * 4), ("fast_cells", ctypes.c_int64),
+                ("band_cvs", ctypes.c_int64 * 4), ("band_faces", ctypes.c_int64 * 4),
+                ("tiny_cvs", ctypes.c_int64 * 4), ("fast_cells", ctypes.c_int64),
                 ("min_alpha", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64)]
 
