@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("hill256", "grf512"), default="hill256")
+    ap.add_argument("--workload", choices=("hill256", "grf512", "ensemble"), default="hill256",
+                    help="ensemble: 64 uneven Gaussian-hill instances advanced together (mixed path)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--precision", choices=("both", "mixed", "f64"), default="both",
                     help="arms to run (profiling runs pick one)")
@@ -51,7 +52,63 @@ def parse():
 
 def workload(name):
     from paper_2604_11959_gb300 import inputs
-    return {"hill256": inputs.HILL_256, "grf512": inputs.GRF_512}[name]
+    return {"hill256": inputs.HILL_256, "grf512": inputs.GRF_512, "ensemble": inputs.HILL_256}[name]
+
+
+def run_ensemble(eb, steps, warmup):
+    """64 uneven Gaussian-hill instances (64x64x32 .. 256x256x64, 94,371,840
+    cells), mixed path, advanced together: one CUDA-graph launch per step,
+    slab heights chosen by the autotuner.  The states (3.8 GB) exceed L2,
+    so no flush is needed between steps."""
+    import torch
+    from paper_2604_11959_gb300 import inputs
+    geoms, states, dts, cells, fast_bytes = [], [], [], 0, 0
+    for b, (n, _, nz, h0, sig) in enumerate(inputs.ensemble_members()):
+        w = inputs.Workload(f"hill-{b}", n, n, nz, 100, terrain="gaussian", hmax=h0)
+        h = inputs.gaussian_hill(n, n, h0=h0, sigma=sig)
+        refs = inputs.cell_reference(nz, w.Lz)
+        g = eb.Geometry(n, n, nz, w.Lx, w.Ly, w.Lz, torch.from_numpy(h).cuda(), precision="mixed",
+                        ref_rho=torch.from_numpy(refs[0]).cuda(), ref_rhotheta=torch.from_numpy(refs[1]).cuda())
+        geoms.append(g)
+        states.append(eb.device_state(w.state("sheltered", seed=b), "mixed", refs))
+        dts.append(w.dt())
+        cells += w.cells()
+        fast_bytes += g.info()["fast_cells"] * 10 * 4
+    ens = eb.Ensemble(geoms)
+    for q, U in enumerate(states):
+        ens.set_state(q, U)
+    slab = ens.tune(dts, reps=2)
+    for q, U in enumerate(states):
+        ens.set_state(q, U)
+    ens.step(dts, warmup)
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for q in range(steps):
+        evs[q][0].record(stream)
+        ens.step(dts, 1)
+        evs[q][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    for g in geoms:
+        eb.sync_status(g)
+    # the dominant kernel: each member's bulk kernel timed alone
+    bulk_ms = 0.0
+    for g, U, dt in zip(geoms, states, dts):
+        prof = [eb.step_profile(g, U, g.empty_state(), dt)[0] for _ in range(3)]
+        bulk_ms += float(np.median(prof))
+    ens.close()
+    for g in geoms:
+        g.close()
+    hbm, kind = peaks()
+    achieved = fast_bytes / (bulk_ms * 1e-3) / 1e9
+    launches = 7 * len(geoms)   # per member and step: bulk, 3 near-EB, 3 redistribution kernels
+    return {"value": cells / (ms * 1e-3), "ms_per_step": ms, "cells": cells, "members": len(geoms),
+            "slab_levels": slab,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": "k_fast_tiled (each member alone, summed)",
+                         "algorithmic_bytes_per_launch": fast_bytes, "peak_kind": kind},
+            "gpu_launches": launches * steps}
 
 
 def peaks():
@@ -246,6 +303,40 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist):
     return geom, res
 
 
+def accuracy(eb, w, h, U, refs, nsteps):
+    """Error of the mixed path against the FP64 path after nsteps steps from
+    the same state (the FP64 path itself agrees with the FP64 CPU oracle to
+    1e-12, which the parity tests check): relative L-inf error per field,
+    max |mixed - f64| / max |f64| over full values (reference added back),
+    for the three-stage Runge-Kutta form (Sec. 5.2, stable at CFL 0.5) and
+    for forward Euler (Sec. 3.1), whose amplification of the shortest waves
+    (about 9% per step at CFL 0.5) magnifies the float rounding."""
+    import torch
+    rr = torch.from_numpy(refs[0]).cuda()[:, None, None]
+    rt = torch.from_numpy(refs[1]).cuda()[:, None, None]
+    res = {"steps": nsteps, "reference": "FP64 GPU path"}
+    for stages, key in ((3, "rk3"), (1, "forward_euler")):
+        out = {}
+        for prec in ("mixed", "f64"):
+            geom = eb.Geometry(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, torch.from_numpy(h).cuda(), precision=prec,
+                               ref_rho=torch.from_numpy(refs[0]).cuda(),
+                               ref_rhotheta=torch.from_numpy(refs[1]).cuda())
+            r = eb.step(geom, eb.device_state(U, prec, refs), w.dt(), nsteps, stages=stages)
+            eb.sync_status(geom)
+            out[prec] = {f: r[f].double() for f in FIELDS}
+            geom.close()
+        err = {}
+        for f in FIELDS:
+            a, b = out["mixed"][f], out["f64"][f]
+            if f == "rho":
+                a, b = a + rr, b + rr
+            elif f == "rhotheta":
+                a, b = a + rt, b + rt
+            err[f] = float((a - b).abs().max() / b.abs().max())
+        res[key] = {"rel_linf_vs_f64": err}
+    return res
+
+
 def e2e(eb, geom, w, U, refs, precision, steps):
     """Same metric through the public API with host buffers: every step
     copies the state from pinned host memory to the device, advances it, and
@@ -298,6 +389,26 @@ def main():
                                   "d2h_bytes_per_step": 0}}))
         return 0
     import torch
+    if args.workload == "ensemble":
+        from paper_2604_11959_gb300 import build as libbuild, eb
+        libbuild.build()
+        eb.load()
+        clk = ClockSampler(torch.cuda.current_device())
+        with clk:
+            r = run_ensemble(eb, args.steps, max(3, args.warmup))
+        if rank == 0:
+            print(json.dumps({
+                "metric": METRIC, "value": r["value"] * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "ensemble-64-gaussian-hills", "cells": r["cells"], "members": r["members"],
+                           "precision": "mixed", "stages": 1, "tuned_slab_levels": r["slab_levels"],
+                           "launch": "one CUDA-graph launch per step of all members",
+                           "l2": "inputs (3.8 GB of state) larger than L2",
+                           "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+                "roofline": r["roofline"], "gpu_launches": r["gpu_launches"], "clocks": clk.summary(),
+                "cpu_baseline": None, "e2e": None}))
+        return 0
     dist = None
     if world > 1:
         import torch.distributed as tdist
@@ -323,6 +434,9 @@ def main():
     if args.precision in ("both", "f64"):
         geom64, f64 = run_precision(eb, w, h, U, refs, "f64", max(10, args.steps // 10), args.warmup, world, dist)
         geom64.close()
+    acc = None
+    if rank == 0 and args.precision == "both":
+        acc = accuracy(eb, w, h, U, refs, w.steps)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline(w)
@@ -349,6 +463,8 @@ def main():
         "geometry": {k: head["geometry"][k] for k in ("cells", "fast_cells", "band_cvs", "small_cvs",
                                                       "affected_cvs", "tiny_cvs", "min_alpha")},
     }
+    if acc:
+        line["accuracy"] = acc
     if mixed and f64:
         line["fp64"] = {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "roofline": f64["roofline"],
                         "step_hbm_frac": f64["step_frac"], "phases_ms": f64["phases_ms"], "steps": f64["steps"]}

@@ -229,11 +229,54 @@ eb_status eb_step(eb_geom geom, const eb_state *Un, eb_state *Unp1, double dt, i
  * One forward-Euler step exactly like eb_step(nsteps = 1, stages = 1), with
  * CUDA events recorded on the stream between its phases.  On return (the
  * stream is synchronised) ms[0] holds the geometry-free bulk flux/update
- * kernel, ms[1] the near-EB flux/update kernel, ms[2] the redistribution
- * passes of all five fields and ms[3] the whole step, in milliseconds.
+ * kernel, ms[1] the near-EB flux/update kernels, ms[2] the redistribution
+ * passes of all five fields and ms[3] the three together, in milliseconds
+ * (the pass-through of covered CVs runs before the first event).  The
+ * phases run one after another here, while eb_step overlaps the first two.
  * Used by benchmarks to time the dominant kernel on its own stream.
  */
 eb_status eb_step_profile(eb_geom geom, const eb_state *Un, eb_state *Unp1, double dt, void *stream, float ms[4]);
+
+/*
+ * Ensembles: many independent terrain instances advanced together.  The
+ * paper has no counterpart (its AMReX box arrays are the closest); this is
+ * the batched serving form of eb_step.
+ *
+ * An ensemble refers to member handles of any sizes, all of one precision
+ * and on the current device; it does not own them (destroy the ensemble
+ * first).  It owns two state buffers per member.  Every step of every member
+ * is forward Euler (Eq. basic_fv_srd), exactly as eb_step(nsteps = 1,
+ * stages = 1) computes it.  One step of the whole ensemble is captured once
+ * as a CUDA graph, each member on its own branch so that the kernels of
+ * small members run side by side; eb_ensemble_step replays it.  Calls on one
+ * ensemble, and on its members' handles, must be serialised.
+ */
+typedef struct eb_ensemble_s *eb_ensemble;
+
+/* members: n handles (copied).  Allocates the state buffers. */
+eb_status eb_ensemble_create(const eb_geom *members, int n, eb_ensemble *out);
+
+/* Load member's state from U (device arrays of that member's sizes; copied
+ * on the stream).  Also fills the covered CVs of the second buffer. */
+eb_status eb_ensemble_set_state(eb_ensemble e, int member, const eb_state *U, void *stream);
+
+/* Copy member's current state into U (device arrays). */
+eb_status eb_ensemble_get_state(eb_ensemble e, int member, eb_state *U, void *stream);
+
+/* Advance every member nsteps steps; dt: host array of one time step per
+ * member.  The graph is captured on the first call and again whenever dt
+ * changes; capture may not already be active on the stream. */
+eb_status eb_ensemble_step(eb_ensemble e, const double *dt, int nsteps, void *stream);
+
+/* Autotuner: times 2 * reps ensemble steps for each candidate slab height
+ * of the bulk kernel's tiles (automatic, 8 .. 64 levels, whole column) and
+ * keeps the fastest for every member; *slab_levels (if not NULL) receives it
+ * (0 = automatic).  The loaded states are restored afterwards.  Synchronises
+ * the stream; allocates a temporary copy of the states. */
+eb_status eb_ensemble_tune(eb_ensemble e, const double *dt, int reps, int *slab_levels, void *stream);
+
+/* Waits for the device, then frees the ensemble's buffers. */
+eb_status eb_ensemble_destroy(eb_ensemble e);
 
 /* Synchronise the stream, then return (and clear) the first device-side
  * error latched since the last call: EB_ERR_NUMERIC or EB_ERR_TIMEOUT. */

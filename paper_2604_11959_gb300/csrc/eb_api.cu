@@ -1,6 +1,6 @@
 // eb_api.cu -- the C ABI of include/eb.h: argument checks, the geometry
 // handle, and the orchestration of the kernels on the caller's stream.
-#include "eb_step.cuh"
+#include "eb_handle.cuh"
 
 #include <math.h>
 #include <stdio.h>
@@ -14,89 +14,37 @@
 #define EB_VERSION_NUM 100
 
 namespace {
-
 thread_local std::string g_last_error;
-
-eb_status fail(eb_status st, const char *fmt, const char *arg = nullptr) {
-  char buf[512];
-  snprintf(buf, sizeof(buf), fmt, arg ? arg : "");
-  g_last_error = buf;
-  return st;
-}
-
-eb_status cuda_fail(cudaError_t e, const char *where) {
-  char buf[512];
-  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
-  g_last_error = buf;
-  return e == cudaErrorMemoryAllocation ? EB_ERR_OOM : EB_ERR_CUDA;
-}
-
-#define CUDA_TRY(x, where)                      \
-  do {                                          \
-    cudaError_t e_ = (x);                       \
-    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
-  } while (0)
-
-inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
-
 }  // namespace
 
-struct eb_geom_s {
-  eb_desc desc;
-  Dims D;
-  eb_precision prec;
-  int device = 0;
-  double *h = nullptr;
-  int *kcov[4] = {}, *kreg[4] = {}, *kxt[4] = {};
-  long long *roff[4] = {};
-  int *kfast = nullptr;
-  int4 *bseg = nullptr;   // bulk kernel work split
-  int *boff = nullptr;
-  int bctas = 0;
-  int kcov_max = 0;
-  GridDev G[4];
-  WsrdDev W[4];
-  double *ref_d[2] = {nullptr, nullptr};
-  float *ref_f[2] = {nullptr, nullptr};
-  double *zero_d = nullptr;
-  float *zero_f = nullptr;
-  unsigned *status = nullptr;
-  void *qhat = nullptr, *sig = nullptr, *pval = nullptr;
-  long long max_small = 0;
-  // scratch of the five-field redistribution pass (small CVs of all fields)
-  void *qhat5 = nullptr, *sig5 = nullptr, *pval5 = nullptr;
-  long long sum_small = 0;
-  // the near-EB kernels run on this stream, forked from and joined to the
-  // caller's stream around the bulk kernel
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  // scratch states for eb_step: 4 x 5 fields
-  void *scr[4][5] = {};
-  std::vector<void *> allocs;
-  eb_geom_info_t info;
+std::string &eb_error_slot() { return g_last_error; }
 
-  template <typename P>
-  cudaError_t alloc(P **p, long long count) {
-    *p = nullptr;
-    if (count < 1) count = 1;
-    cudaError_t e = cudaMalloc((void **)p, sizeof(P) * (size_t)count);
-    if (e == cudaSuccess) {
-      allocs.push_back((void *)*p);
-      info.device_bytes += (int64_t)(sizeof(P) * count);
-    }
-    return e;
+eb_status eb_replan_bulk(eb_geom g, int slab_levels) {
+  std::vector<int> seg, off;
+  CUDA_TRY(bulk_plan(g->D, g->kfast_host.data(), g->prec == EB_F64, slab_levels, seg, off), "bulk work split");
+  // the split arrays are small: the old ones are released right away
+  for (void *p : {(void *)g->bseg, (void *)g->boff}) {
+    if (!p) continue;
+    for (size_t q = 0; q < g->allocs.size(); ++q)
+      if (g->allocs[q] == p) {
+        g->allocs.erase(g->allocs.begin() + q);
+        break;
+      }
+    cudaFree(p);
   }
-  void release() {
-    if (ev_fork) cudaEventDestroy(ev_fork);
-    if (ev_join) cudaEventDestroy(ev_join);
-    if (side) cudaStreamDestroy(side);
-    ev_fork = ev_join = nullptr;
-    side = nullptr;
-    for (void *p : allocs) cudaFree(p);
-    allocs.clear();
-    for (int g = 0; g < 4; ++g) free_wsrd(W[g]);
-  }
-};
+  g->bseg = nullptr;
+  g->boff = nullptr;
+  g->slab_levels = slab_levels;
+  g->bctas = (int)off.size() - 1;
+  CUDA_TRY(g->alloc(&g->bseg, std::max<long long>(1, (long long)seg.size() / 4)), "alloc bulk split");
+  CUDA_TRY(g->alloc(&g->boff, (long long)off.size()), "alloc bulk split");
+  if (!seg.empty())
+    CUDA_TRY(cudaMemcpy(g->bseg, seg.data(), sizeof(int) * seg.size(), cudaMemcpyHostToDevice), "copy bulk split");
+  CUDA_TRY(cudaMemcpy(g->boff, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice), "copy bulk split");
+  return EB_OK;
+}
+
+using namespace ebh;
 
 namespace {
 
@@ -320,15 +268,10 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
   // host-side counts for eb_geom_info
   std::vector<int> kc(ncol), kf(ncol);
   CUDA_TRY(cudaMemcpy(kf.data(), g->kfast, sizeof(int) * ncol, cudaMemcpyDeviceToHost), "read kfast");
+  g->kfast_host = kf;
   {
-    std::vector<int> seg, off;
-    CUDA_TRY(bulk_plan(D, kf.data(), g->prec == EB_F64, seg, off), "bulk work split");
-    g->bctas = (int)off.size() - 1;
-    CUDA_TRY(g->alloc(&g->bseg, std::max<long long>(1, (long long)seg.size() / 4)), "alloc bulk split");
-    CUDA_TRY(g->alloc(&g->boff, (long long)off.size()), "alloc bulk split");
-    if (!seg.empty())
-      CUDA_TRY(cudaMemcpy(g->bseg, seg.data(), sizeof(int) * seg.size(), cudaMemcpyHostToDevice), "copy bulk split");
-    CUDA_TRY(cudaMemcpy(g->boff, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice), "copy bulk split");
+    const eb_status st = eb_replan_bulk(g, 0);
+    if (st != EB_OK) return st;
   }
   g->info.cells = (int64_t)ncol * D.nz;
   g->info.fast_cells = 0;
@@ -365,107 +308,6 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
   return EB_OK;
 }
 
-bool state_ok(const eb_state *U, size_t align) {
-  if (!U) return false;
-  const void *p[5] = {U->rho, U->rhotheta, U->rhou, U->rhov, U->rhow};
-  for (const void *q : p)
-    if (!q || ((uintptr_t)q % align)) return false;
-  return true;
-}
-
-void **state_ptrs(const eb_state *U) { return (void **)&U->rho; }
-
-template <typename T>
-StepArgs<T> step_args(eb_geom g, void *const src[5], void *const base[5], void *const out[5], double dt, int copy) {
-  StepArgs<T> A;
-  A.D = g->D;
-  for (int f = 0; f < 5; ++f) {
-    A.src.f[f] = (const T *)src[f];
-    A.base[f] = base ? (const T *)base[f] : nullptr;
-    A.out[f] = (T *)out[f];
-  }
-  if (sizeof(T) == sizeof(double)) {
-    A.src.ref_rho = (const T *)g->ref_d[0];
-    A.src.ref_rt = (const T *)g->ref_d[1];
-  } else {
-    A.src.ref_rho = (const T *)g->ref_f[0];
-    A.src.ref_rt = (const T *)g->ref_f[1];
-  }
-  A.dt = dt;
-  A.dtT = (T)dt;
-  A.kfast = g->kfast;
-  A.bseg = g->bseg;
-  A.boff = g->boff;
-  A.bctas = g->bctas;
-  for (int q = 0; q < 4; ++q) A.G[q] = g->G[q];
-  A.status = g->status;
-  A.copy_static = copy;
-  A.kcov_max = g->kcov_max;
-  return A;
-}
-
-template <typename T>
-void wsrd_field(eb_geom g, int field, T *u, cudaStream_t s) {
-  const int grid = field <= 1 ? 0 : field - 1;
-  WsrdArgs<T> R;
-  R.D = g->D;
-  R.W = g->W[grid];
-  R.u = u;
-  R.refd = field <= 1 ? g->ref_d[field] : nullptr;
-  R.dev = (T *)g->qhat;
-  R.sig = (T *)g->sig;
-  R.pval = (T *)g->pval;
-  R.status = g->status;
-  launch_wsrd(R, s);
-}
-
-// Flux divergence and provisional update.  The near-EB kernels and the bulk
-// read the same input and write disjoint CVs, so the near-EB kernels run on
-// the handle's side stream alongside the bulk kernel.
-template <typename T>
-void flux_update(eb_geom g, const StepArgs<T> &A, cudaStream_t s) {
-  cudaEventRecord(g->ev_fork, s);
-  cudaStreamWaitEvent(g->side, g->ev_fork, 0);
-  launch_flux_band(A, g->side);
-  launch_flux_fast(A, s);
-  cudaEventRecord(g->ev_join, g->side);
-  cudaStreamWaitEvent(s, g->ev_join, 0);
-}
-
-// Redistribution of all five fields of a state in one pass of three kernels.
-template <typename T>
-void wsrd_all(eb_geom g, void *const out[5], cudaStream_t s) {
-  WsrdSet<T> S;
-  long long os = 0, oa = 0;
-  for (int f = 0; f < 5; ++f) {
-    const int grid = f <= 1 ? 0 : f - 1;
-    WsrdArgs<T> &R = S.f[f];
-    R.D = g->D;
-    R.W = g->W[grid];
-    R.u = (T *)out[f];
-    R.refd = f <= 1 ? g->ref_d[f] : nullptr;
-    R.dev = (T *)g->qhat5 + os;
-    R.pval = (T *)g->pval5 + os;
-    R.sig = (T *)g->sig5 + 3 * os;
-    R.status = g->status;
-    S.off_small[f] = os;
-    S.off_aff[f] = oa;
-    os += g->W[grid].nsmall;
-    oa += g->W[grid].naff;
-  }
-  S.off_small[5] = os;
-  S.off_aff[5] = oa;
-  launch_wsrd5(S, s);
-}
-
-template <typename T>
-void stage(eb_geom g, void *const src[5], void *const base[5], void *const out[5], double dt, int copy,
-           cudaStream_t s) {
-  flux_update(g, step_args<T>(g, src, base, out, dt, copy), s);
-  wsrd_all<T>(g, out, s);
-}
-
-size_t field_count(const Dims &D, int f) { return (size_t)D.nxy * (D.nz + (f == 4 ? 1 : 0)); }
 
 }  // namespace
 
@@ -732,17 +574,20 @@ eb_status eb_step_profile(eb_geom geom, const eb_state *Un, eb_state *Unp1, doub
   cudaStream_t s = as_stream(stream);
   cudaEvent_t ev[4];
   for (int q = 0; q < 4; ++q) CUDA_TRY(cudaEventCreate(&ev[q]), "event");
-  cudaEventRecord(ev[0], s);
   if (geom->prec == EB_F64) {
     StepArgs<double> A = step_args<double>(geom, u0, u0, u1, dt, 1);
-    launch_flux_fast(A, s);
+    launch_static_copy(A, s);
+    cudaEventRecord(ev[0], s);
+    launch_flux_bulk(A, s);
     cudaEventRecord(ev[1], s);
     launch_flux_band(A, s);
     cudaEventRecord(ev[2], s);
     wsrd_all<double>(geom, u1, s);
   } else {
     StepArgs<float> A = step_args<float>(geom, u0, u0, u1, dt, 1);
-    launch_flux_fast(A, s);
+    launch_static_copy(A, s);
+    cudaEventRecord(ev[0], s);
+    launch_flux_bulk(A, s);
     cudaEventRecord(ev[1], s);
     launch_flux_band(A, s);
     cudaEventRecord(ev[2], s);

@@ -482,6 +482,7 @@ template <typename T>
 int resident_ctas_per_sm() {
   constexpr int V = 16 / sizeof(T);
   set_smem_attr<T, V>();
+  set_smem_attr<T, 1>();   // both variants set here, outside any graph capture
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast_tiled<T, V>, BulkTile<T>::NT, BulkTile<T>::BYTES) !=
           cudaSuccess ||
@@ -492,7 +493,8 @@ int resident_ctas_per_sm() {
 
 }  // namespace
 
-cudaError_t bulk_plan(const Dims &D, const int *kfast_host, bool f64, std::vector<int> &seg, std::vector<int> &off) {
+cudaError_t bulk_plan(const Dims &D, const int *kfast_host, bool f64, int slab_levels, std::vector<int> &seg,
+                      std::vector<int> &off) {
   const int TX = BulkTile<float>::TX, TY = BulkTile<float>::TY;
   const int tx = (D.nx + TX - 1) / TX, ty = (D.ny + TY - 1) / TY;
   const long long ntile = (long long)tx * ty;
@@ -517,9 +519,9 @@ cudaError_t bulk_plan(const Dims &D, const int *kfast_host, bool f64, std::vecto
   // Lockstep slabs: every tile is cut at the same levels, and the pieces are
   // launched slab by slab from the top, so CTAs of neighbouring tiles march
   // the same levels at the same time and read each other's halo from L2.
-  // Slabs of at least 16 levels, sized for about three waves of CTAs; the
-  // short pieces of the lowest slabs come last.
-  const long long Lc = std::max(16LL, (W + 3 * slots - 1) / (3 * slots));
+  // Slabs of slab_levels levels, or (0) of at least 16 levels sized for
+  // about three waves of CTAs; the short pieces of the lowest slabs come last.
+  const long long Lc = slab_levels > 0 ? (long long)slab_levels : std::max(16LL, (W + 3 * slots - 1) / (3 * slots));
   const int nslab = (int)((D.nz + Lc - 1) / Lc);
   for (int sl = nslab - 1; sl >= 0; --sl) {
     const int za = (int)(sl * Lc), zb = (int)std::min<long long>(D.nz, (sl + 1) * Lc);
@@ -537,12 +539,26 @@ cudaError_t bulk_plan(const Dims &D, const int *kfast_host, bool f64, std::vecto
 }
 
 template <typename T>
-void launch_flux_fast(const StepArgs<T> &A, cudaStream_t s) {
+void launch_flux_bulk(const StepArgs<T> &A, cudaStream_t s);
+
+template <typename T>
+void launch_static_copy(const StepArgs<T> &A, cudaStream_t s) {
   const Dims &D = A.D;
   if (A.copy_static) {
     dim3 blk(32, 8, 1), grd((D.nx + 31) / 32, (D.ny + 7) / 8, std::max(1, std::min(D.nz, A.kcov_max)));
     k_static<T><<<grd, blk, 0, s>>>(A);
   }
+}
+
+template <typename T>
+void launch_flux_fast(const StepArgs<T> &A, cudaStream_t s) {
+  launch_static_copy(A, s);
+  launch_flux_bulk(A, s);
+}
+
+template <typename T>
+void launch_flux_bulk(const StepArgs<T> &A, cudaStream_t s) {
+  const Dims &D = A.D;
   // 16-byte copies and pair stores need every row of every field to start on
   // a 16-byte boundary: nx a multiple of the copy width and aligned pointers
   constexpr int V = 16 / sizeof(T);
@@ -557,3 +573,7 @@ void launch_flux_fast(const StepArgs<T> &A, cudaStream_t s) {
 
 template void launch_flux_fast<double>(const StepArgs<double> &, cudaStream_t);
 template void launch_flux_fast<float>(const StepArgs<float> &, cudaStream_t);
+template void launch_static_copy<double>(const StepArgs<double> &, cudaStream_t);
+template void launch_static_copy<float>(const StepArgs<float> &, cudaStream_t);
+template void launch_flux_bulk<double>(const StepArgs<double> &, cudaStream_t);
+template void launch_flux_bulk<float>(const StepArgs<float> &, cudaStream_t);

@@ -1,0 +1,210 @@
+// eb_handle.cuh -- the geometry handle and the host-side orchestration of
+// one stage (flux divergence + redistribution), shared by the C ABI's
+// translation units.  Not part of the ABI.
+#pragma once
+
+#include "eb_step.cuh"
+
+#include <stdio.h>
+
+#include <string>
+#include <vector>
+
+// message of the calling thread's last error (eb_last_error)
+std::string &eb_error_slot();
+
+namespace ebh {
+
+inline eb_status fail(eb_status st, const char *fmt, const char *arg = nullptr) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), fmt, arg ? arg : "");
+  eb_error_slot() = buf;
+  return st;
+}
+
+inline eb_status cuda_fail(cudaError_t e, const char *where) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  eb_error_slot() = buf;
+  return e == cudaErrorMemoryAllocation ? EB_ERR_OOM : EB_ERR_CUDA;
+}
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace ebh
+
+#define CUDA_TRY(x, where)                                      \
+  do {                                                          \
+    cudaError_t e_ = (x);                                       \
+    if (e_ != cudaSuccess) return ebh::cuda_fail(e_, where);    \
+  } while (0)
+
+struct eb_geom_s {
+  eb_desc desc;
+  Dims D;
+  eb_precision prec;
+  int device = 0;
+  double *h = nullptr;
+  int *kcov[4] = {}, *kreg[4] = {}, *kxt[4] = {};
+  long long *roff[4] = {};
+  int *kfast = nullptr;
+  int4 *bseg = nullptr;   // bulk kernel work split
+  int *boff = nullptr;
+  int bctas = 0;
+  int slab_levels = 0;    // slab height of the split (0: automatic)
+  std::vector<int> kfast_host;
+  int kcov_max = 0;
+  GridDev G[4];
+  WsrdDev W[4];
+  double *ref_d[2] = {nullptr, nullptr};
+  float *ref_f[2] = {nullptr, nullptr};
+  double *zero_d = nullptr;
+  float *zero_f = nullptr;
+  unsigned *status = nullptr;
+  void *qhat = nullptr, *sig = nullptr, *pval = nullptr;
+  long long max_small = 0;
+  // scratch of the five-field redistribution pass (small CVs of all fields)
+  void *qhat5 = nullptr, *sig5 = nullptr, *pval5 = nullptr;
+  long long sum_small = 0;
+  // the near-EB kernels run on this stream, forked from and joined to the
+  // caller's stream around the bulk kernel
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // scratch states for eb_step: 4 x 5 fields
+  void *scr[4][5] = {};
+  std::vector<void *> allocs;
+  eb_geom_info_t info;
+
+  template <typename P>
+  cudaError_t alloc(P **p, long long count) {
+    *p = nullptr;
+    if (count < 1) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(P) * (size_t)count);
+    if (e == cudaSuccess) {
+      allocs.push_back((void *)*p);
+      info.device_bytes += (int64_t)(sizeof(P) * count);
+    }
+    return e;
+  }
+  void release() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
+    ev_fork = ev_join = nullptr;
+    side = nullptr;
+    for (void *p : allocs) cudaFree(p);
+    allocs.clear();
+    for (int g = 0; g < 4; ++g) free_wsrd(W[g]);
+  }
+};
+
+
+// (Re)build the bulk kernel's work split with slabs of slab_levels levels
+// (0: automatic); the previous split is released.
+eb_status eb_replan_bulk(eb_geom g, int slab_levels);
+
+namespace ebh {
+
+inline bool state_ok(const eb_state *U, size_t align) {
+  if (!U) return false;
+  const void *p[5] = {U->rho, U->rhotheta, U->rhou, U->rhov, U->rhow};
+  for (const void *q : p)
+    if (!q || ((uintptr_t)q % align)) return false;
+  return true;
+}
+
+inline void **state_ptrs(const eb_state *U) { return (void **)&U->rho; }
+
+template <typename T>
+StepArgs<T> step_args(eb_geom g, void *const src[5], void *const base[5], void *const out[5], double dt, int copy) {
+  StepArgs<T> A;
+  A.D = g->D;
+  for (int f = 0; f < 5; ++f) {
+    A.src.f[f] = (const T *)src[f];
+    A.base[f] = base ? (const T *)base[f] : nullptr;
+    A.out[f] = (T *)out[f];
+  }
+  if (sizeof(T) == sizeof(double)) {
+    A.src.ref_rho = (const T *)g->ref_d[0];
+    A.src.ref_rt = (const T *)g->ref_d[1];
+  } else {
+    A.src.ref_rho = (const T *)g->ref_f[0];
+    A.src.ref_rt = (const T *)g->ref_f[1];
+  }
+  A.dt = dt;
+  A.dtT = (T)dt;
+  A.kfast = g->kfast;
+  A.bseg = g->bseg;
+  A.boff = g->boff;
+  A.bctas = g->bctas;
+  for (int q = 0; q < 4; ++q) A.G[q] = g->G[q];
+  A.status = g->status;
+  A.copy_static = copy;
+  A.kcov_max = g->kcov_max;
+  return A;
+}
+
+template <typename T>
+void wsrd_field(eb_geom g, int field, T *u, cudaStream_t s) {
+  const int grid = field <= 1 ? 0 : field - 1;
+  WsrdArgs<T> R;
+  R.D = g->D;
+  R.W = g->W[grid];
+  R.u = u;
+  R.refd = field <= 1 ? g->ref_d[field] : nullptr;
+  R.dev = (T *)g->qhat;
+  R.sig = (T *)g->sig;
+  R.pval = (T *)g->pval;
+  R.status = g->status;
+  launch_wsrd(R, s);
+}
+
+// Flux divergence and provisional update.  The near-EB kernels and the bulk
+// read the same input and write disjoint CVs, so the near-EB kernels run on
+// the handle's side stream alongside the bulk kernel.
+template <typename T>
+void flux_update(eb_geom g, const StepArgs<T> &A, cudaStream_t s) {
+  cudaEventRecord(g->ev_fork, s);
+  cudaStreamWaitEvent(g->side, g->ev_fork, 0);
+  launch_flux_band(A, g->side);
+  launch_flux_fast(A, s);
+  cudaEventRecord(g->ev_join, g->side);
+  cudaStreamWaitEvent(s, g->ev_join, 0);
+}
+
+// Redistribution of all five fields of a state in one pass of three kernels.
+template <typename T>
+void wsrd_all(eb_geom g, void *const out[5], cudaStream_t s) {
+  WsrdSet<T> S;
+  long long os = 0, oa = 0;
+  for (int f = 0; f < 5; ++f) {
+    const int grid = f <= 1 ? 0 : f - 1;
+    WsrdArgs<T> &R = S.f[f];
+    R.D = g->D;
+    R.W = g->W[grid];
+    R.u = (T *)out[f];
+    R.refd = f <= 1 ? g->ref_d[f] : nullptr;
+    R.dev = (T *)g->qhat5 + os;
+    R.pval = (T *)g->pval5 + os;
+    R.sig = (T *)g->sig5 + 3 * os;
+    R.status = g->status;
+    S.off_small[f] = os;
+    S.off_aff[f] = oa;
+    os += g->W[grid].nsmall;
+    oa += g->W[grid].naff;
+  }
+  S.off_small[5] = os;
+  S.off_aff[5] = oa;
+  launch_wsrd5(S, s);
+}
+
+template <typename T>
+void stage(eb_geom g, void *const src[5], void *const base[5], void *const out[5], double dt, int copy,
+           cudaStream_t s) {
+  flux_update(g, step_args<T>(g, src, base, out, dt, copy), s);
+  wsrd_all<T>(g, out, s);
+}
+
+inline size_t field_count(const Dims &D, int f) { return (size_t)D.nxy * (D.nz + (f == 4 ? 1 : 0)); }
+
+}  // namespace ebh

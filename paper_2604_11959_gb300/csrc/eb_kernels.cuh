@@ -52,10 +52,12 @@ void launch_marks_fill(const uint8_t *m, long long n, const long long *pos, unsi
 void launch_export_geometry(const double *h, const Dims &D, int g, const GridDev &G, int field, double *dst,
                             cudaStream_t s);
 
-// eb_fast.cu: split of the bulk kernel's (tile, level) work into equal pieces,
-// one per resident CTA; seg holds (tile, first level, end level, 0) per
-// piece, off[b] .. off[b+1] the pieces of CTA b
-cudaError_t bulk_plan(const Dims &D, const int *kfast_host, bool f64, std::vector<int> &seg, std::vector<int> &off);
+// eb_fast.cu: split of the bulk kernel's (tile, level) work into lockstep
+// slabs of slab_levels levels (0: chosen from the GPU's size); seg holds
+// (tile, first level, end level, 0) per piece, off[b] .. off[b+1] the pieces
+// of CTA b
+cudaError_t bulk_plan(const Dims &D, const int *kfast_host, bool f64, int slab_levels, std::vector<int> &seg,
+                      std::vector<int> &off);
 
 // eb_scan.cu: in-place exclusive scan of n values; total written to *total (device)
 void scan_exclusive(long long *data, long long n, long long *total, cudaStream_t s);

@@ -48,7 +48,11 @@ struct WsrdSet {
 template <typename T>
 void launch_flux_update(const StepArgs<T> &A, cudaStream_t s);
 template <typename T>
-void launch_flux_fast(const StepArgs<T> &A, cudaStream_t s);
+void launch_flux_fast(const StepArgs<T> &A, cudaStream_t s);   // static copy + bulk
+template <typename T>
+void launch_static_copy(const StepArgs<T> &A, cudaStream_t s);
+template <typename T>
+void launch_flux_bulk(const StepArgs<T> &A, cudaStream_t s);
 template <typename T>
 void launch_flux_band(const StepArgs<T> &A, cudaStream_t s);
 

@@ -25,7 +25,9 @@ EXPORT_FIELDS = ("alpha", "cent_x", "cent_y", "cent_z", "beta_x", "beta_y", "bet
 STATUS = {0: "EB_OK", 1: "EB_ERR_INVALID_ARG", 2: "EB_ERR_CUDA", 3: "EB_ERR_OOM", 4: "EB_ERR_NUMERIC",
           5: "EB_ERR_TIMEOUT", 6: "EB_ERR_STATE"}
 EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
-                    "eb_wsrd_noalloc", "eb_step", "eb_step_profile", "eb_sync_status", "eb_last_error", "eb_version")
+                    "eb_wsrd_noalloc", "eb_step", "eb_step_profile", "eb_sync_status", "eb_last_error", "eb_version",
+                    "eb_ensemble_create", "eb_ensemble_set_state", "eb_ensemble_get_state", "eb_ensemble_step",
+                    "eb_ensemble_tune", "eb_ensemble_destroy")
 
 
 class EbError(RuntimeError):
@@ -83,10 +85,18 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_step.argtypes = [V, P(_State), P(_State), D, I, I, V]
     lib.eb_step_profile.argtypes = [V, P(_State), P(_State), D, V, P(ctypes.c_float)]
     lib.eb_sync_status.argtypes = [V, V]
+    lib.eb_ensemble_create.argtypes = [P(V), I, P(V)]
+    lib.eb_ensemble_set_state.argtypes = [V, I, P(_State), V]
+    lib.eb_ensemble_get_state.argtypes = [V, I, P(_State), V]
+    lib.eb_ensemble_step.argtypes = [V, P(D), I, V]
+    lib.eb_ensemble_tune.argtypes = [V, P(D), I, P(I), V]
+    lib.eb_ensemble_destroy.argtypes = [V]
     lib.eb_last_error.restype = ctypes.c_char_p
     lib.eb_version.restype = I
     for name in ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
-                 "eb_wsrd_noalloc", "eb_step", "eb_step_profile", "eb_sync_status"):
+                 "eb_wsrd_noalloc", "eb_step", "eb_step_profile", "eb_sync_status", "eb_ensemble_create",
+                 "eb_ensemble_set_state", "eb_ensemble_get_state", "eb_ensemble_step", "eb_ensemble_tune",
+                 "eb_ensemble_destroy"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -253,3 +263,61 @@ def host_state(U: dict, precision: str, refs=None, pin: bool = True) -> dict:
 def device_state(U: dict, precision: str, refs=None) -> dict:
     """Like host_state, on the current CUDA device."""
     return {f: t.cuda() for f, t in host_state(U, precision, refs, pin=False).items()}
+
+
+class Ensemble:
+    """Independent geometry handles advanced together (``eb_ensemble_*``):
+    one CUDA-graph launch per step of every member, slab heights of the bulk
+    kernel's tiles chosen by ``tune``.  The ensemble does not own the
+    members; close it before them."""
+
+    def __init__(self, members):
+        lib = load()
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m.handle.value for m in self.members])
+        h = ctypes.c_void_p()
+        _check(lib.eb_ensemble_create(arr, len(self.members), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("ensemble is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().eb_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dt(self, dt):
+        dt = [float(x) for x in dt]
+        if len(dt) != len(self.members):
+            raise ValueError("one dt per member")
+        return (ctypes.c_double * len(dt))(*dt)
+
+    def set_state(self, q: int, U: dict, stream=None):
+        g = self.members[q]
+        for f in FIELDS:
+            _require_cuda(U[f], g.dtype, g.shape(f), f)
+        _check(load().eb_ensemble_set_state(self.handle, q, ctypes.byref(g._cstate(U)), _stream(stream)))
+
+    def get_state(self, q: int, out: dict | None = None, stream=None) -> dict:
+        g = self.members[q]
+        out = out if out is not None else g.empty_state()
+        _check(load().eb_ensemble_get_state(self.handle, q, ctypes.byref(g._cstate(out)), _stream(stream)))
+        return out
+
+    def step(self, dt, nsteps: int = 1, stream=None):
+        _check(load().eb_ensemble_step(self.handle, self._dt(dt), int(nsteps), _stream(stream)))
+
+    def tune(self, dt, reps: int = 3, stream=None) -> int:
+        best = ctypes.c_int(0)
+        _check(load().eb_ensemble_tune(self.handle, self._dt(dt), int(reps), ctypes.byref(best), _stream(stream)))
+        return best.value
