@@ -238,6 +238,43 @@ eb_status eb_step(eb_geom geom, const eb_state *Un, eb_state *Unp1, double dt, i
 eb_status eb_step_profile(eb_geom geom, const eb_state *Un, eb_state *Unp1, double dt, void *stream, float ms[4]);
 
 /*
+ * Anelastic projection (Sec. 2.2 anelastic model; Algorithm 2 step 5): the
+ * face momenta m = (rho*u, rho*v, rho*w) of U are made discretely
+ * divergence-free, in place.  The divergence is the cut-cell one of the flux
+ * update, D(m)_c = sum_d (beta_hi m_hi - beta_lo m_lo) / delta_d (walls and
+ * closed faces carry none); the gradient on a face is
+ * G(phi) = (phi_R - phi_L) / delta_d; m <- m - dt G(phi) with
+ * L phi = D(G(phi)) = D(m) / dt.  L is symmetric with the constants as null
+ * space, so the mean of D(m) (rounding) is removed and -L phi = -D(m)/dt is
+ * solved in FP64 by Jacobi-preconditioned conjugate gradients until
+ * ||rhs - L phi|| <= rtol ||rhs|| or maxit iterations.
+ *   phi0     device, nx*ny*nz doubles: initial guess, or NULL for zero.
+ *   phi      device, nx*ny*nz doubles: receives the solution, or NULL.
+ *   iters    host: iterations used (NULL allowed).
+ *   relres   host: final relative residual (NULL allowed).
+ * rho and rho*theta are not touched.  Synchronises the stream every 32
+ * iterations (convergence test).  The first call on a handle allocates its
+ * work space (about 10 doubles per cell), so it must not be inside a stream
+ * capture.
+ */
+eb_status eb_project(eb_geom geom, eb_state *U, double dt, double rtol, int maxit, const double *phi0, double *phi,
+                     int *iters, double *relres, void *stream);
+
+/*
+ * nsteps anelastic steps (Algorithm 2) with two stages in the low-storage
+ * form U* = P[R[U + dt/2 dU(U)]], U' = P[R[U + dt dU(U*)]]: the flux update
+ * and redistribution of eb_step with the density held at the reference
+ * profile (the rho perturbation is set to zero after each stage), then the
+ * projection P above (zero initial guess).  The handle must have been built
+ * with a reference profile (EB_ERR_STATE otherwise); Un holds rho*theta and
+ * the face momenta rho0*u with a zero rho perturbation.  iters (host, NULL
+ * allowed) receives 2*nsteps iteration counts.  Uses handle scratch; Un and
+ * Unp1 must not overlap.
+ */
+eb_status eb_anelastic_step(eb_geom geom, const eb_state *Un, eb_state *Unp1, double dt, int nsteps, double rtol,
+                            int maxit, int *iters, void *stream);
+
+/*
  * Ensembles: many independent terrain instances advanced together.  The
  * paper has no counterpart (its AMReX box arrays are the closest); this is
  * the batched serving form of eb_step.

@@ -85,6 +85,7 @@ cudaError_t fill_ref(eb_geom g, const double *src, double **dd, float **ff, cuda
 }
 
 eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, const double *ref_rt, cudaStream_t s) {
+  g->has_ref = ref_rho != nullptr;
   const Dims &D = g->D;
   const long long ncol = (long long)D.nx * D.ny;
   const long long nh = (long long)(D.nx + 1) * (D.ny + 1);

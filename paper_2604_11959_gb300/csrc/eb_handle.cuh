@@ -39,6 +39,19 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
     if (e_ != cudaSuccess) return ebh::cuda_fail(e_, where);    \
   } while (0)
 
+// Work space of the projection (eb_project), allocated on its first use.
+struct ProjWork {
+  bool ready = false;
+  int nb = 0;                  // blocks of every projection kernel (fixed: deterministic sums)
+  long long nact = 0;          // cells in the solve (diagonal > 0)
+  double *bx = nullptr, *by = nullptr, *bz = nullptr;   // low-face open fractions of the c-cells
+  double *d = nullptr;         // diagonal of -L
+  double *rhs = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x = nullptr;
+  double *part = nullptr;      // partial sums, 8 slots of nb
+  int *conv = nullptr;         // iteration count at convergence (0 = not yet)
+  double *host = nullptr;      // pinned copy of one slot of partial sums
+};
+
 struct eb_geom_s {
   eb_desc desc;
   Dims D;
@@ -74,6 +87,8 @@ struct eb_geom_s {
   void *scr[4][5] = {};
   std::vector<void *> allocs;
   eb_geom_info_t info;
+  bool has_ref = false;   // built with a reference profile
+  ProjWork pw;
 
   template <typename P>
   cudaError_t alloc(P **p, long long count) {
@@ -94,10 +109,17 @@ struct eb_geom_s {
     side = nullptr;
     for (void *p : allocs) cudaFree(p);
     allocs.clear();
+    if (pw.host) cudaFreeHost(pw.host);
+    pw = ProjWork();
     for (int g = 0; g < 4; ++g) free_wsrd(W[g]);
   }
 };
 
+
+// Projection of the face momenta of U (Sec. 2.2 anelastic constraint),
+// implemented in eb_project.cu; phi0 may be NULL (zero start).
+eb_status eb_project_impl(eb_geom g, void *const mom[3], double dt, double rtol, int maxit, const double *phi0,
+                          double *phi_out, int *iters, double *relres, cudaStream_t s);
 
 // (Re)build the bulk kernel's work split with slabs of slab_levels levels
 // (0: automatic); the previous split is released.

@@ -1,0 +1,430 @@
+// eb_project.cu -- the anelastic projection (Sec. 2.2, Algorithm 2 step 5)
+// and the anelastic step.
+//
+// The constraint div(rho0 u) = 0 is imposed on the face momenta with the
+// cut-cell divergence of the flux update,
+//   D(m)_c = sum_d (beta_d,hi m_d,hi - beta_d,lo m_d,lo) / delta_d,
+// beta the open fractions of the c-cell's faces (walls closed).  With the
+// face gradient G(phi) = (phi_R - phi_L) / delta_d, the correction
+// m <- m* - dt G(phi) removes the divergence when L phi = D(G(phi)) = D(m*)/dt.
+// L is the beta-weighted 7-point operator: symmetric, negative semi-definite,
+// null space the constants (the fluid above a height-function terrain is
+// connected), so the mean of the right-hand side (rounding only) is removed
+// and -L phi = -rhs is solved by Jacobi-preconditioned conjugate gradients
+// in FP64 to a relative residual.
+//
+// Every kernel runs on a fixed grid of nb blocks with grid-stride loops and
+// writes one partial sum per block; a consumer block adds the nb partials in
+// a fixed order, so the solve is deterministic.  Convergence is detected on
+// the device (the kernels of later iterations return at once) and read by
+// the host every 32 iterations.
+#include "eb_handle.cuh"
+
+#include <math.h>
+
+using namespace ebh;
+
+namespace {
+
+constexpr int PB = 256;   // threads per block of every projection kernel
+
+enum { S_SUM = 0, S_BB = 1, S_PQ = 2, S_RR = 3, S_RZ0 = 4, S_RZ1 = 5, S_CNT = 6 };
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; thread 0 writes it to part[blockIdx.x].
+__device__ inline void block_partial(double v, double *part) {
+  __shared__ double s[PB / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double a = threadIdx.x < PB / 32 ? s[threadIdx.x] : 0.0;
+    a = warp_sum(a);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+  }
+}
+
+// Total of nb partial sums, the same bits in every block.
+__device__ inline double total(const double *part, int nb) {
+  __shared__ double t;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double a = 0.0;
+    for (int q = threadIdx.x; q < nb; q += 32) a += part[q];
+    a = warp_sum(a);
+    if (threadIdx.x == 0) t = a;
+  }
+  __syncthreads();
+  return t;
+}
+
+struct Nbr {
+  long long xm, xp, ym, yp;
+  int k;
+};
+
+__device__ inline Nbr neighbours(const Dims &D, long long c) {
+  int i, j, k;
+  split_index(D, (unsigned)c, i, j, k);
+  Nbr n;
+  n.xm = i == 0 ? c + D.nx - 1 : c - 1;
+  n.xp = i == D.nx - 1 ? c - (D.nx - 1) : c + 1;
+  n.ym = j == 0 ? c + (long long)D.nx * (D.ny - 1) : c - D.nx;
+  n.yp = j == D.ny - 1 ? c - (long long)D.nx * (D.ny - 1) : c + D.nx;
+  n.k = k;
+  return n;
+}
+
+struct Op {
+  Dims D;
+  const double *bx, *by, *bz, *d;
+  double ix2, iy2, iz2;   // 1 / delta^2
+  // (-L p)_c for an active cell
+  __device__ inline double apply(const double *p, long long c, const Nbr &n) const {
+    const double bzl = bz[c];
+    const double bzh = n.k + 1 < D.nz ? bz[c + D.nxy] : 0.0;
+    double v = d[c] * p[c] - (bx[c] * p[n.xm] + bx[n.xp] * p[n.xp]) * ix2 -
+               (by[c] * p[n.ym] + by[n.yp] * p[n.yp]) * iy2;
+    if (bzl > 0.0) v -= bzl * p[c - D.nxy] * iz2;
+    if (bzh > 0.0) v -= bzh * p[c + D.nxy] * iz2;
+    return v;
+  }
+};
+
+__global__ void k_wall(Dims D, double *bz) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c < D.nxy) bz[c] = 0.0;   // z = 0 carries no flux
+}
+
+__global__ void k_diag(Op O, double *d, double *part) {
+  const Dims &D = O.D;
+  const long long N = D.nxy * D.nz;
+  double cnt = 0.0;
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) {
+    const Nbr n = neighbours(D, c);
+    const double bzh = n.k + 1 < D.nz ? O.bz[c + D.nxy] : 0.0;
+    const double v = (O.bx[c] + O.bx[n.xp]) * O.ix2 + (O.by[c] + O.by[n.yp]) * O.iy2 + (O.bz[c] + bzh) * O.iz2;
+    d[c] = v;
+    cnt += v > 0.0 ? 1.0 : 0.0;
+  }
+  block_partial(cnt, part);
+}
+
+// rhs = D(m) / dt on the active cells
+template <typename T>
+__global__ void k_rhs(Op O, const T *mu, const T *mv, const T *mw, double idt, double *rhs, double *part) {
+  const Dims &D = O.D;
+  const long long N = D.nxy * D.nz;
+  double sum = 0.0;
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) {
+    double v = 0.0;
+    if (O.d[c] > 0.0) {
+      const Nbr n = neighbours(D, c);
+      const double bzh = n.k + 1 < D.nz ? O.bz[c + D.nxy] : 0.0;
+      const double dx = O.bx[n.xp] * (double)mu[n.xp] - O.bx[c] * (double)mu[c];
+      const double dy = O.by[n.yp] * (double)mv[n.yp] - O.by[c] * (double)mv[c];
+      const double dz = bzh * (double)mw[c + D.nxy] - O.bz[c] * (double)mw[c];
+      v = (dx * D.idx + dy * D.idy + dz * D.idz) * idt;
+    }
+    rhs[c] = v;
+    sum += v;
+  }
+  block_partial(sum, part);
+}
+
+// remove the mean of the right-hand side over the active cells
+__global__ void k_center(Op O, double *rhs, const double *psum, const double *pcnt, int nb, double *pbb) {
+  const Dims &D = O.D;
+  const long long N = D.nxy * D.nz;
+  const double mean = total(psum, nb) / fmax(1.0, total(pcnt, nb));
+  double bb = 0.0;
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) {
+    if (O.d[c] > 0.0) {
+      const double v = rhs[c] - mean;
+      rhs[c] = v;
+      bb += v * v;
+    }
+  }
+  block_partial(bb, pbb);
+}
+
+// r = -rhs - A x, z = r / d, p = z
+__global__ void k_init(Op O, const double *x, const double *rhs, double *r, double *z, double *p, double *prz,
+                       double *prr) {
+  const Dims &D = O.D;
+  const long long N = D.nxy * D.nz;
+  double rz = 0.0, rr = 0.0;
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) {
+    double rv = 0.0, zv = 0.0;
+    if (O.d[c] > 0.0) {
+      rv = -rhs[c] - O.apply(x, c, neighbours(D, c));
+      zv = rv / O.d[c];
+    }
+    r[c] = rv;
+    z[c] = zv;
+    p[c] = zv;
+    rz += rv * zv;
+    rr += rv * rv;
+  }
+  block_partial(rz, prz);
+  __syncthreads();
+  block_partial(rr, prr);
+}
+
+// q = A p
+__global__ void k_apply(Op O, const double *p, double *q, double *ppq, const int *conv) {
+  if (*conv) return;
+  const Dims &D = O.D;
+  const long long N = D.nxy * D.nz;
+  double pq = 0.0;
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) {
+    double v = 0.0;
+    if (O.d[c] > 0.0) v = O.apply(p, c, neighbours(D, c));
+    q[c] = v;
+    pq += p[c] * v;
+  }
+  block_partial(pq, ppq);
+}
+
+// alpha = rz / pq; x += alpha p; r -= alpha q; z = r / d
+__global__ void k_update(Op O, double *x, const double *p, const double *q, double *r, double *z, const double *ppq,
+                         const double *prz, double *prz_next, double *prr, int nb, const int *conv) {
+  if (*conv) return;
+  const Dims &D = O.D;
+  const long long N = D.nxy * D.nz;
+  const double alpha = total(prz, nb) / total(ppq, nb);
+  double rz = 0.0, rr = 0.0;
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) {
+    if (O.d[c] > 0.0) {
+      x[c] += alpha * p[c];
+      const double rv = r[c] - alpha * q[c];
+      const double zv = rv / O.d[c];
+      r[c] = rv;
+      z[c] = zv;
+      rz += rv * zv;
+      rr += rv * rv;
+    }
+  }
+  block_partial(rz, prz_next);
+  __syncthreads();
+  block_partial(rr, prr);
+}
+
+// convergence test; else p = z + (rz_next / rz) p
+__global__ void k_direction(Op O, double *p, const double *z, const double *prz, const double *prz_next,
+                            const double *prr, int nb, double thr2, int it, int *conv) {
+  if (*conv) return;
+  const Dims &D = O.D;
+  const long long N = D.nxy * D.nz;
+  const double rr = total(prr, nb);
+  if (rr <= thr2) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *conv = it + 1;
+    return;
+  }
+  const double beta = total(prz_next, nb) / total(prz, nb);
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB)
+    p[c] = z[c] + beta * p[c];
+}
+
+// m -= dt G(x) on the open faces
+template <typename T>
+__global__ void k_correct(Op O, const double *x, double dt, T *mu, T *mv, T *mw) {
+  const Dims &D = O.D;
+  const long long N = D.nxy * D.nz;
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) {
+    const Nbr n = neighbours(D, c);
+    if (O.bx[c] > 0.0) mu[c] = (T)((double)mu[c] - dt * (x[c] - x[n.xm]) * D.idx);
+    if (O.by[c] > 0.0) mv[c] = (T)((double)mv[c] - dt * (x[c] - x[n.ym]) * D.idy);
+    if (n.k >= 1 && O.bz[c] > 0.0) mw[c] = (T)((double)mw[c] - dt * (x[c] - x[c - D.nxy]) * D.idz);
+  }
+}
+
+Op make_op(eb_geom g) {
+  Op O;
+  O.D = g->D;
+  O.bx = g->pw.bx;
+  O.by = g->pw.by;
+  O.bz = g->pw.bz;
+  O.d = g->pw.d;
+  O.ix2 = g->D.idx * g->D.idx;
+  O.iy2 = g->D.idy * g->D.idy;
+  O.iz2 = g->D.idz * g->D.idz;
+  return O;
+}
+
+// work space and the fixed part of the operator, on the first call
+eb_status setup(eb_geom g, cudaStream_t s) {
+  ProjWork &w = g->pw;
+  if (w.ready) return EB_OK;
+  const Dims &D = g->D;
+  const long long N = D.nxy * D.nz;
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev), "device");
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device");
+  w.nb = (int)std::max(1LL, std::min<long long>(4LL * std::max(sms, 1), (N + PB - 1) / PB));
+  for (double **a : {&w.bx, &w.by, &w.bz, &w.d, &w.rhs, &w.r, &w.z, &w.p, &w.q, &w.x})
+    CUDA_TRY(g->alloc(a, N), "alloc projection work space");
+  CUDA_TRY(g->alloc(&w.part, 8LL * w.nb), "alloc projection work space");
+  CUDA_TRY(g->alloc(&w.conv, 1), "alloc projection work space");
+  CUDA_TRY(cudaMallocHost(&w.host, sizeof(double) * (size_t)w.nb), "alloc pinned scratch");
+  launch_export_geometry(g->h, D, 0, g->G[0], EB_X_BETA_X, w.bx, s);
+  launch_export_geometry(g->h, D, 0, g->G[0], EB_X_BETA_Y, w.by, s);
+  launch_export_geometry(g->h, D, 0, g->G[0], EB_X_BETA_Z, w.bz, s);
+  k_wall<<<(unsigned)((D.nxy + 255) / 256), 256, 0, s>>>(D, w.bz);
+  k_diag<<<w.nb, PB, 0, s>>>(make_op(g), w.d, w.part + S_CNT * w.nb);
+  CUDA_TRY(cudaMemcpyAsync(w.host, w.part + S_CNT * w.nb, sizeof(double) * w.nb, cudaMemcpyDeviceToHost, s),
+           "count active cells");
+  CUDA_TRY(cudaStreamSynchronize(s), "count active cells");
+  double cnt = 0.0;
+  for (int q = 0; q < w.nb; ++q) cnt += w.host[q];
+  w.nact = (long long)cnt;
+  w.ready = true;
+  return EB_OK;
+}
+
+double host_total(eb_geom g, int slot, cudaStream_t s, cudaError_t &e) {
+  ProjWork &w = g->pw;
+  e = cudaMemcpyAsync(w.host, w.part + slot * w.nb, sizeof(double) * w.nb, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  double t = 0.0;
+  for (int q = 0; q < w.nb; ++q) t += w.host[q];
+  return t;
+}
+
+template <typename T>
+void launch_rhs(eb_geom g, void *const mom[3], double dt, cudaStream_t s) {
+  ProjWork &w = g->pw;
+  k_rhs<T><<<w.nb, PB, 0, s>>>(make_op(g), (const T *)mom[0], (const T *)mom[1], (const T *)mom[2], 1.0 / dt, w.rhs,
+                               w.part + S_SUM * w.nb);
+}
+
+template <typename T>
+void launch_correct(eb_geom g, void *const mom[3], double dt, cudaStream_t s) {
+  ProjWork &w = g->pw;
+  k_correct<T><<<w.nb, PB, 0, s>>>(make_op(g), w.x, dt, (T *)mom[0], (T *)mom[1], (T *)mom[2]);
+}
+
+}  // namespace
+
+eb_status eb_project_impl(eb_geom g, void *const mom[3], double dt, double rtol, int maxit, const double *phi0,
+                          double *phi_out, int *iters, double *relres, cudaStream_t s) {
+  eb_status st = setup(g, s);
+  if (st != EB_OK) return st;
+  ProjWork &w = g->pw;
+  const Dims &D = g->D;
+  const long long N = D.nxy * D.nz;
+  const Op O = make_op(g);
+  if (g->prec == EB_F64) launch_rhs<double>(g, mom, dt, s);
+  else launch_rhs<float>(g, mom, dt, s);
+  k_center<<<w.nb, PB, 0, s>>>(O, w.rhs, w.part + S_SUM * w.nb, w.part + S_CNT * w.nb, w.nb, w.part + S_BB * w.nb);
+  if (phi0) CUDA_TRY(cudaMemcpyAsync(w.x, phi0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s), "initial guess");
+  else CUDA_TRY(cudaMemsetAsync(w.x, 0, sizeof(double) * N, s), "initial guess");
+  k_init<<<w.nb, PB, 0, s>>>(O, w.x, w.rhs, w.r, w.z, w.p, w.part + S_RZ0 * w.nb, w.part + S_RR * w.nb);
+  CUDA_TRY(cudaMemsetAsync(w.conv, 0, sizeof(int), s), "reset");
+  cudaError_t e = cudaSuccess;
+  const double bb = host_total(g, S_BB, s, e);
+  CUDA_TRY(e, "residual norm");
+  const double rr0 = host_total(g, S_RR, s, e);
+  CUDA_TRY(e, "residual norm");
+  const double thr2 = rtol * rtol * bb;
+  int it = 0;
+  double rr = rr0;
+  if (bb > 0.0 && rr0 > thr2) {
+    int done = 0;
+    for (it = 0; it < maxit; ++it) {
+      double *prz = w.part + (it % 2 ? S_RZ1 : S_RZ0) * w.nb;
+      double *prz_next = w.part + (it % 2 ? S_RZ0 : S_RZ1) * w.nb;
+      k_apply<<<w.nb, PB, 0, s>>>(O, w.p, w.q, w.part + S_PQ * w.nb, w.conv);
+      k_update<<<w.nb, PB, 0, s>>>(O, w.x, w.p, w.q, w.r, w.z, w.part + S_PQ * w.nb, prz, prz_next,
+                                   w.part + S_RR * w.nb, w.nb, w.conv);
+      k_direction<<<w.nb, PB, 0, s>>>(O, w.p, w.z, prz, prz_next, w.part + S_RR * w.nb, w.nb, thr2, it, w.conv);
+      if ((it + 1) % 32 == 0 || it + 1 == maxit) {
+        CUDA_TRY(cudaMemcpyAsync(&done, w.conv, sizeof(int), cudaMemcpyDeviceToHost, s), "convergence flag");
+        CUDA_TRY(cudaStreamSynchronize(s), "convergence flag");
+        if (done) break;
+      }
+    }
+    it = done ? done : maxit;
+    rr = host_total(g, S_RR, s, e);
+    CUDA_TRY(e, "residual norm");
+  }
+  if (g->prec == EB_F64) launch_correct<double>(g, mom, dt, s);
+  else launch_correct<float>(g, mom, dt, s);
+  if (phi_out) CUDA_TRY(cudaMemcpyAsync(phi_out, w.x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s), "phi");
+  CUDA_TRY(cudaGetLastError(), "projection");
+  if (iters) *iters = it;
+  if (relres) *relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  return EB_OK;
+}
+
+extern "C" {
+
+eb_status eb_project(eb_geom geom, eb_state *U, double dt, double rtol, int maxit, const double *phi0, double *phi,
+                     int *iters, double *relres, void *stream) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  const size_t es = geom->prec == EB_F64 ? 8 : 4;
+  if (!state_ok(U, es)) return fail(EB_ERR_INVALID_ARG, "state pointer NULL or misaligned");
+  if (!(dt > 0.0) || !isfinite(dt)) return fail(EB_ERR_INVALID_ARG, "dt must be finite and > 0");
+  if (!(rtol > 0.0) || !(rtol < 1.0)) return fail(EB_ERR_INVALID_ARG, "rtol must lie in (0, 1)");
+  if (maxit < 0) return fail(EB_ERR_INVALID_ARG, "maxit must be >= 0");
+  if ((phi0 && ((uintptr_t)phi0 % 8)) || (phi && ((uintptr_t)phi % 8)))
+    return fail(EB_ERR_INVALID_ARG, "phi pointer misaligned");
+  void **u = state_ptrs(U);
+  void *mom[3] = {u[2], u[3], u[4]};
+  return eb_project_impl(geom, mom, dt, rtol, maxit, phi0, phi, iters, relres, as_stream(stream));
+}
+
+eb_status eb_anelastic_step(eb_geom geom, const eb_state *Un, eb_state *Unp1, double dt, int nsteps, double rtol,
+                            int maxit, int *iters, void *stream) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  if (!geom->has_ref) return fail(EB_ERR_STATE, "the anelastic step needs a handle built with a reference profile");
+  const size_t es = geom->prec == EB_F64 ? 8 : 4;
+  if (!state_ok(Un, es) || !state_ok(Unp1, es)) return fail(EB_ERR_INVALID_ARG, "state pointer NULL or misaligned");
+  if (!(dt > 0.0) || !isfinite(dt)) return fail(EB_ERR_INVALID_ARG, "dt must be finite and > 0");
+  if (nsteps < 1) return fail(EB_ERR_INVALID_ARG, "nsteps must be >= 1");
+  if (!(rtol > 0.0) || !(rtol < 1.0)) return fail(EB_ERR_INVALID_ARG, "rtol must lie in (0, 1)");
+  if (maxit < 0) return fail(EB_ERR_INVALID_ARG, "maxit must be >= 0");
+  void **u0 = state_ptrs(Un), **u1 = state_ptrs(Unp1);
+  for (int f = 0; f < 5; ++f)
+    for (int e = 0; e < 5; ++e) {
+      const char *a = (const char *)u0[f], *b = (const char *)u1[e];
+      if (a < b + field_count(geom->D, e) * es && b < a + field_count(geom->D, f) * es)
+        return fail(EB_ERR_INVALID_ARG, "Un and Unp1 overlap");
+    }
+  cudaStream_t s = as_stream(stream);
+  // scratch states: C, D alternate between steps, A holds the first stage
+  for (int b = 0; b < 3; ++b)
+    for (int f = 0; f < 5; ++f)
+      if (!geom->scr[b][f]) {
+        cudaError_t e = cudaMalloc(&geom->scr[b][f], field_count(geom->D, f) * es);
+        if (e != cudaSuccess) return cuda_fail(e, "alloc step scratch");
+        geom->allocs.push_back(geom->scr[b][f]);
+      }
+  void **C = geom->scr[0], **Dd = geom->scr[1], **A = geom->scr[2];
+  void **cur = u0;
+  for (int n = 0; n < nsteps; ++n) {
+    void **dst = (n == nsteps - 1) ? u1 : (cur == C ? Dd : C);
+    void **srcs[2] = {cur, A}, **outs[2] = {A, dst};
+    const double frac[2] = {0.5, 1.0};
+    for (int q = 0; q < 2; ++q) {
+      if (geom->prec == EB_F64) stage<double>(geom, srcs[q], cur, outs[q], dt * frac[q], 1, s);
+      else stage<float>(geom, srcs[q], cur, outs[q], dt * frac[q], 1, s);
+      // the density stays at the reference: perturbation zero
+      CUDA_TRY(cudaMemsetAsync(outs[q][0], 0, field_count(geom->D, 0) * es, s), "density");
+      void *mom[3] = {outs[q][2], outs[q][3], outs[q][4]};
+      int it = 0;
+      const eb_status st = eb_project_impl(geom, mom, dt * frac[q], rtol, maxit, nullptr, nullptr, &it, nullptr, s);
+      if (st != EB_OK) return st;
+      if (iters) iters[2 * n + q] = it;
+    }
+    cur = dst;
+  }
+  CUDA_TRY(cudaGetLastError(), "anelastic step");
+  return EB_OK;
+}
+
+}  // extern "C"

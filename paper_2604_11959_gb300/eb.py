@@ -27,7 +27,7 @@ STATUS = {0: "EB_OK", 1: "EB_ERR_INVALID_ARG", 2: "EB_ERR_CUDA", 3: "EB_ERR_OOM"
 EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
                     "eb_wsrd_noalloc", "eb_step", "eb_step_profile", "eb_sync_status", "eb_last_error", "eb_version",
                     "eb_ensemble_create", "eb_ensemble_set_state", "eb_ensemble_get_state", "eb_ensemble_step",
-                    "eb_ensemble_tune", "eb_ensemble_destroy")
+                    "eb_ensemble_tune", "eb_ensemble_destroy", "eb_project", "eb_anelastic_step")
 
 
 class EbError(RuntimeError):
@@ -91,12 +91,14 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_ensemble_step.argtypes = [V, P(D), I, V]
     lib.eb_ensemble_tune.argtypes = [V, P(D), I, P(I), V]
     lib.eb_ensemble_destroy.argtypes = [V]
+    lib.eb_project.argtypes = [V, P(_State), D, D, I, V, V, P(I), P(D), V]
+    lib.eb_anelastic_step.argtypes = [V, P(_State), P(_State), D, I, D, I, P(I), V]
     lib.eb_last_error.restype = ctypes.c_char_p
     lib.eb_version.restype = I
     for name in ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
                  "eb_wsrd_noalloc", "eb_step", "eb_step_profile", "eb_sync_status", "eb_ensemble_create",
                  "eb_ensemble_set_state", "eb_ensemble_get_state", "eb_ensemble_step", "eb_ensemble_tune",
-                 "eb_ensemble_destroy"):
+                 "eb_ensemble_destroy", "eb_project", "eb_anelastic_step"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -237,6 +239,35 @@ def step_profile(geom: Geometry, Un: dict, out: dict, dt: float, stream=None):
     _check(load().eb_step_profile(geom.handle, ctypes.byref(geom._cstate(Un)), ctypes.byref(geom._cstate(out)),
                                   float(dt), _stream(stream), ms))
     return tuple(float(v) for v in ms)
+
+
+def project(geom: Geometry, U: dict, dt: float, rtol: float = 1e-10, maxit: int = 100000, phi0=None,
+            phi=None, stream=None):
+    """Projection of the face momenta of U in place (``eb_project``).
+    Returns (iterations, relative residual); phi (if given) receives the
+    solution, phi0 (if given) is the initial guess."""
+    shape = geom.shape(0)
+    for name, t in (("phi0", phi0), ("phi", phi)):
+        if t is not None:
+            _require_cuda(t, torch.float64, shape, name)
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    _check(load().eb_project(geom.handle, ctypes.byref(geom._cstate(U)), float(dt), float(rtol), int(maxit),
+                             phi0.data_ptr() if phi0 is not None else None,
+                             phi.data_ptr() if phi is not None else None, ctypes.byref(it), ctypes.byref(res),
+                             _stream(stream)))
+    return it.value, res.value
+
+
+def anelastic_step(geom: Geometry, Un: dict, dt: float, nsteps: int = 1, rtol: float = 1e-10,
+                   maxit: int = 100000, out: dict | None = None, stream=None):
+    """nsteps anelastic steps (``eb_anelastic_step``); returns (state,
+    iterations of every projection)."""
+    out = out if out is not None else geom.empty_state()
+    its = (ctypes.c_int * (2 * int(nsteps)))()
+    _check(load().eb_anelastic_step(geom.handle, ctypes.byref(geom._cstate(Un)), ctypes.byref(geom._cstate(out)),
+                                    float(dt), int(nsteps), float(rtol), int(maxit), its, _stream(stream)))
+    return out, list(its)
 
 
 def sync_status(geom: Geometry, stream=None) -> None:
