@@ -249,6 +249,17 @@ class Workload:
 WOA_32 = Workload("woa-ridge-32x32x16", 32, 32, 16, 10, terrain="woa", hmax=0.1)
 HILL_256 = Workload("gaussian-hill-256x256x128", 256, 256, 128, 100, terrain="gaussian", hmax=0.15)
 GRF_512 = Workload("grf-k3-512x512x256", 512, 512, 256, 50, terrain="grf", seed=3, hmax=0.2, tiny=16)
+GRF_192 = Workload("grf-k3-192x192x96", 192, 192, 96, 10, terrain="grf", seed=4, hmax=0.15)
+
+
+def anelastic_state(w: Workload, seed=0):
+    """The sheltered wind of ``w`` with the density at the reference profile
+    (the anelastic model's rho = rho0)."""
+    U = w.state("sheltered", seed=seed)
+    U = {f: np.array(v, copy=True) for f, v in U.items()}
+    rho0 = cell_reference(w.nz, w.Lz)[0]
+    U["rho"] = np.broadcast_to(rho0[:, None, None], U["rho"].shape).copy()
+    return U
 
 
 def ensemble_members():
