@@ -275,6 +275,70 @@ eb_status eb_anelastic_step(eb_geom geom, const eb_state *Un, eb_state *Unp1, do
                             int maxit, int *iters, void *stream);
 
 /*
+ * Warm-start network of the anelastic projection (the paper has no
+ * counterpart; it solves from the previous pressure or zero).  A three-level
+ * 3D U-Net: channels 16 / 32 / 64, two 3x3x3 convolutions with zero padding
+ * and ReLU per level, 2x2x2 average pooling down, 2x nearest upsampling up,
+ * skips concatenated after the upsampled channels, a 1x1 output head.
+ * Input: 2 channels (the projection's right-hand side over its RMS, and the
+ * c-cell volume fraction); output: 1 channel, trained to the mean-free
+ * solution over (RMS * dx^2 * scale).  BF16 weights (copied from FP32 master
+ * weights), FP32 activations and accumulation.  Parameters are one flat FP32
+ * vector: per layer, weights [cout][cin][k][k][k] then biases [cout].
+ * Tensors are device arrays [channels][nz][ny][nx]; a network object is
+ * sized for one grid (nx, ny, nz multiples of 4).  Calls on one network
+ * must be serialised.
+ */
+typedef struct eb_unet_s *eb_unet;
+
+/* Number of parameters (353,713). */
+int64_t eb_unet_num_params(void);
+
+/* Activation buffers for an nx x ny x nz grid; parameters start at zero. */
+eb_status eb_unet_create(int nx, int ny, int nz, eb_unet *out);
+
+/* Copy n = eb_unet_num_params() FP32 parameters from / to host memory
+ * (set also resets the optimiser state). Synchronous. */
+eb_status eb_unet_set_params(eb_unet net, const float *host, int64_t n);
+eb_status eb_unet_get_params(eb_unet net, float *host, int64_t n);
+
+/* out (nx*ny*nz floats) = network(in (2*nx*ny*nz floats)). */
+eb_status eb_unet_forward(eb_unet net, const float *in, float *out, void *stream);
+
+/* Masked loss 0.5 sum(mask (y - target)^2) / sum(mask > 0) and its
+ * gradient with respect to every parameter.  mask: 0 / 1 floats selecting at
+ * least one voxel.  loss (host, NULL allowed) and grad_host (host,
+ * eb_unet_num_params() floats, NULL allowed) are filled when given (the
+ * stream is then synchronised). */
+eb_status eb_unet_gradient(eb_unet net, const float *in, const float *target, const float *mask, float *loss,
+                           float *grad_host, void *stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on that
+ * gradient; loss (host, NULL allowed) as above. */
+eb_status eb_unet_train_step(eb_unet net, const float *in, const float *target, const float *mask, float lr,
+                             float *loss, void *stream);
+
+/* Waits for the device, then frees the network. */
+eb_status eb_unet_destroy(eb_unet net);
+
+/* A training sample for the network from the face momenta of U (not
+ * modified): in (2*N floats) = [rhs / rms, alpha] with rhs the projection's
+ * mean-free right-hand side and rms its RMS over the cells in the solve;
+ * target (N floats) = the mean-free solution of eb_project (zero start, rtol,
+ * maxit) over (rms * dx^2 * scale); mask (N floats) = 1 on the cells in the
+ * solve.  iters (host, NULL allowed): solver iterations.  EB_ERR_STATE when
+ * the momenta are already divergence-free. */
+eb_status eb_project_sample(eb_geom geom, const eb_state *U, double dt, double rtol, int maxit, double scale,
+                            float *in, float *target, float *mask, int *iters, void *stream);
+
+/* eb_project with the network's initial guess: phi0 = output * rms * dx^2 *
+ * scale on the cells in the solve (net created for the handle's grid, scale
+ * as in training).  The solve, its stopping rule and the correction are those
+ * of eb_project, so the converged result is the same to the tolerance. */
+eb_status eb_project_warm(eb_geom geom, eb_unet net, eb_state *U, double dt, double rtol, int maxit, double scale,
+                          int *iters, double *relres, void *stream);
+
+/*
  * Ensembles: many independent terrain instances advanced together.  The
  * paper has no counterpart (its AMReX box arrays are the closest); this is
  * the batched serving form of eb_step.

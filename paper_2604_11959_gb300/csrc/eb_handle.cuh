@@ -49,6 +49,8 @@ struct ProjWork {
   double *rhs = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x = nullptr;
   double *part = nullptr;      // partial sums, 8 slots of nb
   int *conv = nullptr;         // iteration count at convergence (0 = not yet)
+  double *alpha = nullptr;     // c-cell volume fractions (warm-start input), on first use
+  float *nin = nullptr, *nout = nullptr;   // network input (2 channels) and output, on first use
   double *host = nullptr;      // pinned copy of one slot of partial sums
 };
 
@@ -119,7 +121,10 @@ struct eb_geom_s {
 // Projection of the face momenta of U (Sec. 2.2 anelastic constraint),
 // implemented in eb_project.cu; phi0 may be NULL (zero start).
 eb_status eb_project_impl(eb_geom g, void *const mom[3], double dt, double rtol, int maxit, const double *phi0,
-                          double *phi_out, int *iters, double *relres, cudaStream_t s);
+                          double *phi_out, int *iters, double *relres, cudaStream_t s, bool correct);
+// The projection's mean-free right-hand side D(m)/dt into g->pw.rhs and its
+// RMS over the active cells (synchronises the stream).
+eb_status eb_project_rhs(eb_geom g, void *const mom[3], double dt, double *rms, cudaStream_t s);
 
 // (Re)build the bulk kernel's work split with slabs of slab_levels levels
 // (0: automatic); the previous split is released.

@@ -310,8 +310,23 @@ void launch_correct(eb_geom g, void *const mom[3], double dt, cudaStream_t s) {
 
 }  // namespace
 
+eb_status eb_project_rhs(eb_geom g, void *const mom[3], double dt, double *rms, cudaStream_t s) {
+  eb_status st = setup(g, s);
+  if (st != EB_OK) return st;
+  ProjWork &w = g->pw;
+  if (g->prec == EB_F64) launch_rhs<double>(g, mom, dt, s);
+  else launch_rhs<float>(g, mom, dt, s);
+  k_center<<<w.nb, PB, 0, s>>>(make_op(g), w.rhs, w.part + S_SUM * w.nb, w.part + S_CNT * w.nb, w.nb,
+                               w.part + S_BB * w.nb);
+  cudaError_t e = cudaSuccess;
+  const double bb = host_total(g, S_BB, s, e);
+  CUDA_TRY(e, "right-hand side");
+  if (rms) *rms = w.nact > 0 ? sqrt(bb / (double)w.nact) : 0.0;
+  return EB_OK;
+}
+
 eb_status eb_project_impl(eb_geom g, void *const mom[3], double dt, double rtol, int maxit, const double *phi0,
-                          double *phi_out, int *iters, double *relres, cudaStream_t s) {
+                          double *phi_out, int *iters, double *relres, cudaStream_t s, bool correct) {
   eb_status st = setup(g, s);
   if (st != EB_OK) return st;
   ProjWork &w = g->pw;
@@ -352,8 +367,10 @@ eb_status eb_project_impl(eb_geom g, void *const mom[3], double dt, double rtol,
     rr = host_total(g, S_RR, s, e);
     CUDA_TRY(e, "residual norm");
   }
-  if (g->prec == EB_F64) launch_correct<double>(g, mom, dt, s);
-  else launch_correct<float>(g, mom, dt, s);
+  if (correct) {
+    if (g->prec == EB_F64) launch_correct<double>(g, mom, dt, s);
+    else launch_correct<float>(g, mom, dt, s);
+  }
   if (phi_out) CUDA_TRY(cudaMemcpyAsync(phi_out, w.x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s), "phi");
   CUDA_TRY(cudaGetLastError(), "projection");
   if (iters) *iters = it;
@@ -375,7 +392,7 @@ eb_status eb_project(eb_geom geom, eb_state *U, double dt, double rtol, int maxi
     return fail(EB_ERR_INVALID_ARG, "phi pointer misaligned");
   void **u = state_ptrs(U);
   void *mom[3] = {u[2], u[3], u[4]};
-  return eb_project_impl(geom, mom, dt, rtol, maxit, phi0, phi, iters, relres, as_stream(stream));
+  return eb_project_impl(geom, mom, dt, rtol, maxit, phi0, phi, iters, relres, as_stream(stream), true);
 }
 
 eb_status eb_anelastic_step(eb_geom geom, const eb_state *Un, eb_state *Unp1, double dt, int nsteps, double rtol,
@@ -417,7 +434,8 @@ eb_status eb_anelastic_step(eb_geom geom, const eb_state *Un, eb_state *Unp1, do
       CUDA_TRY(cudaMemsetAsync(outs[q][0], 0, field_count(geom->D, 0) * es, s), "density");
       void *mom[3] = {outs[q][2], outs[q][3], outs[q][4]};
       int it = 0;
-      const eb_status st = eb_project_impl(geom, mom, dt * frac[q], rtol, maxit, nullptr, nullptr, &it, nullptr, s);
+      const eb_status st =
+          eb_project_impl(geom, mom, dt * frac[q], rtol, maxit, nullptr, nullptr, &it, nullptr, s, true);
       if (st != EB_OK) return st;
       if (iters) iters[2 * n + q] = it;
     }

@@ -27,7 +27,10 @@ STATUS = {0: "EB_OK", 1: "EB_ERR_INVALID_ARG", 2: "EB_ERR_CUDA", 3: "EB_ERR_OOM"
 EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
                     "eb_wsrd_noalloc", "eb_step", "eb_step_profile", "eb_sync_status", "eb_last_error", "eb_version",
                     "eb_ensemble_create", "eb_ensemble_set_state", "eb_ensemble_get_state", "eb_ensemble_step",
-                    "eb_ensemble_tune", "eb_ensemble_destroy", "eb_project", "eb_anelastic_step")
+                    "eb_ensemble_tune", "eb_ensemble_destroy", "eb_project", "eb_anelastic_step",
+                    "eb_unet_num_params", "eb_unet_create", "eb_unet_set_params", "eb_unet_get_params",
+                    "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step", "eb_unet_destroy",
+                    "eb_project_sample", "eb_project_warm")
 
 
 class EbError(RuntimeError):
@@ -93,12 +96,25 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_ensemble_destroy.argtypes = [V]
     lib.eb_project.argtypes = [V, P(_State), D, D, I, V, V, P(I), P(D), V]
     lib.eb_anelastic_step.argtypes = [V, P(_State), P(_State), D, I, D, I, P(I), V]
+    F, L = ctypes.c_float, ctypes.c_int64
+    lib.eb_unet_num_params.restype = L
+    lib.eb_unet_create.argtypes = [I, I, I, P(V)]
+    lib.eb_unet_set_params.argtypes = [V, V, L]
+    lib.eb_unet_get_params.argtypes = [V, V, L]
+    lib.eb_unet_forward.argtypes = [V, V, V, V]
+    lib.eb_unet_gradient.argtypes = [V, V, V, V, P(F), V, V]
+    lib.eb_unet_train_step.argtypes = [V, V, V, V, F, P(F), V]
+    lib.eb_unet_destroy.argtypes = [V]
+    lib.eb_project_sample.argtypes = [V, P(_State), D, D, I, D, V, V, V, P(I), V]
+    lib.eb_project_warm.argtypes = [V, V, P(_State), D, D, I, D, P(I), P(D), V]
     lib.eb_last_error.restype = ctypes.c_char_p
     lib.eb_version.restype = I
     for name in ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
                  "eb_wsrd_noalloc", "eb_step", "eb_step_profile", "eb_sync_status", "eb_ensemble_create",
                  "eb_ensemble_set_state", "eb_ensemble_get_state", "eb_ensemble_step", "eb_ensemble_tune",
-                 "eb_ensemble_destroy", "eb_project", "eb_anelastic_step"):
+                 "eb_ensemble_destroy", "eb_project", "eb_anelastic_step", "eb_unet_create", "eb_unet_set_params",
+                 "eb_unet_get_params", "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step",
+                 "eb_unet_destroy", "eb_project_sample", "eb_project_warm"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -352,3 +368,101 @@ class Ensemble:
         best = ctypes.c_int(0)
         _check(load().eb_ensemble_tune(self.handle, self._dt(dt), int(reps), ctypes.byref(best), _stream(stream)))
         return best.value
+
+
+class UNet:
+    """The warm-start network of the projection (``eb_unet_*``), sized for
+    one grid.  Parameters are a flat float32 numpy vector."""
+
+    def __init__(self, nx: int, ny: int, nz: int):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.eb_unet_create(int(nx), int(ny), int(nz), ctypes.byref(h)))
+        self._h = h
+        self.shape = (int(nz), int(ny), int(nx))
+        self.n = int(lib.eb_unet_num_params())
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("network is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().eb_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.n:
+            raise ValueError("wrong parameter count")
+        _check(load().eb_unet_set_params(self.handle, p.ctypes.data, self.n))
+
+    def get_params(self):
+        import numpy as np
+        p = np.zeros(self.n, dtype=np.float32)
+        _check(load().eb_unet_get_params(self.handle, p.ctypes.data, self.n))
+        return p
+
+    def _need(self, t, ch, name):
+        _require_cuda(t, torch.float32, (ch,) + self.shape if ch > 1 else self.shape, name)
+
+    def forward(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        self._need(x, 2, "input")
+        out = out if out is not None else torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        self._need(out, 1, "out")
+        _check(load().eb_unet_forward(self.handle, x.data_ptr(), out.data_ptr(), _stream(stream)))
+        return out
+
+    def gradient(self, x, target, mask, stream=None):
+        """(loss, flat gradient as numpy float32)."""
+        import numpy as np
+        for t, ch, nm in ((x, 2, "input"), (target, 1, "target"), (mask, 1, "mask")):
+            self._need(t, ch, nm)
+        loss = ctypes.c_float(0.0)
+        g = np.zeros(self.n, dtype=np.float32)
+        _check(load().eb_unet_gradient(self.handle, x.data_ptr(), target.data_ptr(), mask.data_ptr(),
+                                       ctypes.byref(loss), g.ctypes.data, _stream(stream)))
+        return loss.value, g
+
+    def train_step(self, x, target, mask, lr: float, want_loss: bool = False, stream=None):
+        for t, ch, nm in ((x, 2, "input"), (target, 1, "target"), (mask, 1, "mask")):
+            self._need(t, ch, nm)
+        loss = ctypes.c_float(0.0)
+        _check(load().eb_unet_train_step(self.handle, x.data_ptr(), target.data_ptr(), mask.data_ptr(),
+                                         float(lr), ctypes.byref(loss) if want_loss else None, _stream(stream)))
+        return loss.value if want_loss else None
+
+
+def project_sample(geom: Geometry, U: dict, dt: float, scale: float, rtol: float = 1e-10, maxit: int = 100000,
+                   stream=None):
+    """A training sample (input, target, mask, iterations) from the momenta
+    of U (``eb_project_sample``)."""
+    shape = geom.shape(0)
+    x = torch.empty((2,) + shape, dtype=torch.float32, device="cuda")
+    t = torch.empty(shape, dtype=torch.float32, device="cuda")
+    m = torch.empty(shape, dtype=torch.float32, device="cuda")
+    it = ctypes.c_int(0)
+    _check(load().eb_project_sample(geom.handle, ctypes.byref(geom._cstate(U)), float(dt), float(rtol), int(maxit),
+                                    float(scale), x.data_ptr(), t.data_ptr(), m.data_ptr(), ctypes.byref(it),
+                                    _stream(stream)))
+    return x, t, m, it.value
+
+
+def project_warm(geom: Geometry, net: UNet, U: dict, dt: float, scale: float, rtol: float = 1e-10,
+                 maxit: int = 100000, stream=None):
+    """Projection of U's momenta in place from the network's initial guess
+    (``eb_project_warm``); returns (iterations, relative residual)."""
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    _check(load().eb_project_warm(geom.handle, net.handle, ctypes.byref(geom._cstate(U)), float(dt), float(rtol),
+                                  int(maxit), float(scale), ctypes.byref(it), ctypes.byref(res), _stream(stream)))
+    return it.value, res.value
