@@ -138,3 +138,32 @@ def test_warm_started_projection_is_the_same_projection(eb):
     assert its > 0 and float(m.sum()) > 0 and torch.isfinite(t).all()
     net.close()
     geo.close()
+
+
+def test_trained_network_saves_iterations(eb):
+    """Train the network briefly on small random terrains with the library's
+    own samples and kernels, then compare cold and warm starts on held-out
+    terrains: the warm start saves iterations at a loose tolerance and never
+    costs more than a few at 1e-10, with the same converged result."""
+    from paper_2604_11959_gb300 import warmstart as ws
+    r = ws.Recipe(nx=32, ny=32, nz=16, dx=1.0 / 64.0, terrains=12, states_per_terrain=6, epochs=6, lr=2e-3,
+                  seed=300)
+    scale = ws.target_scale(r)
+    data, _ = ws.make_dataset(r, scale)
+    net = ws.train(r, data)
+    params = net.get_params()
+    net.close()
+    cold_l, warm_l, cold_t, warm_t = [], [], [], []
+    for q in range(4):
+        w = ws.workload(r, 900 + q)
+        g, refs = ws.geometry(w)
+        c, h, rc, rw, d = ws.compare(g, params, w, refs, 5 + q, scale, rtol=1e-4)
+        cold_l.append(c)
+        warm_l.append(h)
+        c, h, rc, rw, d = ws.compare(g, params, w, refs, 5 + q, scale, rtol=1e-10)
+        cold_t.append(c)
+        warm_t.append(h)
+        assert rw <= 1e-10 and d <= 1e-7
+        g.close()
+    assert np.mean(warm_l) < np.mean(cold_l), (cold_l, warm_l)
+    assert np.mean(warm_t) <= np.mean(cold_t) + 5, (cold_t, warm_t)
