@@ -17,6 +17,7 @@ replica of the workload; value = all ranks' cell-updates / max time.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import hashlib
 import json
 import os
@@ -51,6 +52,8 @@ def parse():
     ap.add_argument("--precision", choices=("both", "mixed", "f64"), default="both",
                     help="arms to run (profiling runs pick one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--slab-levels", type=int, default=None,
+                    help="bulk kernel slab height (0 = automatic); default: chosen by the autotuner")
     return ap.parse_args()
 
 
@@ -115,7 +118,7 @@ def run_warmstart(eb, terrains, epochs):
                        "momentum_diff": big[4], "ratio": big[0] / max(1, big[1])}}
 
 
-def run_anelastic(eb, steps, warmup):
+def run_anelastic(eb, steps, warmup, clk=None):
     """Anelastic steps (Algorithm 2, two stages, projection to a relative
     residual of 1e-10 from a zero guess) on the 192x192x96 random terrain,
     mixed path; and one projection timed alone.  Per PCG iteration the
@@ -134,10 +137,11 @@ def run_anelastic(eb, steps, warmup):
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    out, its = eb.anelastic_step(g, U, dt, steps, rtol=1e-10)
-    b.record(stream)
-    torch.cuda.synchronize()
+    with clk or contextlib.nullcontext():
+        a.record(stream)
+        out, its = eb.anelastic_step(g, U, dt, steps, rtol=1e-10)
+        b.record(stream)
+        torch.cuda.synchronize()
     ms_step = a.elapsed_time(b) / steps
     eb.sync_status(g)
     # one projection alone: the divergent momenta of the initial state
@@ -162,7 +166,7 @@ def run_anelastic(eb, steps, warmup):
             "workload": w.name}
 
 
-def run_ensemble(eb, steps, warmup):
+def run_ensemble(eb, steps, warmup, clk=None):
     """64 uneven Gaussian-hill instances (64x64x32 .. 256x256x64, 94,371,840
     cells), mixed path, advanced together: one CUDA-graph launch per step,
     slab heights chosen by the autotuner.  The states (3.8 GB) exceed L2,
@@ -191,11 +195,12 @@ def run_ensemble(eb, steps, warmup):
     stream = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
-    for q in range(steps):
-        evs[q][0].record(stream)
-        ens.step(dts, 1)
-        evs[q][1].record(stream)
-    torch.cuda.synchronize()
+    with clk or contextlib.nullcontext():
+        for q in range(steps):
+            evs[q][0].record(stream)
+            ens.step(dts, 1)
+            evs[q][1].record(stream)
+        torch.cuda.synchronize()
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     for g in geoms:
         eb.sync_status(g)
@@ -230,17 +235,65 @@ def peaks():
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
+class _Nvml:
+    """Read-only NVML queries through ctypes (SM clock, its maximum and the
+    clock event reasons); None where the library is not there."""
+    # reason bits of nvmlDeviceGetCurrentClocksEventReasons (public nvml.h)
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    @classmethod
+    def open(cls, device_index):
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            import torch
+            p = torch.cuda.get_device_properties(device_index)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) != 0:
+                return None
+            self = cls()
+            self.lib, self.h, self.ct = lib, h, ctypes
+            get = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.reasons_fn = get
+            return self
+        except Exception:
+            return None
+
+    def sample(self):
+        c, m, r = self.ct.c_uint(), self.ct.c_uint(), self.ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, 1, self.ct.byref(c)) != 0:   # NVML_CLOCK_SM
+            return None
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, self.ct.byref(m))
+        self.reasons_fn(self.h, self.ct.byref(r))
+        return float(c.value), float(m.value), [k for k, b in self.BITS.items() if r.value & b]
+
+
 class ClockSampler:
+    """SM clock and clock event reasons sampled DURING a timed region: NVML
+    every 0.5 ms from a thread when the library is there (a timed loop of a
+    few tens of milliseconds still gets dozens of samples), else
+    nvidia-smi -lms 20.  Enter it around the timed loop only."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index):
-        self.lines = []
+        self.sm, self.mx, self.reasons = [], None, set()
         self.proc = None
         self.dev = device_index
+        self.nvml = _Nvml.open(device_index)
+        self.source = "nvml" if self.nvml else "nvidia-smi"
 
     def __enter__(self):
+        self.stop = threading.Event()
+        if self.nvml:
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            return self
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
                                           "-lms", "20", "-i", str(self.dev)], stdout=subprocess.PIPE,
@@ -251,12 +304,36 @@ class ClockSampler:
             self.proc = None
         return self
 
+    def _poll(self):
+        while not self.stop.is_set():
+            r = self.nvml.sample()
+            if r:
+                self.sm.append(r[0])
+                self.mx = r[1]
+                self.reasons.update(r[2])
+            time.sleep(0.0005)
+
     def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.proc.stdout:
+            parts = [p.strip() for p in ln.strip().split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm, mx = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            self.sm.append(sm)
+            self.mx = mx
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    self.reasons.add(nm)
 
     def __exit__(self, *a):
-        if self.proc:
+        self.stop.set()
+        if self.nvml:
+            self.t.join(timeout=5)
+        elif self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -264,23 +341,11 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        if not self.sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "source": self.source}
+        return {"sm_mhz": float(np.median(self.sm)), "sm_max_mhz": self.mx, "reasons": sorted(self.reasons),
+                "samples": len(self.sm), "sm_mhz_min": float(np.min(self.sm)), "source": self.source,
+                "window": "timed steps only"}
 
 
 # ---------------------------------------------------------------------------
@@ -335,7 +400,7 @@ def traffic_record(kernel, workload_name, precision):
         return None
 
 
-def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist):
+def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=None, slab_levels=None):
     import torch
     geom = eb.Geometry(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, torch.from_numpy(h).cuda(), precision=precision,
                        ref_rho=torch.from_numpy(refs[0]).cuda(), ref_rhotheta=torch.from_numpy(refs[1]).cuda())
@@ -345,6 +410,11 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist):
     # different, eventually degenerate, flow); outputs alternate between two
     # buffers and the L2 is flushed before each timed step
     A = eb.device_state(U, precision, refs)
+    if slab_levels is None:
+        slab = eb.tune(geom, A, w.dt(), reps=5)   # autotuned slab height of the bulk kernel's tiles
+    else:
+        slab = slab_levels
+        eb.set_slab_levels(geom, slab)
     outs = [geom.empty_state(), geom.empty_state()]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     dt = w.dt()
@@ -357,12 +427,13 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist):
         dist.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for q in range(steps):
-        flush.zero_()   # evict the state from L2 (untimed)
-        evs[q][0].record(stream)
-        eb.step(geom, A, dt, 1, out=outs[q % 2])
-        evs[q][1].record(stream)
-    torch.cuda.synchronize()
+    with clk or contextlib.nullcontext():
+        for q in range(steps):
+            flush.zero_()   # evict the state from L2 (untimed)
+            evs[q][0].record(stream)
+            eb.step(geom, A, dt, 1, out=outs[q % 2])
+            evs[q][1].record(stream)
+        torch.cuda.synchronize()
     if dist:
         dist.barrier()
     wall = time.perf_counter() - wall0
@@ -406,6 +477,7 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist):
         "step_frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm,
         "gpu_launches": launches_per_step * steps,
         "steps": steps,
+        "tuned_slab_levels": slab,
     }
     return geom, res
 
@@ -529,8 +601,7 @@ def main():
         libbuild.build()
         eb.load()
         clk = ClockSampler(torch.cuda.current_device())
-        with clk:
-            r = run_anelastic(eb, args.steps, args.warmup)
+        r = run_anelastic(eb, args.steps, args.warmup, clk)
         if rank == 0:
             print(json.dumps({
                 "metric": METRIC, "value": r["value"] * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -548,8 +619,7 @@ def main():
         libbuild.build()
         eb.load()
         clk = ClockSampler(torch.cuda.current_device())
-        with clk:
-            r = run_ensemble(eb, args.steps, max(3, args.warmup))
+        r = run_ensemble(eb, args.steps, max(3, args.warmup), clk)
         if rank == 0:
             print(json.dumps({
                 "metric": METRIC, "value": r["value"] * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -580,13 +650,14 @@ def main():
     mixed = f64 = e2e_res = None
     clk = ClockSampler(dev_index)
     if args.precision in ("both", "mixed"):
-        with clk:
-            geom, mixed = run_precision(eb, w, h, U, refs, "mixed", args.steps, args.warmup, world, dist)
+        geom, mixed = run_precision(eb, w, h, U, refs, "mixed", args.steps, args.warmup, world, dist, clk,
+                                    args.slab_levels)
         if rank == 0 and not args.no_e2e:
             e2e_res = e2e(eb, geom, w, U, refs, "mixed", min(args.steps, 20))
         geom.close()
     if args.precision in ("both", "f64"):
-        geom64, f64 = run_precision(eb, w, h, U, refs, "f64", max(10, args.steps // 10), args.warmup, world, dist)
+        geom64, f64 = run_precision(eb, w, h, U, refs, "f64", max(10, args.steps // 10), args.warmup, world, dist,
+                                    None if mixed else clk, args.slab_levels)
         geom64.close()
     acc = None
     if rank == 0 and args.precision == "both":
@@ -606,6 +677,7 @@ def main():
         "config": {"workload": w.name, "cells": w.cells(), "precision": "mixed" if mixed else "f64", "stages": 1,
                    "state": "stratified, wind u=1 above the terrain, smooth seeded perturbations",
                    "l2": "512 MiB buffer written before every timed step (untimed); per-step CUDA events",
+                   "tuned_slab_levels": head.get("tuned_slab_levels"),
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "roofline": head["roofline"],
         "step_hbm_frac": head["step_frac"],

@@ -379,6 +379,19 @@ eb_status eb_ensemble_tune(eb_ensemble e, const double *dt, int reps, int *slab_
 /* Waits for the device, then frees the ensemble's buffers. */
 eb_status eb_ensemble_destroy(eb_ensemble e);
 
+/* Autotuner of one handle: times reps steps of eb_step(nsteps = 1,
+ * stages = 1) from U (read only; the results go to a temporary state) for each
+ * candidate slab height of the bulk kernel's tiles (automatic, 12 .. 64
+ * levels, whole column) and keeps the fastest; *slab_levels (NULL allowed)
+ * receives it (0 = automatic).  Results of later steps do not depend on it.
+ * Synchronises the stream; allocates and frees the temporary state. */
+eb_status eb_geom_tune(eb_geom geom, const eb_state *U, double dt, int reps, int *slab_levels, void *stream);
+
+/* Sets the bulk kernel's slab height directly (0 = automatic; heights above
+ * nz mean whole columns), e.g. to re-apply a height eb_geom_tune chose
+ * earlier.  Waits for the device to be idle (the old plan may be in use). */
+eb_status eb_geom_set_slab_levels(eb_geom geom, int slab_levels);
+
 /* Synchronise the stream, then return (and clear) the first device-side
  * error latched since the last call: EB_ERR_NUMERIC or EB_ERR_TIMEOUT. */
 eb_status eb_sync_status(eb_geom geom, void *stream);

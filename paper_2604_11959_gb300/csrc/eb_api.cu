@@ -243,6 +243,42 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
     cudaFree(scan_tmp);
     if (e != cudaSuccess) return cuda_fail(e, "face lists");
   }
+  // near-EB rows of the CVs with a record: count, scan, allocate, fill
+  for (int q = 0; q < 4; ++q) {
+    GridDev &G = g->G[q];
+    const long long nr = G.nband_rec;
+    const long long n = 3 * nr + 1;
+    long long *cnt = nullptr, *scan_tmp = nullptr;
+    cudaError_t e = cudaMalloc(&cnt, sizeof(long long) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&scan_tmp, sizeof(long long) * (size_t)(n / 256 + 16));
+    long long nt = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(long long) * (size_t)n, s);
+    if (e == cudaSuccess) {
+      launch_band_rows(D, g->G, q, false, cnt, s);
+      scan_exclusive(cnt, n, scan_tmp, s);
+      e = cudaMemcpyAsync(&nt, scan_tmp, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && nt >= (1LL << 32)) {
+      cudaFree(cnt);
+      cudaFree(scan_tmp);
+      return fail(EB_ERR_INVALID_ARG, "near-EB rows exceed 2^32 terms");
+    }
+    G.nterm = nt;
+    if (e == cudaSuccess) e = g->alloc(&G.srow, n);
+    if (e == cudaSuccess) e = g->alloc(&G.sidx, nt);
+    if (e == cudaSuccess) e = g->alloc(&G.scoef, nt);
+    if (e == cudaSuccess) e = g->alloc(&G.scoef_f, nt);
+    if (e == cudaSuccess) e = g->alloc(&G.stiny, nr);
+    if (e == cudaSuccess) {
+      launch_band_rows(D, g->G, q, true, cnt, s);
+      launch_rows_to_u32(cnt, n, G.srow, s);
+      e = cudaStreamSynchronize(s);
+    }
+    cudaFree(cnt);
+    cudaFree(scan_tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "near-EB rows");
+  }
   long long *tmp = nullptr;
   CUDA_TRY(g->alloc(&tmp, tmp_need), "alloc set-up scratch");
   for (int q = 0; q < 4; ++q) {
@@ -604,6 +640,70 @@ eb_status eb_step_profile(eb_geom geom, const eb_state *Un, eb_state *Unp1, doub
   }
   for (int q = 0; q < 4; ++q) cudaEventDestroy(ev[q]);
   CUDA_TRY(e, "profiled step");
+  return EB_OK;
+}
+
+eb_status eb_geom_set_slab_levels(eb_geom geom, int slab_levels) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  if (slab_levels < 0) return fail(EB_ERR_INVALID_ARG, "slab_levels must be >= 0");
+  CUDA_TRY(cudaDeviceSynchronize(), "drain before re-planning");
+  return eb_replan_bulk(geom, slab_levels);
+}
+
+eb_status eb_geom_tune(eb_geom geom, const eb_state *U, double dt, int reps, int *slab_levels, void *stream) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  const size_t es = geom->prec == EB_F64 ? 8 : 4;
+  if (!state_ok(U, es)) return fail(EB_ERR_INVALID_ARG, "state pointer NULL or misaligned");
+  if (!(dt > 0.0) || !isfinite(dt)) return fail(EB_ERR_INVALID_ARG, "dt must be finite and > 0");
+  if (reps < 1) return fail(EB_ERR_INVALID_ARG, "reps must be >= 1");
+  cudaStream_t s = as_stream(stream);
+  // the trial steps write into a handle-owned state (allocated here)
+  void *out[5] = {};
+  for (int f = 0; f < 5; ++f) {
+    const cudaError_t e = cudaMalloc(&out[f], field_count(geom->D, f) * es);
+    if (e != cudaSuccess) {
+      for (int q = 0; q < f; ++q) cudaFree(out[q]);
+      return cuda_fail(e, "alloc tuning state");
+    }
+  }
+  eb_state O;
+  void **op = state_ptrs(&O);
+  for (int f = 0; f < 5; ++f) op[f] = out[f];
+  std::vector<int> cand = {0, 12, 16, 24, 32, 48, 64};
+  if (geom->D.nz > 64) cand.push_back(geom->D.nz);
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  float best = 0.f;
+  int best_c = 0;
+  eb_status st = EB_OK;
+  for (int c : cand) {
+    if ((st = eb_replan_bulk(geom, c)) != EB_OK) break;
+    if ((st = eb_step(geom, U, &O, dt, 1, 1, stream)) != EB_OK) break;   // warm-up
+    cudaEventRecord(t0, s);
+    for (int q = 0; q < reps && st == EB_OK; ++q) st = eb_step(geom, U, &O, dt, 1, 1, stream);
+    cudaEventRecord(t1, s);
+    if (st != EB_OK) break;
+    const cudaError_t e = cudaEventSynchronize(t1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "tuning step");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    if (c == cand[0] || ms < best) {
+      best = ms;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  cudaStreamSynchronize(s);
+  for (int f = 0; f < 5; ++f) cudaFree(out[f]);
+  cudaMemset(geom->status, 0, sizeof(unsigned));   // flags of the trial steps
+  if (st != EB_OK) return st;
+  if ((st = eb_replan_bulk(geom, best_c)) != EB_OK) return st;
+  if (slab_levels) *slab_levels = best_c;
   return EB_OK;
 }
 

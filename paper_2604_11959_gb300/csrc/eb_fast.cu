@@ -32,6 +32,7 @@
 #include "eb_step.cuh"
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 namespace {
@@ -361,9 +362,10 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
 #pragma unroll
         for (int G = 0; G < 4; ++G) sxy[G] = zero;
       }
-      if (k >= kbeg - 1) {
+      auto zstep = [&](auto H2) {
         // flux through the top of level k: masses from rho*w of levels k, k + 1
-        const bool has1 = k + 1 <= nz - 1, has2 = k + 2 <= nz - 1;
+        constexpr bool has2 = decltype(H2)::value;
+        const bool has1 = has2 || k + 1 <= nz - 1;
         const T *Rk = RAWP(k);
         const T *W1 = RAWP(k + 1) + 4 * NP;
         const P m = has1 ? ld2(W1 + self) : zero;
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
         const P fzc = flux6(m, th[0], th[1], th[2], th[3], has2);
         const P fzu = flux6(mu, uu[0], uu[1], uu[2], uu[3], has2);
         const P fzv = flux6(mv, vv[0], vv[1], vv[2], vv[3], has2);
-        const P fzw = flux6(mw, ww[0], ww[1], ww[2], ww[3], k + 2 <= nz);
+        const P fzw = flux6(mw, ww[0], ww[1], ww[2], ww[3], has2 || k + 2 <= nz);
         if (k >= kbeg && (k >= kfx || k >= kfy)) {
           const T *U = Rk + 2 * NP, *Vv = Rk + 3 * NP;
           const P uc = ld2(U + self);
@@ -421,6 +423,12 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
         zu = fzu;
         zv = fzv;
         zw = fzw;
+      };
+      // below the top two levels the far high CV of every z stencil exists:
+      // a copy of the z step without the run-time fallback selects
+      if (k >= kbeg - 1) {
+        if (k + 2 <= nz - 1) zstep(std::true_type());
+        else zstep(std::false_type());
       }
 #pragma unroll
       for (int G = 0; G < 4; ++G) {

@@ -45,6 +45,15 @@ struct GridDev {
   unsigned *blist;
   long long nband;
   long long nband_rec;   // blist[0, nband_rec): CVs with a record; the rest are regular
+  // near-EB rows of the CVs with a record: dU of CV blist[t] is
+  // sum over d of sum_{q = srow[3t+d]}^{srow[3t+d+1]-1} scoef[q] * fh[d][sidx[q]]
+  // (fhm for the mass of the c grid); built once per geometry
+  unsigned *srow;        // [3 * nband_rec + 1]
+  unsigned *sidx;        // [nterm] face index into the staged arrays of direction d
+  double *scoef;         // [nterm]
+  float *scoef_f;        // [nterm] float copies (mixed path)
+  uint8_t *stiny;        // [nband_rec] 1: tiny cut CV, whose row the mixed path sums in double
+  long long nterm;
   // redistribution per record
   uint8_t *code;
   int *nnb;

@@ -52,6 +52,13 @@ void launch_marks_fill(const uint8_t *m, long long n, const long long *pos, unsi
 void launch_export_geometry(const double *h, const Dims &D, int g, const GridDev &G, int field, double *dst,
                             cudaStream_t s);
 
+// eb_step.cu: near-EB rows of grid g (CVs with a record), two passes: the
+// term count of every (row, direction) segment into cnt[3t + d], then (after
+// the scan of cnt and the allocation of G[g].sidx / scoef / scoef_f / stiny)
+// the terms themselves at the scanned offsets
+void launch_band_rows(const Dims &D, const GridDev G[4], int g, bool fill, long long *cnt, cudaStream_t s);
+void launch_rows_to_u32(const long long *src, long long n, unsigned *dst, cudaStream_t s);
+
 // eb_fast.cu: split of the bulk kernel's (tile, level) work into lockstep
 // slabs of slab_levels levels (0: chosen from the GPU's size); seg holds
 // (tile, first level, end level, 0) per piece, off[b] .. off[b+1] the pieces

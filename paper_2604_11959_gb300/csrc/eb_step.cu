@@ -3,9 +3,12 @@
 //   flux + update (Eqs. update-cc / update-fc, Sec. 4.1):
 //     (the geometry-free bulk above each column's kfast level is in
 //     eb_fast.cu)
-//     k_band  : the non-covered CVs below kfast, with covered-neighbour
-//               fallbacks, open-face fractions and fluxes interpolated to the
-//               cut-face centroids.
+//     k_face_flux    : the provisional flux of every face the near-EB CVs
+//                      read, once, with covered-neighbour fallbacks;
+//     k_band         : the CVs below kfast with a geometry record: open-face
+//                      fractions and fluxes interpolated to the cut-face
+//                      centroids, as rows of coefficients built at set-up;
+//     k_band_regular : the other CVs below kfast (plain face differences).
 //   weighted state redistribution (Sec. 5.1, Eqs. qhat_omega, qrecon,
 //   final_update_omega), on compact lists built at set-up:
 //     k_qhat  : neighbourhood averages of the small CVs;
@@ -32,15 +35,6 @@ __device__ inline bool high_face_exists(const Dims &D, int g, int d, int k) {
   return g == 3 ? (k + 1 <= D.nz) : (k + 1 < D.nz);
 }
 
-// Usable neighbour face for the centroid interpolation: inside the domain
-// (w-grid x/y faces of the wall levels excluded) and open.
-__device__ inline bool face_usable(const GeoBand &geo, const Dims &D, int g, int d, int i, int j, int k) {
-  if (k < 0 || k >= nzg_of(D, g)) return false;
-  if (g == 3 && d != 2 && (k < 1 || k > D.nz - 1)) return false;
-  if (g != 3 && d == 2 && k == 0) return false;   // bottom wall faces carry no flux
-  return geo.beta<float>(D, g, d, i, j, k) > 0.0f;
-}
-
 // Flux through the centroid of the low d-face of CV (i,j,k): bilinear
 // interpolation of the provisional fluxes of the face and of the neighbour
 // faces toward which the centroid is offset (Sec. 4.1), read from the face
@@ -53,52 +47,75 @@ __device__ inline bool face_usable_dense(const GeoBand &geo, const Dims &D, int 
   return (geo.dense(D, g, i, j, k) >> (2 + d)) & 1;
 }
 
-template <typename T>
-__device__ void centroid_flux(const StepArgs<T> &A, const GeoBand &geo, int g, int d, int i, int j, int k, T &fm,
-                              T &fp) {
-  const Dims &D = A.D;
-  const T *FH = (const T *)A.G[g].fh[d];
-  const T *FM = (const T *)A.G[g].fhm[d];
-  const long long c = lin(D, i, j, k);
-  fp = FH[c];
-  fm = FM ? FM[c] : T(0);
-  T ga, gb;
-  geo.fcent<T>(D, g, d, i, j, k, ga, gb);
-  if (ga == T(0) && gb == T(0)) return;
+// The CV that owns a face (its low face): coordinates, state index, dense
+// flag byte and record (-1 without one), looked up once.
+struct FaceOwner {
+  int i, j, k;
+  long long c;
+  uint8_t flag;
+  long long rec;
+};
+
+__device__ inline FaceOwner face_owner(const GeoBand &geo, const Dims &D, int g, int i, int j, int k) {
+  FaceOwner o{i, j, k, lin(D, i, j, k), 0, -1};
+  if (k >= 0 && k < nzg_of(D, g)) {
+    o.flag = geo.G[g].dflag[o.c];
+    if (o.flag & 2) o.rec = geo.record(D, g, i, j, k);
+  }
+  return o;
+}
+
+// open area fraction of the owner's low d-face (float copies on the float path)
+template <typename R>
+__device__ inline R owner_beta(const GeoBand &geo, int g, int d, const FaceOwner &o) {
+  if (o.rec < 0) return (o.flag & 1) ? R(1) : R(0);
+  const long long r = (long long)d * geo.G[g].nrec + o.rec;
+  if (sizeof(R) == sizeof(double)) return (R)geo.G[g].beta[r];
+  return (R)geo.G[g].beta_f[r];
+}
+
+// (index, weight) terms of the flux through the centroid of the owner's low
+// d-face (Sec. 4.1): the face itself and the neighbour faces of the bilinear
+// interpolation toward the centroid; an offset is dropped when a face it
+// needs is closed or outside the domain.  At most four terms.
+__device__ inline int centroid_terms(const GeoBand &geo, const Dims &D, int g, int d, const FaceOwner &o,
+                                     long long idx[4], double w[4]) {
+  idx[0] = o.c;
+  w[0] = 1.0;
+  if (o.rec < 0) return 1;   // no record: open face, centroid at the centre
+  const GridDev &G = geo.G[g];
+  const double ga = G.fcent[(long long)(2 * d) * G.nrec + o.rec];
+  const double gb = G.fcent[(long long)(2 * d + 1) * G.nrec + o.rec];
+  if (ga == 0.0 && gb == 0.0) return 1;
+  const int i = o.i, j = o.j, k = o.k;
   const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
   int ea[3] = {0, 0, 0}, eb[3] = {0, 0, 0};
-  ea[ta] = ga >= T(0) ? 1 : -1;
-  eb[tb] = gb >= T(0) ? 1 : -1;
-  const bool ua = ga != T(0) && face_usable_dense(geo, D, g, d, i + ea[0], j + ea[1], k + ea[2]);
-  const bool ub = gb != T(0) && face_usable_dense(geo, D, g, d, i + eb[0], j + eb[1], k + eb[2]);
-  const bool uab = ga != T(0) && gb != T(0) &&
+  ea[ta] = ga >= 0.0 ? 1 : -1;
+  eb[tb] = gb >= 0.0 ? 1 : -1;
+  const bool ua = ga != 0.0 && face_usable_dense(geo, D, g, d, i + ea[0], j + ea[1], k + ea[2]);
+  const bool ub = gb != 0.0 && face_usable_dense(geo, D, g, d, i + eb[0], j + eb[1], k + eb[2]);
+  const bool uab = ga != 0.0 && gb != 0.0 &&
                    face_usable_dense(geo, D, g, d, i + ea[0] + eb[0], j + ea[1] + eb[1], k + ea[2] + eb[2]);
-  const bool za = ga != T(0) && (!ua || (gb != T(0) && !uab));
-  const bool zb = gb != T(0) && (!ub || (ga != T(0) && !uab));
-  const T wa = za ? T(0) : (ga < T(0) ? -ga : ga);
-  const T wb = zb ? T(0) : (gb < T(0) ? -gb : gb);
-  if (wa == T(0) && wb == T(0)) return;
-  const T w0 = (T(1) - wa) * (T(1) - wb);
-  fm *= w0;
-  fp *= w0;
-  if (wa != T(0)) {
-    const long long n = lin(D, i + ea[0], j + ea[1], k + ea[2]);
-    const T w = wa * (T(1) - wb);
-    fp += w * FH[n];
-    if (FM) fm += w * FM[n];
+  const bool za = ga != 0.0 && (!ua || (gb != 0.0 && !uab));
+  const bool zb = gb != 0.0 && (!ub || (ga != 0.0 && !uab));
+  const double wa = za ? 0.0 : fabs(ga);
+  const double wb = zb ? 0.0 : fabs(gb);
+  if (wa == 0.0 && wb == 0.0) return 1;
+  w[0] = (1.0 - wa) * (1.0 - wb);
+  int n = 1;
+  if (wa != 0.0) {
+    idx[n] = lin(D, i + ea[0], j + ea[1], k + ea[2]);
+    w[n++] = wa * (1.0 - wb);
   }
-  if (wb != T(0)) {
-    const long long n = lin(D, i + eb[0], j + eb[1], k + eb[2]);
-    const T w = wb * (T(1) - wa);
-    fp += w * FH[n];
-    if (FM) fm += w * FM[n];
+  if (wb != 0.0) {
+    idx[n] = lin(D, i + eb[0], j + eb[1], k + eb[2]);
+    w[n++] = wb * (1.0 - wa);
   }
-  if (wa != T(0) && wb != T(0)) {
-    const long long n = lin(D, i + ea[0] + eb[0], j + ea[1] + eb[1], k + ea[2] + eb[2]);
-    const T w = wa * wb;
-    fp += w * FH[n];
-    if (FM) fm += w * FM[n];
+  if (wa != 0.0 && wb != 0.0) {
+    idx[n] = lin(D, i + ea[0] + eb[0], j + ea[1] + eb[1], k + ea[2] + eb[2]);
+    w[n++] = wa * wb;
   }
+  return n;
 }
 
 template <typename T>
@@ -119,69 +136,148 @@ __device__ inline void write_out_d(const StepArgs<T> &A, int f, long long c, dou
   if (!isfinite(v)) atomicOr(A.status, EB_DEV_NUMERIC);
 }
 
-// dU of a non-covered CV near the EB (general geometry): Eqs. update-cc /
-// update-fc.  The face sums run in the state's precision, except for tiny cut
-// CVs (alpha < 1e-3) of the float path, whose sums, area fractions and
-// volume fraction are taken in double.
-template <typename T, typename R>
-__device__ void band_divergence(const StepArgs<T> &A, const GeoBand &geo, int g, int i, int j, int k, R &sm,
-                                R &sp) {
-  const Dims &D = A.D;
-  const R inv[3] = {R(D.idx), R(D.idy), R(D.idz)};
-  sm = R(0);
-  sp = R(0);
-#pragma unroll
+// Near-EB rows.  For a CV with a geometry record, the open area fractions,
+// the centroid interpolation weights, 1 / dx_d and 1 / alpha depend on the
+// geometry alone, so its dU of Eqs. update-cc / update-fc is a fixed linear
+// combination of the staged face fluxes: each term of the low d-face enters
+// with +beta w / (dx_d alpha), each term of the high d-face with
+// -beta w / (dx_d alpha).  The rows are built once per geometry (a count pass,
+// a scan, a fill pass) in double; every step applies them (k_band).
+struct RowBuild {
+  Dims D;
+  GridDev G[4];
+  int g;
+  long long *cnt;
+};
+
+template <bool FILL>
+__global__ void k_band_rows(RowBuild B) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int g = B.g;
+  const GridDev &G = B.G[g];
+  if (t >= G.nband_rec) return;
+  GeoBand geo;
+  geo.G = B.G;
+  const Dims &D = B.D;
+  int i, j, k;
+  split_index(D, G.blist[t], i, j, k);
+  const FaceOwner own = face_owner(geo, D, g, i, j, k);
+  const double alpha = own.rec >= 0 ? G.alpha[own.rec] : 1.0;
+  const double inv[3] = {D.idx, D.idy, D.idz};
+  long long pos = FILL ? B.cnt[3 * t] : 0;
   for (int d = 0; d < 3; ++d) {
-    const int di = d == 0, dj = d == 1, dk = d == 2;
-    const bool lo_wall = (g != 3 && d == 2 && k == 0);
-    const R bl = lo_wall ? R(0) : geo.beta<R>(D, g, d, i, j, k);
-    R bh = R(0);
-    if (high_face_exists(D, g, d, k)) bh = geo.beta<R>(D, g, d, i + di, j + dj, k + dk);
-    T ml = T(0), pl = T(0), mh = T(0), ph = T(0);
-    if (bl > R(0)) centroid_flux(A, geo, g, d, i, j, k, ml, pl);
-    if (bh > R(0)) centroid_flux(A, geo, g, d, i + di, j + dj, k + dk, mh, ph);
-    sm += (bh * (R)mh - bl * (R)ml) * inv[d];
-    sp += (bh * (R)ph - bl * (R)pl) * inv[d];
+    const bool lo_wall = g != 3 && d == 2 && k == 0;
+    const double bl = lo_wall ? 0.0 : owner_beta<double>(geo, g, d, own);
+    const bool hx = high_face_exists(D, g, d, k);
+    const FaceOwner hi = hx ? face_owner(geo, D, g, i + (d == 0), j + (d == 1), k + (d == 2))
+                            : FaceOwner{i, j, k, own.c, 0, -1};
+    const double bh = hx ? owner_beta<double>(geo, g, d, hi) : 0.0;
+    int n = 0;
+    for (int side = 0; side < 2; ++side) {
+      const double b = side ? -bh : bl;
+      if (b == 0.0) continue;
+      long long idx[4];
+      double w[4];
+      const int m = centroid_terms(geo, D, g, d, side ? hi : own, idx, w);
+      if (FILL) {
+        for (int q = 0; q < m; ++q, ++pos) {
+          const double coef = b * w[q] * inv[d] / alpha;
+          G.sidx[pos] = (unsigned)idx[q];
+          G.scoef[pos] = coef;
+          G.scoef_f[pos] = (float)coef;
+        }
+      }
+      n += m;
+    }
+    if (!FILL) B.cnt[3 * t + d] = n;
   }
+  if (FILL) G.stiny[t] = (own.rec >= 0 && alpha < 1e-3) ? 1 : 0;
 }
 
-template <typename T>
-__device__ void band_cv(const StepArgs<T> &A, int g, int i, int j, int k) {
-  const Dims &D = A.D;
-  GeoBand geo;
-  geo.G = A.G;
-  const long long c = lin(D, i, j, k);
-  const uint8_t f = geo.dense(D, g, i, j, k);
-  const bool rec = f & 2;
-  const long long r = rec ? geo.record(D, g, i, j, k) : -1;
-  const bool tiny = rec && A.G[g].alpha[r] < 1e-3;
-  if (sizeof(T) == sizeof(double) || tiny) {
-    const double alpha = rec ? A.G[g].alpha[r] : 1.0;
-    double sm, sp;
-    band_divergence<T, double>(A, geo, g, i, j, k, sm, sp);
-    const double ia = 1.0 / alpha;
-    if (g == 0) {
-      write_out_d(A, 0, c, -sm * ia);
-      write_out_d(A, 1, c, -sp * ia);
-    } else {
-      write_out_d(A, g + 1, c, -sp * ia);
-    }
-  } else {
-    const T ia = rec ? T(1) / (T)A.G[g].alpha_f[r] : T(1);
-    T sm, sp;
-    band_divergence<T, T>(A, geo, g, i, j, k, sm, sp);
-    if (g == 0) {
-      write_out(A, 0, c, -sm * ia);
-      write_out(A, 1, c, -sp * ia);
-    } else {
-      write_out(A, g + 1, c, -sp * ia);
-    }
-  }
+__global__ void k_rows_to_u32(const long long *src, long long n, unsigned *dst) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) dst[t] = (unsigned)src[t];
 }
 
 // Phase A of the near-EB path: the provisional flux of every listed face,
 // once (general geometry: covered-neighbour fallbacks, zero momentum of
 // covered CVs).
+// The provisional flux of Sec. 4.1 through the low Dd-face of CV c =
+// (i, j, k) of grid G, with the availability rules of the general face flux
+// (covered or absent CVs carry no momentum, the centred value replaces the
+// third-order one when the far upstream CV is not available), written for
+// one (grid, direction) pair at a time: every neighbour index is the face's
+// own index plus a periodic offset computed once.
+template <typename T, int G, int Dd>
+__device__ inline void face_flux_lean(const StepArgs<T> &A, long long c, int i, int j, int k, T &fm, T &fp) {
+  const Dims &D = A.D;
+  constexpr int S = G - 1;      // stagger direction of a face grid (c grid: none)
+  constexpr int MG = Dd + 1;    // momentum grid normal to the face
+  const int crd[3] = {i, j, k};
+  // index offset of a step s along direction dir from coordinate x (periodic in x, y)
+  auto off = [&](int dir, int x, int s) -> long long {
+    if (dir == 2) return (long long)s * D.nxy;
+    const int n = dir == 0 ? D.nx : D.ny;
+    int t = x + s;
+    t = t < 0 ? t + n : (t >= n ? t - n : t);
+    return (long long)(t - x) * (dir == 0 ? 1 : D.nx);
+  };
+  auto fluid = [&](int q, long long idx, int kk) -> bool {
+    return kk >= 0 && kk < nzg_of(D, q) && (A.G[q].dflag[idx] & 1);
+  };
+  // momentum of grid MG entering a mass flux
+  auto mom = [&](long long idx, int kk) -> T {
+    if (MG == 3 && (kk <= 0 || kk >= D.nz)) return T(0);
+    return fluid(MG, idx, kk) ? A.src.f[MG + 1][idx] : T(0);
+  };
+  auto rho = [&](long long idx, int kk) -> T { return A.src.ref_rho[kk] + A.src.f[0][idx]; };
+  // advected value of the grid-G CV t steps along Dd from the face's CV
+  auto advected = [&](int t) -> T {
+    const long long idx = c + off(Dd, crd[Dd], t);
+    const int kk = k + (Dd == 2 ? t : 0);
+    if (G == 0) return eb_div(A.src.ref_rt[kk] + A.src.f[1][idx], rho(idx, kk));
+    if (G == 3 && (kk <= 0 || kk >= D.nz)) return T(0);
+    // the two c-cells beside the face-grid CV: one step back along S, and
+    // itself (the CV's own coordinate along S, wrapped, when S is Dd)
+    const int cs = S == Dd ? (S == 2 ? kk : wrapi(crd[S] + t, S == 0 ? D.nx : D.ny)) : crd[S];
+    const long long ia = idx + off(S, cs, -1);
+    const int ka = kk - (S == 2 ? 1 : 0);
+    const bool a = fluid(0, ia, ka), b = fluid(0, idx, kk);
+    T rb;
+    if (a && b) rb = T(0.5) * (rho(ia, ka) + rho(idx, kk));
+    else if (a) rb = rho(ia, ka);
+    else if (b) rb = rho(idx, kk);
+    else return T(0);
+    return eb_div(A.src.f[G + 1][idx], rb);
+  };
+  auto cv_fluid = [&](int t) -> bool {
+    const long long idx = c + off(Dd, crd[Dd], t);
+    return fluid(G, idx, k + (Dd == 2 ? t : 0));
+  };
+  // mass flux
+  if (G == 0) {
+    fm = mom(c, k);
+  } else if (G == MG) {
+    fm = T(0.5) * (mom(c + off(Dd, crd[Dd], -1), k - (Dd == 2 ? 1 : 0)) + mom(c, k));
+  } else {
+    fm = T(0.5) * (mom(c + off(S, crd[S], -1), k - (S == 2 ? 1 : 0)) + mom(c, k));
+  }
+  fp = T(0);
+  if (fm == T(0)) return;
+  const T pL = advected(-1), pR = advected(0);
+  T val;
+  if (fm > T(0)) {
+    const bool has = cv_fluid(-2);
+    const T pF = has ? advected(-2) : T(0);
+    val = upwind_value(fm, pF, pL, pR, T(0), has, false);
+  } else {
+    const bool has = cv_fluid(1);
+    const T pF = has ? advected(1) : T(0);
+    val = upwind_value(fm, T(0), pL, pR, pF, false, has);
+  }
+  fp = fm * val;
+}
+
 template <typename T>
 __global__ void k_face_flux(StepArgs<T> A) {
   const Dims &D = A.D;
@@ -198,34 +294,50 @@ __global__ void k_face_flux(StepArgs<T> A) {
   const unsigned c = A.G[g].flist[d][t];
   int i, j, k;
   split_index(D, c, i, j, k);
-  GeoBand geo;
-  geo.G = A.G;
   T fm, fp;
-  // one compiled copy per (grid, direction): the generic flux code folds
-  // to the staggering of that pair
+  // one compiled copy per (grid, direction)
   switch (g * 3 + d) {
-    case 0: face_flux(A.src, geo, D, 0, 0, i, j, k, fm, fp); break;
-    case 1: face_flux(A.src, geo, D, 0, 1, i, j, k, fm, fp); break;
-    case 2: face_flux(A.src, geo, D, 0, 2, i, j, k, fm, fp); break;
-    case 3: face_flux(A.src, geo, D, 1, 0, i, j, k, fm, fp); break;
-    case 4: face_flux(A.src, geo, D, 1, 1, i, j, k, fm, fp); break;
-    case 5: face_flux(A.src, geo, D, 1, 2, i, j, k, fm, fp); break;
-    case 6: face_flux(A.src, geo, D, 2, 0, i, j, k, fm, fp); break;
-    case 7: face_flux(A.src, geo, D, 2, 1, i, j, k, fm, fp); break;
-    case 8: face_flux(A.src, geo, D, 2, 2, i, j, k, fm, fp); break;
-    case 9: face_flux(A.src, geo, D, 3, 0, i, j, k, fm, fp); break;
-    case 10: face_flux(A.src, geo, D, 3, 1, i, j, k, fm, fp); break;
-    default: face_flux(A.src, geo, D, 3, 2, i, j, k, fm, fp); break;
+    case 0: face_flux_lean<T, 0, 0>(A, c, i, j, k, fm, fp); break;
+    case 1: face_flux_lean<T, 0, 1>(A, c, i, j, k, fm, fp); break;
+    case 2: face_flux_lean<T, 0, 2>(A, c, i, j, k, fm, fp); break;
+    case 3: face_flux_lean<T, 1, 0>(A, c, i, j, k, fm, fp); break;
+    case 4: face_flux_lean<T, 1, 1>(A, c, i, j, k, fm, fp); break;
+    case 5: face_flux_lean<T, 1, 2>(A, c, i, j, k, fm, fp); break;
+    case 6: face_flux_lean<T, 2, 0>(A, c, i, j, k, fm, fp); break;
+    case 7: face_flux_lean<T, 2, 1>(A, c, i, j, k, fm, fp); break;
+    case 8: face_flux_lean<T, 2, 2>(A, c, i, j, k, fm, fp); break;
+    case 9: face_flux_lean<T, 3, 0>(A, c, i, j, k, fm, fp); break;
+    case 10: face_flux_lean<T, 3, 1>(A, c, i, j, k, fm, fp); break;
+    default: face_flux_lean<T, 3, 2>(A, c, i, j, k, fm, fp); break;
   }
   ((T *)A.G[g].fh[d])[c] = fp;
   if (A.G[g].fhm[d]) ((T *)A.G[g].fhm[d])[c] = fm;
 }
 
-// Phase B: interpolation to the cut-face centroids and the divergence of
-// every listed CV of every grid.
+// Phase B: the divergence of every listed CV with a geometry record, from
+// its precomputed row; the mixed path sums the rows of tiny cut CVs
+// (alpha < 1e-3, whose coefficients carry 1 / alpha) in double.
+template <typename T, typename R, typename C>
+__device__ inline void apply_row(const StepArgs<T> &A, const GridDev &G, const C *coef, long long t, R &sm,
+                                 R &sp) {
+  sm = R(0);
+  sp = R(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const T *FH = (const T *)G.fh[d];
+    const T *FM = (const T *)G.fhm[d];
+    const unsigned q1 = G.srow[3 * t + d + 1];
+    for (unsigned q = G.srow[3 * t + d]; q < q1; ++q) {
+      const unsigned f = G.sidx[q];
+      const R cq = (R)coef[q];
+      sp += cq * (R)FH[f];
+      if (FM) sm += cq * (R)FM[f];
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_band(StepArgs<T> A) {
-  const Dims &D = A.D;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int g = 0;
   for (g = 0; g < 4; ++g) {
@@ -233,14 +345,26 @@ __global__ void k_band(StepArgs<T> A) {
     t -= A.G[g].nband_rec;
   }
   if (g >= 4) return;
-  const unsigned c = A.G[g].blist[t];
-  int i, j, k;
-  split_index(D, c, i, j, k);
-  switch (g) {   // one compiled copy per grid
-    case 0: band_cv(A, 0, i, j, k); break;
-    case 1: band_cv(A, 1, i, j, k); break;
-    case 2: band_cv(A, 2, i, j, k); break;
-    default: band_cv(A, 3, i, j, k); break;
+  const GridDev &G = A.G[g];
+  const unsigned c = G.blist[t];
+  if (sizeof(T) == sizeof(double) || G.stiny[t]) {
+    double sm, sp;
+    apply_row<T, double, double>(A, G, G.scoef, t, sm, sp);
+    if (g == 0) {
+      write_out_d(A, 0, c, sm);
+      write_out_d(A, 1, c, sp);
+    } else {
+      write_out_d(A, g + 1, c, sp);
+    }
+  } else {
+    T sm, sp;
+    apply_row<T, T, float>(A, G, G.scoef_f, t, sm, sp);
+    if (g == 0) {
+      write_out(A, 0, c, sm);
+      write_out(A, 1, c, sp);
+    } else {
+      write_out(A, g + 1, c, sp);
+    }
   }
 }
 
@@ -530,7 +654,7 @@ void launch_flux_band(const StepArgs<T> &A, cudaStream_t s) {
     for (int d = 0; d < 3; ++d) nf += A.G[g].nface[d];
   }
   if (nf) k_face_flux<T><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(A);
-  if (nb) k_band<T><<<(unsigned)((nb + 127) / 128), 128, 0, s>>>(A);
+  if (nb) k_band<T><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(A);
   if (nr) k_band_regular<T><<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(A);
 }
 
@@ -556,6 +680,22 @@ void launch_wsrd5(const WsrdSet<T> &S, cudaStream_t s) {
     k_sigma5<T><<<(unsigned)((S.off_small[5] * 32 + 255) / 256), 256, 0, s>>>(S);
   }
   if (S.off_aff[5]) k_final5<T><<<(unsigned)((S.off_aff[5] + 127) / 128), 128, 0, s>>>(S);
+}
+
+void launch_band_rows(const Dims &D, const GridDev G[4], int g, bool fill, long long *cnt, cudaStream_t s) {
+  if (G[g].nband_rec == 0) return;
+  RowBuild B;
+  B.D = D;
+  for (int q = 0; q < 4; ++q) B.G[q] = G[q];
+  B.g = g;
+  B.cnt = cnt;
+  const unsigned blocks = (unsigned)((G[g].nband_rec + 127) / 128);
+  if (fill) k_band_rows<true><<<blocks, 128, 0, s>>>(B);
+  else k_band_rows<false><<<blocks, 128, 0, s>>>(B);
+}
+
+void launch_rows_to_u32(const long long *src, long long n, unsigned *dst, cudaStream_t s) {
+  if (n > 0) k_rows_to_u32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, n, dst);
 }
 
 template void launch_flux_update<double>(const StepArgs<double> &, cudaStream_t);

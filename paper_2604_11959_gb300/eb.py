@@ -30,7 +30,8 @@ EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom
                     "eb_ensemble_tune", "eb_ensemble_destroy", "eb_project", "eb_anelastic_step",
                     "eb_unet_num_params", "eb_unet_create", "eb_unet_set_params", "eb_unet_get_params",
                     "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step", "eb_unet_destroy",
-                    "eb_project_sample", "eb_project_warm")
+                    "eb_project_sample", "eb_project_warm", "eb_geom_tune",
+                    "eb_geom_set_slab_levels")
 
 
 class EbError(RuntimeError):
@@ -107,6 +108,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_unet_destroy.argtypes = [V]
     lib.eb_project_sample.argtypes = [V, P(_State), D, D, I, D, V, V, V, P(I), V]
     lib.eb_project_warm.argtypes = [V, V, P(_State), D, D, I, D, P(I), P(D), V]
+    lib.eb_geom_tune.argtypes = [V, P(_State), D, I, P(I), V]
+    lib.eb_geom_set_slab_levels.argtypes = [V, I]
     lib.eb_last_error.restype = ctypes.c_char_p
     lib.eb_version.restype = I
     for name in ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
@@ -114,7 +117,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                  "eb_ensemble_set_state", "eb_ensemble_get_state", "eb_ensemble_step", "eb_ensemble_tune",
                  "eb_ensemble_destroy", "eb_project", "eb_anelastic_step", "eb_unet_create", "eb_unet_set_params",
                  "eb_unet_get_params", "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step",
-                 "eb_unet_destroy", "eb_project_sample", "eb_project_warm"):
+                 "eb_unet_destroy", "eb_project_sample", "eb_project_warm", "eb_geom_tune",
+                 "eb_geom_set_slab_levels"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -284,6 +288,20 @@ def anelastic_step(geom: Geometry, Un: dict, dt: float, nsteps: int = 1, rtol: f
     _check(load().eb_anelastic_step(geom.handle, ctypes.byref(geom._cstate(Un)), ctypes.byref(geom._cstate(out)),
                                     float(dt), int(nsteps), float(rtol), int(maxit), its, _stream(stream)))
     return out, list(its)
+
+
+def tune(geom: Geometry, U: dict, dt: float, reps: int = 5, stream=None) -> int:
+    """Autotune the bulk kernel's slab height on U (``eb_geom_tune``);
+    returns the chosen height (0 = automatic)."""
+    best = ctypes.c_int(0)
+    _check(load().eb_geom_tune(geom.handle, ctypes.byref(geom._cstate(U)), float(dt), int(reps), ctypes.byref(best),
+                               _stream(stream)))
+    return best.value
+
+
+def set_slab_levels(geom: Geometry, levels: int) -> None:
+    """Set the bulk kernel's slab height (``eb_geom_set_slab_levels``)."""
+    _check(load().eb_geom_set_slab_levels(geom.handle, int(levels)))
 
 
 def sync_status(geom: Geometry, stream=None) -> None:

@@ -265,3 +265,26 @@ def test_non_finite_state_is_reported(eb):
         eb.sync_status(geom)
     assert e.value.code == 4
     eb.sync_status(geom)   # cleared
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_tuning_changes_no_result(eb, precision):
+    """eb_geom_tune only re-splits the bulk kernel's columns into slabs: every
+    cell's arithmetic is the same, so steps after tuning equal the steps before
+    it bit for bit, and the tuner leaves its input state untouched."""
+    w = rough_workload()
+    refs = refs_for(w.nz, w.Lz)
+    U = w.state("uniform", pert=1e-2, seed=6)
+    geom = make_geometry(eb, w, w.heights(), precision, refs)
+    A = to_device(U, precision, refs)
+    before = eb.step(geom, A, w.dt(), 3)
+    keep = {f: A[f].clone() for f in A}
+    best = eb.tune(geom, A, w.dt(), reps=1)
+    assert best in (0, 12, 16, 24, 32, 48, 64, w.nz)
+    for f in A:
+        assert torch.equal(A[f], keep[f]), f
+    after = eb.step(geom, A, w.dt(), 3)
+    for f in FIELDS:
+        assert torch.equal(before[f], after[f]), (precision, f)
+    eb.sync_status(geom)
+    geom.close()
