@@ -232,12 +232,16 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
         G.nface[d] = nf;
         if (e == cudaSuccess) e = g->alloc(&G.flist[d], nf);
         if (e == cudaSuccess && nf > 0) launch_marks_fill(mk[d], nfa, cnt, G.flist[d], s);
+        if (e == cudaSuccess) e = g->alloc(&G.fmask[d], nf);
         if (e == cudaSuccess) e = g->alloc((char **)&G.fh[d], (long long)(nfa * es));
         G.fhm[d] = nullptr;
         if (e == cudaSuccess && q == 0) e = g->alloc((char **)&G.fhm[d], (long long)(nfa * es));
       }
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+      launch_face_masks(D, g->G, s);
+      e = cudaStreamSynchronize(s);
+    }
     for (int d = 0; d < 3; ++d) cudaFree(mk[d]);
     cudaFree(cnt);
     cudaFree(scan_tmp);
@@ -327,6 +331,23 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
     g->info.band_cvs[q] = band;
     g->info.band_faces[q] = g->G[q].nface[0] + g->G[q].nface[1] + g->G[q].nface[2];
     for (long long c = 0; c < ncol; ++c) g->kcov_max = std::max(g->kcov_max, kc[c]);
+    {
+      // pass-through list: covered CVs level by level, then (w grid) the walls
+      std::vector<unsigned> st;
+      const int k0 = q == 3 ? 1 : 0, k1 = q == 3 ? D.nz : nzg;
+      for (int k = k0; k < k1; ++k)
+        for (long long c = 0; c < ncol; ++c)
+          if (k < kc[c]) st.push_back((unsigned)(c + D.nxy * k));
+      if (q == 3)
+        for (int k : {0, D.nz})
+          for (long long c = 0; c < ncol; ++c) st.push_back((unsigned)(c + D.nxy * k));
+      GridDev &G = g->G[q];
+      G.nstatic = (long long)st.size();
+      CUDA_TRY(g->alloc(&G.slist, G.nstatic), "alloc pass-through list");
+      if (G.nstatic)
+        CUDA_TRY(cudaMemcpy(G.slist, st.data(), sizeof(unsigned) * st.size(), cudaMemcpyHostToDevice),
+                 "write pass-through list");
+    }
     const long long n = nrec[q];
     std::vector<double> al(n > 0 ? n : 1);
     std::vector<uint8_t> fl(n > 0 ? n : 1);

@@ -445,27 +445,26 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
   if (!(isfinite(bad.x) && isfinite(bad.y))) atomicOr(A.status, EB_DEV_NUMERIC);
 }
 
-// Pass-through of the CVs no kernel updates: covered CVs (levels below
-// kcov_max) and the two wall levels of rho*w (or zeros when dU itself is
-// written).
+// Pass-through of the CVs no kernel updates (covered CVs and the two wall
+// levels of rho*w; zeros when dU itself is written), from per-grid lists
+// built at set-up: one thread per listed CV.
 template <typename T>
 __global__ void k_static(StepArgs<T> A) {
-  const Dims &D = A.D;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= D.nx || j >= D.ny) return;
-  const int col = i + D.nx * j;
-  auto put = [&](int f, long long c) { A.out[f][c] = A.base[0] ? A.base[f][c] : T(0); };
-  const long long c = lin(D, i, j, k);
-  if (k < A.G[0].kcov[col]) {
-    put(0, c);
-    put(1, c);
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int q = 0;
+  for (q = 0; q < 4; ++q) {
+    if (t < A.G[q].nstatic) break;
+    t -= A.G[q].nstatic;
   }
-  if (k < A.G[1].kcov[col]) put(2, c);
-  if (k < A.G[2].kcov[col]) put(3, c);
-  if (k < A.G[3].kcov[col] || k == 0) put(4, c);
-  if (k == 0) put(4, lin(D, i, j, D.nz));
+  if (q >= 4) return;
+  const unsigned c = A.G[q].slist[t];
+  auto put = [&](int f) { A.out[f][c] = A.base[0] ? A.base[f][c] : T(0); };
+  if (q == 0) {
+    put(0);
+    put(1);
+  } else {
+    put(q + 1);
+  }
 }
 
 template <typename T, int V>
@@ -553,8 +552,8 @@ template <typename T>
 void launch_static_copy(const StepArgs<T> &A, cudaStream_t s) {
   const Dims &D = A.D;
   if (A.copy_static) {
-    dim3 blk(32, 8, 1), grd((D.nx + 31) / 32, (D.ny + 7) / 8, std::max(1, std::min(D.nz, A.kcov_max)));
-    k_static<T><<<grd, blk, 0, s>>>(A);
+    const long long n = A.G[0].nstatic + A.G[1].nstatic + A.G[2].nstatic + A.G[3].nstatic;
+    if (n > 0) k_static<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A);
   }
 }
 

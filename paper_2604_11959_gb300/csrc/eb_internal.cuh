@@ -40,6 +40,11 @@ struct GridDev {
   // faces whose provisional flux the near-EB path needs, per direction
   unsigned *flist[3];
   long long nface[3];
+  // per listed face, the geometry-only availability tests of its provisional
+  // flux as bits (built once): bit 0, 1 the two momenta of the mass flux,
+  // bits 2 + 2 (t + 2), 3 + 2 (t + 2) the two c-cells beside the grid CV t
+  // steps along the face normal (t = -2 .. 1), bits 10, 11 the far CVs t = -2, 1
+  uint16_t *fmask[3];
   // CVs the near-EB kernel updates (non-covered, prognostic, below kfast),
   // state indices in plane-major order
   unsigned *blist;
@@ -54,6 +59,10 @@ struct GridDev {
   float *scoef_f;        // [nterm] float copies (mixed path)
   uint8_t *stiny;        // [nband_rec] 1: tiny cut CV, whose row the mixed path sums in double
   long long nterm;
+  // CVs of this grid that no flux kernel writes and a step passes through:
+  // covered CVs, and on the w grid the two wall levels; state indices
+  unsigned *slist;
+  long long nstatic;
   // redistribution per record
   uint8_t *code;
   int *nnb;

@@ -15,12 +15,14 @@ struct WsrdDev {
   long long *s_rec = nullptr;     // record
   int *s_nmem = nullptr;          // members incl. itself (<= 8)
   int *s_piv = nullptr;           // pivot member of the deviation form
+  long long *s_plin = nullptr;    // state index of the pivot member
   long long *s_mlin = nullptr;    // [8 * nsmall] member state indices (slot 0: itself)
   double *s_mw = nullptr;         // [8 * nsmall] Qhat weights (sum 1)
   double *s_me = nullptr;         // [24 * nsmall] member centroid - xhat (limiter points)
   long long *s_loff = nullptr;    // [nsmall + 1] LSQ stencil offsets
   long long *l_lin = nullptr;     // [nlsq] stencil CV state index
   int *l_sid = nullptr;           // [nlsq] small id of the stencil CV or -1
+  long long *l_plin = nullptr;    // [nlsq] pivot state index of that small CV, else the CV's own index
   double *l_c = nullptr;          // [3 * nlsq] gradient coefficient rows
   // per affected CV
   long long *a_lin = nullptr;
@@ -58,6 +60,8 @@ void launch_export_geometry(const double *h, const Dims &D, int g, const GridDev
 // the terms themselves at the scanned offsets
 void launch_band_rows(const Dims &D, const GridDev G[4], int g, bool fill, long long *cnt, cudaStream_t s);
 void launch_rows_to_u32(const long long *src, long long n, unsigned *dst, cudaStream_t s);
+// eb_step.cu: availability bits of every listed face into G[q].fmask[d]
+void launch_face_masks(const Dims &D, const GridDev G[4], cudaStream_t s);
 
 // eb_fast.cu: split of the bulk kernel's (tile, level) work into lockstep
 // slabs of slab_levels levels (0: chosen from the GPU's size); seg holds

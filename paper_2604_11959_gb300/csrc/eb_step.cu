@@ -208,8 +208,9 @@ __global__ void k_rows_to_u32(const long long *src, long long n, unsigned *dst) 
 // third-order one when the far upstream CV is not available), written for
 // one (grid, direction) pair at a time: every neighbour index is the face's
 // own index plus a periodic offset computed once.
-template <typename T, int G, int Dd>
-__device__ inline void face_flux_lean(const StepArgs<T> &A, long long c, int i, int j, int k, T &fm, T &fp) {
+template <typename T, int G, int Dd, bool MASK>
+__device__ inline unsigned face_flux_lean(const StepArgs<T> &A, long long c, int i, int j, int k, unsigned bits,
+                                          T &fm, T &fp) {
   const Dims &D = A.D;
   constexpr int S = G - 1;      // stagger direction of a face grid (c grid: none)
   constexpr int MG = Dd + 1;    // momentum grid normal to the face
@@ -222,27 +223,36 @@ __device__ inline void face_flux_lean(const StepArgs<T> &A, long long c, int i, 
     t = t < 0 ? t + n : (t >= n ? t - n : t);
     return (long long)(t - x) * (dir == 0 ? 1 : D.nx);
   };
-  auto fluid = [&](int q, long long idx, int kk) -> bool {
-    return kk >= 0 && kk < nzg_of(D, q) && (A.G[q].dflag[idx] & 1);
+  // availability test number n: evaluated from the dense flags when the
+  // masks are built (MASK), read from the face's mask bits otherwise
+  unsigned out = 0;
+  auto fluid = [&](int n, int q, long long idx, int kk) -> bool {
+    if (!MASK) return (bits >> n) & 1;
+    const bool f = kk >= 0 && kk < nzg_of(D, q) && (A.G[q].dflag[idx] & 1);
+    out |= (unsigned)f << n;
+    return f;
   };
-  // momentum of grid MG entering a mass flux
-  auto mom = [&](long long idx, int kk) -> T {
+  // momentum of grid MG entering a mass flux (test n)
+  auto mom = [&](int n, long long idx, int kk) -> T {
     if (MG == 3 && (kk <= 0 || kk >= D.nz)) return T(0);
-    return fluid(MG, idx, kk) ? A.src.f[MG + 1][idx] : T(0);
+    const bool f = fluid(n, MG, idx, kk);
+    if (MASK) return T(0);
+    return f ? A.src.f[MG + 1][idx] : T(0);
   };
   auto rho = [&](long long idx, int kk) -> T { return A.src.ref_rho[kk] + A.src.f[0][idx]; };
   // advected value of the grid-G CV t steps along Dd from the face's CV
   auto advected = [&](int t) -> T {
     const long long idx = c + off(Dd, crd[Dd], t);
     const int kk = k + (Dd == 2 ? t : 0);
-    if (G == 0) return eb_div(A.src.ref_rt[kk] + A.src.f[1][idx], rho(idx, kk));
+    if (G == 0) return MASK ? T(0) : eb_div(A.src.ref_rt[kk] + A.src.f[1][idx], rho(idx, kk));
     if (G == 3 && (kk <= 0 || kk >= D.nz)) return T(0);
     // the two c-cells beside the face-grid CV: one step back along S, and
     // itself (the CV's own coordinate along S, wrapped, when S is Dd)
     const int cs = S == Dd ? (S == 2 ? kk : wrapi(crd[S] + t, S == 0 ? D.nx : D.ny)) : crd[S];
     const long long ia = idx + off(S, cs, -1);
     const int ka = kk - (S == 2 ? 1 : 0);
-    const bool a = fluid(0, ia, ka), b = fluid(0, idx, kk);
+    const bool a = fluid(2 + 2 * (t + 2), 0, ia, ka), b = fluid(3 + 2 * (t + 2), 0, idx, kk);
+    if (MASK) return T(0);
     T rb;
     if (a && b) rb = T(0.5) * (rho(ia, ka) + rho(idx, kk));
     else if (a) rb = rho(ia, ka);
@@ -250,66 +260,94 @@ __device__ inline void face_flux_lean(const StepArgs<T> &A, long long c, int i, 
     else return T(0);
     return eb_div(A.src.f[G + 1][idx], rb);
   };
-  auto cv_fluid = [&](int t) -> bool {
+  auto cv_fluid = [&](int n, int t) -> bool {
     const long long idx = c + off(Dd, crd[Dd], t);
-    return fluid(G, idx, k + (Dd == 2 ? t : 0));
+    return fluid(n, G, idx, k + (Dd == 2 ? t : 0));
   };
+  if (MASK) {   // every test, whatever the flow direction
+    if (G != 0) mom(0, c + off(G == MG ? Dd : S, crd[G == MG ? Dd : S], -1), k - ((G == MG ? Dd : S) == 2 ? 1 : 0));
+    mom(1, c, k);
+    for (int t = -2; t <= 1; ++t) advected(t);
+    cv_fluid(10, -2);
+    cv_fluid(11, 1);
+    return out;
+  }
   // mass flux
   if (G == 0) {
-    fm = mom(c, k);
+    fm = mom(1, c, k);
   } else if (G == MG) {
-    fm = T(0.5) * (mom(c + off(Dd, crd[Dd], -1), k - (Dd == 2 ? 1 : 0)) + mom(c, k));
+    fm = T(0.5) * (mom(0, c + off(Dd, crd[Dd], -1), k - (Dd == 2 ? 1 : 0)) + mom(1, c, k));
   } else {
-    fm = T(0.5) * (mom(c + off(S, crd[S], -1), k - (S == 2 ? 1 : 0)) + mom(c, k));
+    fm = T(0.5) * (mom(0, c + off(S, crd[S], -1), k - (S == 2 ? 1 : 0)) + mom(1, c, k));
   }
   fp = T(0);
-  if (fm == T(0)) return;
+  if (fm == T(0)) return 0;
   const T pL = advected(-1), pR = advected(0);
   T val;
   if (fm > T(0)) {
-    const bool has = cv_fluid(-2);
+    const bool has = cv_fluid(10, -2);
     const T pF = has ? advected(-2) : T(0);
     val = upwind_value(fm, pF, pL, pR, T(0), has, false);
   } else {
-    const bool has = cv_fluid(1);
+    const bool has = cv_fluid(11, 1);
     const T pF = has ? advected(1) : T(0);
     val = upwind_value(fm, T(0), pL, pR, pF, false, has);
   }
   fp = fm * val;
+  return 0;
+}
+
+// list entry t of all faces -> (grid, direction, entry of that list)
+template <typename T>
+__device__ inline bool face_of(const StepArgs<T> &A, long long &t, int &g, int &d) {
+  for (g = 0; g < 4; ++g) {
+    for (d = 0; d < 3; ++d) {
+      if (t < A.G[g].nface[d]) return true;
+      t -= A.G[g].nface[d];
+    }
+  }
+  return false;
+}
+
+template <typename T, bool MASK>
+__device__ inline unsigned face_dispatch(const StepArgs<T> &A, int g, int d, unsigned c, unsigned bits, T &fm,
+                                         T &fp) {
+  int i, j, k;
+  split_index(A.D, c, i, j, k);
+  // one compiled copy per (grid, direction)
+  switch (g * 3 + d) {
+    case 0: return face_flux_lean<T, 0, 0, MASK>(A, c, i, j, k, bits, fm, fp);
+    case 1: return face_flux_lean<T, 0, 1, MASK>(A, c, i, j, k, bits, fm, fp);
+    case 2: return face_flux_lean<T, 0, 2, MASK>(A, c, i, j, k, bits, fm, fp);
+    case 3: return face_flux_lean<T, 1, 0, MASK>(A, c, i, j, k, bits, fm, fp);
+    case 4: return face_flux_lean<T, 1, 1, MASK>(A, c, i, j, k, bits, fm, fp);
+    case 5: return face_flux_lean<T, 1, 2, MASK>(A, c, i, j, k, bits, fm, fp);
+    case 6: return face_flux_lean<T, 2, 0, MASK>(A, c, i, j, k, bits, fm, fp);
+    case 7: return face_flux_lean<T, 2, 1, MASK>(A, c, i, j, k, bits, fm, fp);
+    case 8: return face_flux_lean<T, 2, 2, MASK>(A, c, i, j, k, bits, fm, fp);
+    case 9: return face_flux_lean<T, 3, 0, MASK>(A, c, i, j, k, bits, fm, fp);
+    case 10: return face_flux_lean<T, 3, 1, MASK>(A, c, i, j, k, bits, fm, fp);
+    default: return face_flux_lean<T, 3, 2, MASK>(A, c, i, j, k, bits, fm, fp);
+  }
+}
+
+// Set-up: the availability bits of every listed face.
+__global__ void k_face_mask(StepArgs<float> A) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int g, d;
+  if (!face_of(A, t, g, d)) return;
+  float fm, fp;
+  A.G[g].fmask[d][t] = (uint16_t)face_dispatch<float, true>(A, g, d, A.G[g].flist[d][t], 0u, fm, fp);
 }
 
 template <typename T>
 __global__ void k_face_flux(StepArgs<T> A) {
-  const Dims &D = A.D;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  int g = 0, d = 0;
-  for (g = 0; g < 4; ++g) {
-    for (d = 0; d < 3; ++d) {
-      if (t < A.G[g].nface[d]) break;
-      t -= A.G[g].nface[d];
-    }
-    if (d < 3) break;
-  }
-  if (g >= 4) return;
+  int g, d;
+  if (!face_of(A, t, g, d)) return;
   const unsigned c = A.G[g].flist[d][t];
-  int i, j, k;
-  split_index(D, c, i, j, k);
   T fm, fp;
-  // one compiled copy per (grid, direction)
-  switch (g * 3 + d) {
-    case 0: face_flux_lean<T, 0, 0>(A, c, i, j, k, fm, fp); break;
-    case 1: face_flux_lean<T, 0, 1>(A, c, i, j, k, fm, fp); break;
-    case 2: face_flux_lean<T, 0, 2>(A, c, i, j, k, fm, fp); break;
-    case 3: face_flux_lean<T, 1, 0>(A, c, i, j, k, fm, fp); break;
-    case 4: face_flux_lean<T, 1, 1>(A, c, i, j, k, fm, fp); break;
-    case 5: face_flux_lean<T, 1, 2>(A, c, i, j, k, fm, fp); break;
-    case 6: face_flux_lean<T, 2, 0>(A, c, i, j, k, fm, fp); break;
-    case 7: face_flux_lean<T, 2, 1>(A, c, i, j, k, fm, fp); break;
-    case 8: face_flux_lean<T, 2, 2>(A, c, i, j, k, fm, fp); break;
-    case 9: face_flux_lean<T, 3, 0>(A, c, i, j, k, fm, fp); break;
-    case 10: face_flux_lean<T, 3, 1>(A, c, i, j, k, fm, fp); break;
-    default: face_flux_lean<T, 3, 2>(A, c, i, j, k, fm, fp); break;
-  }
+  face_dispatch<T, false>(A, g, d, c, A.G[g].fmask[d][t], fm, fp);
   ((T *)A.G[g].fh[d])[c] = fp;
   if (A.G[g].fhm[d]) ((T *)A.G[g].fhm[d])[c] = fm;
 }
@@ -327,7 +365,28 @@ __device__ inline void apply_row(const StepArgs<T> &A, const GridDev &G, const C
     const T *FH = (const T *)G.fh[d];
     const T *FM = (const T *)G.fhm[d];
     const unsigned q1 = G.srow[3 * t + d + 1];
-    for (unsigned q = G.srow[3 * t + d]; q < q1; ++q) {
+    unsigned q = G.srow[3 * t + d];
+    // four terms at a time: their index, coefficient and flux loads are independent
+    for (; q + 4 <= q1; q += 4) {
+      unsigned f[4];
+      R cq[4], h[4], m[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        f[e] = G.sidx[q + e];
+        cq[e] = (R)coef[q + e];
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        h[e] = (R)FH[f[e]];
+        m[e] = FM ? (R)FM[f[e]] : R(0);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        sp += cq[e] * h[e];
+        sm += cq[e] * m[e];
+      }
+    }
+    for (; q < q1; ++q) {
       const unsigned f = G.sidx[q];
       const R cq = (R)coef[q];
       sp += cq * (R)FH[f];
@@ -482,7 +541,7 @@ struct CompSum<double> {
 template <typename T>
 __device__ inline void qhat_one(const WsrdArgs<T> &R, long long s) {
   const int n = R.W.s_nmem[s], p = R.W.s_piv[s];
-  const long long lp = R.W.s_mlin[8 * s + p];
+  const long long lp = R.W.s_plin[s];
   CompSum<T> acc;
   for (int q = 0; q < n; ++q) {
     if (q == p) continue;
@@ -493,25 +552,18 @@ __device__ inline void qhat_one(const WsrdArgs<T> &R, long long s) {
 }
 
 // One warp per small CV: lanes walk the stencil, shuffles reduce the slope
-// and the stencil's range of Qhat - Qhat_r; lane 0 applies the limiter at the
-// members' centroids.
+// and the stencil's range of Qhat - Qhat_r; lane q evaluates the limiter at
+// member q's centroid and a min-reduction combines them.
 template <typename T>
 __device__ inline void sigma_one(const WsrdArgs<T> &R, long long s, int lane) {
   const long long o0 = R.W.s_loff[s], o1 = R.W.s_loff[s + 1];
-  const long long pr = R.W.s_mlin[8 * s + R.W.s_piv[s]];
+  const long long pr = R.W.s_plin[s];
   const T dr = R.dev[s];
   T sx = T(0), sy = T(0), sz = T(0), bmax = T(0), bmin = T(0);
   for (long long o = o0 + lane; o < o1; o += 32) {
     const int sid = R.W.l_sid[o];
-    long long pm;
-    T dm;
-    if (sid >= 0) {
-      pm = R.W.s_mlin[8 * (long long)sid + R.W.s_piv[sid]];
-      dm = R.dev[sid];
-    } else {
-      pm = R.W.l_lin[o];
-      dm = T(0);
-    }
+    const long long pm = R.W.l_plin[o];
+    const T dm = sid >= 0 ? R.dev[sid] : T(0);
     const T b = vdiff(R, pm, pr) + (dm - dr);
     const T *lc = tab<T>(R.W.l_c, R.W.l_c_f) + 3 * o;
     sx += lc[0] * b;
@@ -529,20 +581,20 @@ __device__ inline void sigma_one(const WsrdArgs<T> &R, long long s, int lane) {
     bmax = a > bmax ? a : bmax;
     bmin = c < bmin ? c : bmin;
   }
-  if (lane != 0) return;
   T phi = T(1);
-  if (o1 > o0) {
-    const int n = R.W.s_nmem[s];
-    for (int q = 0; q < n; ++q) {
-      const T *e = tab<T>(R.W.s_me, R.W.s_me_f) + 24 * s + 3 * q;
-      const T del = sx * e[0] + sy * e[1] + sz * e[2];
-      T ph = T(1);
-      if (del > T(0)) ph = bmax / del;
-      else if (del < T(0)) ph = bmin / del;
-      if (ph > T(1)) ph = T(1);
-      if (ph < phi) phi = ph;
-    }
+  if (o1 > o0 && lane < R.W.s_nmem[s]) {
+    const T *e = tab<T>(R.W.s_me, R.W.s_me_f) + 24 * s + 3 * lane;
+    const T del = sx * e[0] + sy * e[1] + sz * e[2];
+    T ph = T(1);
+    if (del > T(0)) ph = bmax / del;
+    else if (del < T(0)) ph = bmin / del;
+    phi = ph < T(1) ? ph : T(1);   // a value that is not below 1 (or NaN) leaves phi at 1
   }
+  for (int off = 4; off > 0; off >>= 1) {   // members are lanes 0 .. 7
+    const T o = __shfl_xor_sync(0xffffffffu, phi, off);
+    phi = o < phi ? o : phi;
+  }
+  if (lane != 0) return;
   R.sig[3 * s] = sx * phi;
   R.sig[3 * s + 1] = sy * phi;
   R.sig[3 * s + 2] = sz * phi;
@@ -563,7 +615,7 @@ __device__ inline void final_one(const WsrdArgs<T> &R, long long a) {
   if (sid >= 0) {
     const T *e = tab<T>(R.W.a_eself, R.W.a_eself_f) + 3 * a;
     si = R.sig[3 * sid] * e[0] + R.sig[3 * sid + 1] * e[1] + R.sig[3 * sid + 2] * e[2];
-    pi = R.W.s_mlin[8 * (long long)sid + R.W.s_piv[sid]];
+    pi = R.W.s_plin[sid];
     pvi = R.pval[sid];
     di = R.dev[sid];
   }
@@ -571,7 +623,7 @@ __device__ inline void final_one(const WsrdArgs<T> &R, long long a) {
   for (long long o = R.W.a_woff[a]; o < R.W.a_woff[a + 1]; ++o) {
     const int r = R.W.w_sid[o];
     const T *e = tab<T>(R.W.w_e, R.W.w_e_f) + 3 * o;
-    const long long pr = R.W.s_mlin[8 * (long long)r + R.W.s_piv[r]];
+    const long long pr = R.W.s_plin[r];
     const T sr = R.sig[3 * r] * e[0] + R.sig[3 * r + 1] * e[1] + R.sig[3 * r + 2] * e[2];
     const T diff = vdiff_vals(R, R.pval[r], pr, pvi, pi) + (R.dev[r] - di) + (sr - si);
     acc.add(tab<T>(R.W.w_k, R.W.w_k_f)[o] * diff);
@@ -692,6 +744,17 @@ void launch_band_rows(const Dims &D, const GridDev G[4], int g, bool fill, long 
   const unsigned blocks = (unsigned)((G[g].nband_rec + 127) / 128);
   if (fill) k_band_rows<true><<<blocks, 128, 0, s>>>(B);
   else k_band_rows<false><<<blocks, 128, 0, s>>>(B);
+}
+
+void launch_face_masks(const Dims &D, const GridDev G[4], cudaStream_t s) {
+  StepArgs<float> A{};
+  A.D = D;
+  long long nf = 0;
+  for (int q = 0; q < 4; ++q) {
+    A.G[q] = G[q];
+    for (int d = 0; d < 3; ++d) nf += G[q].nface[d];
+  }
+  if (nf) k_face_mask<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(A);
 }
 
 void launch_rows_to_u32(const long long *src, long long n, unsigned *dst, cudaStream_t s) {

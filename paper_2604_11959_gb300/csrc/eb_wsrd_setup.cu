@@ -401,6 +401,17 @@ __global__ void k_lsq_fill(Dims D, int g, GridDev G, WsrdDev W) {
       }
 }
 
+// Pivot state indices, looked up once here instead of twice per step.
+__global__ void k_pivot_lin(WsrdDev W) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s < W.nsmall) W.s_plin[s] = W.s_mlin[8 * s + W.s_piv[s]];
+}
+
+__global__ void k_stencil_pivot_lin(WsrdDev W) {
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (o < W.nlsq) W.l_plin[o] = W.l_sid[o] >= 0 ? W.s_plin[W.l_sid[o]] : W.l_lin[o];
+}
+
 // Per affected CV: its own small id and the neighbourhoods that hold it.
 __global__ void k_aff_count(Dims D, int g, GridDev G, const long long *aff_id, WsrdDev W, long long *wcnt) {
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
@@ -529,6 +540,10 @@ cudaError_t build_wsrd(const Dims &D, int g, GridDev &G, const GridDev *all, dou
   CK(dalloc(&W.l_sid, W.nlsq));
   CK(dalloc(&W.l_c, 3 * W.nlsq));
   if (W.nsmall) k_lsq_fill<<<lin_blocks(W.nsmall), 128, 0, s>>>(D, g, G, W);
+  CK(dalloc(&W.s_plin, W.nsmall));
+  CK(dalloc(&W.l_plin, W.nlsq));
+  if (W.nsmall) k_pivot_lin<<<lin_blocks(W.nsmall), 128, 0, s>>>(W);
+  if (W.nlsq) k_stencil_pivot_lin<<<lin_blocks(W.nlsq), 128, 0, s>>>(W);
   // affected CVs and their neighbourhood lists
   CK(cudaMemsetAsync(W.a_woff, 0, sizeof(long long) * (W.naff + 1), s));
   k_aff_count<<<cb, 128, 0, s>>>(D, g, G, aff_id, W, W.a_woff);
@@ -559,7 +574,7 @@ cudaError_t build_wsrd(const Dims &D, int g, GridDev &G, const GridDev *all, dou
 void free_wsrd(WsrdDev &W) {
   void *ptrs[] = {W.sid, W.s_lin, W.s_rec, W.s_nmem, W.s_piv, W.s_mlin, W.s_mw, W.s_me, W.s_loff, W.l_lin,
                   W.l_sid, W.l_c, W.a_lin, W.a_sid, W.a_eself, W.a_woff, W.w_sid, W.w_k, W.w_e,
-                  W.s_mw_f, W.s_me_f, W.l_c_f, W.a_eself_f, W.w_k_f, W.w_e_f};
+                  W.s_mw_f, W.s_me_f, W.l_c_f, W.a_eself_f, W.w_k_f, W.w_e_f, W.s_plin, W.l_plin};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   W = WsrdDev();
