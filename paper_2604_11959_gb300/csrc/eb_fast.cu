@@ -22,10 +22,18 @@
 //   phase 2a: the x / y face fluxes of level p of the four advected
 //            quantities, once per face, into shared face planes;
 //   barrier;
-//   phase 2b: the x / y part of each CV's divergence at level p (kept in
-//            registers for two levels), the z flux through the top of level
-//            k = p - 2 from a register window of the thread's own columns,
-//            and the update of level k.
+//   phase 2b: the x / y part of each CV's divergence at level p (kept for
+//            two levels), the z flux through the top of level k = p - 2 from
+//            a window of the thread's own columns (levels p - 3 .. p), and
+//            the update of level k.
+// On the float path the window, the two pending x / y parts and the carried
+// bottom z fluxes (58 words per thread) live in tensor memory between the
+// levels that use them: shared memory is full with the ring, and in
+// registers they would hold 58 of the 128 a thread has at two CTAs per SM
+// through every phase.  Each level stores its new window level and x / y
+// part and reloads the rest in one batch before the z step (tcgen05.st /
+// tcgen05.ld, 32x32b shapes: TMEM lane = the thread's lane).  The double
+// path keeps them in registers.
 // Every field is read from HBM once per level (halo re-reads hit L2) and
 // written once.  Advective face fluxes carry a factor 6 that the divergence
 // removes with 1/(6 dx).
@@ -55,6 +63,54 @@ template <int N>
 __device__ inline void copy_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+
+
+// ---- tensor memory as per-thread storage (float path) -----------------------
+// The z window of a thread's own columns, the carried x / y divergence parts
+// and the carried bottom z fluxes live in tensor memory between the levels
+// that use them: TMEM lane = the thread's lane in its warp's lane quarter,
+// 64 columns per warp (two warps per quarter).
+__device__ inline void tm_alloc(unsigned *dst, unsigned ncols) {   // one whole warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ inline void tm_dealloc(unsigned taddr, unsigned ncols) {   // one whole warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ inline void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ inline void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ inline void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+__device__ inline void tm_st8(unsigned taddr, float2 a, float2 b, float2 c, float2 d) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(taddr),
+               "r"(__float_as_uint(a.x)), "r"(__float_as_uint(a.y)), "r"(__float_as_uint(b.x)),
+               "r"(__float_as_uint(b.y)), "r"(__float_as_uint(c.x)), "r"(__float_as_uint(c.y)),
+               "r"(__float_as_uint(d.x)), "r"(__float_as_uint(d.y))
+               : "memory");
+}
+__device__ inline void tm_st2(unsigned taddr, float2 a) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};\n" ::"r"(taddr), "r"(__float_as_uint(a.x)),
+               "r"(__float_as_uint(a.y))
+               : "memory");
+}
+// window levels at a0, a1, a2 (8 words each), x / y parts at aq (8), bottom
+// fluxes at az (10): after any pending stores, loaded and waited for
+__device__ inline void tm_load_z(unsigned a0, unsigned a1, unsigned a2, unsigned aq, unsigned az, unsigned o[42]) {
+    asm volatile(
+        "tcgen05.wait::st.sync.aligned;\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%42];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%43];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%44];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%45];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32, %33, %34, %35, %36, %37, %38, %39}, [%46];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%40, %41}, [%47];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7]), "=r"(o[8]), "=r"(o[9]), "=r"(o[10]), "=r"(o[11]), "=r"(o[12]), "=r"(o[13]), "=r"(o[14]), "=r"(o[15]), "=r"(o[16]), "=r"(o[17]), "=r"(o[18]), "=r"(o[19]), "=r"(o[20]), "=r"(o[21]), "=r"(o[22]), "=r"(o[23]), "=r"(o[24]), "=r"(o[25]), "=r"(o[26]), "=r"(o[27]), "=r"(o[28]), "=r"(o[29]), "=r"(o[30]), "=r"(o[31]), "=r"(o[32]), "=r"(o[33]), "=r"(o[34]), "=r"(o[35]), "=r"(o[36]), "=r"(o[37]), "=r"(o[38]), "=r"(o[39]), "=r"(o[40]), "=r"(o[41])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(aq), "r"(az), "r"(az + 8u)
+        : "memory");
+}
+__device__ inline float2 w2(const unsigned *o, int q) { return make_float2(__uint_as_float(o[q]), __uint_as_float(o[q + 1])); }
 
 // ---- pairs of adjacent columns ----------------------------------------------
 template <typename T>
@@ -170,6 +226,16 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
   P bad = zero;   // becomes NaN once any written value is not finite
 
   auto RAWP = [&](int L) -> const T * { return raw + (L % TL::SLOTS) * 5 * NP; };
+  constexpr bool TM = sizeof(T) == sizeof(float);
+  __shared__ unsigned tm_base_s;
+  unsigned tbase = 0;
+  if constexpr (TM) {
+    if (tid < 32) tm_alloc(&tm_base_s, 128u);
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    tbase = tm_base_s + ((unsigned)(32 * ((tid >> 5) & 3)) << 16) + 64u * (unsigned)(tid >> 7);
+  }
 
   for (int sgi = A.boff[blockIdx.x]; sgi < A.boff[blockIdx.x + 1]; ++sgi) {
     const int4 sg = A.bseg[sgi];
@@ -307,21 +373,34 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
       request(p + 2 <= p1 ? p + 2 : -1);
 
       // ---- phase 2a: own window; x / y faces of level p
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        th[q] = th[q + 1];
-        uu[q] = uu[q + 1];
-        vv[q] = vv[q + 1];
-        ww[q] = ww[q + 1];
-      }
-      if (p < nz) {
-        const T *Q = prim + TL::qi(2 * tx, ty);
-        th[3] = ld2(Q);
-        uu[3] = ld2(Q + NQ);
-        vv[3] = ld2(Q + 2 * NQ);
-        ww[3] = ld2(Q + 3 * NQ);
+      if constexpr (TM) {
+        P a0 = zero, a1 = zero, a2 = zero, a3 = zero;   // above the top: zeros (w wall level nz)
+        if (p < nz) {
+          const T *Q = prim + TL::qi(2 * tx, ty);
+          a0 = ld2(Q);
+          a1 = ld2(Q + NQ);
+          a2 = ld2(Q + 2 * NQ);
+          a3 = ld2(Q + 3 * NQ);
+        }
+        __syncwarp();
+        tm_st8(tbase + 8u * (unsigned)(p & 3), a0, a1, a2, a3);
       } else {
-        th[3] = uu[3] = vv[3] = ww[3] = zero;   // above the top; w wall level nz
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          th[q] = th[q + 1];
+          uu[q] = uu[q + 1];
+          vv[q] = vv[q + 1];
+          ww[q] = ww[q + 1];
+        }
+        if (p < nz) {
+          const T *Q = prim + TL::qi(2 * tx, ty);
+          th[3] = ld2(Q);
+          uu[3] = ld2(Q + NQ);
+          vv[3] = ld2(Q + 2 * NQ);
+          ww[3] = ld2(Q + 3 * NQ);
+        } else {
+          th[3] = uu[3] = vv[3] = ww[3] = zero;   // above the top; w wall level nz
+        }
       }
       const bool face_level = p >= kbeg && p < kend;
       P fx[4], fy[4];
@@ -427,13 +506,52 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
       // below the top two levels the far high CV of every z stencil exists:
       // a copy of the z step without the run-time fallback selects
       if (k >= kbeg - 1) {
+        if constexpr (TM) {
+          unsigned o[42];
+          __syncwarp();
+          tm_load_z(tbase + 8u * (unsigned)((p + 1) & 3), tbase + 8u * (unsigned)((p + 2) & 3),
+                    tbase + 8u * (unsigned)((p + 3) & 3), tbase + 32u + 8u * (unsigned)(p & 1), tbase + 48u, o);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            th[q] = w2(o, 8 * q);
+            uu[q] = w2(o, 8 * q + 2);
+            vv[q] = w2(o, 8 * q + 4);
+            ww[q] = w2(o, 8 * q + 6);
+          }
+#pragma unroll
+          for (int G = 0; G < 4; ++G) q0[G] = w2(o, 24 + 2 * G);
+          zc_m = w2(o, 32);
+          zc_t = w2(o, 34);
+          zu = w2(o, 36);
+          zv = w2(o, 38);
+          zw = w2(o, 40);
+          if (p < nz) {
+            const T *Q = prim + TL::qi(2 * tx, ty);
+            th[3] = ld2(Q);
+            uu[3] = ld2(Q + NQ);
+            vv[3] = ld2(Q + 2 * NQ);
+            ww[3] = ld2(Q + 3 * NQ);
+          } else {
+            th[3] = uu[3] = vv[3] = ww[3] = zero;
+          }
+        }
         if (k + 2 <= nz - 1) zstep(std::true_type());
         else zstep(std::false_type());
+        if constexpr (TM) {
+          __syncwarp();
+          tm_st8(tbase + 48u, zc_m, zc_t, zu, zv);
+          tm_st2(tbase + 56u, zw);
+        }
       }
+      if constexpr (TM) {
+        __syncwarp();
+        tm_st8(tbase + 32u + 8u * (unsigned)(p & 1), sxy[0], sxy[1], sxy[2], sxy[3]);
+      } else {
 #pragma unroll
-      for (int G = 0; G < 4; ++G) {
-        q0[G] = q1[G];
-        q1[G] = sxy[G];
+        for (int G = 0; G < 4; ++G) {
+          q0[G] = q1[G];
+          q1[G] = sxy[G];
+        }
       }
       rr_m = rr_p;
       rr_p = rr_n;
@@ -441,6 +559,13 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
     }
     copy_wait<0>();
     __syncthreads();   // the next march reuses the shared ring
+  }
+  if constexpr (TM) {
+    tm_wait_st();
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (tid < 32) tm_dealloc(tm_base_s, 128u);
   }
   if (!(isfinite(bad.x) && isfinite(bad.y))) atomicOr(A.status, EB_DEV_NUMERIC);
 }

@@ -5,10 +5,11 @@
 //     eb_fast.cu)
 //     k_face_flux    : the provisional flux of every face the near-EB CVs
 //                      read, once, with covered-neighbour fallbacks;
-//     k_band         : the CVs below kfast with a geometry record: open-face
+//     k_band         : the CVs below kfast with a geometry record (open-face
 //                      fractions and fluxes interpolated to the cut-face
-//                      centroids, as rows of coefficients built at set-up;
-//     k_band_regular : the other CVs below kfast (plain face differences).
+//                      centroids, as rows of coefficients built at set-up),
+//                      then, in the same launch, the other CVs below kfast
+//                      (plain face differences).
 //   weighted state redistribution (Sec. 5.1, Eqs. qhat_omega, qrecon,
 //   final_update_omega), on compact lists built at set-up:
 //     k_qhat  : neighbourhood averages of the small CVs;
@@ -395,45 +396,12 @@ __device__ inline void apply_row(const StepArgs<T> &A, const GridDev &G, const C
   }
 }
 
-template <typename T>
-__global__ void k_band(StepArgs<T> A) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  int g = 0;
-  for (g = 0; g < 4; ++g) {
-    if (t < A.G[g].nband_rec) break;
-    t -= A.G[g].nband_rec;
-  }
-  if (g >= 4) return;
-  const GridDev &G = A.G[g];
-  const unsigned c = G.blist[t];
-  if (sizeof(T) == sizeof(double) || G.stiny[t]) {
-    double sm, sp;
-    apply_row<T, double, double>(A, G, G.scoef, t, sm, sp);
-    if (g == 0) {
-      write_out_d(A, 0, c, sm);
-      write_out_d(A, 1, c, sp);
-    } else {
-      write_out_d(A, g + 1, c, sp);
-    }
-  } else {
-    T sm, sp;
-    apply_row<T, T, float>(A, G, G.scoef_f, t, sm, sp);
-    if (g == 0) {
-      write_out(A, 0, c, sm);
-      write_out(A, 1, c, sp);
-    } else {
-      write_out(A, g + 1, c, sp);
-    }
-  }
-}
-
 // Near-EB CVs without a geometry record are regular: every face is open
 // with its centroid at the face centre, so the divergence is the difference
 // of the staged face fluxes (the sums of band_divergence with beta = 1).
 template <typename T>
-__global__ void k_band_regular(StepArgs<T> A) {
+__device__ inline void regular_cv(const StepArgs<T> &A, long long t) {
   const Dims &D = A.D;
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int g = 0;
   for (g = 0; g < 4; ++g) {
     const long long n = A.G[g].nband - A.G[g].nband_rec;
@@ -471,6 +439,43 @@ __global__ void k_band_regular(StepArgs<T> A) {
     write_out(A, 1, c, -sp);
   } else {
     write_out(A, g + 1, c, -sp);
+  }
+}
+
+template <typename T>
+__global__ void k_band(StepArgs<T> A) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nrec = A.G[0].nband_rec + A.G[1].nband_rec + A.G[2].nband_rec + A.G[3].nband_rec;
+  if (t >= nrec) {   // CVs without a record follow the rows in the same launch
+    regular_cv(A, t - nrec);
+    return;
+  }
+  int g = 0;
+  for (g = 0; g < 4; ++g) {
+    if (t < A.G[g].nband_rec) break;
+    t -= A.G[g].nband_rec;
+  }
+  if (g >= 4) return;
+  const GridDev &G = A.G[g];
+  const unsigned c = G.blist[t];
+  if (sizeof(T) == sizeof(double) || G.stiny[t]) {
+    double sm, sp;
+    apply_row<T, double, double>(A, G, G.scoef, t, sm, sp);
+    if (g == 0) {
+      write_out_d(A, 0, c, sm);
+      write_out_d(A, 1, c, sp);
+    } else {
+      write_out_d(A, g + 1, c, sp);
+    }
+  } else {
+    T sm, sp;
+    apply_row<T, T, float>(A, G, G.scoef_f, t, sm, sp);
+    if (g == 0) {
+      write_out(A, 0, c, sm);
+      write_out(A, 1, c, sp);
+    } else {
+      write_out(A, g + 1, c, sp);
+    }
   }
 }
 
@@ -706,8 +711,7 @@ void launch_flux_band(const StepArgs<T> &A, cudaStream_t s) {
     for (int d = 0; d < 3; ++d) nf += A.G[g].nface[d];
   }
   if (nf) k_face_flux<T><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(A);
-  if (nb) k_band<T><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(A);
-  if (nr) k_band_regular<T><<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(A);
+  if (nb + nr) k_band<T><<<(unsigned)((nb + nr + 255) / 256), 256, 0, s>>>(A);
 }
 
 template <typename T>
