@@ -556,16 +556,23 @@ __device__ inline void qhat_one(const WsrdArgs<T> &R, long long s) {
   R.pval[s] = R.u[lp];   // snapshot: the final update overwrites the field in place
 }
 
-// One warp per small CV: lanes walk the stencil, shuffles reduce the slope
-// and the stencil's range of Qhat - Qhat_r; lane q evaluates the limiter at
-// member q's centroid and a min-reduction combines them.
-template <typename T>
-__device__ inline void sigma_one(const WsrdArgs<T> &R, long long s, int lane) {
-  const long long o0 = R.W.s_loff[s], o1 = R.W.s_loff[s + 1];
-  const long long pr = R.W.s_plin[s];
-  const T dr = R.dev[s];
+// One group of GS lanes (half a warp) per small CV: lanes walk the stencil,
+// shuffles reduce the slope and the stencil's range of Qhat - Qhat_r; lane q
+// evaluates the limiter at member q's centroid and a min-reduction combines
+// them.  A group without a CV (valid false) takes part in the shuffles only.
+template <typename T, int GS>
+__device__ inline void sigma_one(const WsrdArgs<T> &R, long long s, int lane, bool valid) {
+  static_assert(GS == 16 || GS == 32, "lane groups are half or whole warps");
+  long long o0 = 0, o1 = 0, pr = 0;
+  T dr = T(0);
+  if (valid) {
+    o0 = R.W.s_loff[s];
+    o1 = R.W.s_loff[s + 1];
+    pr = R.W.s_plin[s];
+    dr = R.dev[s];
+  }
   T sx = T(0), sy = T(0), sz = T(0), bmax = T(0), bmin = T(0);
-  for (long long o = o0 + lane; o < o1; o += 32) {
+  for (long long o = o0 + lane; o < o1; o += GS) {
     const int sid = R.W.l_sid[o];
     const long long pm = R.W.l_plin[o];
     const T dm = sid >= 0 ? R.dev[sid] : T(0);
@@ -577,7 +584,7 @@ __device__ inline void sigma_one(const WsrdArgs<T> &R, long long s, int lane) {
     bmax = b > bmax ? b : bmax;
     bmin = b < bmin ? b : bmin;
   }
-  for (int off = 16; off > 0; off >>= 1) {
+  for (int off = GS / 2; off > 0; off >>= 1) {   // stays within the group
     sx += __shfl_xor_sync(0xffffffffu, sx, off);
     sy += __shfl_xor_sync(0xffffffffu, sy, off);
     sz += __shfl_xor_sync(0xffffffffu, sz, off);
@@ -587,7 +594,7 @@ __device__ inline void sigma_one(const WsrdArgs<T> &R, long long s, int lane) {
     bmin = c < bmin ? c : bmin;
   }
   T phi = T(1);
-  if (o1 > o0 && lane < R.W.s_nmem[s]) {
+  if (o1 > o0 && lane < R.W.s_nmem[s]) {   // o1 > o0 only for a valid group
     const T *e = tab<T>(R.W.s_me, R.W.s_me_f) + 24 * s + 3 * lane;
     const T del = sx * e[0] + sy * e[1] + sz * e[2];
     T ph = T(1);
@@ -599,7 +606,7 @@ __device__ inline void sigma_one(const WsrdArgs<T> &R, long long s, int lane) {
     const T o = __shfl_xor_sync(0xffffffffu, phi, off);
     phi = o < phi ? o : phi;
   }
-  if (lane != 0) return;
+  if (lane != 0 || !valid) return;
   R.sig[3 * s] = sx * phi;
   R.sig[3 * s + 1] = sy * phi;
   R.sig[3 * s + 2] = sz * phi;
@@ -659,8 +666,8 @@ __global__ void k_qhat(WsrdArgs<T> R) {
 }
 template <typename T>
 __global__ void k_sigma(WsrdArgs<T> R) {
-  const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  if (s < R.W.nsmall) sigma_one(R, s, threadIdx.x & 31);
+  const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4;
+  sigma_one<T, 16>(R, s, threadIdx.x & 15, s < R.W.nsmall);
 }
 template <typename T>
 __global__ void k_final(WsrdArgs<T> R) {
@@ -684,10 +691,10 @@ __global__ void k_qhat5(const __grid_constant__ WsrdSet<T> S) {
 }
 template <typename T>
 __global__ void k_sigma5(const __grid_constant__ WsrdSet<T> S) {
-  const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  if (t >= S.off_small[5]) return;
-  const int f = field_of(S.off_small, t);
-  sigma_one(S.f[f], t - S.off_small[f], threadIdx.x & 31);
+  const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4;
+  const bool valid = t < S.off_small[5];
+  const int f = valid ? field_of(S.off_small, t) : 0;
+  sigma_one<T, 16>(S.f[f], valid ? t - S.off_small[f] : 0, threadIdx.x & 15, valid);
 }
 template <typename T>
 __global__ void k_final5(const __grid_constant__ WsrdSet<T> S) {
@@ -724,7 +731,7 @@ template <typename T>
 void launch_wsrd(const WsrdArgs<T> &R, cudaStream_t s) {
   if (R.W.nsmall) {
     k_qhat<T><<<(unsigned)((R.W.nsmall + 127) / 128), 128, 0, s>>>(R);
-    k_sigma<T><<<(unsigned)((R.W.nsmall * 32 + 255) / 256), 256, 0, s>>>(R);
+    k_sigma<T><<<(unsigned)((R.W.nsmall * 16 + 255) / 256), 256, 0, s>>>(R);
   }
   if (R.W.naff) k_final<T><<<(unsigned)((R.W.naff + 127) / 128), 128, 0, s>>>(R);
 }
@@ -733,7 +740,7 @@ template <typename T>
 void launch_wsrd5(const WsrdSet<T> &S, cudaStream_t s) {
   if (S.off_small[5]) {
     k_qhat5<T><<<(unsigned)((S.off_small[5] + 127) / 128), 128, 0, s>>>(S);
-    k_sigma5<T><<<(unsigned)((S.off_small[5] * 32 + 255) / 256), 256, 0, s>>>(S);
+    k_sigma5<T><<<(unsigned)((S.off_small[5] * 16 + 255) / 256), 256, 0, s>>>(S);
   }
   if (S.off_aff[5]) k_final5<T><<<(unsigned)((S.off_aff[5] + 127) / 128), 128, 0, s>>>(S);
 }
