@@ -260,6 +260,25 @@ eb_status eb_step_profile(eb_geom geom, const eb_state *Un, eb_state *Unp1, doub
 eb_status eb_project(eb_geom geom, eb_state *U, double dt, double rtol, int maxit, const double *phi0, double *phi,
                      int *iters, double *relres, void *stream);
 
+/* Preconditioner of the projection's conjugate gradients (eb_project and
+ * eb_anelastic_step) for this handle.  Sec. 2.2 leaves the Poisson solver
+ * open; both choices converge to the same projection.
+ *   EB_PRECOND_JACOBI (default): z = r / diag(-L).
+ *   EB_PRECOND_MG: one symmetric multigrid V-cycle in FP32 (the outer
+ *     conjugate gradients, residuals and dot products stay FP64).  The cell grid
+ *     is coarsened by 2 in every direction while all three sizes are even
+ *     and at least 4, until the grid has 512 cells or fewer; a coarse face
+ *     takes the mean open fraction of the four fine faces it covers and the
+ *     coarse spacing; two damped Jacobi sweeps (weight 0.8) before and after
+ *     the coarse correction, averaging restriction, injection prolongation,
+ *     64 Jacobi sweeps on the coarsest grid.  Fewer iterations, each more
+ *     costly; the extra device memory is about three FP64 fields.
+ * Errors: EB_ERR_INVALID_ARG for another kind, or for EB_PRECOND_MG when the
+ * grid cannot be coarsened at least once to a coarsest grid of at most 32768
+ * cells.  The hierarchy is built on the first projection that uses it. */
+typedef enum { EB_PRECOND_JACOBI = 0, EB_PRECOND_MG = 1 } eb_precond;
+eb_status eb_project_set_preconditioner(eb_geom geom, int kind);
+
 /*
  * nsteps anelastic steps (Algorithm 2) with two stages in the low-storage
  * form U* = P[R[U + dt/2 dU(U)]], U' = P[R[U + dt dU(U*)]]: the flux update

@@ -40,7 +40,22 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
   } while (0)
 
 // Work space of the projection (eb_project), allocated on its first use.
+// One level of the projection's multigrid preconditioner (FP32): the cell
+// grid coarsened 2^l times in every direction, face open fractions averaged
+// over the fine faces a coarse face covers, 1 / delta^2 of the coarse spacing.
+struct MgLevel {
+  Dims D;
+  float ix2 = 0, iy2 = 0, iz2 = 0;
+  float *bx = nullptr, *by = nullptr, *bz = nullptr;   // low-face open fractions
+  float *x = nullptr, *t = nullptr, *b = nullptr;      // correction, sweep target, right-hand side (coarse levels)
+  int nb = 0;                                          // blocks of its kernels
+};
+constexpr int kMgMaxLevels = 16;
+
 struct ProjWork {
+  int precond = 0;             // 0: Jacobi, 1: multigrid V-cycle
+  int nlev = 0;                // levels of the multigrid hierarchy (0: not built yet)
+  MgLevel lev[kMgMaxLevels];
   bool ready = false;
   int nb = 0;                  // blocks of every projection kernel (fixed: deterministic sums)
   long long nact = 0;          // cells in the solve (diagonal > 0)

@@ -17,7 +17,7 @@
 // writes one partial sum per block; a consumer block adds the nb partials in
 // a fixed order, so the solve is deterministic.  Convergence is detected on
 // the device (the kernels of later iterations return at once) and read by
-// the host every 32 iterations.
+// the host every 32 iterations (every 4 with the multigrid preconditioner).
 #include "eb_handle.cuh"
 
 #include <math.h>
@@ -28,7 +28,7 @@ namespace {
 
 constexpr int PB = 256;   // threads per block of every projection kernel
 
-enum { S_SUM = 0, S_BB = 1, S_PQ = 2, S_RR = 3, S_RZ0 = 4, S_RZ1 = 5, S_CNT = 6 };
+enum { S_SUM = 0, S_BB = 1, S_PQ = 2, S_RR = 3, S_RZ0 = 4, S_RZ1 = 5, S_CNT = 6, S_TMP = 7 };
 
 __device__ inline double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -190,7 +190,9 @@ __global__ void k_apply(Op O, const double *p, double *q, double *ppq, const int
   block_partial(pq, ppq);
 }
 
-// alpha = rz / pq; x += alpha p; r -= alpha q; z = r / d
+// alpha = rz / pq; x += alpha p; r -= alpha q; z = r / d (Jacobi; the
+// multigrid preconditioner forms z and r.z afterwards)
+template <bool JAC>
 __global__ void k_update(Op O, double *x, const double *p, const double *q, double *r, double *z, const double *ppq,
                          const double *prz, double *prz_next, double *prr, int nb, const int *conv) {
   if (*conv) return;
@@ -202,15 +204,19 @@ __global__ void k_update(Op O, double *x, const double *p, const double *q, doub
     if (O.d[c] > 0.0) {
       x[c] += alpha * p[c];
       const double rv = r[c] - alpha * q[c];
-      const double zv = rv / O.d[c];
       r[c] = rv;
-      z[c] = zv;
-      rz += rv * zv;
+      if (JAC) {
+        const double zv = rv / O.d[c];
+        z[c] = zv;
+        rz += rv * zv;
+      }
       rr += rv * rv;
     }
   }
-  block_partial(rz, prz_next);
-  __syncthreads();
+  if (JAC) {
+    block_partial(rz, prz_next);
+    __syncthreads();
+  }
   block_partial(rr, prr);
 }
 
@@ -241,6 +247,176 @@ __global__ void k_correct(Op O, const double *x, double dt, T *mu, T *mv, T *mw)
     if (O.by[c] > 0.0) mv[c] = (T)((double)mv[c] - dt * (x[c] - x[n.ym]) * D.idy);
     if (n.k >= 1 && O.bz[c] > 0.0) mw[c] = (T)((double)mw[c] - dt * (x[c] - x[c - D.nxy]) * D.idz);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid preconditioner (EB_PRECOND_MG): z = V(r), one V-cycle in FP32
+// (FP64 arithmetic is scarce on this GPU; the outer conjugate gradients stay
+// in FP64).  Damped Jacobi with the same weight before and after the coarse
+// correction, restriction = 1/8 of the transpose of the injection
+// prolongation, and a fixed number of Jacobi sweeps from zero on the
+// coarsest grid: up to float rounding V is a fixed symmetric positive
+// semi-definite operator, as conjugate gradients need.
+// ---------------------------------------------------------------------------
+constexpr float MG_OMEGA = 0.8f;
+constexpr int MG_COARSE_SWEEPS = 64;   // even: the coarsest result ends in x
+
+// the operator of one level: S = sum_f a_f x_nb (off-diagonal part) and the
+// diagonal d = sum_f a_f, from the six face coefficients of cell c
+struct Op32 {
+  Dims D;
+  const float *bx, *by, *bz;
+  float ix2, iy2, iz2;
+  __device__ inline void parts(const float *x, long long c, float &S, float &d) const {
+    const Nbr n = neighbours(D, c);
+    const float axl = bx[c] * ix2, axh = bx[n.xp] * ix2, ayl = by[c] * iy2, ayh = by[n.yp] * iy2;
+    const float azl = bz[c] * iz2, azh = n.k + 1 < D.nz ? bz[c + D.nxy] * iz2 : 0.f;
+    d = axl + axh + ayl + ayh + azl + azh;
+    S = axl * x[n.xm] + axh * x[n.xp] + ayl * x[n.ym] + ayh * x[n.yp];
+    if (azl > 0.f) S += azl * x[c - D.nxy];
+    if (azh > 0.f) S += azh * x[c + D.nxy];
+  }
+  __device__ inline float diag(long long c) const {
+    const Nbr n = neighbours(D, c);
+    const float azh = n.k + 1 < D.nz ? bz[c + D.nxy] * iz2 : 0.f;
+    return (bx[c] + bx[n.xp]) * ix2 + (by[c] + by[n.yp]) * iy2 + bz[c] * iz2 + azh;
+  }
+};
+
+// level 0: float copies of the open fractions
+__global__ void k_mg_copy(long long N, const double *bx, const double *by, const double *bz, float *fx, float *fy,
+                          float *fz) {
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) {
+    fx[c] = (float)bx[c];
+    fy[c] = (float)by[c];
+    fz[c] = (float)bz[c];
+  }
+}
+
+// coarse open fractions: the mean over the four fine faces a coarse face covers
+__global__ void k_mg_coarsen(Op32 F, Dims C, float *bx, float *by, float *bz) {
+  const long long N = C.nxy * C.nz;
+  const long long sy = F.D.nx, sz = F.D.nxy;
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) {
+    int I, J, K;
+    split_index(C, (unsigned)c, I, J, K);
+    const long long f = 2LL * I + sy * 2LL * J + sz * 2LL * K;
+    bx[c] = 0.25f * (F.bx[f] + F.bx[f + sy] + F.bx[f + sz] + F.bx[f + sy + sz]);
+    by[c] = 0.25f * (F.by[f] + F.by[f + 1] + F.by[f + sz] + F.by[f + 1 + sz]);
+    bz[c] = 0.25f * (F.bz[f] + F.bz[f + 1] + F.bz[f + sy] + F.bz[f + 1 + sy]);
+  }
+}
+
+// one damped Jacobi sweep, xout = (1 - w) xin + w (b + S(xin)) / d (xin = 0
+// when first); B is the right-hand side's type (the FP64 residual on level
+// 0).  FINAL: the finest level's last sweep, which writes the FP64 z and the
+// block partials of r.z.
+template <typename B, bool FINAL>
+__global__ void k_mg_sweep(Op32 L, const float *xin, float *xout, double *zout, const B *b, int first, double *prz,
+                           const int *conv) {
+  if (*conv) return;
+  const long long N = L.D.nxy * L.D.nz;
+  double rz = 0.0;
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) {
+    float v = 0.f;
+    if (first) {
+      const float d = L.diag(c);
+      if (d > 0.f) v = MG_OMEGA * (float)b[c] / d;
+    } else {
+      float S, d;
+      L.parts(xin, c, S, d);
+      if (d > 0.f) v = (1.f - MG_OMEGA) * xin[c] + MG_OMEGA * ((float)b[c] + S) / d;
+    }
+    if (FINAL) {
+      zout[c] = (double)v;
+      rz += (double)b[c] * (double)v;
+    } else {
+      xout[c] = v;
+    }
+  }
+  if (FINAL) block_partial(rz, prz);
+}
+
+// coarse right-hand side: the mean of the eight children's residuals b - A x
+template <typename B>
+__global__ void k_mg_restrict(Op32 F, const float *x, const B *b, Dims C, float *bc, const int *conv) {
+  if (*conv) return;
+  const long long N = C.nxy * C.nz;
+  const long long sy = F.D.nx, sz = F.D.nxy;
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) {
+    int I, J, K;
+    split_index(C, (unsigned)c, I, J, K);
+    const long long f0 = 2LL * I + sy * 2LL * J + sz * 2LL * K;
+    float sum = 0.f;
+    for (int q = 0; q < 8; ++q) {
+      const long long f = f0 + (q & 1) + ((q >> 1) & 1) * sy + (q >> 2) * sz;
+      float S, d;
+      F.parts(x, f, S, d);
+      if (d > 0.f) sum += (float)b[f] - d * x[f] + S;
+    }
+    bc[c] = 0.125f * sum;
+  }
+}
+
+// x += the parent's coarse correction (injection), on active cells
+__global__ void k_mg_prolong(Op32 F, Dims C, const float *xc, float *x, const int *conv) {
+  if (*conv) return;
+  const long long N = F.D.nxy * F.D.nz;
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) {
+    if (F.diag(c) > 0.f) {
+      int i, j, k;
+      split_index(F.D, (unsigned)c, i, j, k);
+      x[c] += xc[(i >> 1) + (long long)C.nx * ((j >> 1) + (long long)C.ny * (k >> 1))];
+    }
+  }
+}
+
+// the coarsest grid: MG_COARSE_SWEEPS Jacobi sweeps from zero in one block
+__global__ void k_mg_coarsest(Op32 L, const float *b, float *x, float *t, const int *conv) {
+  if (*conv) return;
+  const long long N = L.D.nxy * L.D.nz;
+  for (int sw = 0; sw < MG_COARSE_SWEEPS; ++sw) {
+    const float *in = (sw & 1) ? t : x;
+    float *out = (sw & 1) ? x : t;
+    for (long long c = threadIdx.x; c < N; c += blockDim.x) {
+      float v = 0.f;
+      if (sw == 0) {
+        const float d = L.diag(c);
+        if (d > 0.f) v = MG_OMEGA * b[c] / d;
+      } else {
+        float S, d;
+        L.parts(in, c, S, d);
+        if (d > 0.f) v = (1.f - MG_OMEGA) * in[c] + MG_OMEGA * (b[c] + S) / d;
+      }
+      out[c] = v;
+    }
+    __syncthreads();   // the block's global writes are visible to the next sweep
+  }
+}
+
+Op32 level_op(const MgLevel &L) {
+  Op32 O;
+  O.D = L.D;
+  O.bx = L.bx;
+  O.by = L.by;
+  O.bz = L.bz;
+  O.ix2 = L.ix2;
+  O.iy2 = L.iy2;
+  O.iz2 = L.iz2;
+  return O;
+}
+
+// sizes of the levels (level 0 = the cell grid); false if multigrid does not apply
+bool mg_plan(const Dims &D, int dims[kMgMaxLevels][3], int &nlev) {
+  int nx = D.nx, ny = D.ny, nz = D.nz;
+  nlev = 0;
+  dims[nlev][0] = nx, dims[nlev][1] = ny, dims[nlev][2] = nz, ++nlev;
+  while (nlev < kMgMaxLevels && (long long)nx * ny * nz > 512 && nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0 &&
+         nx >= 4 && ny >= 4 && nz >= 4) {
+    nx /= 2, ny /= 2, nz /= 2;
+    dims[nlev][0] = nx, dims[nlev][1] = ny, dims[nlev][2] = nz, ++nlev;
+  }
+  return nlev >= 2 && (long long)nx * ny * nz <= 32768;
 }
 
 Op make_op(eb_geom g) {
@@ -284,6 +460,76 @@ eb_status setup(eb_geom g, cudaStream_t s) {
   w.nact = (long long)cnt;
   w.ready = true;
   return EB_OK;
+}
+
+// the multigrid hierarchy, on the first projection that uses it
+eb_status mg_setup(eb_geom g, cudaStream_t s) {
+  ProjWork &w = g->pw;
+  if (w.nlev) return EB_OK;
+  int dims[kMgMaxLevels][3], nlev = 0;
+  if (!mg_plan(g->D, dims, nlev)) return fail(EB_ERR_INVALID_ARG, "grid cannot be coarsened for multigrid");
+  const Op O0 = make_op(g);
+  MgLevel &L0 = w.lev[0];
+  L0.D = g->D;
+  L0.ix2 = (float)O0.ix2, L0.iy2 = (float)O0.iy2, L0.iz2 = (float)O0.iz2;
+  L0.nb = w.nb;
+  const long long N0 = g->D.nxy * g->D.nz;
+  for (float **a : {&L0.bx, &L0.by, &L0.bz, &L0.x, &L0.t}) CUDA_TRY(g->alloc(a, N0), "alloc multigrid level");
+  k_mg_copy<<<L0.nb, PB, 0, s>>>(N0, w.bx, w.by, w.bz, L0.bx, L0.by, L0.bz);
+  for (int l = 1; l < nlev; ++l) {
+    MgLevel &L = w.lev[l];
+    const MgLevel &F = w.lev[l - 1];
+    Dims &C = L.D;
+    C = F.D;
+    C.nx = dims[l][0], C.ny = dims[l][1], C.nz = dims[l][2];
+    C.nxy = (long long)C.nx * C.ny;
+    C.dx = 2 * F.D.dx, C.dy = 2 * F.D.dy, C.dz = 2 * F.D.dz;
+    C.idx = 0.5 * F.D.idx, C.idy = 0.5 * F.D.idy, C.idz = 0.5 * F.D.idz;
+    C.fnx.init((unsigned)C.nx);
+    C.fny.init((unsigned)C.ny);
+    C.fnxy.init((unsigned)C.nxy);
+    L.ix2 = 0.25f * F.ix2, L.iy2 = 0.25f * F.iy2, L.iz2 = 0.25f * F.iz2;
+    const long long N = C.nxy * C.nz;
+    L.nb = (int)std::max(1LL, std::min<long long>(w.nb, (N + PB - 1) / PB));
+    for (float **a : {&L.bx, &L.by, &L.bz, &L.x, &L.t, &L.b}) CUDA_TRY(g->alloc(a, N), "alloc multigrid level");
+    k_mg_coarsen<<<L.nb, PB, 0, s>>>(level_op(F), C, L.bx, L.by, L.bz);
+  }
+  CUDA_TRY(cudaGetLastError(), "multigrid set-up");
+  w.nlev = nlev;
+  return EB_OK;
+}
+
+// z = V(r) (FP64 in and out) and the partial sums of r.z into prz
+void vcycle(eb_geom g, const double *r, double *z, double *prz, cudaStream_t s) {
+  ProjWork &w = g->pw;
+  const MgLevel *L = w.lev;
+  const int top = w.nlev - 1;
+  // level 0: right-hand side r (FP64)
+  {
+    const Op32 O = level_op(L[0]);
+    k_mg_sweep<double, false><<<L[0].nb, PB, 0, s>>>(O, nullptr, L[0].t, nullptr, r, 1, nullptr, w.conv);
+    k_mg_sweep<double, false><<<L[0].nb, PB, 0, s>>>(O, L[0].t, L[0].x, nullptr, r, 0, nullptr, w.conv);
+    k_mg_restrict<double><<<L[1].nb, PB, 0, s>>>(O, L[0].x, r, L[1].D, L[1].b, w.conv);
+  }
+  for (int l = 1; l < top; ++l) {
+    const Op32 O = level_op(L[l]);
+    k_mg_sweep<float, false><<<L[l].nb, PB, 0, s>>>(O, nullptr, L[l].t, nullptr, L[l].b, 1, nullptr, w.conv);
+    k_mg_sweep<float, false><<<L[l].nb, PB, 0, s>>>(O, L[l].t, L[l].x, nullptr, L[l].b, 0, nullptr, w.conv);
+    k_mg_restrict<float><<<L[l + 1].nb, PB, 0, s>>>(O, L[l].x, L[l].b, L[l + 1].D, L[l + 1].b, w.conv);
+  }
+  k_mg_coarsest<<<1, 1024, 0, s>>>(level_op(L[top]), L[top].b, L[top].x, L[top].t, w.conv);
+  for (int l = top - 1; l >= 1; --l) {
+    const Op32 O = level_op(L[l]);
+    k_mg_prolong<<<L[l].nb, PB, 0, s>>>(O, L[l + 1].D, L[l + 1].x, L[l].x, w.conv);
+    k_mg_sweep<float, false><<<L[l].nb, PB, 0, s>>>(O, L[l].x, L[l].t, nullptr, L[l].b, 0, nullptr, w.conv);
+    k_mg_sweep<float, false><<<L[l].nb, PB, 0, s>>>(O, L[l].t, L[l].x, nullptr, L[l].b, 0, nullptr, w.conv);
+  }
+  {
+    const Op32 O = level_op(L[0]);
+    k_mg_prolong<<<L[0].nb, PB, 0, s>>>(O, L[1].D, L[1].x, L[0].x, w.conv);
+    k_mg_sweep<double, false><<<L[0].nb, PB, 0, s>>>(O, L[0].x, L[0].t, nullptr, r, 0, nullptr, w.conv);
+    k_mg_sweep<double, true><<<L[0].nb, PB, 0, s>>>(O, L[0].t, nullptr, z, r, 0, prz, w.conv);
+  }
 }
 
 double host_total(eb_geom g, int slot, cudaStream_t s, cudaError_t &e) {
@@ -338,8 +584,17 @@ eb_status eb_project_impl(eb_geom g, void *const mom[3], double dt, double rtol,
   k_center<<<w.nb, PB, 0, s>>>(O, w.rhs, w.part + S_SUM * w.nb, w.part + S_CNT * w.nb, w.nb, w.part + S_BB * w.nb);
   if (phi0) CUDA_TRY(cudaMemcpyAsync(w.x, phi0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s), "initial guess");
   else CUDA_TRY(cudaMemsetAsync(w.x, 0, sizeof(double) * N, s), "initial guess");
-  k_init<<<w.nb, PB, 0, s>>>(O, w.x, w.rhs, w.r, w.z, w.p, w.part + S_RZ0 * w.nb, w.part + S_RR * w.nb);
+  const bool mg = w.precond == EB_PRECOND_MG;
+  if (mg) {
+    st = mg_setup(g, s);
+    if (st != EB_OK) return st;
+  }
   CUDA_TRY(cudaMemsetAsync(w.conv, 0, sizeof(int), s), "reset");
+  k_init<<<w.nb, PB, 0, s>>>(O, w.x, w.rhs, w.r, w.z, w.p, w.part + S_RZ0 * w.nb, w.part + S_RR * w.nb);
+  if (mg) {   // z = V(r), p = z
+    vcycle(g, w.r, w.z, w.part + S_RZ0 * w.nb, s);
+    CUDA_TRY(cudaMemcpyAsync(w.p, w.z, sizeof(double) * N, cudaMemcpyDeviceToDevice, s), "search direction");
+  }
   cudaError_t e = cudaSuccess;
   const double bb = host_total(g, S_BB, s, e);
   CUDA_TRY(e, "residual norm");
@@ -354,10 +609,18 @@ eb_status eb_project_impl(eb_geom g, void *const mom[3], double dt, double rtol,
       double *prz = w.part + (it % 2 ? S_RZ1 : S_RZ0) * w.nb;
       double *prz_next = w.part + (it % 2 ? S_RZ0 : S_RZ1) * w.nb;
       k_apply<<<w.nb, PB, 0, s>>>(O, w.p, w.q, w.part + S_PQ * w.nb, w.conv);
-      k_update<<<w.nb, PB, 0, s>>>(O, w.x, w.p, w.q, w.r, w.z, w.part + S_PQ * w.nb, prz, prz_next,
-                                   w.part + S_RR * w.nb, w.nb, w.conv);
+      if (mg) {
+        k_update<false><<<w.nb, PB, 0, s>>>(O, w.x, w.p, w.q, w.r, w.z, w.part + S_PQ * w.nb, prz, prz_next,
+                                            w.part + S_RR * w.nb, w.nb, w.conv);
+        vcycle(g, w.r, w.z, prz_next, s);
+      } else {
+        k_update<true><<<w.nb, PB, 0, s>>>(O, w.x, w.p, w.q, w.r, w.z, w.part + S_PQ * w.nb, prz, prz_next,
+                                           w.part + S_RR * w.nb, w.nb, w.conv);
+      }
       k_direction<<<w.nb, PB, 0, s>>>(O, w.p, w.z, prz, prz_next, w.part + S_RR * w.nb, w.nb, thr2, it, w.conv);
-      if ((it + 1) % 32 == 0 || it + 1 == maxit) {
+      // the host reads the convergence flag every few iterations (a V-cycle
+      // iteration costs far more than a Jacobi one, so it looks sooner)
+      if ((it + 1) % (mg ? 4 : 32) == 0 || it + 1 == maxit) {
         CUDA_TRY(cudaMemcpyAsync(&done, w.conv, sizeof(int), cudaMemcpyDeviceToHost, s), "convergence flag");
         CUDA_TRY(cudaStreamSynchronize(s), "convergence flag");
         if (done) break;
@@ -393,6 +656,19 @@ eb_status eb_project(eb_geom geom, eb_state *U, double dt, double rtol, int maxi
   void **u = state_ptrs(U);
   void *mom[3] = {u[2], u[3], u[4]};
   return eb_project_impl(geom, mom, dt, rtol, maxit, phi0, phi, iters, relres, as_stream(stream), true);
+}
+
+eb_status eb_project_set_preconditioner(eb_geom geom, int kind) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  if (kind != EB_PRECOND_JACOBI && kind != EB_PRECOND_MG) return fail(EB_ERR_INVALID_ARG, "unknown preconditioner");
+  if (kind == EB_PRECOND_MG) {
+    int dims[kMgMaxLevels][3], nlev = 0;
+    if (!mg_plan(geom->D, dims, nlev))
+      return fail(EB_ERR_INVALID_ARG,
+                  "grid cannot be coarsened for multigrid (even sizes needed; coarsest grid <= 32768 cells)");
+  }
+  geom->pw.precond = kind;
+  return EB_OK;
 }
 
 eb_status eb_anelastic_step(eb_geom geom, const eb_state *Un, eb_state *Unp1, double dt, int nsteps, double rtol,

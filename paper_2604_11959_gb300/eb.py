@@ -31,7 +31,7 @@ EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom
                     "eb_unet_num_params", "eb_unet_create", "eb_unet_set_params", "eb_unet_get_params",
                     "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step", "eb_unet_destroy",
                     "eb_project_sample", "eb_project_warm", "eb_geom_tune",
-                    "eb_geom_set_slab_levels")
+                    "eb_geom_set_slab_levels", "eb_project_set_preconditioner")
 
 
 class EbError(RuntimeError):
@@ -110,6 +110,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_project_warm.argtypes = [V, V, P(_State), D, D, I, D, P(I), P(D), V]
     lib.eb_geom_tune.argtypes = [V, P(_State), D, I, P(I), V]
     lib.eb_geom_set_slab_levels.argtypes = [V, I]
+    lib.eb_project_set_preconditioner.argtypes = [V, I]
     lib.eb_last_error.restype = ctypes.c_char_p
     lib.eb_version.restype = I
     for name in ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
@@ -118,7 +119,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                  "eb_ensemble_destroy", "eb_project", "eb_anelastic_step", "eb_unet_create", "eb_unet_set_params",
                  "eb_unet_get_params", "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step",
                  "eb_unet_destroy", "eb_project_sample", "eb_project_warm", "eb_geom_tune",
-                 "eb_geom_set_slab_levels"):
+                 "eb_geom_set_slab_levels", "eb_project_set_preconditioner"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -297,6 +298,17 @@ def tune(geom: Geometry, U: dict, dt: float, reps: int = 5, stream=None) -> int:
     _check(load().eb_geom_tune(geom.handle, ctypes.byref(geom._cstate(U)), float(dt), int(reps), ctypes.byref(best),
                                _stream(stream)))
     return best.value
+
+
+PRECONDITIONERS = {"jacobi": 0, "mg": 1}
+
+
+def set_preconditioner(geom: Geometry, kind: str) -> None:
+    """Preconditioner of the projection's conjugate gradients for this handle
+    (``eb_project_set_preconditioner``): "jacobi" (default) or "mg"."""
+    if kind not in PRECONDITIONERS:
+        raise ValueError(f"unknown preconditioner {kind!r}")
+    _check(load().eb_project_set_preconditioner(geom.handle, PRECONDITIONERS[kind]))
 
 
 def set_slab_levels(geom: Geometry, levels: int) -> None:
