@@ -459,9 +459,9 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=
     hbm, kind = peaks()
     achieved = fast_bytes / (prof[0] * 1e-3) / 1e9
     # per step: static pass-through (a fresh output buffer every call), the
-    # tiled bulk kernel, the three near-EB kernels (face fluxes, CVs with a
-    # record, regular CVs) and the three fused redistribution passes
-    launches_per_step = 2 + (3 if sum(info["band_cvs"]) else 0) + (2 if sum(info["small_cvs"]) else 0) + \
+    # tiled bulk kernel, the two near-EB kernels (face fluxes; CVs with and
+    # without a record in one launch) and the three fused redistribution passes
+    launches_per_step = 2 + (2 if sum(info["band_cvs"]) else 0) + (2 if sum(info["small_cvs"]) else 0) + \
         (1 if sum(info["affected_cvs"]) else 0)
     # bytes the whole step must move: every non-covered CV read and written
     # once, plus the band geometry records read by the near-EB kernel
