@@ -64,7 +64,6 @@ __device__ inline void copy_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-
 // ---- tensor memory as per-thread storage (float path) -----------------------
 // The z window of a thread's own columns, the carried x / y divergence parts
 // and the carried bottom z fluxes live in tensor memory between the levels
@@ -97,20 +96,27 @@ __device__ inline void tm_st2(unsigned taddr, float2 a) {
 // window levels at a0, a1, a2 (8 words each), x / y parts at aq (8), bottom
 // fluxes at az (10): after any pending stores, loaded and waited for
 __device__ inline void tm_load_z(unsigned a0, unsigned a1, unsigned a2, unsigned aq, unsigned az, unsigned o[42]) {
-    asm volatile(
-        "tcgen05.wait::st.sync.aligned;\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%42];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%43];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%44];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%45];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32, %33, %34, %35, %36, %37, %38, %39}, [%46];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%40, %41}, [%47];\n"
-        "tcgen05.wait::ld.sync.aligned;\n"
-        : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7]), "=r"(o[8]), "=r"(o[9]), "=r"(o[10]), "=r"(o[11]), "=r"(o[12]), "=r"(o[13]), "=r"(o[14]), "=r"(o[15]), "=r"(o[16]), "=r"(o[17]), "=r"(o[18]), "=r"(o[19]), "=r"(o[20]), "=r"(o[21]), "=r"(o[22]), "=r"(o[23]), "=r"(o[24]), "=r"(o[25]), "=r"(o[26]), "=r"(o[27]), "=r"(o[28]), "=r"(o[29]), "=r"(o[30]), "=r"(o[31]), "=r"(o[32]), "=r"(o[33]), "=r"(o[34]), "=r"(o[35]), "=r"(o[36]), "=r"(o[37]), "=r"(o[38]), "=r"(o[39]), "=r"(o[40]), "=r"(o[41])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(aq), "r"(az), "r"(az + 8u)
-        : "memory");
+  asm volatile(
+      "tcgen05.wait::st.sync.aligned;\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%42];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%43];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%44];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%45];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32, %33, %34, %35, %36, %37, %38, %39}, [%46];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%40, %41}, [%47];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]),
+        "=r"(o[7]), "=r"(o[8]), "=r"(o[9]), "=r"(o[10]), "=r"(o[11]), "=r"(o[12]), "=r"(o[13]),
+        "=r"(o[14]), "=r"(o[15]), "=r"(o[16]), "=r"(o[17]), "=r"(o[18]), "=r"(o[19]), "=r"(o[20]),
+        "=r"(o[21]), "=r"(o[22]), "=r"(o[23]), "=r"(o[24]), "=r"(o[25]), "=r"(o[26]), "=r"(o[27]),
+        "=r"(o[28]), "=r"(o[29]), "=r"(o[30]), "=r"(o[31]), "=r"(o[32]), "=r"(o[33]), "=r"(o[34]),
+        "=r"(o[35]), "=r"(o[36]), "=r"(o[37]), "=r"(o[38]), "=r"(o[39]), "=r"(o[40]), "=r"(o[41])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(aq), "r"(az), "r"(az + 8u)
+      : "memory");
 }
-__device__ inline float2 w2(const unsigned *o, int q) { return make_float2(__uint_as_float(o[q]), __uint_as_float(o[q + 1])); }
+__device__ inline float2 w2(const unsigned *o, int q) {
+  return make_float2(__uint_as_float(o[q]), __uint_as_float(o[q + 1]));
+}
 
 // ---- pairs of adjacent columns ----------------------------------------------
 template <typename T>
@@ -299,31 +305,6 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
         fyo[G] = flux6(my[G], ld2(Q - 2 * QX), ld2(Q - QX), pc, ld2(Q + QX));
       }
     };
-    // y faces of the column pair at even tile x on row y (the high y edge)
-    auto yfaces = [&](const T *Rk, const T *Rkm, int x, int y, P fyo[4]) {
-      const int c = TL::ri(x, y);
-      const T *Vv = Rk + 3 * NP;
-      const P vc = ld2(Vv + c), vl = ld2(Vv + c - 2), vd = ld2(Vv + c - PX), vkm = ld2(Rkm + 3 * NP + c);
-      const P my[4] = {vc, pmul(padd(mk(vl.y, vc.x), vc), half), pmul(padd(vd, vc), half), pmul(padd(vkm, vc), half)};
-#pragma unroll
-      for (int G = 0; G < 4; ++G) {
-        const T *Q = prim + G * NQ + TL::qi(x, y);
-        fyo[G] = flux6(my[G], ld2(Q - 2 * QX), ld2(Q - QX), ld2(Q), ld2(Q + QX));
-      }
-    };
-    // x face at tile x = TX (the high x edge) on row y, all four grids
-    auto xedge = [&](const T *Rk, const T *Rkm, int y, T fxo[4]) {
-      const int c = TL::ri(TX, y);
-      const T *U = Rk + 2 * NP;
-      const T u0 = U[c];
-      const T mx[4] = {u0, T(0.5) * (U[c - 1] + u0), T(0.5) * (U[c - PX] + u0), T(0.5) * (Rkm[2 * NP + c] + u0)};
-#pragma unroll
-      for (int G = 0; G < 4; ++G) {
-        const T *Q = prim + G * NQ + TL::qi(TX, y);
-        fxo[G] = flux6(splat(mx[G]), splat(Q[-2]), splat(Q[-1]), splat(Q[0]), splat(Q[1])).x;
-      }
-    };
-
     auto ref_r = [&](int L) -> T { return (L >= 0 && L < nz) ? A.src.ref_rho[L] : T(0); };
     auto ref_t = [&](int L) -> T { return (L >= 0 && L < nz) ? A.src.ref_rt[L] : T(0); };
     const int p0 = kbeg - 2, p1 = kend + 1;
@@ -412,16 +393,32 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
           FX[G * TL::NFX + ty * TL::FXW + tx] = fx[G].x;
           st2(FY + G * TL::NFY + ty * TX + 2 * tx, fy[G]);
         }
-        if (ty == 0) {   // faces on the high y edge of the tile
-          P e[4];
-          yfaces(Rk, Rkm, 2 * tx, TY, e);
-#pragma unroll
-          for (int G = 0; G < 4; ++G) st2(FY + G * TL::NFY + TY * TX + 2 * tx, e[G]);
-        } else if (ty == TY - 1) {   // faces on the high x edge of the tile (row tx)
-          T e[4];
-          xedge(Rk, Rkm, tx, e);
-#pragma unroll
-          for (int G = 0; G < 4; ++G) FX[G * TL::NFX + tx * TL::FXW + NPX] = e[G];
+        if (ty <= 1) {   // faces on the high y edge of the tile: row ty takes grids 2 ty, 2 ty + 1
+          const int G0 = 2 * ty;
+          const int c = TL::ri(2 * tx, TY);
+          const T *Vv = Rk + 3 * NP;
+          const P vc = ld2(Vv + c);
+          const P mA = ty ? pmul(padd(ld2(Vv + c - PX), vc), half) : vc;
+          const P mB = pmul(padd(ty ? ld2(Rkm + 3 * NP + c) : mk(Vv[c - 1], vc.x), vc), half);
+          const T *Q = prim + G0 * NQ + TL::qi(2 * tx, TY);
+          const P fA = flux6(mA, ld2(Q - 2 * QX), ld2(Q - QX), ld2(Q), ld2(Q + QX));
+          Q += NQ;
+          const P fB = flux6(mB, ld2(Q - 2 * QX), ld2(Q - QX), ld2(Q), ld2(Q + QX));
+          st2(FY + G0 * TL::NFY + TY * TX + 2 * tx, fA);
+          st2(FY + (G0 + 1) * TL::NFY + TY * TX + 2 * tx, fB);
+        } else if (ty >= TY - 2) {   // faces on the high x edge of the tile (row tx): two grids per row
+          const int hi = ty - (TY - 2), G0 = 2 * hi;
+          const int c = TL::ri(TX, tx);
+          const T *U = Rk + 2 * NP;
+          const T u0 = U[c];
+          const T mA = hi ? T(0.5) * (U[c - PX] + u0) : u0;
+          const T mB = T(0.5) * ((hi ? Rkm[2 * NP + c] : U[c - 1]) + u0);
+          const T *Q = prim + G0 * NQ + TL::qi(TX, tx);
+          FX[G0 * TL::NFX + tx * TL::FXW + NPX] =
+              flux6(splat(mA), splat(Q[-2]), splat(Q[-1]), splat(Q[0]), splat(Q[1])).x;
+          Q += NQ;
+          FX[(G0 + 1) * TL::NFX + tx * TL::FXW + NPX] =
+              flux6(splat(mB), splat(Q[-2]), splat(Q[-1]), splat(Q[0]), splat(Q[1])).x;
         }
       }
       copy_wait<1>();   // raw p + 1 landed (this thread's copies)
