@@ -570,22 +570,35 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
 // Pass-through of the CVs no kernel updates (covered CVs and the two wall
 // levels of rho*w; zeros when dU itself is written), from per-grid lists
 // built at set-up: one thread per listed CV.
+// one grid's list per block range (bstart[q] .. bstart[q + 1] - 1); each
+// thread copies up to four listed CVs, their loads issued together
+struct StaticBlocks {
+  unsigned bstart[5];
+};
+constexpr int STATIC_PER_THREAD = 4;
+
 template <typename T>
-__global__ void k_static(StepArgs<T> A) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__global__ void k_static(StepArgs<T> A, StaticBlocks SB) {
   int q = 0;
-  for (q = 0; q < 4; ++q) {
-    if (t < A.G[q].nstatic) break;
-    t -= A.G[q].nstatic;
+  while (q < 3 && blockIdx.x >= SB.bstart[q + 1]) ++q;
+  const long long n = A.G[q].nstatic;
+  const long long t0 = (long long)(blockIdx.x - SB.bstart[q]) * blockDim.x * STATIC_PER_THREAD + threadIdx.x;
+  const unsigned *L = A.G[q].slist;
+  const int f0 = q == 0 ? 0 : q + 1, nf = q == 0 ? 2 : 1;
+  unsigned c[STATIC_PER_THREAD];
+#pragma unroll
+  for (int e = 0; e < STATIC_PER_THREAD; ++e) {
+    const long long t = t0 + (long long)e * blockDim.x;
+    c[e] = t < n ? L[t] : 0xffffffffu;
   }
-  if (q >= 4) return;
-  const unsigned c = A.G[q].slist[t];
-  auto put = [&](int f) { A.out[f][c] = A.base[0] ? A.base[f][c] : T(0); };
-  if (q == 0) {
-    put(0);
-    put(1);
-  } else {
-    put(q + 1);
+  for (int f = f0; f < f0 + nf; ++f) {
+    T v[STATIC_PER_THREAD];
+#pragma unroll
+    for (int e = 0; e < STATIC_PER_THREAD; ++e)
+      v[e] = (c[e] != 0xffffffffu && A.base[0]) ? A.base[f][c[e]] : T(0);
+#pragma unroll
+    for (int e = 0; e < STATIC_PER_THREAD; ++e)
+      if (c[e] != 0xffffffffu) A.out[f][c[e]] = v[e];
   }
 }
 
@@ -674,8 +687,12 @@ template <typename T>
 void launch_static_copy(const StepArgs<T> &A, cudaStream_t s) {
   const Dims &D = A.D;
   if (A.copy_static) {
-    const long long n = A.G[0].nstatic + A.G[1].nstatic + A.G[2].nstatic + A.G[3].nstatic;
-    if (n > 0) k_static<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A);
+    StaticBlocks SB;
+    SB.bstart[0] = 0;
+    for (int q = 0; q < 4; ++q)
+      SB.bstart[q + 1] = SB.bstart[q] + (unsigned)((A.G[q].nstatic + 256 * STATIC_PER_THREAD - 1) /
+                                                   (256 * STATIC_PER_THREAD));
+    if (SB.bstart[4] > 0) k_static<T><<<SB.bstart[4], 256, 0, s>>>(A, SB);
   }
 }
 

@@ -13,7 +13,7 @@
 //   weighted state redistribution (Sec. 5.1, Eqs. qhat_omega, qrecon,
 //   final_update_omega), on compact lists built at set-up:
 //     k_qhat  : neighbourhood averages of the small CVs;
-//     k_sigma : least-squares slopes and the limiter, one warp per small CV;
+//     k_sigma : least-squares slopes and the limiter, 8 lanes per small CV;
 //     k_final : the final update of every CV the redistribution changes.
 //
 // Every kernel writes a disjoint set of CVs, so no atomics are needed and
@@ -556,13 +556,14 @@ __device__ inline void qhat_one(const WsrdArgs<T> &R, long long s) {
   R.pval[s] = R.u[lp];   // snapshot: the final update overwrites the field in place
 }
 
-// One group of GS lanes (half a warp) per small CV: lanes walk the stencil,
-// shuffles reduce the slope and the stencil's range of Qhat - Qhat_r; lane q
-// evaluates the limiter at member q's centroid and a min-reduction combines
-// them.  A group without a CV (valid false) takes part in the shuffles only.
+// One group of GS lanes per small CV (8 in the kernels: four CVs per warp):
+// lanes walk the stencil, shuffles reduce the slope and the stencil's range
+// of Qhat - Qhat_r; lane q evaluates the limiter at member q's centroid and a
+// min-reduction combines them.  A group without a CV (valid false) takes part
+// in the shuffles only.
 template <typename T, int GS>
 __device__ inline void sigma_one(const WsrdArgs<T> &R, long long s, int lane, bool valid) {
-  static_assert(GS == 16 || GS == 32, "lane groups are half or whole warps");
+  static_assert(GS == 8 || GS == 16 || GS == 32, "lane groups of 8, 16 or 32 lanes");
   long long o0 = 0, o1 = 0, pr = 0;
   T dr = T(0);
   if (valid) {
@@ -572,6 +573,7 @@ __device__ inline void sigma_one(const WsrdArgs<T> &R, long long s, int lane, bo
     dr = R.dev[s];
   }
   T sx = T(0), sy = T(0), sz = T(0), bmax = T(0), bmin = T(0);
+#pragma unroll 2
   for (long long o = o0 + lane; o < o1; o += GS) {
     const int sid = R.W.l_sid[o];
     const long long pm = R.W.l_plin[o];
@@ -666,8 +668,8 @@ __global__ void k_qhat(WsrdArgs<T> R) {
 }
 template <typename T>
 __global__ void k_sigma(WsrdArgs<T> R) {
-  const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4;
-  sigma_one<T, 16>(R, s, threadIdx.x & 15, s < R.W.nsmall);
+  const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 3;
+  sigma_one<T, 8>(R, s, threadIdx.x & 7, s < R.W.nsmall);
 }
 template <typename T>
 __global__ void k_final(WsrdArgs<T> R) {
@@ -691,10 +693,10 @@ __global__ void k_qhat5(const __grid_constant__ WsrdSet<T> S) {
 }
 template <typename T>
 __global__ void k_sigma5(const __grid_constant__ WsrdSet<T> S) {
-  const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4;
+  const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 3;
   const bool valid = t < S.off_small[5];
   const int f = valid ? field_of(S.off_small, t) : 0;
-  sigma_one<T, 16>(S.f[f], valid ? t - S.off_small[f] : 0, threadIdx.x & 15, valid);
+  sigma_one<T, 8>(S.f[f], valid ? t - S.off_small[f] : 0, threadIdx.x & 7, valid);
 }
 template <typename T>
 __global__ void k_final5(const __grid_constant__ WsrdSet<T> S) {
@@ -731,7 +733,7 @@ template <typename T>
 void launch_wsrd(const WsrdArgs<T> &R, cudaStream_t s) {
   if (R.W.nsmall) {
     k_qhat<T><<<(unsigned)((R.W.nsmall + 127) / 128), 128, 0, s>>>(R);
-    k_sigma<T><<<(unsigned)((R.W.nsmall * 16 + 255) / 256), 256, 0, s>>>(R);
+    k_sigma<T><<<(unsigned)((R.W.nsmall * 8 + 255) / 256), 256, 0, s>>>(R);
   }
   if (R.W.naff) k_final<T><<<(unsigned)((R.W.naff + 127) / 128), 128, 0, s>>>(R);
 }
@@ -740,7 +742,7 @@ template <typename T>
 void launch_wsrd5(const WsrdSet<T> &S, cudaStream_t s) {
   if (S.off_small[5]) {
     k_qhat5<T><<<(unsigned)((S.off_small[5] + 127) / 128), 128, 0, s>>>(S);
-    k_sigma5<T><<<(unsigned)((S.off_small[5] * 16 + 255) / 256), 256, 0, s>>>(S);
+    k_sigma5<T><<<(unsigned)((S.off_small[5] * 8 + 255) / 256), 256, 0, s>>>(S);
   }
   if (S.off_aff[5]) k_final5<T><<<(unsigned)((S.off_aff[5] + 127) / 128), 128, 0, s>>>(S);
 }
