@@ -242,6 +242,45 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
       launch_face_masks(D, g->G, s);
       e = cudaStreamSynchronize(s);
     }
+    // FP64 path: the CVs whose advected values the face stencils read, staged
+    // once per step (the float path forms them per face)
+    uint8_t *sm[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long nsm[4] = {0, 0, 0, 0};
+    const bool staging = g->prec == EB_F64;
+    for (int q = 0; q < 4; ++q) {
+      g->G[q].nstage = 0;
+      g->G[q].stlist = nullptr;
+      g->G[q].pv = nullptr;
+    }
+    for (int q = 0; q < 4 && e == cudaSuccess && staging; ++q) {
+      g->G[q].nst = std::min(nzg_of(D, q), kface + 1);
+      nsm[q] = std::max(1LL, D.nxy * (long long)g->G[q].nst);
+      e = cudaMalloc(&sm[q], (size_t)nsm[q]);
+      if (e == cudaSuccess) e = cudaMemsetAsync(sm[q], 0, (size_t)nsm[q], s);
+    }
+    long long *cnt2 = nullptr, *tmp2 = nullptr;
+    long long nmax = std::max(std::max(nsm[0], nsm[1]), std::max(nsm[2], nsm[3]));
+    if (e == cudaSuccess) e = cudaMalloc(&cnt2, sizeof(long long) * (size_t)(nmax + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&tmp2, sizeof(long long) * (size_t)(nmax / 256 + 16));
+    if (e == cudaSuccess && staging) launch_stage_marks(D, g->G, sm, s);
+    for (int q = 0; q < 4 && e == cudaSuccess && staging; ++q) {
+      GridDev &G = g->G[q];
+      e = cudaMemsetAsync(cnt2, 0, sizeof(long long) * (size_t)(nsm[q] + 1), s);
+      launch_marks_to_counts(sm[q], nsm[q], cnt2, s);
+      scan_exclusive(cnt2, nsm[q] + 1, tmp2, s);
+      long long n = 0;
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&n, tmp2, sizeof(long long), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      G.nstage = n;
+      if (e == cudaSuccess) e = g->alloc(&G.stlist, n);
+      if (e == cudaSuccess && n > 0) launch_marks_fill(sm[q], nsm[q], cnt2, G.stlist, s);
+      if (e == cudaSuccess) e = g->alloc((char **)&G.pv, (long long)(nsm[q] * es));
+      if (e == cudaSuccess) e = cudaMemsetAsync(G.pv, 0, (size_t)nsm[q] * es, s);   // never-staged CVs read 0
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int q = 0; q < 4; ++q) cudaFree(sm[q]);
+    cudaFree(cnt2);
+    cudaFree(tmp2);
     for (int d = 0; d < 3; ++d) cudaFree(mk[d]);
     cudaFree(cnt);
     cudaFree(scan_tmp);

@@ -45,6 +45,13 @@ struct GridDev {
   // bits 2 + 2 (t + 2), 3 + 2 (t + 2) the two c-cells beside the grid CV t
   // steps along the face normal (t = -2 .. 1), bits 10, 11 the far CVs t = -2, 1
   uint16_t *fmask[3];
+  // advected value of every CV some listed face's stencil reads (the CV's
+  // theta or face velocity, 0 where it holds no fluid), formed once per step
+  // (k_stage) into the dense array pv (levels below nst) from the list stlist
+  unsigned *stlist;
+  long long nstage;
+  void *pv;
+  int nst;
   // CVs the near-EB kernel updates (non-covered, prognostic, below kfast),
   // state indices in plane-major order
   unsigned *blist;

@@ -62,6 +62,9 @@ void launch_band_rows(const Dims &D, const GridDev G[4], int g, bool fill, long 
 void launch_rows_to_u32(const long long *src, long long n, unsigned *dst, cudaStream_t s);
 // eb_step.cu: availability bits of every listed face into G[q].fmask[d]
 void launch_face_masks(const Dims &D, const GridDev G[4], cudaStream_t s);
+// eb_step.cu: marks[q][idx] = 1 for every CV of grid q a listed face's
+// stencil reads (marks[q] covers levels below G[q].nst)
+void launch_stage_marks(const Dims &D, const GridDev G[4], uint8_t *const marks[4], cudaStream_t s);
 
 // eb_fast.cu: split of the bulk kernel's (tile, level) work into lockstep
 // slabs of slab_levels levels (0: chosen from the GPU's size); seg holds

@@ -209,6 +209,37 @@ __global__ void k_rows_to_u32(const long long *src, long long n, unsigned *dst) 
 // third-order one when the far upstream CV is not available), written for
 // one (grid, direction) pair at a time: every neighbour index is the face's
 // own index plus a periodic offset computed once.
+// index offset of a step s along direction dir from coordinate x (periodic in x, y)
+__device__ inline long long step_off(const Dims &D, int dir, int x, int s) {
+  if (dir == 2) return (long long)s * D.nxy;
+  const int n = dir == 0 ? D.nx : D.ny;
+  int t = x + s;
+  t = t < 0 ? t + n : (t >= n ? t - n : t);
+  return (long long)(t - x) * (dir == 0 ? 1 : D.nx);
+}
+
+// advected value of CV (i, j, k) of grid G (state index idx): theta on the c
+// grid; on a face grid the momentum over the mean density of the non-covered
+// c-cells beside the CV, 0 when both are covered (Sec. 4.1)
+template <typename T, int G>
+__device__ inline T cv_advected(const StepArgs<T> &A, long long idx, int i, int j, int k) {
+  const Dims &D = A.D;
+  auto rho = [&](long long q, int kk) -> T { return A.src.ref_rho[kk] + A.src.f[0][q]; };
+  if (G == 0) return eb_div(A.src.ref_rt[k] + A.src.f[1][idx], rho(idx, k));
+  constexpr int S = G - 1;
+  const int crd[3] = {i, j, k};
+  const long long ia = idx + step_off(D, S, crd[S], -1);
+  const int ka = k - (S == 2 ? 1 : 0);
+  auto fluid0 = [&](long long q, int kk) -> bool { return kk >= 0 && kk < D.nz && (A.G[0].dflag[q] & 1); };
+  const bool a = fluid0(ia, ka), b = fluid0(idx, k);
+  T rb;
+  if (a && b) rb = T(0.5) * (rho(ia, ka) + rho(idx, k));
+  else if (a) rb = rho(ia, ka);
+  else if (b) rb = rho(idx, k);
+  else return T(0);
+  return eb_div(A.src.f[G + 1][idx], rb);
+}
+
 template <typename T, int G, int Dd, bool MASK>
 __device__ inline unsigned face_flux_lean(const StepArgs<T> &A, long long c, int i, int j, int k, unsigned bits,
                                           T &fm, T &fp) {
@@ -283,15 +314,23 @@ __device__ inline unsigned face_flux_lean(const StepArgs<T> &A, long long c, int
   }
   fp = T(0);
   if (fm == T(0)) return 0;
-  const T pL = advected(-1), pR = advected(0);
+  // FP64 path: advected values staged once per CV this step (k_stage; zero on
+  // the w-grid wall levels, which are never staged), as FP64 divisions are
+  // scarce on this GPU; the float path forms them here
+  const T *PV = (const T *)A.G[G].pv;
+  auto staged = [&](int t) -> T {
+    if constexpr (sizeof(T) == sizeof(double)) return PV[c + off(Dd, crd[Dd], t)];
+    else return advected(t);
+  };
+  const T pL = staged(-1), pR = staged(0);
   T val;
   if (fm > T(0)) {
     const bool has = cv_fluid(10, -2);
-    const T pF = has ? advected(-2) : T(0);
+    const T pF = has ? staged(-2) : T(0);
     val = upwind_value(fm, pF, pL, pR, T(0), has, false);
   } else {
     const bool has = cv_fluid(11, 1);
-    const T pF = has ? advected(1) : T(0);
+    const T pF = has ? staged(1) : T(0);
     val = upwind_value(fm, T(0), pL, pR, pF, false, has);
   }
   fp = fm * val;
@@ -351,6 +390,78 @@ __global__ void k_face_flux(StepArgs<T> A) {
   face_dispatch<T, false>(A, g, d, c, A.G[g].fmask[d][t], fm, fp);
   ((T *)A.G[g].fh[d])[c] = fp;
   if (A.G[g].fhm[d]) ((T *)A.G[g].fhm[d])[c] = fm;
+}
+
+// Set-up: every CV of grid G a listed (G, Dd) face's stencil reads (t = -2 .. 1
+// along the face normal; w-grid wall levels excluded: their value is 0).
+template <int G, int Dd>
+__device__ inline void stage_marks_one(const Dims &D, const GridDev *GG, unsigned c, uint8_t *const marks[4]) {
+  int i, j, k;
+  split_index(D, c, i, j, k);
+  const int crd[3] = {i, j, k};
+  for (int t = -2; t <= 1; ++t) {
+    const int kk = k + (Dd == 2 ? t : 0);
+    if (kk < 0 || kk >= GG[G].nst || kk >= nzg_of(D, G)) continue;
+    if (G == 3 && (kk <= 0 || kk >= D.nz)) continue;
+    marks[G][c + step_off(D, Dd, crd[Dd], t)] = 1;
+  }
+}
+
+struct StageMarkArgs {
+  Dims D;
+  GridDev G[4];
+  uint8_t *marks[4];
+};
+
+__global__ void k_stage_marks(StageMarkArgs M) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int g = 0, d = 0;
+  for (g = 0; g < 4; ++g) {
+    for (d = 0; d < 3; ++d) {
+      if (t < M.G[g].nface[d]) break;
+      t -= M.G[g].nface[d];
+    }
+    if (d < 3) break;
+  }
+  if (g >= 4) return;
+  const unsigned c = M.G[g].flist[d][t];
+  switch (g * 3 + d) {
+    case 0: stage_marks_one<0, 0>(M.D, M.G, c, M.marks); break;
+    case 1: stage_marks_one<0, 1>(M.D, M.G, c, M.marks); break;
+    case 2: stage_marks_one<0, 2>(M.D, M.G, c, M.marks); break;
+    case 3: stage_marks_one<1, 0>(M.D, M.G, c, M.marks); break;
+    case 4: stage_marks_one<1, 1>(M.D, M.G, c, M.marks); break;
+    case 5: stage_marks_one<1, 2>(M.D, M.G, c, M.marks); break;
+    case 6: stage_marks_one<2, 0>(M.D, M.G, c, M.marks); break;
+    case 7: stage_marks_one<2, 1>(M.D, M.G, c, M.marks); break;
+    case 8: stage_marks_one<2, 2>(M.D, M.G, c, M.marks); break;
+    case 9: stage_marks_one<3, 0>(M.D, M.G, c, M.marks); break;
+    case 10: stage_marks_one<3, 1>(M.D, M.G, c, M.marks); break;
+    default: stage_marks_one<3, 2>(M.D, M.G, c, M.marks); break;
+  }
+}
+
+// Phase A0: the advected value of every staged CV, once per step.
+template <typename T>
+__global__ void k_stage(StepArgs<T> A) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int g = 0;
+  for (g = 0; g < 4; ++g) {
+    if (t < A.G[g].nstage) break;
+    t -= A.G[g].nstage;
+  }
+  if (g >= 4) return;
+  const unsigned c = A.G[g].stlist[t];
+  int i, j, k;
+  split_index(A.D, c, i, j, k);
+  T v;
+  switch (g) {
+    case 0: v = cv_advected<T, 0>(A, c, i, j, k); break;
+    case 1: v = cv_advected<T, 1>(A, c, i, j, k); break;
+    case 2: v = cv_advected<T, 2>(A, c, i, j, k); break;
+    default: v = cv_advected<T, 3>(A, c, i, j, k); break;
+  }
+  ((T *)A.G[g].pv)[c] = v;
 }
 
 // Phase B: the divergence of every listed CV with a geometry record, from
@@ -719,6 +830,9 @@ void launch_flux_band(const StepArgs<T> &A, cudaStream_t s) {
     nr += A.G[g].nband - A.G[g].nband_rec;
     for (int d = 0; d < 3; ++d) nf += A.G[g].nface[d];
   }
+  long long ns = 0;
+  for (int g = 0; g < 4; ++g) ns += A.G[g].nstage;
+  if (ns) k_stage<T><<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(A);
   if (nf) k_face_flux<T><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(A);
   if (nb + nr) k_band<T><<<(unsigned)((nb + nr + 255) / 256), 256, 0, s>>>(A);
 }
@@ -768,6 +882,18 @@ void launch_face_masks(const Dims &D, const GridDev G[4], cudaStream_t s) {
     for (int d = 0; d < 3; ++d) nf += G[q].nface[d];
   }
   if (nf) k_face_mask<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(A);
+}
+
+void launch_stage_marks(const Dims &D, const GridDev G[4], uint8_t *const marks[4], cudaStream_t s) {
+  StageMarkArgs M;
+  M.D = D;
+  long long nf = 0;
+  for (int q = 0; q < 4; ++q) {
+    M.G[q] = G[q];
+    M.marks[q] = marks[q];
+    for (int d = 0; d < 3; ++d) nf += G[q].nface[d];
+  }
+  if (nf) k_stage_marks<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(M);
 }
 
 void launch_rows_to_u32(const long long *src, long long n, unsigned *dst, cudaStream_t s) {
