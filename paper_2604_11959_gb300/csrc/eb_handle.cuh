@@ -60,6 +60,7 @@ struct ProjWork {
   int nb = 0;                  // blocks of every projection kernel (fixed: deterministic sums)
   long long nact = 0;          // cells in the solve (diagonal > 0)
   double *bx = nullptr, *by = nullptr, *bz = nullptr;   // low-face open fractions of the c-cells
+  double *ax = nullptr, *ay = nullptr, *az = nullptr;   // the same times 1 / delta^2 (the operator's coefficients)
   double *d = nullptr;         // diagonal of -L
   double *rhs = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x = nullptr;
   double *part = nullptr;      // partial sums, 8 slots of nb
