@@ -62,6 +62,7 @@ struct ProjWork {
   double *bx = nullptr, *by = nullptr, *bz = nullptr;   // low-face open fractions of the c-cells
   double *ax = nullptr, *ay = nullptr, *az = nullptr;   // the same times 1 / delta^2 (the operator's coefficients)
   double *d = nullptr;         // diagonal of -L
+  double *id = nullptr;        // its reciprocal (0 off the active cells): the Jacobi preconditioner
   double *rhs = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x = nullptr;
   double *part = nullptr;      // partial sums, 8 slots of nb
   int *conv = nullptr;         // iteration count at convergence (0 = not yet)

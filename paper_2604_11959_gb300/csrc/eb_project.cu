@@ -81,7 +81,7 @@ __device__ inline Nbr neighbours(const Dims &D, long long c) {
 
 struct Op {
   Dims D;
-  const double *bx, *by, *bz, *d;
+  const double *bx, *by, *bz, *d, *id;
   const double *ax, *ay, *az;   // open fractions times 1 / delta^2 (set-up)
   double ix2, iy2, iz2;   // 1 / delta^2
   // (-L p)_c for an active cell: one product and six fused multiply-adds
@@ -99,6 +99,11 @@ struct Op {
     return v;
   }
 };
+
+__global__ void k_recip(long long N, const double *d, double *id) {
+  for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB)
+    id[c] = d[c] > 0.0 ? 1.0 / d[c] : 0.0;
+}
 
 __global__ void k_scale(long long N, const double *b, double s, double *a) {
   for (long long c = blockIdx.x * (long long)PB + threadIdx.x; c < N; c += (long long)gridDim.x * PB) a[c] = b[c] * s;
@@ -171,7 +176,7 @@ __global__ void k_init(Op O, const double *x, const double *rhs, double *r, doub
     double rv = 0.0, zv = 0.0;
     if (O.d[c] > 0.0) {
       rv = -rhs[c] - O.apply(x, c, neighbours(D, c));
-      zv = rv / O.d[c];
+      zv = rv * O.id[c];
     }
     r[c] = rv;
     z[c] = zv;
@@ -215,7 +220,7 @@ __global__ void k_update(Op O, double *x, const double *p, const double *q, doub
       const double rv = r[c] - alpha * q[c];
       r[c] = rv;
       if (JAC) {
-        const double zv = rv / O.d[c];
+        const double zv = rv * O.id[c];
         z[c] = zv;
         rz += rv * zv;
       }
@@ -435,6 +440,7 @@ Op make_op(eb_geom g) {
   O.by = g->pw.by;
   O.bz = g->pw.bz;
   O.d = g->pw.d;
+  O.id = g->pw.id;
   O.ax = g->pw.ax;
   O.ay = g->pw.ay;
   O.az = g->pw.az;
@@ -454,7 +460,7 @@ eb_status setup(eb_geom g, cudaStream_t s) {
   CUDA_TRY(cudaGetDevice(&dev), "device");
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device");
   w.nb = (int)std::max(1LL, std::min<long long>(4LL * std::max(sms, 1), (N + PB - 1) / PB));
-  for (double **a : {&w.bx, &w.by, &w.bz, &w.ax, &w.ay, &w.az, &w.d, &w.rhs, &w.r, &w.z, &w.p, &w.q, &w.x})
+  for (double **a : {&w.bx, &w.by, &w.bz, &w.ax, &w.ay, &w.az, &w.d, &w.id, &w.rhs, &w.r, &w.z, &w.p, &w.q, &w.x})
     CUDA_TRY(g->alloc(a, N), "alloc projection work space");
   CUDA_TRY(g->alloc(&w.part, 8LL * w.nb), "alloc projection work space");
   CUDA_TRY(g->alloc(&w.conv, 1), "alloc projection work space");
@@ -467,6 +473,7 @@ eb_status setup(eb_geom g, cudaStream_t s) {
   k_scale<<<w.nb, PB, 0, s>>>(N, w.by, D.idy * D.idy, w.ay);
   k_scale<<<w.nb, PB, 0, s>>>(N, w.bz, D.idz * D.idz, w.az);
   k_diag<<<w.nb, PB, 0, s>>>(make_op(g), w.d, w.part + S_CNT * w.nb);
+  k_recip<<<w.nb, PB, 0, s>>>(N, w.d, w.id);
   CUDA_TRY(cudaMemcpyAsync(w.host, w.part + S_CNT * w.nb, sizeof(double) * w.nb, cudaMemcpyDeviceToHost, s),
            "count active cells");
   CUDA_TRY(cudaStreamSynchronize(s), "count active cells");
