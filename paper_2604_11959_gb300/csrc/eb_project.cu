@@ -408,6 +408,45 @@ __global__ void k_mg_coarsest(Op32 L, const float *b, float *x, float *t, const 
   }
 }
 
+// the same on a coarsest grid of at most MG_SMEM_CELLS cells, held in shared
+// memory for the sweeps (same arithmetic, same order)
+constexpr int MG_SMEM_CELLS = 1024;
+__global__ void k_mg_coarsest_smem(Op32 L, const float *b, float *x, const int *conv) {
+  if (*conv) return;
+  __shared__ float sbx[MG_SMEM_CELLS], sby[MG_SMEM_CELLS], sbz[MG_SMEM_CELLS], sb[MG_SMEM_CELLS];
+  __shared__ float sx[MG_SMEM_CELLS], st[MG_SMEM_CELLS];
+  const int N = (int)(L.D.nxy * L.D.nz);
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    sbx[c] = L.bx[c];
+    sby[c] = L.by[c];
+    sbz[c] = L.bz[c];
+    sb[c] = b[c];
+  }
+  __syncthreads();
+  Op32 S = L;
+  S.bx = sbx;
+  S.by = sby;
+  S.bz = sbz;
+  for (int sw = 0; sw < MG_COARSE_SWEEPS; ++sw) {
+    const float *in = (sw & 1) ? st : sx;
+    float *out = (sw & 1) ? sx : st;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+      float v = 0.f;
+      if (sw == 0) {
+        const float d = S.diag(c);
+        if (d > 0.f) v = MG_OMEGA * sb[c] / d;
+      } else {
+        float Sv, d;
+        S.parts(in, c, Sv, d);
+        if (d > 0.f) v = (1.f - MG_OMEGA) * in[c] + MG_OMEGA * (sb[c] + Sv) / d;
+      }
+      out[c] = v;
+    }
+    __syncthreads();
+  }
+  for (int c = threadIdx.x; c < N; c += blockDim.x) x[c] = sx[c];
+}
+
 Op32 level_op(const MgLevel &L) {
   Op32 O;
   O.D = L.D;
@@ -539,7 +578,10 @@ void vcycle(eb_geom g, const double *r, double *z, double *prz, cudaStream_t s) 
     k_mg_sweep<float, false><<<L[l].nb, PB, 0, s>>>(O, L[l].t, L[l].x, nullptr, L[l].b, 0, nullptr, w.conv);
     k_mg_restrict<float><<<L[l + 1].nb, PB, 0, s>>>(O, L[l].x, L[l].b, L[l + 1].D, L[l + 1].b, w.conv);
   }
-  k_mg_coarsest<<<1, 1024, 0, s>>>(level_op(L[top]), L[top].b, L[top].x, L[top].t, w.conv);
+  if (L[top].D.nxy * L[top].D.nz <= MG_SMEM_CELLS)
+    k_mg_coarsest_smem<<<1, 1024, 0, s>>>(level_op(L[top]), L[top].b, L[top].x, w.conv);
+  else
+    k_mg_coarsest<<<1, 1024, 0, s>>>(level_op(L[top]), L[top].b, L[top].x, L[top].t, w.conv);
   for (int l = top - 1; l >= 1; --l) {
     const Op32 O = level_op(L[l]);
     k_mg_prolong<<<L[l].nb, PB, 0, s>>>(O, L[l + 1].D, L[l + 1].x, L[l].x, w.conv);
