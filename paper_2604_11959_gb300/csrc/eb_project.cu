@@ -447,6 +447,77 @@ __global__ void k_mg_coarsest_smem(Op32 L, const float *b, float *x, const int *
   for (int c = threadIdx.x; c < N; c += blockDim.x) x[c] = sx[c];
 }
 
+// The lower part of the V-cycle (every level from lt down, each at most
+// MG_LOWER_CELLS cells) in one block: the same sweeps, restrictions, coarsest
+// sweeps and prolongations as the multi-block kernels, separated by block
+// barriers instead of launches (these levels are launch-bound otherwise).
+constexpr long long MG_LOWER_CELLS = 8192;
+struct MgLower {
+  Op32 L[kMgMaxLevels];
+  float *x[kMgMaxLevels], *t[kMgMaxLevels], *b[kMgMaxLevels];
+  int lt, top;
+};
+
+__device__ inline void lower_sweep(const Op32 &L, const float *xin, float *xout, const float *b, bool first) {
+  const long long N = L.D.nxy * L.D.nz;
+  for (long long c = threadIdx.x; c < N; c += blockDim.x) {
+    float v = 0.f;
+    if (first) {
+      const float d = L.diag(c);
+      if (d > 0.f) v = MG_OMEGA * b[c] / d;
+    } else {
+      float S, d;
+      L.parts(xin, c, S, d);
+      if (d > 0.f) v = (1.f - MG_OMEGA) * xin[c] + MG_OMEGA * (b[c] + S) / d;
+    }
+    xout[c] = v;
+  }
+  __syncthreads();
+}
+
+__global__ void k_mg_lower(const __grid_constant__ MgLower M, const int *conv) {
+  if (*conv) return;
+  for (int l = M.lt; l < M.top; ++l) {
+    const Op32 &F = M.L[l];
+    lower_sweep(F, nullptr, M.t[l], M.b[l], true);
+    lower_sweep(F, M.t[l], M.x[l], M.b[l], false);
+    const Dims &C = M.L[l + 1].D;
+    const long long N = C.nxy * C.nz, sy = F.D.nx, sz = F.D.nxy;
+    for (long long c = threadIdx.x; c < N; c += blockDim.x) {   // as k_mg_restrict
+      int I, J, K;
+      split_index(C, (unsigned)c, I, J, K);
+      const long long f0 = 2LL * I + sy * 2LL * J + sz * 2LL * K;
+      float sum = 0.f;
+      for (int q = 0; q < 8; ++q) {
+        const long long f = f0 + (q & 1) + ((q >> 1) & 1) * sy + (q >> 2) * sz;
+        float S, d;
+        F.parts(M.x[l], f, S, d);
+        if (d > 0.f) sum += M.b[l][f] - d * M.x[l][f] + S;
+      }
+      M.b[l + 1][c] = 0.125f * sum;
+    }
+    __syncthreads();
+  }
+  const int top = M.top;
+  for (int sw = 0; sw < MG_COARSE_SWEEPS; ++sw)   // as k_mg_coarsest: the result ends in x
+    lower_sweep(M.L[top], (sw & 1) ? M.t[top] : M.x[top], (sw & 1) ? M.x[top] : M.t[top], M.b[top], sw == 0);
+  for (int l = top - 1; l >= M.lt; --l) {
+    const Op32 &F = M.L[l];
+    const Dims &C = M.L[l + 1].D;
+    const long long N = F.D.nxy * F.D.nz;
+    for (long long c = threadIdx.x; c < N; c += blockDim.x) {   // as k_mg_prolong
+      if (F.diag(c) > 0.f) {
+        int i, j, k;
+        split_index(F.D, (unsigned)c, i, j, k);
+        M.x[l][c] += M.x[l + 1][(i >> 1) + (long long)C.nx * ((j >> 1) + (long long)C.ny * (k >> 1))];
+      }
+    }
+    __syncthreads();
+    lower_sweep(F, M.x[l], M.t[l], M.b[l], false);
+    lower_sweep(F, M.t[l], M.x[l], M.b[l], false);
+  }
+}
+
 Op32 level_op(const MgLevel &L) {
   Op32 O;
   O.D = L.D;
@@ -565,6 +636,9 @@ void vcycle(eb_geom g, const double *r, double *z, double *prz, cudaStream_t s) 
   ProjWork &w = g->pw;
   const MgLevel *L = w.lev;
   const int top = w.nlev - 1;
+  // levels lt .. top (at most MG_LOWER_CELLS cells each) run in one block; level 0 never does
+  int lt = top;
+  while (lt > 1 && L[lt - 1].D.nxy * L[lt - 1].D.nz <= MG_LOWER_CELLS) --lt;
   // level 0: right-hand side r (FP64)
   {
     const Op32 O = level_op(L[0]);
@@ -572,17 +646,27 @@ void vcycle(eb_geom g, const double *r, double *z, double *prz, cudaStream_t s) 
     k_mg_sweep<double, false><<<L[0].nb, PB, 0, s>>>(O, L[0].t, L[0].x, nullptr, r, 0, nullptr, w.conv);
     k_mg_restrict<double><<<L[1].nb, PB, 0, s>>>(O, L[0].x, r, L[1].D, L[1].b, w.conv);
   }
-  for (int l = 1; l < top; ++l) {
+  for (int l = 1; l < lt; ++l) {
     const Op32 O = level_op(L[l]);
     k_mg_sweep<float, false><<<L[l].nb, PB, 0, s>>>(O, nullptr, L[l].t, nullptr, L[l].b, 1, nullptr, w.conv);
     k_mg_sweep<float, false><<<L[l].nb, PB, 0, s>>>(O, L[l].t, L[l].x, nullptr, L[l].b, 0, nullptr, w.conv);
     k_mg_restrict<float><<<L[l + 1].nb, PB, 0, s>>>(O, L[l].x, L[l].b, L[l + 1].D, L[l + 1].b, w.conv);
   }
-  if (L[top].D.nxy * L[top].D.nz <= MG_SMEM_CELLS)
+  if (lt == top && L[top].D.nxy * L[top].D.nz <= MG_SMEM_CELLS) {
     k_mg_coarsest_smem<<<1, 1024, 0, s>>>(level_op(L[top]), L[top].b, L[top].x, w.conv);
-  else
-    k_mg_coarsest<<<1, 1024, 0, s>>>(level_op(L[top]), L[top].b, L[top].x, L[top].t, w.conv);
-  for (int l = top - 1; l >= 1; --l) {
+  } else {
+    MgLower M;
+    for (int l = lt; l <= top; ++l) {
+      M.L[l] = level_op(L[l]);
+      M.x[l] = L[l].x;
+      M.t[l] = L[l].t;
+      M.b[l] = L[l].b;
+    }
+    M.lt = lt;
+    M.top = top;
+    k_mg_lower<<<1, 1024, 0, s>>>(M, w.conv);
+  }
+  for (int l = lt - 1; l >= 1; --l) {
     const Op32 O = level_op(L[l]);
     k_mg_prolong<<<L[l].nb, PB, 0, s>>>(O, L[l + 1].D, L[l + 1].x, L[l].x, w.conv);
     k_mg_sweep<float, false><<<L[l].nb, PB, 0, s>>>(O, L[l].x, L[l].t, nullptr, L[l].b, 0, nullptr, w.conv);
