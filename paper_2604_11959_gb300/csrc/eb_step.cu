@@ -3,6 +3,8 @@
 //   flux + update (Eqs. update-cc / update-fc, Sec. 4.1):
 //     (the geometry-free bulk above each column's kfast level is in
 //     eb_fast.cu)
+//     k_stage        : (FP64 path) the advected value of every CV the face
+//                      stencils read, once;
 //     k_face_flux    : the provisional flux of every face the near-EB CVs
 //                      read, once, with covered-neighbour fallbacks;
 //     k_band         : the CVs below kfast with a geometry record (open-face
