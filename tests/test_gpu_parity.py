@@ -38,6 +38,9 @@ CASES = {
     # odd nx and ny: rows not 16-byte aligned (element-wise copies in the bulk
     # kernel) and ragged tiles in both directions
     "odd": (inputs.Workload("grf-45x38x20", 45, 38, 20, 5, terrain="grf", seed=9, hmax=0.2, tiny=2), None),
+    # the smallest grids: stencils wrap around the periodic boundaries several
+    # times, one ragged tile holds the whole domain
+    "tiny": (inputs.Workload("grf-6x5x4", 6, 5, 4, 3, terrain="grf", seed=11, hmax=0.2), None),
 }
 
 
