@@ -13,6 +13,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -208,6 +209,23 @@ class Geometry:
 
     def empty_state(self) -> dict:
         return {f: torch.empty(self.shape(f), dtype=self.dtype, device="cuda") for f in FIELDS}
+
+    def packed_state(self, device: str = "cuda", pin: bool = False):
+        """One allocation holding all five fields (each starting on a 256-byte
+        boundary), returned as (flat tensor, dict of per-field views): a whole
+        state moves between host and device with one copy of the flat tensor."""
+        es = torch.empty((), dtype=self.dtype).element_size()
+        align = 256 // es
+        offs, n = {}, 0
+        for f in FIELDS:
+            offs[f] = n
+            cnt = int(np.prod(self.shape(f)))
+            n += (cnt + align - 1) // align * align
+        flat = torch.empty(n, dtype=self.dtype, device=device)
+        if pin:
+            flat = flat.pin_memory()
+        views = {f: flat[offs[f]:offs[f] + int(np.prod(self.shape(f)))].view(self.shape(f)) for f in FIELDS}
+        return flat, views
 
     def _cstate(self, U: dict) -> _State:
         for f in FIELDS:

@@ -291,3 +291,22 @@ def test_tuning_changes_no_result(eb, precision):
         assert torch.equal(before[f], after[f]), (precision, f)
     eb.sync_status(geom)
     geom.close()
+
+
+def test_packed_state_gives_the_same_step(eb):
+    """A state held in one allocation (Geometry.packed_state: per-field views,
+    each on a 256-byte boundary) steps exactly like separate tensors."""
+    w = rough_workload()
+    refs = refs_for(w.nz, w.Lz)
+    geom = make_geometry(eb, w, w.heights(), "mixed", refs)
+    A = to_device(w.state("uniform", pert=1e-2, seed=8), "mixed", refs)
+    flat, views = geom.packed_state()
+    for f in FIELDS:
+        views[f].copy_(A[f])
+        assert views[f].data_ptr() % 256 == 0
+    oflat, oviews = geom.packed_state()
+    want = eb.step(geom, A, w.dt(), 2)
+    eb.step(geom, views, w.dt(), 2, out=oviews)
+    for f in FIELDS:
+        assert torch.equal(want[f], oviews[f]), f
+    geom.close()
