@@ -8,13 +8,14 @@
 // Parameters are one flat vector: per layer, weights [cout][cin][k^3] then
 // biases [cout].  Activations are [channels][nz][ny][nx].
 //
-// Convolution forward: a CTA computes 8 output channels on a 16 x 8 x 2 tile
-// of voxels; input channels stream through shared memory 8 at a time (tile
-// plus a one-voxel halo), with the matching weights, and every thread
-// accumulates its voxel's 8 outputs.  The input gradient is the same kernel
-// on the output gradient with the weights transposed and flipped.  The
-// weight gradient reduces dOut x input over tiles of voxels in shared memory
-// and adds each tile's sums atomically.
+// Convolutions run on the tensor cores (mma.sync, BF16 operands, FP32
+// accumulation) as implicit GEMMs, with the FP32 activations split into BF16
+// hi + lo so that the products keep FP32-level accuracy: the forward pass
+// (rows = voxels, columns = output channels, K = input channels x taps), the
+// input gradient (the same kernel on the output gradient with the weights
+// transposed and flipped) and the weight gradient (rows = output channels,
+// columns = input channels, K = voxels, per tap; tiles add their sums
+// atomically).
 #include "eb_handle.cuh"
 
 #include <cuda_bf16.h>
@@ -44,63 +45,119 @@ struct Vol {
   __host__ __device__ long long n() const { return (long long)nx * ny * nz; }
 };
 
-constexpr int TX = 16, TY = 8, TZ = 2, COB = 8, CIC = 8;
+constexpr int TX = 16, TY = 8, TZ = 2;   // voxel tile of the weight gradient
 constexpr int HXn = TX + 2, HYn = TY + 2, HZn = TZ + 2, HN = HXn * HYn * HZn;
 
-// out[co][v] = b[co] + sum_ci sum_a W[co][ci][a] in[ci][v + a - 1]
-// (zero outside), optionally ReLU; 8 output channels per CTA (blockIdx.y).
-__global__ void __launch_bounds__(TX *TY *TZ) k_conv3(const float *in, int cin, const __nv_bfloat16 *W,
-                                                       const float *bias, float *out, int cout, Vol V, int relu) {
-  __shared__ float s_in[CIC * HN];
-  __shared__ float s_w[COB * CIC * 27];
-  const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
-  const int ntx = (V.nx + TX - 1) / TX, nty = (V.ny + TY - 1) / TY;
+// ---- tensor-core convolution (forward and input gradient) ------------------
+// The same convolution as an implicit GEMM on the tensor cores (mma.sync,
+// BF16 operands, FP32 accumulation): rows = 16 voxels along x (one warp per
+// row; a CTA covers 16 x 8 x 1 voxels), columns = 32 output channels (four
+// 8-wide tiles), K = 16 input channels per tap, 27 taps.  The FP32 inputs
+// are split into BF16 hi + lo (v = hi + lo to about 2^-17 relative) and both
+// parts are multiplied by the BF16 weights, so the products keep FP32-level
+// accuracy.  Shared memory holds the 16-channel halo (channels fastest, a
+// pitch of 24 halfwords: conflict-free 32-bit fragment loads) and the chunk's
+// weights [tap][output channel][input channel].
+constexpr int TC_CH = 16, TC_P = 24, TC_RZ = 2;   // channels per K chunk, channel pitch, z rows per warp
+constexpr int TC_HX = 18, TC_HY = 10, TC_HZ = TC_RZ + 2, TC_HN = TC_HX * TC_HY * TC_HZ;
+template <int NT>
+constexpr size_t tc_smem() {
+  return (size_t)(2 * TC_HN * TC_P + 27 * NT * 8 * TC_P) * sizeof(__nv_bfloat16);
+}
+
+__device__ inline void mma_bf16(float c[4], const unsigned a[4], const unsigned b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// NT 8-wide tiles of output channels per CTA (8 NT channels); a CTA covers
+// 16 x 8 x TC_RZ voxels, warp w the rows y0 + w, z0 .. z0 + TC_RZ - 1
+template <int NT>
+__global__ void __launch_bounds__(256) k_conv3_tc(const float *in, int cin, const __nv_bfloat16 *W, const float *bias,
+                                                  float *out, int cout, Vol V, int relu) {
+  constexpr int NCO = NT * 8;
+  extern __shared__ __align__(16) unsigned char tc_smem[];
+  __nv_bfloat16 *s_hi = reinterpret_cast<__nv_bfloat16 *>(tc_smem);
+  __nv_bfloat16 *s_lo = s_hi + TC_HN * TC_P;
+  __nv_bfloat16 *s_w = s_lo + TC_HN * TC_P;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int ntx = (V.nx + 15) / 16, nty = (V.ny + 7) / 8;
   const int tile = blockIdx.x;
-  const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY, z0 = (tile / (ntx * nty)) * TZ;
-  const int co0 = blockIdx.y * COB;
+  const int x0 = (tile % ntx) * 16, y0 = ((tile / ntx) % nty) * 8, z0 = (tile / (ntx * nty)) * TC_RZ;
+  const int co0 = blockIdx.y * NCO;
   const long long N = V.n();
-  float acc[COB];
+  float acc[TC_RZ][NT][4];
 #pragma unroll
-  for (int c = 0; c < COB; ++c) acc[c] = 0.f;
-  for (int ci0 = 0; ci0 < cin; ci0 += CIC) {
+  for (int rz = 0; rz < TC_RZ; ++rz)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[rz][nt][e] = 0.f;
+  for (int c0 = 0; c0 < cin; c0 += TC_CH) {
     __syncthreads();
-    for (int q = threadIdx.x; q < CIC * HN; q += blockDim.x) {
-      const int c = q / HN, r = q % HN;
-      const int hx = r % HXn, hy = (r / HXn) % HYn, hz = r / (HXn * HYn);
+    for (int q = threadIdx.x; q < TC_CH * TC_HN; q += blockDim.x) {
+      const int c = q / TC_HN, h = q % TC_HN;
+      const int hx = h % TC_HX, hy = (h / TC_HX) % TC_HY, hz = h / (TC_HX * TC_HY);
       const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
       float v = 0.f;
-      if (ci0 + c < cin && x >= 0 && x < V.nx && y >= 0 && y < V.ny && z >= 0 && z < V.nz)
-        v = in[(long long)(ci0 + c) * N + ((long long)z * V.ny + y) * V.nx + x];
-      s_in[q] = v;
+      if (c0 + c < cin && x >= 0 && x < V.nx && y >= 0 && y < V.ny && z >= 0 && z < V.nz)
+        v = in[(long long)(c0 + c) * N + ((long long)z * V.ny + y) * V.nx + x];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      s_hi[h * TC_P + c] = hi;
+      s_lo[h * TC_P + c] = __float2bfloat16_rn(v - __bfloat162float(hi));
     }
-    for (int q = threadIdx.x; q < COB * CIC * 27; q += blockDim.x) {
-      const int co = q / (CIC * 27), r = q % (CIC * 27), c = r / 27, a = r % 27;
-      float w = 0.f;
-      if (co0 + co < cout && ci0 + c < cin) w = __bfloat162float(W[((long long)(co0 + co) * cin + ci0 + c) * 27 + a]);
-      s_w[q] = w;
+    for (int q = threadIdx.x; q < 27 * NCO * TC_CH; q += blockDim.x) {
+      const int a = q % 27, r = q / 27, c = r % TC_CH, co = r / TC_CH;   // consecutive threads: consecutive taps
+      __nv_bfloat16 w = __float2bfloat16_rn(0.f);
+      if (co0 + co < cout && c0 + c < cin) w = W[((long long)(co0 + co) * cin + c0 + c) * 27 + a];
+      s_w[(a * NCO + co) * TC_P + c] = w;
     }
     __syncthreads();
-    const int nc = min(CIC, cin - ci0);
-    for (int c = 0; c < nc; ++c) {
-      const float *src = s_in + c * HN;
+    for (int a = 0; a < 27; ++a) {
+      const int dz = a / 9, dy = (a / 3) % 3, dx = a % 3;
+      unsigned b[NT][2];
 #pragma unroll
-      for (int a = 0; a < 27; ++a) {
-        const int dz = a / 9, dy = (a / 3) % 3, dx = a % 3;
-        const float v = src[((tz + dz) * HYn + (ty + dy)) * HXn + (tx + dx)];
+      for (int nt = 0; nt < NT; ++nt) {
+        const unsigned *pb = reinterpret_cast<const unsigned *>(s_w + (a * NCO + nt * 8 + g) * TC_P + 2 * t);
+        b[nt][0] = pb[0];
+        b[nt][1] = pb[4];
+      }
 #pragma unroll
-        for (int co = 0; co < COB; ++co) acc[co] = fmaf(v, s_w[(co * CIC + c) * 27 + a], acc[co]);
+      for (int rz = 0; rz < TC_RZ; ++rz) {
+        const int h0 = ((rz + dz) * TC_HY + (warp + dy)) * TC_HX + dx;   // halo voxel of row 0
+        const unsigned *ph = reinterpret_cast<const unsigned *>(s_hi + (h0 + g) * TC_P + 2 * t);
+        const unsigned *ph8 = reinterpret_cast<const unsigned *>(s_hi + (h0 + g + 8) * TC_P + 2 * t);
+        const unsigned *pl = reinterpret_cast<const unsigned *>(s_lo + (h0 + g) * TC_P + 2 * t);
+        const unsigned *pl8 = reinterpret_cast<const unsigned *>(s_lo + (h0 + g + 8) * TC_P + 2 * t);
+        const unsigned ahi[4] = {ph[0], ph8[0], ph[4], ph8[4]};
+        const unsigned alo[4] = {pl[0], pl8[0], pl[4], pl8[4]};
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          mma_bf16(acc[rz][nt], ahi, b[nt]);
+          mma_bf16(acc[rz][nt], alo, b[nt]);
+        }
       }
     }
   }
-  const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
-  if (x >= V.nx || y >= V.ny || z >= V.nz) return;
-  const long long v = ((long long)z * V.ny + y) * V.nx + x;
+  const int y = y0 + warp;
+  if (y >= V.ny) return;
 #pragma unroll
-  for (int co = 0; co < COB; ++co) {
-    if (co0 + co >= cout) break;
-    float r = acc[co] + (bias ? bias[co0 + co] : 0.f);
-    if (relu) r = fmaxf(r, 0.f);
-    out[(long long)(co0 + co) * N + v] = r;
+  for (int rz = 0; rz < TC_RZ; ++rz) {
+    const int z = z0 + rz;
+    if (z >= V.nz) break;
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int x = x0 + g + (e >= 2 ? 8 : 0), co = co0 + nt * 8 + 2 * t + (e & 1);
+        if (x >= V.nx || co >= cout) continue;
+        float r = acc[rz][nt][e] + (bias ? bias[co] : 0.f);
+        if (relu) r = fmaxf(r, 0.f);
+        out[(long long)co * N + ((long long)z * V.ny + y) * V.nx + x] = r;
+      }
   }
 }
 
@@ -146,48 +203,107 @@ __global__ void k_flip(const __nv_bfloat16 *W, int cout, int cin, __nv_bfloat16 
   Wt[((long long)ci * cout + co) * 27 + (26 - a)] = W[q];
 }
 
-// dW[co][ci][a] += sum_v dOut[co][v] in[ci][v + a - 1], 8 x 8 channel block
-// per CTA over one tile of voxels
-__global__ void __launch_bounds__(TX *TY *TZ) k_conv3_wgrad(const float *in, int cin, const float *dout, int cout,
-                                                            Vol V, float *dW) {
-  __shared__ float s_in[CIC * HN];
-  __shared__ float s_d[COB * TX * TY * TZ];
+// Weight gradient on the tensor cores: per tap a, dW[co][ci][a] += sum over
+// the tile's voxels of dOut[co][v] in[ci][v + a] -- a GEMM with rows = 16
+// output channels, columns = 16 input channels (two 8-wide tiles), K = the
+// 16 x 8 x 2 voxels of a tile (16 per step, one x-row).  Both operands are
+// split into BF16 hi + lo and multiplied as hi.hi + hi.lo + lo.hi (relative
+// error about 2^-16).  Warp w takes taps w, w + 8, w + 16, w + 24.  The input
+// halo is held twice, the second copy shifted by one voxel along x, so that
+// the voxel pairs of the x-shift dx = 1 start on a 32-bit boundary.  Row
+// pitches (264 and 728 halfwords) keep the fragment loads conflict-free.
+// Each tile adds its sums atomically.
+constexpr int WG_DP = 264, WG_IP = 728, WG_C = 16;
+constexpr size_t WG_SMEM = (size_t)(2 * WG_C * WG_DP + 4 * WG_C * WG_IP) * sizeof(__nv_bfloat16);
+
+__global__ void __launch_bounds__(256) k_conv3_wgrad_tc(const float *in, int cin, const float *dout, int cout,
+                                                        Vol V, float *dW) {
+  extern __shared__ __align__(16) unsigned char wg_smem[];
+  __nv_bfloat16 *d_hi = reinterpret_cast<__nv_bfloat16 *>(wg_smem);
+  __nv_bfloat16 *d_lo = d_hi + WG_C * WG_DP;
+  __nv_bfloat16 *i0h = d_lo + WG_C * WG_DP, *i0l = i0h + WG_C * WG_IP;
+  __nv_bfloat16 *i1h = i0l + WG_C * WG_IP, *i1l = i1h + WG_C * WG_IP;
   const int ntx = (V.nx + TX - 1) / TX, nty = (V.ny + TY - 1) / TY;
   const int tile = blockIdx.x;
   const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY, z0 = (tile / (ntx * nty)) * TZ;
-  const int co0 = blockIdx.y * COB, ci0 = blockIdx.z * CIC;
+  const int co0 = blockIdx.y * WG_C, ci0 = blockIdx.z * WG_C;
   const long long N = V.n();
-  for (int q = threadIdx.x; q < CIC * HN; q += blockDim.x) {
-    const int c = q / HN, r = q % HN;
-    const int hx = r % HXn, hy = (r / HXn) % HYn, hz = r / (HXn * HYn);
+  constexpr int NV = TX * TY * TZ;   // 256 voxels
+  for (int q = threadIdx.x; q < WG_C * HN; q += blockDim.x) {
+    const int c = q / HN, h = q % HN;
+    const int hx = h % HXn, hy = (h / HXn) % HYn, hz = h / (HXn * HYn);
     const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
     float v = 0.f;
     if (ci0 + c < cin && x >= 0 && x < V.nx && y >= 0 && y < V.ny && z >= 0 && z < V.nz)
       v = in[(long long)(ci0 + c) * N + ((long long)z * V.ny + y) * V.nx + x];
-    s_in[q] = v;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v), lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    i0h[c * WG_IP + h] = hi;
+    i0l[c * WG_IP + h] = lo;
+    if (h >= 1) {   // shifted copy: i1[h - 1] = i0[h]
+      i1h[c * WG_IP + h - 1] = hi;
+      i1l[c * WG_IP + h - 1] = lo;
+    }
+    if (h == HN - 1) {
+      i1h[c * WG_IP + h] = __float2bfloat16_rn(0.f);
+      i1l[c * WG_IP + h] = __float2bfloat16_rn(0.f);
+    }
   }
-  constexpr int NT = TX * TY * TZ;
-  for (int q = threadIdx.x; q < COB * NT; q += blockDim.x) {
-    const int co = q / NT, r = q % NT;
+  for (int q = threadIdx.x; q < WG_C * NV; q += blockDim.x) {
+    const int co = q / NV, r = q % NV;
     const int x = x0 + r % TX, y = y0 + (r / TX) % TY, z = z0 + r / (TX * TY);
     float v = 0.f;
-    if (co0 + co < cout && x < V.nx && y < V.ny && z < V.nz) v = dout[(long long)(co0 + co) * N + ((long long)z * V.ny + y) * V.nx + x];
-    s_d[q] = v;
+    if (co0 + co < cout && x < V.nx && y < V.ny && z < V.nz)
+      v = dout[(long long)(co0 + co) * N + ((long long)z * V.ny + y) * V.nx + x];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    d_hi[co * WG_DP + r] = hi;
+    d_lo[co * WG_DP + r] = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
   __syncthreads();
-  // (co, ci, a) outputs of this CTA: 8 * 8 * 27 = 1728, strided over threads
-  for (int o = threadIdx.x; o < COB * CIC * 27; o += blockDim.x) {
-    const int co = o / (CIC * 27), c = (o / 27) % CIC, a = o % 27;
-    if (co0 + co >= cout || ci0 + c >= cin) continue;
-    const int dz = a / 9, dy = (a / 3) % 3, dx = a % 3;
-    const float *d = s_d + co * NT;
-    const float *src = s_in + c * HN;
-    float s = 0.f;
-    for (int r = 0; r < NT; ++r) {
-      const int tx = r % TX, ty = (r / TX) % TY, tz = r / (TX * TY);
-      s = fmaf(d[r], src[((tz + dz) * HYn + (ty + dy)) * HXn + (tx + dx)], s);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float acc[4][2][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[j][nt][e] = 0.f;
+  auto u32 = [](const __nv_bfloat16 *p) { return *reinterpret_cast<const unsigned *>(p); };
+  for (int row = 0; row < TY * TZ; ++row) {   // K steps: one x-row of 16 voxels each
+    const int ty = row % TY, tz = row / TY, kb = row * TX;
+    const unsigned ahi[4] = {u32(d_hi + g * WG_DP + kb + 2 * t), u32(d_hi + (g + 8) * WG_DP + kb + 2 * t),
+                             u32(d_hi + g * WG_DP + kb + 2 * t + 8), u32(d_hi + (g + 8) * WG_DP + kb + 2 * t + 8)};
+    const unsigned alo[4] = {u32(d_lo + g * WG_DP + kb + 2 * t), u32(d_lo + (g + 8) * WG_DP + kb + 2 * t),
+                             u32(d_lo + g * WG_DP + kb + 2 * t + 8), u32(d_lo + (g + 8) * WG_DP + kb + 2 * t + 8)};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int a = warp + 8 * j;
+      if (a >= 27) break;
+      const int dz = a / 9, dy = (a / 3) % 3, dx = a % 3;
+      const int base = ((tz + dz) * HYn + (ty + dy)) * HXn;
+      const __nv_bfloat16 *bh = dx == 1 ? i1h : i0h, *bl = dx == 1 ? i1l : i0l;
+      const int off = base + 2 * t + (dx == 2 ? 2 : 0);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int ci = nt * 8 + g;
+        const unsigned bhi[2] = {u32(bh + ci * WG_IP + off), u32(bh + ci * WG_IP + off + 8)};
+        const unsigned blo[2] = {u32(bl + ci * WG_IP + off), u32(bl + ci * WG_IP + off + 8)};
+        mma_bf16(acc[j][nt], ahi, bhi);
+        mma_bf16(acc[j][nt], ahi, blo);
+        mma_bf16(acc[j][nt], alo, bhi);
+      }
     }
-    atomicAdd(dW + ((long long)(co0 + co) * cin + ci0 + c) * 27 + a, s);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int a = warp + 8 * j;
+    if (a >= 27) break;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int co = co0 + g + (e >= 2 ? 8 : 0), ci = ci0 + nt * 8 + 2 * t + (e & 1);
+        if (co < cout && ci < cin) atomicAdd(dW + ((long long)co * cin + ci) * 27 + a, acc[j][nt][e]);
+      }
   }
 }
 
@@ -314,26 +430,49 @@ struct eb_unet_s {
 
 namespace {
 
+// the tensor-core convolution on a volume: 16 x 8 x 4 voxel tiles, 8 NT output
+// channels per CTA with NT = 1, 2 or 4 from the number of output channels
+template <int NT>
+void conv3_tc_nt(const float *in, int cin, const __nv_bfloat16 *W, const float *bias, float *out, int cout,
+                 const Vol &V, bool relu, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv3_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<NT>());
+    attr = true;
+  }
+  const unsigned tiles = (unsigned)(((V.nx + 15) / 16) * ((V.ny + 7) / 8) * ((V.nz + TC_RZ - 1) / TC_RZ));
+  k_conv3_tc<NT><<<dim3(tiles, (cout + NT * 8 - 1) / (NT * 8)), 256, tc_smem<NT>(), s>>>(in, cin, W, bias, out,
+                                                                                        cout, V, relu ? 1 : 0);
+}
+
+void conv3_tc(const float *in, int cin, const __nv_bfloat16 *W, const float *bias, float *out, int cout,
+              const Vol &V, bool relu, cudaStream_t s) {
+  if (cout <= 8) conv3_tc_nt<1>(in, cin, W, bias, out, cout, V, relu, s);
+  else if (cout <= 16) conv3_tc_nt<2>(in, cin, W, bias, out, cout, V, relu, s);
+  else conv3_tc_nt<4>(in, cin, W, bias, out, cout, V, relu, s);
+}
+
 void conv3(eb_unet u, int l, const float *in, float *out, const Vol &V, bool relu, cudaStream_t s) {
   const LayerSpec &L = kLayers[l];
-  const unsigned tiles = (unsigned)(((V.nx + TX - 1) / TX) * ((V.ny + TY - 1) / TY) * ((V.nz + TZ - 1) / TZ));
-  k_conv3<<<dim3(tiles, (L.cout + COB - 1) / COB), TX * TY * TZ, 0, s>>>(in, L.cin, u->pb + u->off_w[l],
-                                                                         u->p + u->off_b[l], out, L.cout, V, relu);
+  conv3_tc(in, L.cin, u->pb + u->off_w[l], u->p + u->off_b[l], out, L.cout, V, relu, s);
 }
 
 // input gradient of layer l: din = conv of dout with flipped, transposed W
 void conv3_dgrad(eb_unet u, int l, const float *dout, float *din, const Vol &V, cudaStream_t s) {
   const LayerSpec &L = kLayers[l];
   k_flip<<<nblk(layer_w(l)), 256, 0, s>>>(u->pb + u->off_w[l], L.cout, L.cin, u->wt);
-  const unsigned tiles = (unsigned)(((V.nx + TX - 1) / TX) * ((V.ny + TY - 1) / TY) * ((V.nz + TZ - 1) / TZ));
-  k_conv3<<<dim3(tiles, (L.cin + COB - 1) / COB), TX * TY * TZ, 0, s>>>(dout, L.cout, u->wt, nullptr, din, L.cin, V,
-                                                                        0);
+  conv3_tc(dout, L.cout, u->wt, nullptr, din, L.cin, V, false, s);
 }
 
 void conv3_wgrad(eb_unet u, int l, const float *in, const float *dout, const Vol &V, cudaStream_t s) {
   const LayerSpec &L = kLayers[l];
   const unsigned tiles = (unsigned)(((V.nx + TX - 1) / TX) * ((V.ny + TY - 1) / TY) * ((V.nz + TZ - 1) / TZ));
-  k_conv3_wgrad<<<dim3(tiles, (L.cout + COB - 1) / COB, (L.cin + CIC - 1) / CIC), TX * TY * TZ, 0, s>>>(
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WG_SMEM);
+    attr = true;
+  }
+  k_conv3_wgrad_tc<<<dim3(tiles, (L.cout + WG_C - 1) / WG_C, (L.cin + WG_C - 1) / WG_C), 256, WG_SMEM, s>>>(
       in, L.cin, dout, L.cout, V, u->g + u->off_w[l]);
   k_chan_dot<<<dim3(64, L.cout), 256, 0, s>>>(dout, nullptr, L.cout, V.n(), u->g + u->off_b[l]);
 }
