@@ -273,7 +273,7 @@ __global__ void k_correct(Op O, const double *x, double dt, T *mu, T *mv, T *mw)
 // semi-definite operator, as conjugate gradients need.
 // ---------------------------------------------------------------------------
 constexpr float MG_OMEGA = 0.8f;
-constexpr int MG_COARSE_SWEEPS = 64;   // even: the coarsest result ends in x
+constexpr int MG_COARSE_SWEEPS = 64;   // even: the result ends in x
 
 // the operator of one level: S = sum_f a_f x_nb (off-diagonal part) and the
 // diagonal d = sum_f a_f, from the six face coefficients of cell c
@@ -385,31 +385,8 @@ __global__ void k_mg_prolong(Op32 F, Dims C, const float *xc, float *x, const in
   }
 }
 
-// the coarsest grid: MG_COARSE_SWEEPS Jacobi sweeps from zero in one block
-__global__ void k_mg_coarsest(Op32 L, const float *b, float *x, float *t, const int *conv) {
-  if (*conv) return;
-  const long long N = L.D.nxy * L.D.nz;
-  for (int sw = 0; sw < MG_COARSE_SWEEPS; ++sw) {
-    const float *in = (sw & 1) ? t : x;
-    float *out = (sw & 1) ? x : t;
-    for (long long c = threadIdx.x; c < N; c += blockDim.x) {
-      float v = 0.f;
-      if (sw == 0) {
-        const float d = L.diag(c);
-        if (d > 0.f) v = MG_OMEGA * b[c] / d;
-      } else {
-        float S, d;
-        L.parts(in, c, S, d);
-        if (d > 0.f) v = (1.f - MG_OMEGA) * in[c] + MG_OMEGA * (b[c] + S) / d;
-      }
-      out[c] = v;
-    }
-    __syncthreads();   // the block's global writes are visible to the next sweep
-  }
-}
-
-// the same on a coarsest grid of at most MG_SMEM_CELLS cells, held in shared
-// memory for the sweeps (same arithmetic, same order)
+// the coarsest grid (at most MG_SMEM_CELLS cells): MG_COARSE_SWEEPS Jacobi
+// sweeps from zero in one block, the grid held in shared memory
 constexpr int MG_SMEM_CELLS = 1024;
 __global__ void k_mg_coarsest_smem(Op32 L, const float *b, float *x, const int *conv) {
   if (*conv) return;
@@ -499,7 +476,7 @@ __global__ void k_mg_lower(const __grid_constant__ MgLower M, const int *conv) {
     __syncthreads();
   }
   const int top = M.top;
-  for (int sw = 0; sw < MG_COARSE_SWEEPS; ++sw)   // as k_mg_coarsest: the result ends in x
+  for (int sw = 0; sw < MG_COARSE_SWEEPS; ++sw)   // coarsest sweeps; the result ends in x
     lower_sweep(M.L[top], (sw & 1) ? M.t[top] : M.x[top], (sw & 1) ? M.x[top] : M.t[top], M.b[top], sw == 0);
   for (int l = top - 1; l >= M.lt; --l) {
     const Op32 &F = M.L[l];

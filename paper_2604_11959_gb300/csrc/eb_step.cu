@@ -510,8 +510,8 @@ __device__ inline void apply_row(const StepArgs<T> &A, const GridDev &G, const C
 }
 
 // Near-EB CVs without a geometry record are regular: every face is open
-// with its centroid at the face centre, so the divergence is the difference
-// of the staged face fluxes (the sums of band_divergence with beta = 1).
+// with its centroid at the face centre, so the divergence is the plain
+// difference of the staged face fluxes.
 template <typename T>
 __device__ inline void regular_cv(const StepArgs<T> &A, long long t) {
   const Dims &D = A.D;
