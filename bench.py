@@ -392,11 +392,12 @@ def cpu_baseline(w, budget_s=15.0, window=96):
 # ---------------------------------------------------------------------------
 def traffic_record(kernel, workload_name, precision):
     """DRAM bytes per launch of a kernel from a committed ncu summary, valid
-    only while the kernel source is unchanged (hash recorded with it)."""
+    only while the kernel source and the set-up that decides its work (the
+    first fast level of every column) are unchanged (hash recorded with it)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}_{precision}.txt")
-    src = os.path.join(ROOT, "paper_2604_11959_gb300", "csrc", "eb_fast.cu")
+    srcs = [os.path.join(ROOT, "paper_2604_11959_gb300", "csrc", f) for f in ("eb_fast.cu", "eb_geom.cu")]
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()[:16]
         rec = {}
         for line in open(path):
             if ":" in line:
@@ -487,6 +488,7 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=
         "gpu_launches": launches_per_step * steps,
         "steps": steps,
         "tuned_slab_levels": slab,
+        "bulk_high_priority": int(geom.info()["bulk_high_priority"]),
     }
     return geom, res
 
@@ -694,6 +696,7 @@ def main():
                    "state": "stratified, wind u=1 above the terrain, smooth seeded perturbations",
                    "l2": "512 MiB buffer written before every timed step (untimed); per-step CUDA events",
                    "tuned_slab_levels": head.get("tuned_slab_levels"),
+                   "tuned_bulk_high_priority": head.get("bulk_high_priority"),
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "roofline": head["roofline"],
         "step_hbm_frac": head["step_frac"],

@@ -122,6 +122,10 @@ typedef struct {
   int64_t fast_cells;       /* base cells updated by the geometry-free kernel  */
   double min_alpha;         /* smallest positive volume fraction, any grid    */
   int64_t device_bytes;     /* device memory held by the handle               */
+  int64_t slab_levels;      /* slab height of the bulk kernel's tiles in use
+                               (0 = automatic)                                */
+  int64_t bulk_high_priority; /* 1: the bulk kernel runs on a stream of the
+                               highest priority beside the near-EB kernels    */
 } eb_geom_info_t;
 
 /*
@@ -401,10 +405,22 @@ eb_status eb_ensemble_destroy(eb_ensemble e);
 /* Autotuner of one handle: times reps steps of eb_step(nsteps = 1,
  * stages = 1) from U (read only; the results go to a temporary state) for each
  * candidate slab height of the bulk kernel's tiles (automatic, 12 .. 64
- * levels, whole column) and keeps the fastest; *slab_levels (NULL allowed)
- * receives it (0 = automatic).  Results of later steps do not depend on it.
- * Synchronises the stream; allocates and frees the temporary state. */
+ * levels, whole column), each with the bulk kernel at the same and at a
+ * higher stream priority than the near-EB kernels (eb_geom_set_bulk_priority),
+ * and keeps the fastest pair; *slab_levels (NULL allowed) receives the height
+ * (0 = automatic), eb_geom_info the pair.  Results of later steps do not
+ * depend on either.  Synchronises the stream; allocates and frees the
+ * temporary state. */
 eb_status eb_geom_tune(eb_geom geom, const eb_state *U, double dt, int reps, int *slab_levels, void *stream);
+
+/* Stream priority of the bulk kernel within a step (scheduling only: results
+ * do not depend on it).  high = 0: the bulk kernel runs on the caller's stream
+ * and the near-EB kernels on the handle's side stream, at the same priority.
+ * high = 1: the bulk kernel runs on a handle stream of the highest priority,
+ * so that its CTAs take their SMs before the near-EB kernels' blocks; this
+ * pays where the near-EB work is large (rough terrain).  Default 0;
+ * eb_geom_tune chooses.  EB_ERR_INVALID_ARG for another value. */
+eb_status eb_geom_set_bulk_priority(eb_geom geom, int high);
 
 /* Sets the bulk kernel's slab height directly (0 = automatic; heights above
  * nz mean whole columns), e.g. to re-apply a height eb_geom_tune chose

@@ -109,9 +109,6 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
     scan_exclusive(g->roff[q], ncol + 1, counts, s);
     CUDA_TRY(cudaMemcpyAsync(&nrec[q], counts, sizeof(long long), cudaMemcpyDeviceToHost, s), "read nrec");
   }
-  CUDA_TRY(g->alloc(&g->kfast, ncol), "alloc kfast");
-  const int *kr[4] = {g->kreg[0], g->kreg[1], g->kreg[2], g->kreg[3]};
-  launch_fast_level(D, kr, g->kfast, s);
   CUDA_TRY(cudaGetLastError(), "band kernels");
   CUDA_TRY(cudaStreamSynchronize(s), "band sync");
   long long tmp_need = 0;
@@ -145,6 +142,20 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
     tmp_need = std::max(tmp_need, 2 * (n + 1) + 1 + (n + 1) / 256 + 8);
   }
   CUDA_TRY(cudaGetLastError(), "geometry kernels");
+  // first level of the bulk kernel per column, from the regular and fluid
+  // levels of all grids
+  {
+    CUDA_TRY(g->alloc(&g->kfast, ncol), "alloc kfast");
+    int *kflu = nullptr;
+    CUDA_TRY(cudaMalloc(&kflu, sizeof(int) * (size_t)(4 * ncol)), "alloc fluid levels");
+    const int *kr[4] = {g->kreg[0], g->kreg[1], g->kreg[2], g->kreg[3]};
+    const int *kfl[4] = {kflu, kflu + ncol, kflu + 2 * ncol, kflu + 3 * ncol};
+    for (int q = 0; q < 4; ++q) launch_fluid_level(D, g->G[q], kflu + q * ncol, s);
+    launch_fast_level(D, kr, kfl, g->kfast, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(kflu);
+    CUDA_TRY(e, "fast levels");
+  }
   // dense availability bytes and the near-EB update lists
   std::vector<int> kf_host(ncol);
   CUDA_TRY(cudaMemcpy(kf_host.data(), g->kfast, sizeof(int) * ncol, cudaMemcpyDeviceToHost), "read kfast");
@@ -180,28 +191,37 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
     cudaFree(scan_tmp);
     if (e != cudaSuccess) return cuda_fail(e, "band lists");
   }
-  // each band list: CVs with a geometry record first, then the regular ones
-  // (levels at or above kxt), which take a shorter kernel; plane order kept
+  // each band list: the cut CVs, which take a row of coefficients, first;
+  // then the regular ones, with or without a record (all faces open, centroids
+  // at the face centres: plain face differences, a shorter kernel); plane
+  // order kept
   {
-    std::vector<int> kx(ncol);
+    std::vector<int> kx(ncol), kc(ncol);
+    std::vector<long long> ro(ncol + 1);
+    std::vector<uint8_t> fl;
     std::vector<unsigned> bl, ord;
     for (int q = 0; q < 4; ++q) {
       GridDev &G = g->G[q];
       G.nband_rec = 0;
       if (G.nband == 0) continue;
       bl.resize(G.nband);
+      fl.resize(std::max(1LL, G.nrec));
       CUDA_TRY(cudaMemcpy(bl.data(), G.blist, sizeof(unsigned) * G.nband, cudaMemcpyDeviceToHost), "read band list");
       CUDA_TRY(cudaMemcpy(kx.data(), g->kxt[q], sizeof(int) * ncol, cudaMemcpyDeviceToHost), "read kxt");
+      CUDA_TRY(cudaMemcpy(kc.data(), g->kcov[q], sizeof(int) * ncol, cudaMemcpyDeviceToHost), "read kcov");
+      CUDA_TRY(cudaMemcpy(ro.data(), g->roff[q], sizeof(long long) * (ncol + 1), cudaMemcpyDeviceToHost), "read roff");
+      if (G.nrec)
+        CUDA_TRY(cudaMemcpy(fl.data(), G.flag, sizeof(uint8_t) * G.nrec, cudaMemcpyDeviceToHost), "read flags");
+      auto takes_row = [&](unsigned c) {
+        const long long k = c / D.nxy, col = c % D.nxy;
+        return k < kx[col] && fl[ro[col] + (k - kc[col])] != EBK_REGULAR;
+      };
       ord.clear();
       for (int pass = 0; pass < 2; ++pass)
-        for (unsigned c : bl) {
-          const long long k = c / D.nxy, col = c % D.nxy;
-          if ((k < kx[col]) == (pass == 0)) ord.push_back(c);
-        }
-      for (unsigned c : bl) {
-        const long long k = c / D.nxy, col = c % D.nxy;
-        if (k < kx[col]) ++G.nband_rec;
-      }
+        for (unsigned c : bl)
+          if (takes_row(c) == (pass == 0)) ord.push_back(c);
+      for (unsigned c : bl)
+        if (takes_row(c)) ++G.nband_rec;
       CUDA_TRY(cudaMemcpy(G.blist, ord.data(), sizeof(unsigned) * G.nband, cudaMemcpyHostToDevice), "write band list");
     }
   }
@@ -338,9 +358,15 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
   CUDA_TRY(g->alloc((double **)&g->qhat5, g->sum_small), "alloc qhat");
   CUDA_TRY(g->alloc((double **)&g->sig5, 3 * g->sum_small), "alloc sig");
   CUDA_TRY(g->alloc((double **)&g->pval5, g->sum_small), "alloc pivot values");
-  CUDA_TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking), "side stream");
+  {
+    int least = 0, greatest = 0;
+    CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
+    CUDA_TRY(cudaStreamCreateWithPriority(&g->bulk, cudaStreamNonBlocking, greatest), "bulk stream");
+    CUDA_TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking), "side stream");
+  }
   CUDA_TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming), "event");
   CUDA_TRY(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming), "event");
+  CUDA_TRY(cudaEventCreateWithFlags(&g->ev_join_bulk, cudaEventDisableTiming), "event");
   CUDA_TRY(fill_ref<double>(g, ref_rho, &g->ref_d[0], &g->ref_f[0], s), "reference");
   CUDA_TRY(fill_ref<double>(g, ref_rt, &g->ref_d[1], &g->ref_f[1], s), "reference");
   CUDA_TRY(g->alloc(&g->status, 1), "alloc status");
@@ -517,6 +543,8 @@ eb_status eb_geom_destroy(eb_geom geom) {
 eb_status eb_geom_info(eb_geom geom, eb_geom_info_t *info) {
   if (!geom || !info) return fail(EB_ERR_INVALID_ARG, "NULL handle or info");
   *info = geom->info;
+  info->slab_levels = geom->slab_levels;
+  info->bulk_high_priority = geom->bulk_high;
   return EB_OK;
 }
 
@@ -710,6 +738,13 @@ eb_status eb_geom_set_slab_levels(eb_geom geom, int slab_levels) {
   return eb_replan_bulk(geom, slab_levels);
 }
 
+eb_status eb_geom_set_bulk_priority(eb_geom geom, int high) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  if (high != 0 && high != 1) return fail(EB_ERR_INVALID_ARG, "high must be 0 or 1");
+  geom->bulk_high = high;
+  return EB_OK;
+}
+
 eb_status eb_geom_tune(eb_geom geom, const eb_state *U, double dt, int reps, int *slab_levels, void *stream) {
   if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
   const size_t es = geom->prec == EB_F64 ? 8 : 4;
@@ -735,27 +770,35 @@ eb_status eb_geom_tune(eb_geom geom, const eb_state *U, double dt, int reps, int
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
   float best = 0.f;
-  int best_c = 0;
+  int best_c = 0, best_h = 0;
+  bool first = true;
   eb_status st = EB_OK;
   for (int c : cand) {
     if ((st = eb_replan_bulk(geom, c)) != EB_OK) break;
-    if ((st = eb_step(geom, U, &O, dt, 1, 1, stream)) != EB_OK) break;   // warm-up
-    cudaEventRecord(t0, s);
-    for (int q = 0; q < reps && st == EB_OK; ++q) st = eb_step(geom, U, &O, dt, 1, 1, stream);
-    cudaEventRecord(t1, s);
+    for (int hp = 0; hp < 2 && st == EB_OK; ++hp) {
+      geom->bulk_high = hp;
+      if ((st = eb_step(geom, U, &O, dt, 1, 1, stream)) != EB_OK) break;   // warm-up
+      cudaEventRecord(t0, s);
+      for (int q = 0; q < reps && st == EB_OK; ++q) st = eb_step(geom, U, &O, dt, 1, 1, stream);
+      cudaEventRecord(t1, s);
+      if (st != EB_OK) break;
+      const cudaError_t e = cudaEventSynchronize(t1);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "tuning step");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if (first || ms < best) {
+        best = ms;
+        best_c = c;
+        best_h = hp;
+        first = false;
+      }
+    }
     if (st != EB_OK) break;
-    const cudaError_t e = cudaEventSynchronize(t1);
-    if (e != cudaSuccess) {
-      st = cuda_fail(e, "tuning step");
-      break;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, t0, t1);
-    if (c == cand[0] || ms < best) {
-      best = ms;
-      best_c = c;
-    }
   }
+  geom->bulk_high = best_h;
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   cudaStreamSynchronize(s);

@@ -433,20 +433,40 @@ __global__ void k_band_top(Dims D, int nzg, const int *kcov, const int *kreg, in
   count[col] = top - kcov[col];
 }
 
-// First level of the geometry-free path, shared by all grids: three levels
-// above the highest non-regular CV of any grid within three columns.
+// First level of grid g's column from which every CV holds fluid (alpha > 0,
+// the availability test of the flux stencils): the covered levels and any
+// record without fluid lie below it.
+__global__ void k_fluid_level(Dims D, GridDev G, int *kflu) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= D.nx * D.ny) return;
+  const int kc = G.kcov[col];
+  int kf = kc;
+  for (int k = kc; k < G.kxt[col]; ++k)
+    if (!(G.alpha[G.roff[col] + (k - kc)] > 0.0)) kf = k + 1;
+  kflu[col] = kf;
+}
+
+// First level of the geometry-free path, shared by all grids.  From it up,
+// the CVs of all four grids in the column are regular, and every CV that
+// their flux stencils read (Sec. 4.1: up to three columns across, through the
+// staggered averages, and three levels down, through the w-grid's advected
+// values) holds fluid, so that every availability test passes and the plain
+// stencil is the scheme's flux.  At least level 3, so that no stencil reaches
+// the bottom wall.
 __global__ void k_fast_level(Dims D, const int *kreg0, const int *kreg1, const int *kreg2, const int *kreg3,
+                             const int *kflu0, const int *kflu1, const int *kflu2, const int *kflu3,
                              int *kfast) {
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= D.nx * D.ny) return;
   const int i = col % D.nx, j = col / D.nx;
-  int top = 0;
+  const int reg = max(max(kreg0[col], kreg1[col]), max(kreg2[col], kreg3[col]));
+  int flu = 0;
   for (int dj = -3; dj <= 3; ++dj)
     for (int di = -3; di <= 3; ++di) {
       const int c = wrapi(i + di, D.nx) + D.nx * wrapi(j + dj, D.ny);
-      top = max(top, max(max(kreg0[c], kreg1[c]), max(kreg2[c], kreg3[c])));
+      flu = max(flu, max(max(kflu0[c], kflu1[c]), max(kflu2[c], kflu3[c])));
     }
-  kfast[col] = min(D.nz, max(3, top + 3));
+  kfast[col] = min(D.nz, max(3, max(reg, flu + 3)));
 }
 
 // Geometry records of the band of every column.
@@ -655,8 +675,14 @@ void launch_band_top(const Dims &D, int nzg, const int *kcov, const int *kreg, i
   k_band_top<<<nblk((long long)D.nx * D.ny, 256), 256, 0, s>>>(D, nzg, kcov, kreg, kxt, count);
 }
 
-void launch_fast_level(const Dims &D, const int *const kreg[4], int *kfast, cudaStream_t s) {
-  k_fast_level<<<nblk((long long)D.nx * D.ny, 256), 256, 0, s>>>(D, kreg[0], kreg[1], kreg[2], kreg[3], kfast);
+void launch_fluid_level(const Dims &D, const GridDev &G, int *kflu, cudaStream_t s) {
+  k_fluid_level<<<nblk((long long)D.nx * D.ny, 256), 256, 0, s>>>(D, G, kflu);
+}
+
+void launch_fast_level(const Dims &D, const int *const kreg[4], const int *const kflu[4], int *kfast,
+                       cudaStream_t s) {
+  k_fast_level<<<nblk((long long)D.nx * D.ny, 256), 256, 0, s>>>(D, kreg[0], kreg[1], kreg[2], kreg[3], kflu[0],
+                                                                   kflu[1], kflu[2], kflu[3], kfast);
 }
 
 void launch_band_geometry(const double *h, const Dims &D, int g, const GridDev &G, cudaStream_t s) {

@@ -84,6 +84,7 @@ struct eb_geom_s {
   int *boff = nullptr;
   int bctas = 0;
   int slab_levels = 0;    // slab height of the split (0: automatic)
+  int bulk_high = 0;      // 1: the bulk kernel runs on the high-priority stream
   std::vector<int> kfast_host;
   int kcov_max = 0;
   GridDev G[4];
@@ -98,10 +99,11 @@ struct eb_geom_s {
   // scratch of the five-field redistribution pass (small CVs of all fields)
   void *qhat5 = nullptr, *sig5 = nullptr, *pval5 = nullptr;
   long long sum_small = 0;
-  // the near-EB kernels run on this stream, forked from and joined to the
-  // caller's stream around the bulk kernel
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // the near-EB kernels run on the side stream and (bulk_high) the bulk
+  // kernel on a stream of the highest priority, forked from and joined to the
+  // caller's stream
+  cudaStream_t side = nullptr, bulk = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_bulk = nullptr;
   // scratch states for eb_step: 4 x 5 fields
   void *scr[4][5] = {};
   std::vector<void *> allocs;
@@ -123,9 +125,11 @@ struct eb_geom_s {
   void release() {
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_join_bulk) cudaEventDestroy(ev_join_bulk);
     if (side) cudaStreamDestroy(side);
-    ev_fork = ev_join = nullptr;
-    side = nullptr;
+    if (bulk) cudaStreamDestroy(bulk);
+    ev_fork = ev_join = ev_join_bulk = nullptr;
+    side = bulk = nullptr;
     for (void *p : allocs) cudaFree(p);
     allocs.clear();
     if (pw.host) cudaFreeHost(pw.host);
@@ -204,14 +208,27 @@ void wsrd_field(eb_geom g, int field, T *u, cudaStream_t s) {
 }
 
 // Flux divergence and provisional update.  The near-EB kernels and the bulk
-// read the same input and write disjoint CVs, so the near-EB kernels run on
-// the handle's side stream alongside the bulk kernel.
+// read the same input and write disjoint CVs, so they run side by side: the
+// near-EB kernels on the handle's side stream, the bulk kernel either on the
+// caller's stream (same priority: the scheduler interleaves the two) or on
+// the handle's stream of the highest priority (its CTAs, one wave of two per
+// SM, take their SMs first and the near-EB kernels fill the remaining SMs
+// meanwhile and all of them afterwards; faster where the near-EB work is
+// large).  eb_geom_tune times both.
 template <typename T>
 void flux_update(eb_geom g, const StepArgs<T> &A, cudaStream_t s) {
   cudaEventRecord(g->ev_fork, s);
   cudaStreamWaitEvent(g->side, g->ev_fork, 0);
-  launch_flux_band(A, g->side);
-  launch_flux_fast(A, s);
+  if (g->bulk_high) {
+    cudaStreamWaitEvent(g->bulk, g->ev_fork, 0);
+    launch_flux_fast(A, g->bulk);
+    launch_flux_band(A, g->side);
+    cudaEventRecord(g->ev_join_bulk, g->bulk);
+    cudaStreamWaitEvent(s, g->ev_join_bulk, 0);
+  } else {
+    launch_flux_band(A, g->side);
+    launch_flux_fast(A, s);
+  }
   cudaEventRecord(g->ev_join, g->side);
   cudaStreamWaitEvent(s, g->ev_join, 0);
 }

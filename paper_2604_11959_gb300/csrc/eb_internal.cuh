@@ -7,8 +7,9 @@
 // above kxt are regular (full cell, open faces).  The band covers the cut CVs
 // plus one level of the redistribution neighbourhoods above them.  A column's
 // records are contiguous from roff[col].  kfast[col] is the first level from
-// which every CV of every grid at that column and all CVs its flux stencil
-// reads are regular, so the bulk kernel needs no geometry at all there.
+// which every CV of every grid at that column is regular and every CV its
+// flux stencils read holds fluid, so the bulk kernel needs no geometry at all
+// there.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -56,7 +57,7 @@ struct GridDev {
   // state indices in plane-major order
   unsigned *blist;
   long long nband;
-  long long nband_rec;   // blist[0, nband_rec): CVs with a record; the rest are regular
+  long long nband_rec;   // blist[0, nband_rec): cut CVs (rows below); the rest are regular
   // near-EB rows of the CVs with a record: dU of CV blist[t] is
   // sum over d of sum_{q = srow[3t+d]}^{srow[3t+d+1]-1} scoef[q] * fh[d][sidx[q]]
   // (fhm for the mass of the c grid); built once per geometry

@@ -41,7 +41,9 @@ struct WsrdDev {
 void launch_band_bounds(const double *h, const Dims &D, int g, int *kcov, int *kreg, cudaStream_t s);
 void launch_band_top(const Dims &D, int nzg, const int *kcov, const int *kreg, int *kxt, long long *count,
                      cudaStream_t s);
-void launch_fast_level(const Dims &D, const int *const kreg[4], int *kfast, cudaStream_t s);
+void launch_fluid_level(const Dims &D, const GridDev &G, int *kflu, cudaStream_t s);
+void launch_fast_level(const Dims &D, const int *const kreg[4], const int *const kflu[4], int *kfast,
+                       cudaStream_t s);
 void launch_band_geometry(const double *h, const Dims &D, int g, const GridDev &G, cudaStream_t s);
 void launch_dense_flags(const Dims &D, int g, const GridDev &G, cudaStream_t s);
 void launch_band_marks(const Dims &D, int g, const int *kcov, const int *kfast, int kmax, long long *mark,

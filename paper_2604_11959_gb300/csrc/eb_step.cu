@@ -7,11 +7,11 @@
 //                      stencils read, once;
 //     k_face_flux    : the provisional flux of every face the near-EB CVs
 //                      read, once, with covered-neighbour fallbacks;
-//     k_band         : the CVs below kfast with a geometry record (open-face
-//                      fractions and fluxes interpolated to the cut-face
-//                      centroids, as rows of coefficients built at set-up),
-//                      then, in the same launch, the other CVs below kfast
-//                      (plain face differences).
+//     k_band         : the cut CVs below kfast (open-face fractions and
+//                      fluxes interpolated to the cut-face centroids, as rows
+//                      of coefficients built at set-up), then, in the same
+//                      launch, the regular CVs below kfast (plain face
+//                      differences).
 //   weighted state redistribution (Sec. 5.1, Eqs. qhat_omega, qrecon,
 //   final_update_omega), on compact lists built at set-up:
 //     k_qhat  : neighbourhood averages of the small CVs;
@@ -139,7 +139,7 @@ __device__ inline void write_out_d(const StepArgs<T> &A, int f, long long c, dou
   if (!isfinite(v)) atomicOr(A.status, EB_DEV_NUMERIC);
 }
 
-// Near-EB rows.  For a CV with a geometry record, the open area fractions,
+// Near-EB rows.  For a cut CV (it has a geometry record), the open area fractions,
 // the centroid interpolation weights, 1 / dx_d and 1 / alpha depend on the
 // geometry alone, so its dU of Eqs. update-cc / update-fc is a fixed linear
 // combination of the staged face fluxes: each term of the low d-face enters
@@ -466,7 +466,7 @@ __global__ void k_stage(StepArgs<T> A) {
   ((T *)A.G[g].pv)[c] = v;
 }
 
-// Phase B: the divergence of every listed CV with a geometry record, from
+// Phase B: the divergence of every listed cut CV, from
 // its precomputed row; the mixed path sums the rows of tiny cut CVs
 // (alpha < 1e-3, whose coefficients carry 1 / alpha) in double.
 template <typename T, typename R, typename C>
@@ -509,9 +509,9 @@ __device__ inline void apply_row(const StepArgs<T> &A, const GridDev &G, const C
   }
 }
 
-// Near-EB CVs without a geometry record are regular: every face is open
-// with its centroid at the face centre, so the divergence is the plain
-// difference of the staged face fluxes.
+// The other near-EB CVs are regular (with a geometry record or without):
+// every face is open with its centroid at the face centre, so the divergence
+// is the plain difference of the staged face fluxes.
 template <typename T>
 __device__ inline void regular_cv(const StepArgs<T> &A, long long t) {
   const Dims &D = A.D;
@@ -559,7 +559,7 @@ template <typename T>
 __global__ void k_band(StepArgs<T> A) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nrec = A.G[0].nband_rec + A.G[1].nband_rec + A.G[2].nband_rec + A.G[3].nband_rec;
-  if (t >= nrec) {   // CVs without a record follow the rows in the same launch
+  if (t >= nrec) {   // the regular CVs follow the rows in the same launch
     regular_cv(A, t - nrec);
     return;
   }

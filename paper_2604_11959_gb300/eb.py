@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom
                     "eb_unet_num_params", "eb_unet_create", "eb_unet_set_params", "eb_unet_get_params",
                     "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step", "eb_unet_destroy",
                     "eb_project_sample", "eb_project_warm", "eb_geom_tune",
-                    "eb_geom_set_slab_levels", "eb_project_set_preconditioner")
+                    "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner")
 
 
 class EbError(RuntimeError):
@@ -56,7 +56,8 @@ class GeomInfo(ctypes.Structure):
                 ("band_cvs", ctypes.c_int64 * 4), ("band_faces", ctypes.c_int64 * 4),
                 ("tiny_cvs", ctypes.c_int64 * 4), ("fast_cells", ctypes.c_int64),
                 ("min_alpha", ctypes.c_double),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("slab_levels", ctypes.c_int64),
+                ("bulk_high_priority", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -111,6 +112,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_project_warm.argtypes = [V, V, P(_State), D, D, I, D, P(I), P(D), V]
     lib.eb_geom_tune.argtypes = [V, P(_State), D, I, P(I), V]
     lib.eb_geom_set_slab_levels.argtypes = [V, I]
+    lib.eb_geom_set_bulk_priority.argtypes = [V, I]
     lib.eb_project_set_preconditioner.argtypes = [V, I]
     lib.eb_last_error.restype = ctypes.c_char_p
     lib.eb_version.restype = I
@@ -120,7 +122,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                  "eb_ensemble_destroy", "eb_project", "eb_anelastic_step", "eb_unet_create", "eb_unet_set_params",
                  "eb_unet_get_params", "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step",
                  "eb_unet_destroy", "eb_project_sample", "eb_project_warm", "eb_geom_tune",
-                 "eb_geom_set_slab_levels", "eb_project_set_preconditioner"):
+                 "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -327,6 +329,12 @@ def set_preconditioner(geom: Geometry, kind: str) -> None:
     if kind not in PRECONDITIONERS:
         raise ValueError(f"unknown preconditioner {kind!r}")
     _check(load().eb_project_set_preconditioner(geom.handle, PRECONDITIONERS[kind]))
+
+
+def set_bulk_priority(geom: Geometry, high: bool) -> None:
+    """Run the bulk kernel on a high-priority stream beside the near-EB
+    kernels, or on the caller's stream (``eb_geom_set_bulk_priority``)."""
+    _check(load().eb_geom_set_bulk_priority(geom.handle, 1 if high else 0))
 
 
 def set_slab_levels(geom: Geometry, levels: int) -> None:

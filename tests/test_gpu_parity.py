@@ -284,11 +284,37 @@ def test_tuning_changes_no_result(eb, precision):
     keep = {f: A[f].clone() for f in A}
     best = eb.tune(geom, A, w.dt(), reps=1)
     assert best in (0, 12, 16, 24, 32, 48, 64, w.nz)
+    info = geom.info()
+    assert info["slab_levels"] == best and info["bulk_high_priority"] in (0, 1)
     for f in A:
         assert torch.equal(A[f], keep[f]), f
     after = eb.step(geom, A, w.dt(), 3)
     for f in FIELDS:
         assert torch.equal(before[f], after[f]), (precision, f)
+    eb.sync_status(geom)
+    geom.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_bulk_priority_changes_no_result(eb, precision):
+    """The bulk kernel on the high-priority stream or on the caller's stream
+    (eb_geom_set_bulk_priority) only changes the schedule: the steps agree
+    bit for bit, the choice shows in eb_geom_info, and other values are
+    rejected."""
+    w = rough_workload()
+    refs = refs_for(w.nz, w.Lz)
+    U = w.state("uniform", pert=1e-2, seed=7)
+    geom = make_geometry(eb, w, w.heights(), precision, refs)
+    A = to_device(U, precision, refs)
+    eb.set_bulk_priority(geom, False)
+    assert geom.info()["bulk_high_priority"] == 0
+    low = eb.step(geom, A, w.dt(), 3)
+    eb.set_bulk_priority(geom, True)
+    assert geom.info()["bulk_high_priority"] == 1
+    high = eb.step(geom, A, w.dt(), 3)
+    for f in FIELDS:
+        assert torch.equal(low[f], high[f]), (precision, f)
+    assert eb.load().eb_geom_set_bulk_priority(geom.handle, 2) == 1   # EB_ERR_INVALID_ARG
     eb.sync_status(geom)
     geom.close()
 
