@@ -351,6 +351,20 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
     g->info.small_cvs[q] = g->W[q].nsmall;
     g->info.affected_cvs[q] = g->W[q].naff;
   }
+  // the redistribution may run beside the bulk kernel when every CV it reads
+  // or writes is produced by the near-EB kernels
+  {
+    unsigned *far = nullptr, far_h = 1;
+    CUDA_TRY(cudaMalloc(&far, sizeof(unsigned)), "alloc reach flag");
+    cudaError_t e = cudaMemsetAsync(far, 0, sizeof(unsigned), s);
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q) launch_wsrd_reach(D, q, g->W[q], g->kcov[q], g->kfast, far, s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&far_h, far, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(far);
+    CUDA_TRY(e, "redistribution reach");
+    g->wsrd_side = far_h == 0 ? 1 : 0;
+  }
   CUDA_TRY(g->alloc((double **)&g->qhat, g->max_small), "alloc qhat");
   CUDA_TRY(g->alloc((double **)&g->sig, 3 * g->max_small), "alloc sig");
   CUDA_TRY(g->alloc((double **)&g->pval, g->max_small), "alloc pivot values");
@@ -545,6 +559,7 @@ eb_status eb_geom_info(eb_geom geom, eb_geom_info_t *info) {
   *info = geom->info;
   info->slab_levels = geom->slab_levels;
   info->bulk_high_priority = geom->bulk_high;
+  info->wsrd_beside_bulk = geom->wsrd_side;
   return EB_OK;
 }
 

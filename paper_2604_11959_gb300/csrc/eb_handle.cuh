@@ -85,6 +85,7 @@ struct eb_geom_s {
   int bctas = 0;
   int slab_levels = 0;    // slab height of the split (0: automatic)
   int bulk_high = 0;      // 1: the bulk kernel runs on the high-priority stream
+  int wsrd_side = 0;      // 1: the redistribution runs on the side stream (see stage)
   std::vector<int> kfast_host;
   int kcov_max = 0;
   GridDev G[4];
@@ -215,22 +216,29 @@ void wsrd_field(eb_geom g, int field, T *u, cudaStream_t s) {
 // SM, take their SMs first and the near-EB kernels fill the remaining SMs
 // meanwhile and all of them afterwards; faster where the near-EB work is
 // large).  eb_geom_tune times both.
-template <typename T>
-void flux_update(eb_geom g, const StepArgs<T> &A, cudaStream_t s) {
+template <typename T, typename Side>
+void flux_update(eb_geom g, const StepArgs<T> &A, cudaStream_t s, Side &&after_band) {
   cudaEventRecord(g->ev_fork, s);
   cudaStreamWaitEvent(g->side, g->ev_fork, 0);
   if (g->bulk_high) {
     cudaStreamWaitEvent(g->bulk, g->ev_fork, 0);
     launch_flux_fast(A, g->bulk);
     launch_flux_band(A, g->side);
+    after_band(g->side);
     cudaEventRecord(g->ev_join_bulk, g->bulk);
     cudaStreamWaitEvent(s, g->ev_join_bulk, 0);
   } else {
     launch_flux_band(A, g->side);
+    after_band(g->side);
     launch_flux_fast(A, s);
   }
   cudaEventRecord(g->ev_join, g->side);
   cudaStreamWaitEvent(s, g->ev_join, 0);
+}
+
+template <typename T>
+void flux_update(eb_geom g, const StepArgs<T> &A, cudaStream_t s) {
+  flux_update(g, A, s, [](cudaStream_t) {});
 }
 
 // Redistribution of all five fields of a state in one pass of three kernels.
@@ -259,11 +267,20 @@ void wsrd_all(eb_geom g, void *const out[5], cudaStream_t s) {
   launch_wsrd5(S, s);
 }
 
+// One stage: flux update, then redistribution.  When every CV the
+// redistribution reads or writes is a near-EB CV (checked at set-up), it
+// follows the near-EB kernels on the side stream, beside the bulk kernel;
+// otherwise it follows the join.
 template <typename T>
 void stage(eb_geom g, void *const src[5], void *const base[5], void *const out[5], double dt, int copy,
            cudaStream_t s) {
-  flux_update(g, step_args<T>(g, src, base, out, dt, copy), s);
-  wsrd_all<T>(g, out, s);
+  const StepArgs<T> A = step_args<T>(g, src, base, out, dt, copy);
+  if (g->wsrd_side) {
+    flux_update(g, A, s, [&](cudaStream_t side) { wsrd_all<T>(g, out, side); });
+  } else {
+    flux_update(g, A, s);
+    wsrd_all<T>(g, out, s);
+  }
 }
 
 inline size_t field_count(const Dims &D, int f) { return (size_t)D.nxy * (D.nz + (f == 4 ? 1 : 0)); }

@@ -83,6 +83,10 @@ struct SetupScratch;
 cudaError_t build_wsrd(const Dims &D, int g, GridDev &G, const GridDev *all, double vt, WsrdDev &W,
                        cudaStream_t s, long long *dev_tmp);
 void free_wsrd(WsrdDev &W);
+// sets *far when a CV the redistribution of grid g reads or writes is not a
+// near-EB CV (see k_wsrd_reach)
+void launch_wsrd_reach(const Dims &D, int g, const WsrdDev &W, const int *kcov, const int *kfast, unsigned *far,
+                       cudaStream_t s);
 
 // device allocation helper that tracks every pointer for one release
 struct DevArena;

@@ -483,6 +483,31 @@ cudaError_t dalloc(P **p, long long count) {
   return cudaMalloc((void **)p, sizeof(P) * (size_t)count);
 }
 
+// Does a CV that the redistribution of grid g reads or writes lie outside the
+// near-EB set (covered, a w wall level, or at or above kfast, where the bulk
+// kernel writes it)?  One thread per table entry: pivots, members, LSQ
+// stencil pivots, affected CVs.
+__global__ void k_wsrd_reach(Dims D, int g, WsrdDev W, const int *kcov, const int *kfast, unsigned *far) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long c;
+  if (t < W.nsmall) {
+    c = W.s_plin[t];
+  } else if ((t -= W.nsmall) < 8 * W.nsmall) {
+    if (t % 8 >= W.s_nmem[t / 8]) return;
+    c = W.s_mlin[t];
+  } else if ((t -= 8 * W.nsmall) < W.nlsq) {
+    c = W.l_plin[t];
+  } else if ((t -= W.nlsq) < W.naff) {
+    c = W.a_lin[t];
+  } else {
+    return;
+  }
+  const long long col = c % D.nxy;
+  const int k = (int)(c / D.nxy);
+  const bool wall = g == 3 && (k == 0 || k == D.nz);
+  if (wall || k < kcov[col] || k >= kfast[col]) atomicOr(far, 1u);
+}
+
 }  // namespace
 
 #define CK(x)                         \
@@ -578,4 +603,10 @@ void free_wsrd(WsrdDev &W) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   W = WsrdDev();
+}
+
+void launch_wsrd_reach(const Dims &D, int g, const WsrdDev &W, const int *kcov, const int *kfast, unsigned *far,
+                       cudaStream_t s) {
+  const long long n = 9 * W.nsmall + W.nlsq + W.naff;
+  if (n > 0) k_wsrd_reach<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(D, g, W, kcov, kfast, far);
 }

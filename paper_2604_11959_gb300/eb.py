@@ -57,7 +57,7 @@ class GeomInfo(ctypes.Structure):
                 ("tiny_cvs", ctypes.c_int64 * 4), ("fast_cells", ctypes.c_int64),
                 ("min_alpha", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("slab_levels", ctypes.c_int64),
-                ("bulk_high_priority", ctypes.c_int64)]
+                ("bulk_high_priority", ctypes.c_int64), ("wsrd_beside_bulk", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
