@@ -127,8 +127,9 @@ typedef struct {
   int64_t bulk_high_priority; /* 1: the bulk kernel runs on a stream of the
                                highest priority beside the near-EB kernels    */
   int64_t wsrd_beside_bulk; /* 1: every CV the redistribution reads or writes
-                               is a near-EB CV, so it runs right after the
-                               near-EB kernels, beside the bulk kernel        */
+                               is a near-EB CV, so eb_step runs it right after
+                               the near-EB kernels, beside the bulk kernel
+                               (ensembles keep it after the bulk kernel)      */
 } eb_geom_info_t;
 
 /*

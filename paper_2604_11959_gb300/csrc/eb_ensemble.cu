@@ -62,7 +62,7 @@ void member_stage(eb_ensemble e, int q, int from, cudaStream_t s) {
     src[f] = e->field(from, q, f);
     dst[f] = e->field(1 - from, q, f);
   }
-  stage<T>(e->m[q], src, src, dst, e->dt[q], 0, s);
+  stage<T>(e->m[q], src, src, dst, e->dt[q], 0, s, false);
 }
 
 // One step of every member, buffer `from` to 1 - from, captured as a graph

@@ -268,14 +268,16 @@ void wsrd_all(eb_geom g, void *const out[5], cudaStream_t s) {
 }
 
 // One stage: flux update, then redistribution.  When every CV the
-// redistribution reads or writes is a near-EB CV (checked at set-up), it
-// follows the near-EB kernels on the side stream, beside the bulk kernel;
-// otherwise it follows the join.
+// redistribution reads or writes is a near-EB CV (checked at set-up) and the
+// caller allows it, it follows the near-EB kernels on the side stream, beside
+// the bulk kernel; otherwise it follows the join.  (Ensembles keep it after
+// the join: their members already fill the GPU side by side, and the longer
+// branches cost more than the shorter critical path gains.)
 template <typename T>
 void stage(eb_geom g, void *const src[5], void *const base[5], void *const out[5], double dt, int copy,
-           cudaStream_t s) {
+           cudaStream_t s, bool wsrd_beside = true) {
   const StepArgs<T> A = step_args<T>(g, src, base, out, dt, copy);
-  if (g->wsrd_side) {
+  if (g->wsrd_side && wsrd_beside) {
     flux_update(g, A, s, [&](cudaStream_t side) { wsrd_all<T>(g, out, side); });
   } else {
     flux_update(g, A, s);

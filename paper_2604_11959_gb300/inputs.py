@@ -215,12 +215,13 @@ class Workload:
     seed: int = 0
     hmax: float = 0.15
     tiny: int = 0
+    sigma: float = 0.08
 
     def heights(self):
         if self.terrain == "woa":
             return woa_ridge(self.nx, self.ny, self.Lx)
         if self.terrain == "gaussian":
-            return gaussian_hill(self.nx, self.ny, self.Lx, self.Ly, h0=self.hmax)
+            return gaussian_hill(self.nx, self.ny, self.Lx, self.Ly, h0=self.hmax, sigma=self.sigma)
         if self.terrain == "grf":
             h = grf_terrain(self.nx, self.ny, self.seed, hmax=self.hmax)
             if self.tiny:

@@ -41,7 +41,16 @@ CASES = {
     # the smallest grids: stencils wrap around the periodic boundaries several
     # times, one ragged tile holds the whole domain
     "tiny": (inputs.Workload("grf-6x5x4", 6, 5, 4, 3, terrain="grf", seed=11, hmax=0.2), None),
+    # a steep, narrow hill (about ten levels per column): cut regions several
+    # levels deep, so the redistribution reaches CVs the bulk kernel writes and
+    # has to wait for it
+    "steep": (inputs.Workload("steep-hill-32x32x32", 32, 32, 32, 3, terrain="gaussian", hmax=0.25, sigma=0.03), None),
 }
+
+# where every CV the redistribution touches is a near-EB CV, eb_step runs it
+# beside the bulk kernel (set-up check); the steep hill is the case where it
+# cannot
+WSRD_BESIDE_BULK = {"woa": None, "grf": None, "hill": 1, "odd": None, "tiny": None, "steep": 0}
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
@@ -171,6 +180,19 @@ def test_steps_match(eb, case, oracle, precision, stages, kind):
         static = ~act[g]
         ref_in = to_host(to_device({k: U[k] for k in FIELDS}, precision, refs), refs)[f]
         assert np.array_equal(got[f][static], ref_in[static]), (name, f)
+
+
+def test_redistribution_schedule(eb, case):
+    """The set-up check that lets the redistribution run beside the bulk kernel
+    gives the expected answer on the cases where it is known; the steps of
+    every case match the oracle either way (test_steps_match)."""
+    name, w, h, dom, G, T = case
+    geom = make_geometry(eb, w, h, "f64", refs_for(w.nz, w.Lz))
+    flag = geom.info()["wsrd_beside_bulk"]
+    assert flag in (0, 1)
+    if WSRD_BESIDE_BULK[name] is not None:
+        assert flag == WSRD_BESIDE_BULK[name], (name, flag)
+    geom.close()
 
 
 def test_deterministic(eb):
