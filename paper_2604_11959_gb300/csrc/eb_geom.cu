@@ -622,7 +622,6 @@ __global__ void k_export_geometry(const double *h, Dims D, int g, GridDev G, int
       }
     } else if (field <= EB_X_EBC_Z) {
       double vals[20];
-      bool have = true;
       if (wall) {
         cv_geometry(h, D, g, i, j, k, vals);
       } else if (ci.rec >= 0) {
@@ -637,12 +636,10 @@ __global__ void k_export_geometry(const double *h, Dims D, int g, GridDev G, int
         for (int q = 0; q < 6; ++q) vals[7 + q] = G.fcent[q * n + r];
         vals[16] = G.aeb[r];
       } else {
-        have = false;
         const bool reg = ci.flag == EBK_REGULAR;
         for (int q = 0; q < 20; ++q) vals[q] = 0.0;
         if (reg) vals[0] = vals[4] = vals[5] = vals[6] = 1.0;
       }
-      (void)have;
       // field order of the export enum: alpha, cent[3], beta[3], fcent[6], aeb, nrm[3], ebc[3]
       const int map[20] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 16, 13, 14, 15, 17, 18, 19};
       v = vals[map[field]];
