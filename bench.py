@@ -129,8 +129,9 @@ def run_anelastic(eb, steps, warmup, clk=None):
     192x192x96 random terrain, mixed path; and one projection timed alone
     with each preconditioner.  Algorithmic traffic per PCG iteration: 136
     bytes per cell for the FP64 conjugate-gradient vectors (operator 48,
-    update 64, direction 24), plus 175 for the FP32 V-cycle (156 on the
-    finest level, about 1/8 more on the coarse ones)."""
+    update 64, direction 24), plus 231 for the FP32 V-cycle (212 on the
+    finest level: six sweeps of about 28 bytes each, restriction and
+    prolongation; 19 more on the coarse levels)."""
     import torch
     from paper_2604_11959_gb300 import inputs
     w = inputs.GRF_192
@@ -156,7 +157,7 @@ def run_anelastic(eb, steps, warmup, clk=None):
     cells = w.cells()
     hbm, kind = peaks()
     proj = {}
-    for pc, bpc in (("mg", 136 + 175), ("jacobi", 136)):
+    for pc, bpc in (("mg", 136 + 231), ("jacobi", 136)):
         eb.set_preconditioner(g, pc)
         eb.project(g, {f: U[f].clone() for f in U}, dt, rtol=1e-10)   # work space, warm-up
         W = {f: U[f].clone() for f in U}
