@@ -277,7 +277,7 @@ eb_status eb_project(eb_geom geom, eb_state *U, double dt, double rtol, int maxi
  *     is coarsened by 2 in every direction while all three sizes are even
  *     and at least 4, until the grid has 512 cells or fewer; a coarse face
  *     takes the mean open fraction of the four fine faces it covers and the
- *     coarse spacing; damped Jacobi sweeps (weight 0.8) before and after
+ *     coarse spacing; damped Jacobi sweeps (weight 0.9) before and after
  *     the coarse correction, three of each on the finest grid and two on the
  *     coarser ones; averaging restriction, injection prolongation,
  *     64 Jacobi sweeps on the coarsest grid.  Fewer iterations, each more

@@ -275,7 +275,12 @@ __global__ void k_correct(Op O, const double *x, double dt, T *mu, T *mv, T *mw)
 // coarsest grid: up to float rounding V is a fixed symmetric positive
 // semi-definite operator, as conjugate gradients need.
 // ---------------------------------------------------------------------------
-constexpr float MG_OMEGA = 0.8f;
+// Jacobi weight: the rows of the operator have off-diagonal magnitudes
+// summing to the diagonal, so the eigenvalues of D^-1 A lie in [0, 2] and any
+// weight below 1 keeps the smoother convergent and the V-cycle definite; 0.9
+// took the 192x192x96 random terrain's projection from 16 iterations (0.8) to
+// 13 at rtol 1e-10, 0.95 back up to 17.
+constexpr float MG_OMEGA = 0.9f;
 constexpr int MG_COARSE_SWEEPS = 64;   // even: the result ends in x
 
 // the operator of one level: S = sum_f a_f x_nb (off-diagonal part) and the
