@@ -280,7 +280,7 @@ eb_status eb_project(eb_geom geom, eb_state *U, double dt, double rtol, int maxi
  *     coarse spacing; damped Jacobi sweeps (weight 0.9) before and after
  *     the coarse correction, three of each on the finest grid and two on the
  *     coarser ones; averaging restriction, injection prolongation,
- *     64 Jacobi sweeps on the coarsest grid.  Fewer iterations, each more
+ *     16 Jacobi sweeps on the coarsest grid.  Fewer iterations, each more
  *     costly; the extra device memory is about three FP64 fields.
  * Errors: EB_ERR_INVALID_ARG for another kind, or for EB_PRECOND_MG when the
  * grid cannot be coarsened at least once to a coarsest grid of at most 32768
