@@ -215,7 +215,10 @@ void wsrd_field(eb_geom g, int field, T *u, cudaStream_t s) {
 // the handle's stream of the highest priority (its CTAs, one wave of two per
 // SM, take their SMs first and the near-EB kernels fill the remaining SMs
 // meanwhile and all of them afterwards; faster where the near-EB work is
-// large).  eb_geom_tune times both.
+// large).  eb_geom_tune times both.  after_band(side) launches work that
+// follows the near-EB kernels on the side stream (the redistribution, when
+// stage allows it); both streams are joined to the caller's stream at the
+// end.
 template <typename T, typename Side>
 void flux_update(eb_geom g, const StepArgs<T> &A, cudaStream_t s, Side &&after_band) {
   cudaEventRecord(g->ev_fork, s);
