@@ -123,7 +123,41 @@ def run_warmstart(eb, terrains, epochs):
                                  "ratio": big_mg[0] / max(1, big_mg[1])}}
 
 
-def run_anelastic(eb, steps, warmup, clk=None):
+def init_ranks(world):
+    """One process per GPU under torchrun (RANK, LOCAL_RANK, WORLD_SIZE and
+    MASTER_* from the environment): the rank's GPU and a process group, NCCL
+    between GPUs and gloo where CUDA is absent (the CPU tests).  None for a
+    single process."""
+    if world <= 1:
+        return None
+    import torch
+    import torch.distributed as tdist
+    if torch.cuda.is_available():
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+    else:
+        tdist.init_process_group("gloo")
+    return tdist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(value, dist):
+    """The largest of the ranks' values: the slowest replica sets the job's
+    time.  The value itself for a single process."""
+    if dist is None:
+        return float(value)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_anelastic(eb, steps, warmup, clk=None, dist=None):
     """Anelastic steps (Algorithm 2, two stages, projection to a relative
     residual of 1e-10 from a zero guess, multigrid-preconditioned) on the
     192x192x96 random terrain, mixed path; and one projection timed alone
@@ -143,15 +177,17 @@ def run_anelastic(eb, steps, warmup, clk=None):
     U = eb.device_state(inputs.anelastic_state(w, seed=1), "mixed", refs)
     dt = w.dt()
     out, its = eb.anelastic_step(g, U, dt, max(1, warmup), rtol=1e-10)
-    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    torch.cuda.synchronize()
     with clk or contextlib.nullcontext():
         a.record(stream)
         out, its = eb.anelastic_step(g, U, dt, steps, rtol=1e-10)
         b.record(stream)
         torch.cuda.synchronize()
-    ms_step = a.elapsed_time(b) / steps
+    barrier(dist)
+    ms_step = max_over_ranks(a.elapsed_time(b) / steps, dist)
     eb.sync_status(g)
     # one projection alone with each preconditioner: the divergent momenta of the initial state
     cells = w.cells()
@@ -176,7 +212,7 @@ def run_anelastic(eb, steps, warmup, clk=None):
             "projection": proj, "workload": w.name}
 
 
-def run_ensemble(eb, steps, warmup, clk=None):
+def run_ensemble(eb, steps, warmup, clk=None, dist=None):
     """64 uneven Gaussian-hill instances (64x64x32 .. 256x256x64, 94,371,840
     cells), mixed path, advanced together: one CUDA-graph launch per step,
     slab heights chosen by the autotuner.  Like the single-domain line, every
@@ -211,6 +247,7 @@ def run_ensemble(eb, steps, warmup, clk=None):
         ens.step(dts, 1)
     stream = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier(dist)
     torch.cuda.synchronize()
     with clk or contextlib.nullcontext():
         for q in range(steps):
@@ -219,7 +256,8 @@ def run_ensemble(eb, steps, warmup, clk=None):
             ens.step(dts, 1)
             evs[q][1].record(stream)
         torch.cuda.synchronize()
-    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    barrier(dist)
+    ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in evs])), dist)
     for g in geoms:
         eb.sync_status(g)
     # the dominant kernel: each member's bulk kernel timed alone
@@ -442,8 +480,7 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=
     eb.sync_status(geom)
     stream = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    if dist:
-        dist.barrier()
+    barrier(dist)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     with clk or contextlib.nullcontext():
@@ -453,16 +490,11 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=
             eb.step(geom, A, dt, 1, out=outs[q % 2])
             evs[q][1].record(stream)
         torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    barrier(dist)
     wall = time.perf_counter() - wall0
     ms = [a.elapsed_time(b) for a, b in evs]
     eb.sync_status(geom)
-    ms_step = float(np.mean(ms))
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(float(np.mean(ms)), dist)
     # the dominant kernel alone, timed with events on its stream
     prof = []
     for q in range(max(5, min(steps, 20))):
@@ -612,6 +644,17 @@ def main():
                                   "d2h_bytes_per_step": 0}}))
         return 0
     import torch
+    dist = init_ranks(world)
+    try:
+        return run_arm(args, rank, world, w, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+def run_arm(args, rank, world, w, dist):
+    """Our arm, every workload: one JSON line from rank 0."""
+    import torch
     if args.workload == "warmstart":
         from paper_2604_11959_gb300 import build as libbuild, eb
         libbuild.build()
@@ -627,7 +670,7 @@ def main():
         libbuild.build()
         eb.load()
         clk = ClockSampler(torch.cuda.current_device())
-        r = run_anelastic(eb, args.steps, args.warmup, clk)
+        r = run_anelastic(eb, args.steps, args.warmup, clk, dist)
         if rank == 0:
             print(json.dumps({
                 "metric": METRIC, "value": r["value"] * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -646,7 +689,7 @@ def main():
         libbuild.build()
         eb.load()
         clk = ClockSampler(torch.cuda.current_device())
-        r = run_ensemble(eb, args.steps, max(3, args.warmup), clk)
+        r = run_ensemble(eb, args.steps, max(3, args.warmup), clk, dist)
         if rank == 0:
             print(json.dumps({
                 "metric": METRIC, "value": r["value"] * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -661,13 +704,6 @@ def main():
                 "roofline": r["roofline"], "gpu_launches": r["gpu_launches"], "clocks": clk.summary(),
                 "cpu_baseline": None, "e2e": None}))
         return 0
-    dist = None
-    if world > 1:
-        import torch.distributed as tdist
-        local = int(os.environ.get("LOCAL_RANK", "0"))
-        torch.cuda.set_device(local)
-        tdist.init_process_group("nccl")
-        dist = tdist
     from paper_2604_11959_gb300 import build as libbuild, eb, inputs
     libbuild.build()
     eb.load()
@@ -693,8 +729,6 @@ def main():
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline(w)
-    if dist:
-        dist.destroy_process_group()
     if rank != 0:
         return 0
     head = mixed or f64
