@@ -242,6 +242,7 @@ def run_ensemble(eb, steps, warmup, clk=None, dist=None):
 
     reload()
     slab = ens.tune(dts, reps=2)
+    prio = int(geoms[0].info()["bulk_high_priority"])
     for _ in range(warmup):
         reload()
         ens.step(dts, 1)
@@ -272,7 +273,7 @@ def run_ensemble(eb, steps, warmup, clk=None, dist=None):
     achieved = fast_bytes / (bulk_ms * 1e-3) / 1e9
     launches = 7 * len(geoms)   # per member and step: bulk, 3 near-EB, 3 redistribution kernels
     return {"value": cells / (ms * 1e-3), "ms_per_step": ms, "cells": cells, "members": len(geoms),
-            "slab_levels": slab,
+            "slab_levels": slab, "bulk_high_priority": prio,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": None, "kernel": "k_fast_tiled (each member alone, summed)",
                          "algorithmic_bytes_per_launch": fast_bytes, "peak_kind": kind},
@@ -697,6 +698,7 @@ def run_arm(args, rank, world, w, dist):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": "ensemble-64-gaussian-hills", "cells": r["cells"], "members": r["members"],
                            "precision": "mixed", "stages": 1, "tuned_slab_levels": r["slab_levels"],
+                           "tuned_bulk_high_priority": r["bulk_high_priority"],
                            "launch": "one CUDA-graph launch per step of all members",
                            "l2": "the same input states (3.8 GB, larger than L2) reloaded untimed before every "
                                  "timed step; per-step CUDA events",

@@ -398,10 +398,12 @@ eb_status eb_ensemble_get_state(eb_ensemble e, int member, eb_state *U, void *st
 eb_status eb_ensemble_step(eb_ensemble e, const double *dt, int nsteps, void *stream);
 
 /* Autotuner: times 2 * reps ensemble steps for each candidate slab height
- * of the bulk kernel's tiles (automatic, 8 .. 64 levels, whole column) and
- * keeps the fastest for every member; *slab_levels (if not NULL) receives it
- * (0 = automatic).  The loaded states are restored afterwards.  Synchronises
- * the stream; allocates a temporary copy of the states. */
+ * of the bulk kernel's tiles (automatic, 8 .. 64 levels, whole column), each
+ * with every member's bulk kernel at the same and at a higher stream priority
+ * (eb_geom_set_bulk_priority), and keeps the fastest pair for every member;
+ * *slab_levels (if not NULL) receives the height (0 = automatic).  Results do
+ * not depend on either.  The loaded states are restored afterwards.
+ * Synchronises the stream; allocates a temporary copy of the states. */
 eb_status eb_ensemble_tune(eb_ensemble e, const double *dt, int reps, int *slab_levels, void *stream);
 
 /* Waits for the device, then frees the ensemble's buffers. */
