@@ -426,7 +426,9 @@ eb_status eb_geom_tune(eb_geom geom, const eb_state *U, double dt, int reps, int
  * high = 1: the bulk kernel runs on a handle stream of the highest priority,
  * so that its CTAs take their SMs before the near-EB kernels' blocks; this
  * pays where the near-EB work is large (rough terrain).  Default 0;
- * eb_geom_tune chooses.  EB_ERR_INVALID_ARG for another value. */
+ * eb_geom_tune chooses.  An ensemble that has already captured its step
+ * graph keeps the schedule it captured until it is tuned again.
+ * EB_ERR_INVALID_ARG for another value. */
 eb_status eb_geom_set_bulk_priority(eb_geom geom, int high);
 
 /* Sets the bulk kernel's slab height directly (0 = automatic; heights above
