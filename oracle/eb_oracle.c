@@ -997,10 +997,11 @@ static double lsq_gradient(const OrcDomain *D, int g, const OrcGeom *Gg, const O
  * update is written as U_i = P_i + (1/N_i) sum_{r in W-_i} kappa_r
  * (q_r(x_i) - P_i) with P_i = q_i(x_i), which is Eq. final_update_omega
  * because omega_i = 1 - (1/N_i) sum kappa_r (Eq. omega).  If sigma_out /
- * phi_out are not NULL they receive the limited gradient (3n) and the limiter
- * factor (n, 1 where no gradient was fitted). */
+ * phi_out / qhat_out are not NULL they receive the limited gradient (3n), the
+ * limiter factor (n, 1 where no gradient was fitted) and the neighbourhood
+ * average Qhat of every CV (n; Uhat itself where the CV is not small). */
 int orc_wsrd_apply(const OrcDomain *D, int g, const OrcGeom *Gg, const OrcWsrd *W, const double *Uh, double *Un,
-                   double *sigma_out, double *phi_out) {
+                   double *sigma_out, double *phi_out, double *qhat_out) {
   long n = ncv(D, g);
   int nzg = nzg_of(D, g);
   long *piv = malloc(sizeof(long) * (size_t)n);
@@ -1097,6 +1098,8 @@ int orc_wsrd_apply(const OrcDomain *D, int g, const OrcGeom *Gg, const OrcWsrd *
         else Un[id] = Uh[id] + acc / W->nnb[id];
       }
   if (sigma_out) memcpy(sigma_out, sg, sizeof(double) * (size_t)n * 3);
+  if (qhat_out)
+    for (long c = 0; c < n; c++) qhat_out[c] = Uh[piv[c]] + Dv[c];
   free(piv);
   free(Dv);
   free(sg);
@@ -1117,7 +1120,7 @@ int orc_stage(const OrcDomain *D, const OrcGeom *G, const OrcWsrd *W, const OrcS
     double *hat = scratch->f[f];
     for (long c = 0; c < n; c++) hat[c] = Ubase->f[f][c] + dt * hat[c];
     /* covered and non-prognostic CVs keep their value: dU is zero there */
-    orc_wsrd_apply(D, g, &G[g], &W[g], hat, Uout->f[f], NULL, NULL);
+    orc_wsrd_apply(D, g, &G[g], &W[g], hat, Uout->f[f], NULL, NULL, NULL);
   }
   return 0;
 }

@@ -81,7 +81,7 @@ def _load():
             lib.orc_wsrd_setup.argtypes = [P(_Domain), ctypes.c_int, P(_Geom), ctypes.c_double, P(_Wsrd)]
             lib.orc_flux_div.argtypes = [P(_Domain), P(_Geom), P(_State), P(_State)]
             lib.orc_wsrd_apply.argtypes = [P(_Domain), ctypes.c_int, P(_Geom), P(_Wsrd), ctypes.c_void_p,
-                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_stage.argtypes = [P(_Domain), P(_Geom), P(_Wsrd), P(_State), P(_State), ctypes.c_double,
                                       P(_State), P(_State)]
             _lib = lib
@@ -191,7 +191,10 @@ def flux_div(dom: Domain, geom: dict, U: dict) -> dict:
 
 
 def wsrd(dom: Domain, geom: dict, tabs: dict, g: int, Uhat: np.ndarray, diag: bool = False):
-    """Redistribution of one field on grid g (Eqs. qhat_omega .. final_update_omega)."""
+    """Redistribution of one field on grid g (Eqs. qhat_omega .. final_update_omega).
+    With ``diag`` also the limited slopes sigma (3, ...), the limiter factors
+    phi and the neighbourhood averages Qhat of every CV (Uhat where the CV is
+    not small)."""
     lib = _load()
     Uhat = np.ascontiguousarray(Uhat, dtype=np.float64)
     assert Uhat.shape == dom.shape(g)
@@ -201,10 +204,11 @@ def wsrd(dom: Domain, geom: dict, tabs: dict, g: int, Uhat: np.ndarray, diag: bo
     cw = _Wsrd(*(_ptr(T[k]) for k in ("code", "nnb", "kappa", "omega", "vhat", "xhat")))
     sig = np.zeros((3,) + Uhat.shape) if diag else None
     phi = np.zeros(Uhat.shape) if diag else None
+    qh = np.zeros(Uhat.shape) if diag else None
     lib.orc_wsrd_apply(ctypes.byref(dom._c), g, ctypes.byref(cg[g]), ctypes.byref(cw), _ptr(Uhat), _ptr(out),
-                       _ptr(sig) if diag else None, _ptr(phi) if diag else None)
+                       _ptr(sig) if diag else None, _ptr(phi) if diag else None, _ptr(qh) if diag else None)
     if diag:
-        return out, sig, phi
+        return out, sig, phi, qh
     return out
 
 

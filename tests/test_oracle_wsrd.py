@@ -178,7 +178,7 @@ def test_linearity_preserved(hill, oracle):
         k, j, i = np.meshgrid(np.arange(s[0]), np.arange(s[1]), np.arange(s[2]), indexing="ij")
         pos = np.stack([i, j, k]).astype(float) + G[g]["cent"]
         f = 2.0 + np.tensordot(grad, pos, axes=1)
-        U, sig, phi = oracle.wsrd(dom, G, T, g, f, diag=True)
+        U, sig, phi, _ = oracle.wsrd(dom, G, T, g, f, diag=True)
         act = active_mask(dom, G, g)
         small = act & (T[g]["code"] > 0)
         exact = small & np.all(np.abs(sig - grad[:, None, None, None]) < 1e-10, axis=0)
@@ -207,7 +207,7 @@ def test_small_cell_alone(hill, oracle):
     rng = np.random.default_rng(5)
     for g in range(4):
         Uh = rng.uniform(0, 1, dom.shape(g))
-        U, sig, phi = oracle.wsrd(dom, G, T, g, Uh, diag=True)
+        U, sig, phi, _ = oracle.wsrd(dom, G, T, g, Uh, diag=True)
         t = T[g]
         act = active_mask(dom, G, g)
         sel = act & (t["code"] > 0) & (t["nnb"] == 1)
