@@ -153,6 +153,28 @@ typedef struct {
 eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision prec, const double *ref_rho,
                         const double *ref_rhotheta, void *stream, eb_geom *out);
 
+/*
+ * Background momentum profile of the state (Sec. 2: the reference /
+ * perturbation split of the governing equations, carried over to the
+ * horizontal momenta of a prescribed background wind).  After this call the
+ * rho*u and rho*v arguments of eb_flux_div, eb_wsrd, eb_wsrd_noalloc,
+ * eb_step, eb_step_profile, eb_geom_tune and the eb_ensemble_* calls hold
+ * values minus ref_rhou[k] (ref_rhov[k]) at cell-centre level k, as rho and
+ * rho*theta do for ref_rho and ref_rhotheta.  The method is unchanged: every
+ * flux is formed from the full values, and a profile changes only how the
+ * stored numbers round (on the mixed path the float state then carries the
+ * wind's deviation from the profile, not the wind itself).  dU of
+ * eb_flux_div is the full derivative, with or without a profile.
+ *   ref_rhou, ref_rhov  device, nz doubles each, finite; NULL means zero.
+ *                       Copied during the call (the stream is synchronised
+ *                       and the device drained first).
+ * The anelastic calls (eb_project, eb_anelastic_step, eb_project_sample,
+ * eb_project_warm) need full momenta and return EB_ERR_STATE on a handle
+ * with a nonzero profile.  Setting both to NULL (or zeros) restores full
+ * values.
+ */
+eb_status eb_geom_set_wind_reference(eb_geom geom, const double *ref_rhou, const double *ref_rhov, void *stream);
+
 /* Free everything the handle owns (synchronises the device).  NULL is OK. */
 eb_status eb_geom_destroy(eb_geom geom);
 
@@ -212,8 +234,11 @@ eb_status eb_wsrd(eb_geom geom, eb_field field, const void *Uhat, void *Unew, vo
  * handle's device current.  That first call therefore belongs before any
  * stream capture and outside any section that must not touch the driver;
  * later calls only launch kernels (and one device-to-device copy when Uhat
- * and Unew differ).  The current device must be the handle's device
- * (EB_ERR_INVALID_ARG otherwise).
+ * and Unew differ).  The address is cached per device and per CUDA context:
+ * after the device's context is destroyed and created again (cudaDeviceReset)
+ * the next call looks it up again, and is then a first call in the sense
+ * above.  Handles themselves do not survive a device reset.  The current
+ * device must be the handle's device (EB_ERR_INVALID_ARG otherwise).
  *
  * Races: there is ONE scratch block per device, shared by every handle and
  * every thread.  Two calls whose work may overlap on the device (different
@@ -445,6 +470,18 @@ const char *eb_last_error(void);
 
 /* Library version as major*10000 + minor*100 + patch. */
 int eb_version(void);
+
+/*
+ * Benchmark instrument (no counterpart in the paper): the measured rate of
+ * independent fused multiply-adds on the current device, the denominator of
+ * the arithmetic roofline of a kernel bound by one arithmetic type.
+ *   kind    0 FP64 (DFMA), 1 FP32 (FFMA), 2 packed FP32x2 (FFMA2)
+ *   gflops  host; receives the best of three timed launches (after one
+ *           untimed), an FMA counted as two flops (four for FFMA2)
+ * Allocates a small device buffer, launches on the stream and synchronises
+ * it.  EB_ERR_INVALID_ARG for another kind.
+ */
+eb_status eb_fma_peak(int kind, double *gflops, void *stream);
 
 #ifdef __cplusplus
 }

@@ -383,6 +383,8 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
   CUDA_TRY(cudaEventCreateWithFlags(&g->ev_join_bulk, cudaEventDisableTiming), "event");
   CUDA_TRY(fill_ref<double>(g, ref_rho, &g->ref_d[0], &g->ref_f[0], s), "reference");
   CUDA_TRY(fill_ref<double>(g, ref_rt, &g->ref_d[1], &g->ref_f[1], s), "reference");
+  CUDA_TRY(fill_ref<double>(g, nullptr, &g->ref_d[2], &g->ref_f[2], s), "reference");
+  CUDA_TRY(fill_ref<double>(g, nullptr, &g->ref_d[3], &g->ref_f[3], s), "reference");
   CUDA_TRY(g->alloc(&g->status, 1), "alloc status");
   CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(unsigned), s), "memset status");
   // host-side counts for eb_geom_info
@@ -458,17 +460,49 @@ namespace {
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[kNoallocMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kNoallocMaxDevices] = {};
+
+// Unique id of the calling thread's current CUDA context (never reused within
+// the process, unlike a context handle), through the driver entry points that
+// the runtime hands out, so the library needs no link to libcuda.  0 when the
+// driver does not provide it.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void **);
+  using GetId = int (*)(void *, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *a = nullptr, *b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+        qa == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+        qb == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<GetCurrent>(a);
+      get_id = reinterpret_cast<GetId>(b);
+    }
+  });
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 // Device address of the fixed scratch on `device`, which must be current.
-// Looked up once per device; later calls read the cached pointer.
+// Looked up once per device and context: a context torn down and created
+// again (cudaDeviceReset by the application or another library) loads the
+// library's device image afresh, so its address is looked up again.
 eb_status noalloc_scratch(int device, void **out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (device < 0 || device >= kNoallocMaxDevices) return fail(EB_ERR_INVALID_ARG, "device index out of range");
-  if (!g_noalloc_addr[device]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_noalloc_addr[device] || ctx == 0 || ctx != g_noalloc_ctx[device]) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_wsrd_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "address of the fixed redistribution scratch");
     g_noalloc_addr[device] = p;
+    g_noalloc_ctx[device] = ctx;
   }
   *out = g_noalloc_addr[device];
   return EB_OK;
@@ -486,7 +520,7 @@ void wsrd_field_scratch(eb_geom g, int field, T *u, char *scratch, cudaStream_t 
   R.D = g->D;
   R.W = g->W[grid];
   R.u = u;
-  R.refd = field <= 1 ? g->ref_d[field] : nullptr;
+  R.refd = field <= 3 ? g->ref_d[field] : nullptr;
   R.dev = (T *)scratch;
   R.pval = (T *)(scratch + one);
   R.sig = (T *)(scratch + 2 * one);
@@ -751,6 +785,41 @@ eb_status eb_geom_set_slab_levels(eb_geom geom, int slab_levels) {
   if (slab_levels < 0) return fail(EB_ERR_INVALID_ARG, "slab_levels must be >= 0");
   CUDA_TRY(cudaDeviceSynchronize(), "drain before re-planning");
   return eb_replan_bulk(geom, slab_levels);
+}
+
+eb_status eb_geom_set_wind_reference(eb_geom geom, const double *ref_rhou, const double *ref_rhov, void *stream) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  const int nz = geom->D.nz;
+  cudaStream_t s = as_stream(stream);
+  std::vector<double> hv[2];
+  const double *src[2] = {ref_rhou, ref_rhov};
+  bool nonzero = false;
+  for (int q = 0; q < 2; ++q) {
+    hv[q].assign(nz, 0.0);
+    if (src[q]) {
+      if ((uintptr_t)src[q] % 8) return fail(EB_ERR_INVALID_ARG, "reference profile pointer misaligned");
+      CUDA_TRY(cudaMemcpyAsync(hv[q].data(), src[q], sizeof(double) * nz, cudaMemcpyDeviceToHost, s),
+               "read momentum profile");
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(s), "read momentum profile");
+  for (int q = 0; q < 2; ++q)
+    for (int k = 0; k < nz; ++k) {
+      if (!isfinite(hv[q][k])) return fail(EB_ERR_INVALID_ARG, "momentum profile holds a non-finite value");
+      nonzero = nonzero || hv[q][k] != 0.0;
+    }
+  // the handle's work on its own streams reads the profiles: let it finish
+  CUDA_TRY(cudaDeviceSynchronize(), "drain before replacing the momentum profile");
+  for (int q = 0; q < 2; ++q) {
+    std::vector<float> hf(nz);
+    for (int k = 0; k < nz; ++k) hf[k] = (float)hv[q][k];
+    CUDA_TRY(cudaMemcpy(geom->ref_d[2 + q], hv[q].data(), sizeof(double) * nz, cudaMemcpyHostToDevice),
+             "write momentum profile");
+    CUDA_TRY(cudaMemcpy(geom->ref_f[2 + q], hf.data(), sizeof(float) * nz, cudaMemcpyHostToDevice),
+             "write momentum profile");
+  }
+  geom->has_wind_ref = nonzero;
+  return EB_OK;
 }
 
 eb_status eb_geom_set_bulk_priority(eb_geom geom, int high) {

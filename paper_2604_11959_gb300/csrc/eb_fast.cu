@@ -290,11 +290,14 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
     // face fluxes (x 6) through the low x and y faces of the column pair at
     // even tile x, row y of level p, all four grids: each momentum and
     // primitive value is read from shared memory once
-    auto faces = [&](const T *Rk, const T *Rkm, int x, int y, P fxo[4], P fyo[4]) {
+    auto faces = [&](const T *Rk, const T *Rkm, int x, int y, T ru, T rv, T rum, T rvm, P fxo[4], P fyo[4]) {
       const int c = TL::ri(x, y);
       const T *U = Rk + 2 * NP, *Vv = Rk + 3 * NP;
-      const P uc = ld2(U + c), ul = ld2(U + c - 2), ud = ld2(U + c - PX), ub = ld2(Rkm + 2 * NP + c);
-      const P vc = ld2(Vv + c), vl = ld2(Vv + c - 2), vd = ld2(Vv + c - PX), vkm = ld2(Rkm + 3 * NP + c);
+      const P pru = splat(ru), prv = splat(rv);
+      const P uc = padd(ld2(U + c), pru), ul = padd(ld2(U + c - 2), pru), ud = padd(ld2(U + c - PX), pru),
+              ub = padd(ld2(Rkm + 2 * NP + c), splat(rum));
+      const P vc = padd(ld2(Vv + c), prv), vl = padd(ld2(Vv + c - 2), prv), vd = padd(ld2(Vv + c - PX), prv),
+              vkm = padd(ld2(Rkm + 3 * NP + c), splat(rvm));
       const P mx[4] = {uc, pmul(padd(mk(ul.y, uc.x), uc), half), pmul(padd(ud, uc), half), pmul(padd(ub, uc), half)};
       const P my[4] = {vc, pmul(padd(mk(vl.y, vc.x), vc), half), pmul(padd(vd, vc), half), pmul(padd(vkm, vc), half)};
 #pragma unroll
@@ -307,8 +310,11 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
     };
     auto ref_r = [&](int L) -> T { return (L >= 0 && L < nz) ? A.src.ref_rho[L] : T(0); };
     auto ref_t = [&](int L) -> T { return (L >= 0 && L < nz) ? A.src.ref_rt[L] : T(0); };
+    auto ref_u = [&](int L) -> T { return (L >= 0 && L < nz) ? A.src.ref_u[L] : T(0); };
+    auto ref_v = [&](int L) -> T { return (L >= 0 && L < nz) ? A.src.ref_v[L] : T(0); };
     const int p0 = kbeg - 2, p1 = kend + 1;
     T rr_m = ref_r(p0 - 1), rr_p = ref_r(p0), rt_p = ref_t(p0);
+    T ru_m = ref_u(p0 - 1), ru_p = ref_u(p0), rv_m = ref_v(p0 - 1), rv_p = ref_v(p0);
 
     // prologue: raw levels p0 - 1, p0 landed, p0 + 1 in flight
     request(p0 - 1);
@@ -330,7 +336,7 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
 
     for (int p = p0; p <= p1; ++p, cidx += D.nxy) {
       const int k = p - 2;
-      const T rr_n = ref_r(p + 1), rt_n = ref_t(p + 1);
+      const T rr_n = ref_r(p + 1), rt_n = ref_t(p + 1), ru_n = ref_u(p + 1), rv_n = ref_v(p + 1);
       // ---- phase 1: primitive plane of level p
       if (p < nz) {
         const T *R = RAWP(p), *Rm = RAWP(p - 1);
@@ -345,8 +351,8 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
           const P rhod = padd(ld2(R + c - PX), rrp);
           const P rhob = padd(ld2(Rm + c), splat(rr_m));
           st2(Q, pmul(padd(ld2(R + NP + c), splat(rt_p)), prcp(rho)));
-          st2(Q + NQ, pmul(ld2(R + 2 * NP + c), prcp(pmul(padd(rhol, rho), half))));
-          st2(Q + 2 * NQ, pmul(ld2(R + 3 * NP + c), prcp(pmul(padd(rhod, rho), half))));
+          st2(Q + NQ, pmul(padd(ld2(R + 2 * NP + c), splat(ru_p)), prcp(pmul(padd(rhol, rho), half))));
+          st2(Q + 2 * NQ, pmul(padd(ld2(R + 3 * NP + c), splat(rv_p)), prcp(pmul(padd(rhod, rho), half))));
           st2(Q + 3 * NQ, pmul(ld2(R + 4 * NP + c), prcp(pmul(padd(rhob, rho), half))));
         }
       }
@@ -387,7 +393,7 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
       P fx[4], fy[4];
       if (face_level) {
         const T *Rk = RAWP(p), *Rkm = RAWP(p - 1);
-        faces(Rk, Rkm, 2 * tx, ty, fx, fy);
+        faces(Rk, Rkm, 2 * tx, ty, ru_p, rv_p, ru_m, rv_m, fx, fy);
 #pragma unroll
         for (int G = 0; G < 4; ++G) {
           FX[G * TL::NFX + ty * TL::FXW + tx] = fx[G].x;
@@ -397,9 +403,11 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
           const int G0 = 2 * ty;
           const int c = TL::ri(2 * tx, TY);
           const T *Vv = Rk + 3 * NP;
-          const P vc = ld2(Vv + c);
-          const P mA = ty ? pmul(padd(ld2(Vv + c - PX), vc), half) : vc;
-          const P mB = pmul(padd(ty ? ld2(Rkm + 3 * NP + c) : mk(Vv[c - 1], vc.x), vc), half);
+          const P prv = splat(rv_p);
+          const P vc = padd(ld2(Vv + c), prv);
+          const P mA = ty ? pmul(padd(padd(ld2(Vv + c - PX), prv), vc), half) : vc;
+          const P mB =
+              pmul(padd(ty ? padd(ld2(Rkm + 3 * NP + c), splat(rv_m)) : mk(Vv[c - 1] + rv_p, vc.x), vc), half);
           const T *Q = prim + G0 * NQ + TL::qi(2 * tx, TY);
           const P fA = flux6(mA, ld2(Q - 2 * QX), ld2(Q - QX), ld2(Q), ld2(Q + QX));
           Q += NQ;
@@ -410,9 +418,9 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
           const int hi = ty - (TY - 2), G0 = 2 * hi;
           const int c = TL::ri(TX, tx);
           const T *U = Rk + 2 * NP;
-          const T u0 = U[c];
-          const T mA = hi ? T(0.5) * (U[c - PX] + u0) : u0;
-          const T mB = T(0.5) * ((hi ? Rkm[2 * NP + c] : U[c - 1]) + u0);
+          const T u0 = U[c] + ru_p;
+          const T mA = hi ? T(0.5) * ((U[c - PX] + ru_p) + u0) : u0;
+          const T mB = T(0.5) * ((hi ? Rkm[2 * NP + c] + ru_m : U[c - 1] + ru_p) + u0);
           const T *Q = prim + G0 * NQ + TL::qi(TX, tx);
           FX[G0 * TL::NFX + tx * TL::FXW + NPX] =
               flux6(splat(mA), splat(Q[-2]), splat(Q[-1]), splat(Q[0]), splat(Q[1])).x;
@@ -553,6 +561,10 @@ __global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_f
       rr_m = rr_p;
       rr_p = rr_n;
       rt_p = rt_n;
+      ru_m = ru_p;
+      ru_p = ru_n;
+      rv_m = rv_p;
+      rv_p = rv_n;
     }
     copy_wait<0>();
     __syncthreads();   // the next march reuses the shared ring

@@ -90,8 +90,11 @@ struct eb_geom_s {
   int kcov_max = 0;
   GridDev G[4];
   WsrdDev W[4];
-  double *ref_d[2] = {nullptr, nullptr};
-  float *ref_f[2] = {nullptr, nullptr};
+  // per-level reference profiles (zeros where none was given): rho0,
+  // rho0*theta0, and the background momenta of rho*u and rho*v; states hold
+  // each field minus its profile
+  double *ref_d[4] = {nullptr, nullptr, nullptr, nullptr};
+  float *ref_f[4] = {nullptr, nullptr, nullptr, nullptr};
   double *zero_d = nullptr;
   float *zero_f = nullptr;
   unsigned *status = nullptr;
@@ -109,7 +112,8 @@ struct eb_geom_s {
   void *scr[4][5] = {};
   std::vector<void *> allocs;
   eb_geom_info_t info;
-  bool has_ref = false;   // built with a reference profile
+  bool has_ref = false;        // built with a reference profile
+  bool has_wind_ref = false;   // a nonzero background momentum profile was set
   ProjWork pw;
 
   template <typename P>
@@ -176,9 +180,13 @@ StepArgs<T> step_args(eb_geom g, void *const src[5], void *const base[5], void *
   if (sizeof(T) == sizeof(double)) {
     A.src.ref_rho = (const T *)g->ref_d[0];
     A.src.ref_rt = (const T *)g->ref_d[1];
+    A.src.ref_u = (const T *)g->ref_d[2];
+    A.src.ref_v = (const T *)g->ref_d[3];
   } else {
     A.src.ref_rho = (const T *)g->ref_f[0];
     A.src.ref_rt = (const T *)g->ref_f[1];
+    A.src.ref_u = (const T *)g->ref_f[2];
+    A.src.ref_v = (const T *)g->ref_f[3];
   }
   A.dt = dt;
   A.dtT = (T)dt;
@@ -200,7 +208,7 @@ void wsrd_field(eb_geom g, int field, T *u, cudaStream_t s) {
   R.D = g->D;
   R.W = g->W[grid];
   R.u = u;
-  R.refd = field <= 1 ? g->ref_d[field] : nullptr;
+  R.refd = field <= 3 ? g->ref_d[field] : nullptr;
   R.dev = (T *)g->qhat;
   R.sig = (T *)g->sig;
   R.pval = (T *)g->pval;
@@ -255,7 +263,7 @@ void wsrd_all(eb_geom g, void *const out[5], cudaStream_t s) {
     R.D = g->D;
     R.W = g->W[grid];
     R.u = (T *)out[f];
-    R.refd = f <= 1 ? g->ref_d[f] : nullptr;
+    R.refd = f <= 3 ? g->ref_d[f] : nullptr;
     R.dev = (T *)g->qhat5 + os;
     R.pval = (T *)g->pval5 + os;
     R.sig = (T *)g->sig5 + 3 * os;

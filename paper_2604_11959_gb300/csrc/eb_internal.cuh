@@ -186,6 +186,7 @@ template <typename T>
 struct StateIn {
   const T *f[5];             // rho, rho*theta, rho*u, rho*v, rho*w
   const T *ref_rho, *ref_rt; // per cell level, reference added back to rho and rho*theta
+  const T *ref_u, *ref_v;    // per cell level, background momenta added back to rho*u and rho*v
 };
 
 template <typename T>
@@ -194,15 +195,9 @@ struct StateOut {
 };
 
 // ---------------------------------------------------------------------------
-// Geometry policies of the flux code.  Fast: every CV the stencil touches is
-// a regular CV (only the z range limits what exists).  Band: full lookups.
+// Geometry lookups of the near-EB code: dense per-CV flag bytes and the
+// geometry records of the cut band.
 // ---------------------------------------------------------------------------
-struct GeoFast {
-  __device__ static inline bool exists(const Dims &D, int g, int k) {
-    return k >= 0 && k < nzg_of(D, g);
-  }
-};
-
 struct GeoBand {
   const GridDev *G;   // four grids
   __device__ inline uint8_t dense(const Dims &D, int g, int i, int j, int k) const {
@@ -250,97 +245,3 @@ struct GeoBand {
     }
   }
 };
-
-// ---------------------------------------------------------------------------
-// Values entering the fluxes (Sec. 4.1)
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ inline T rho_at(const StateIn<T> &U, const Dims &D, int i, int j, int k) {
-  return U.ref_rho[k] + U.f[0][lin(D, i, j, k)];
-}
-
-template <typename T>
-__device__ inline T theta_at(const StateIn<T> &U, const Dims &D, int i, int j, int k) {
-  long long c = lin(D, i, j, k);
-  return eb_div(U.ref_rt[k] + U.f[1][c], U.ref_rho[k] + U.f[0][c]);
-}
-
-// Is CV (i,j,k) of grid g usable by a flux stencil (exists, not covered)?
-template <class Geo>
-__device__ inline bool avail(const Geo &geo, const Dims &D, int g, int i, int j, int k);
-
-template <>
-__device__ inline bool avail<GeoFast>(const GeoFast &, const Dims &D, int g, int i, int j, int k) {
-  return GeoFast::exists(D, g, k);
-}
-
-template <>
-__device__ inline bool avail<GeoBand>(const GeoBand &geo, const Dims &D, int g, int i, int j, int k) {
-  return geo.holds_fluid(D, g, i, j, k);
-}
-
-// Momentum of a face-grid CV as it enters a mass flux: zero where covered,
-// absent, or on the wall levels of w.
-template <typename T, class Geo>
-__device__ inline T mom_at(const StateIn<T> &U, const Geo &geo, const Dims &D, int g, int i, int j, int k) {
-  if (g == 3 && (k <= 0 || k >= D.nz)) return T(0);
-  if (!avail(geo, D, g, i, j, k)) return T(0);
-  return U.f[g + 1][lin(D, i, j, k)];
-}
-
-// Advected value of CV (i,j,k) of grid g (caller checked availability):
-// theta on c, the velocity on u, v, w (momentum over the mean density of
-// the non-covered cells beside the face; zero on the w walls).
-template <typename T, class Geo>
-__device__ inline T advected_at(const StateIn<T> &U, const Geo &geo, const Dims &D, int g, int i, int j, int k) {
-  if (g == 0) return theta_at(U, D, i, j, k);
-  if (g == 3 && (k <= 0 || k >= D.nz)) return T(0);
-  const int di = g == 1, dj = g == 2, dk = g == 3;
-  const bool a = avail(geo, D, 0, i - di, j - dj, k - dk);
-  const bool b = avail(geo, D, 0, i, j, k);
-  T rb;
-  if (a && b) rb = T(0.5) * (rho_at(U, D, i - di, j - dj, k - dk) + rho_at(U, D, i, j, k));
-  else if (a) rb = rho_at(U, D, i - di, j - dj, k - dk);
-  else if (b) rb = rho_at(U, D, i, j, k);
-  else return T(0);
-  return eb_div(U.f[g + 1][lin(D, i, j, k)], rb);
-}
-
-// Mass flux through the low d-face of CV (i,j,k) of grid g.
-template <typename T, class Geo>
-__device__ inline T mass_flux(const StateIn<T> &U, const Geo &geo, const Dims &D, int g, int d, int i, int j, int k) {
-  const int mg = d + 1;   // momentum grid normal to direction d
-  if (g == 0) return mom_at(U, geo, D, mg, i, j, k);
-  if (mg == g) {
-    const int di = d == 0, dj = d == 1, dk = d == 2;
-    return T(0.5) * (mom_at(U, geo, D, mg, i - di, j - dj, k - dk) + mom_at(U, geo, D, mg, i, j, k));
-  }
-  const int si = g == 1, sj = g == 2, sk = g == 3;
-  return T(0.5) * (mom_at(U, geo, D, mg, i - si, j - sj, k - sk) + mom_at(U, geo, D, mg, i, j, k));
-}
-
-// Provisional flux through the low d-face of CV (i,j,k) of grid g: mass flux
-// fm and advective flux fp = m * (third-order upwind value, or the centred
-// average when the far upstream CV is covered or beyond a wall).  The caller
-// guarantees the face is open.
-template <typename T, class Geo>
-__device__ inline void face_flux(const StateIn<T> &U, const Geo &geo, const Dims &D, int g, int d, int i, int j,
-                                 int k, T &fm, T &fp) {
-  const int di = d == 0, dj = d == 1, dk = d == 2;
-  fm = mass_flux(U, geo, D, g, d, i, j, k);
-  fp = T(0);
-  if (fm == T(0)) return;
-  const T pL = advected_at(U, geo, D, g, i - di, j - dj, k - dk);
-  const T pR = advected_at(U, geo, D, g, i, j, k);
-  T val;
-  if (fm > T(0)) {
-    const bool has = avail(geo, D, g, i - 2 * di, j - 2 * dj, k - 2 * dk);
-    const T pF = has ? advected_at(U, geo, D, g, i - 2 * di, j - 2 * dj, k - 2 * dk) : T(0);
-    val = upwind_value(fm, pF, pL, pR, T(0), has, false);
-  } else {
-    const bool has = avail(geo, D, g, i + di, j + dj, k + dk);
-    const T pF = has ? advected_at(U, geo, D, g, i + di, j + dj, k + dk) : T(0);
-    val = upwind_value(fm, T(0), pL, pR, pF, false, has);
-  }
-  fp = fm * val;
-}

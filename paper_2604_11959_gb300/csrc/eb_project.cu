@@ -696,6 +696,8 @@ void launch_correct(eb_geom g, void *const mom[3], double dt, cudaStream_t s) {
 }  // namespace
 
 eb_status eb_project_rhs(eb_geom g, void *const mom[3], double dt, double *rms, cudaStream_t s) {
+  if (g->has_wind_ref)
+    return fail(EB_ERR_STATE, "the projection needs full momenta: this handle has a background momentum profile");
   eb_status st = setup(g, s);
   if (st != EB_OK) return st;
   ProjWork &w = g->pw;
@@ -712,6 +714,8 @@ eb_status eb_project_rhs(eb_geom g, void *const mom[3], double dt, double *rms, 
 
 eb_status eb_project_impl(eb_geom g, void *const mom[3], double dt, double rtol, int maxit, const double *phi0,
                           double *phi_out, int *iters, double *relres, cudaStream_t s, bool correct) {
+  if (g->has_wind_ref)
+    return fail(EB_ERR_STATE, "the projection needs full momenta: this handle has a background momentum profile");
   eb_status st = setup(g, s);
   if (st != EB_OK) return st;
   ProjWork &w = g->pw;

@@ -220,6 +220,16 @@ __device__ inline long long step_off(const Dims &D, int dir, int x, int s) {
   return (long long)(t - x) * (dir == 0 ? 1 : D.nx);
 }
 
+// full momentum of face-grid G (1: rho*u, 2: rho*v, 3: rho*w) at state index
+// idx on level k: the stored value plus the background profile (rho*w has none)
+template <typename T, int G>
+__device__ inline T momentum(const StateIn<T> &U, long long idx, int k) {
+  if constexpr (G == 1) return U.f[2][idx] + U.ref_u[k];
+  else if constexpr (G == 2) return U.f[3][idx] + U.ref_v[k];
+  else if constexpr (G == 3) return U.f[4][idx];
+  else return T(0);   // the c grid has no momentum of its own (never called)
+}
+
 // advected value of CV (i, j, k) of grid G (state index idx): theta on the c
 // grid; on a face grid the momentum over the mean density of the non-covered
 // c-cells beside the CV, 0 when both are covered (Sec. 4.1)
@@ -239,7 +249,7 @@ __device__ inline T cv_advected(const StepArgs<T> &A, long long idx, int i, int 
   else if (a) rb = rho(ia, ka);
   else if (b) rb = rho(idx, k);
   else return T(0);
-  return eb_div(A.src.f[G + 1][idx], rb);
+  return eb_div(momentum<T, G>(A.src, idx, k), rb);
 }
 
 template <typename T, int G, int Dd, bool MASK>
@@ -271,7 +281,7 @@ __device__ inline unsigned face_flux_lean(const StepArgs<T> &A, long long c, int
     if (MG == 3 && (kk <= 0 || kk >= D.nz)) return T(0);
     const bool f = fluid(n, MG, idx, kk);
     if (MASK) return T(0);
-    return f ? A.src.f[MG + 1][idx] : T(0);
+    return f ? momentum<T, MG>(A.src, idx, kk) : T(0);
   };
   auto rho = [&](long long idx, int kk) -> T { return A.src.ref_rho[kk] + A.src.f[0][idx]; };
   // advected value of the grid-G CV t steps along Dd from the face's CV
@@ -292,7 +302,7 @@ __device__ inline unsigned face_flux_lean(const StepArgs<T> &A, long long c, int
     else if (a) rb = rho(ia, ka);
     else if (b) rb = rho(idx, kk);
     else return T(0);
-    return eb_div(A.src.f[G + 1][idx], rb);
+    return eb_div(momentum<T, G>(A.src, idx, kk), rb);
   };
   auto cv_fluid = [&](int n, int t) -> bool {
     const long long idx = c + off(Dd, crd[Dd], t);

@@ -28,7 +28,7 @@ struct WsrdArgs {
   Dims D;
   WsrdDev W;
   T *u;                // field on its grid, redistributed in place
-  const double *refd;  // per-level reference added to u (c-grid fields) or nullptr
+  const double *refd;  // per-level reference profile of the field (stored values are u - refd) or nullptr
   T *dev;              // [nsmall] deviation sums D of the neighbourhood averages
   T *pval;             // [nsmall] field value at each neighbourhood's pivot
   T *sig;              // [3 * nsmall] limited slopes

@@ -32,7 +32,8 @@ EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom
                     "eb_unet_num_params", "eb_unet_create", "eb_unet_set_params", "eb_unet_get_params",
                     "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step", "eb_unet_destroy",
                     "eb_project_sample", "eb_project_warm", "eb_geom_tune",
-                    "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner")
+                    "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
+                    "eb_geom_set_wind_reference", "eb_fma_peak")
 
 
 class EbError(RuntimeError):
@@ -114,6 +115,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_geom_set_slab_levels.argtypes = [V, I]
     lib.eb_geom_set_bulk_priority.argtypes = [V, I]
     lib.eb_project_set_preconditioner.argtypes = [V, I]
+    lib.eb_geom_set_wind_reference.argtypes = [V, V, V, V]
+    lib.eb_fma_peak.argtypes = [I, P(D), V]
     lib.eb_last_error.restype = ctypes.c_char_p
     lib.eb_version.restype = I
     for name in ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
@@ -122,7 +125,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                  "eb_ensemble_destroy", "eb_project", "eb_anelastic_step", "eb_unet_create", "eb_unet_set_params",
                  "eb_unet_get_params", "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step",
                  "eb_unet_destroy", "eb_project_sample", "eb_project_warm", "eb_geom_tune",
-                 "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner"):
+                 "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
+                 "eb_geom_set_wind_reference", "eb_fma_peak"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -155,7 +159,7 @@ class Geometry:
     (``eb_geom_build``)."""
 
     def __init__(self, nx, ny, nz, Lx, Ly, Lz, h_nodes: torch.Tensor, precision: str = "f64", ref_rho=None,
-                 ref_rhotheta=None, v_target_frac: float = 0.5, stream=None):
+                 ref_rhotheta=None, v_target_frac: float = 0.5, stream=None, ref_rhou=None, ref_rhov=None):
         lib = load()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.Lx, self.Ly, self.Lz = float(Lx), float(Ly), float(Lz)
@@ -176,6 +180,20 @@ class Geometry:
                                  refs[1].data_ptr() if refs[1] is not None else None, _stream(stream),
                                  ctypes.byref(handle)))
         self._h = handle
+        if ref_rhou is not None or ref_rhov is not None:
+            self.set_wind_reference(ref_rhou, ref_rhov, stream)
+
+    def set_wind_reference(self, ref_rhou=None, ref_rhov=None, stream=None):
+        """Background momentum profiles (``eb_geom_set_wind_reference``):
+        CUDA float64 tensors of nz values or None (zero).  Later rho*u and
+        rho*v states hold values minus the profile."""
+        for r in (ref_rhou, ref_rhov):
+            if r is not None:
+                _require_cuda(r, torch.float64, (self.nz,), "momentum profile")
+        _check(load().eb_geom_set_wind_reference(self.handle, ref_rhou.data_ptr() if ref_rhou is not None else None,
+                                                 ref_rhov.data_ptr() if ref_rhov is not None else None,
+                                                 _stream(stream)))
+        self._wind = (ref_rhou, ref_rhov)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -342,22 +360,38 @@ def set_slab_levels(geom: Geometry, levels: int) -> None:
     _check(load().eb_geom_set_slab_levels(geom.handle, int(levels)))
 
 
+def fma_peak(kind: str, stream=None) -> float:
+    """Measured fused multiply-add throughput of this GPU in GFLOP/s
+    (``eb_fma_peak``): kind "f64" (DFMA), "f32" (FFMA) or "f32x2" (packed
+    FFMA2); an FMA counts as two flops."""
+    out = ctypes.c_double(0.0)
+    _check(load().eb_fma_peak({"f64": 0, "f32": 1, "f32x2": 2}[kind], ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
 def sync_status(geom: Geometry, stream=None) -> None:
     """Raise EbError if a kernel latched a device-side error (``eb_sync_status``)."""
     _check(load().eb_sync_status(geom.handle, _stream(stream)))
 
 
+# fields that carry a per-level profile, in the order of a ``refs`` tuple
+REF_FIELDS = ("rho", "rhotheta", "rhou", "rhov")
+
+
 def host_state(U: dict, precision: str, refs=None, pin: bool = True) -> dict:
     """CPU tensors of a state given as numpy full values: float64 or float32,
-    rho and rho*theta minus the reference profile ``refs = (rho0, rho0*theta0)``
-    (per level) when given.  Pinned for asynchronous copies."""
+    each field minus its per-level profile when ``refs`` gives one: ``refs =
+    (rho0, rho0*theta0)`` or ``(rho0, rho0*theta0, ref_rhou, ref_rhov)`` (the
+    last two as set with ``Geometry.set_wind_reference``; None entries are
+    zero).  Pinned for asynchronous copies."""
     import numpy as np
     dt = torch.float64 if precision == "f64" else torch.float32
     out = {}
     for f in FIELDS:
         a = U[f]
-        if refs is not None and f in ("rho", "rhotheta"):
-            a = a - np.asarray(refs[0] if f == "rho" else refs[1])[:, None, None]
+        q = REF_FIELDS.index(f) if f in REF_FIELDS else None
+        if refs is not None and q is not None and q < len(refs) and refs[q] is not None:
+            a = a - np.asarray(refs[q])[:, None, None]
         t = torch.from_numpy(np.ascontiguousarray(a)).to(dt)
         out[f] = t.pin_memory() if pin else t
     return out
@@ -366,6 +400,19 @@ def host_state(U: dict, precision: str, refs=None, pin: bool = True) -> dict:
 def device_state(U: dict, precision: str, refs=None) -> dict:
     """Like host_state, on the current CUDA device."""
     return {f: t.cuda() for f, t in host_state(U, precision, refs, pin=False).items()}
+
+
+def full_values(U: dict, refs=None) -> dict:
+    """numpy float64 full values of a state (torch tensors, device or host):
+    the inverse of host_state / device_state, profiles added back."""
+    out = {}
+    for f in FIELDS:
+        a = U[f].double().cpu().numpy()
+        q = REF_FIELDS.index(f) if f in REF_FIELDS else None
+        if refs is not None and q is not None and q < len(refs) and refs[q] is not None:
+            a = a + np.asarray(refs[q])[:, None, None]
+        out[f] = a
+    return out
 
 
 class Ensemble:

@@ -151,6 +151,17 @@ def initial_state(nx, ny, nz, Lz, u0=(1.0, 0.0, 0.0), pert=0.0, seed=0):
             "rhow": np.ascontiguousarray(rhow)}
 
 
+def background_momentum(nz, Lz, u0=1.0, z_calm=None, ramp=None):
+    """Per-level background momenta (rho0 u_bg(z), 0) at the cell-centre
+    levels, the horizontal wind the states below are built around: the wind
+    u0 along x everywhere, or (z_calm, ramp given) calm below z_calm and
+    ramping linearly to u0 over ``ramp``, as in ``sheltered_state``."""
+    r0, _ = cell_reference(nz, Lz)
+    zc = (np.arange(nz) + 0.5) * (Lz / nz)
+    prof = np.ones(nz) if z_calm is None else np.clip((zc - z_calm) / ramp, 0.0, 1.0)
+    return r0 * u0 * prof, np.zeros(nz)
+
+
 def sheltered_state(nx, ny, nz, Lx, Ly, Lz, z_calm, ramp, u0=1.0, pert=1e-2, seed=0, modes=3):
     """Stratified state for long runs: the wind u0 blows along x above
     z_calm + ramp, is calm below z_calm (which lies above the terrain) and
@@ -245,6 +256,19 @@ class Workload:
 
     def cells(self):
         return self.nx * self.ny * self.nz
+
+    def references(self, kind="uniform"):
+        """Per-level profiles (rho0, rho0 theta0, rho0 u_bg, rho0 v_bg) of the
+        state ``kind``: the stratified reference and the background wind the
+        state is built around (the wind of ``state(kind)`` without its
+        perturbations)."""
+        r0, rt0 = cell_reference(self.nz, self.Lz)
+        if kind == "uniform":
+            ru, rv = background_momentum(self.nz, self.Lz)
+        else:
+            dz = self.Lz / self.nz
+            ru, rv = background_momentum(self.nz, self.Lz, z_calm=self.hmax + dz, ramp=8 * dz)
+        return r0, rt0, ru, rv
 
 
 WOA_32 = Workload("woa-ridge-32x32x16", 32, 32, 16, 10, terrain="woa", hmax=0.1)

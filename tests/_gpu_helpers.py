@@ -12,21 +12,39 @@ FGRID = {"rho": 0, "rhotheta": 0, "rhou": 1, "rhov": 2, "rhow": 3}
 TOL = {"f64": 1e-12, "mixed": 1e-5}
 
 
+# fields with a per-level profile, in the order of a refs tuple:
+# (rho0, rho0 theta0) or (rho0, rho0 theta0, background rho*u, background rho*v)
+REF_FIELDS = ("rho", "rhotheta", "rhou", "rhov")
+
+
 def refs_for(nz, Lz):
     from paper_2604_11959_gb300 import inputs
     return inputs.cell_reference(nz, Lz)
 
 
+def wind_refs(w, kind):
+    """The stratified reference plus the background wind of state ``kind``."""
+    return w.references(kind)
+
+
+def _profile(refs, f):
+    if refs is None or f not in REF_FIELDS:
+        return None
+    q = REF_FIELDS.index(f)
+    return refs[q] if q < len(refs) else None
+
+
 def to_device(U, precision, refs=None):
-    """numpy full-value state -> torch CUDA state (perturbations about refs
-    for rho and rho*theta when refs are given)."""
+    """numpy full-value state -> torch CUDA state (perturbations about the
+    per-level profiles in refs, where given)."""
     import torch
     dt = torch.float64 if precision == "f64" else torch.float32
     out = {}
     for f in FIELDS:
         a = U[f]
-        if refs is not None and f in ("rho", "rhotheta"):
-            a = a - (refs[0] if f == "rho" else refs[1])[:, None, None]
+        r = _profile(refs, f)
+        if r is not None:
+            a = a - np.asarray(r)[:, None, None]
         out[f] = torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dt)
     return out
 
@@ -35,8 +53,9 @@ def to_host(U, refs=None):
     out = {}
     for f in FIELDS:
         a = U[f].double().cpu().numpy()
-        if refs is not None and f in ("rho", "rhotheta"):
-            a = a + (refs[0] if f == "rho" else refs[1])[:, None, None]
+        r = _profile(refs, f)
+        if r is not None:
+            a = a + np.asarray(r)[:, None, None]
         out[f] = a
     return out
 
@@ -73,11 +92,16 @@ def active_masks(G, nz):
 
 
 def make_geometry(eb, w, h, precision, refs=None, vt=0.5):
+    """A geometry handle; with a 4-entry refs tuple the background momenta
+    are set too (eb_geom_set_wind_reference)."""
     import torch
     ht = torch.from_numpy(h).cuda()
     kw = {}
     if refs is not None:
         kw = dict(ref_rho=torch.from_numpy(refs[0]).cuda(), ref_rhotheta=torch.from_numpy(refs[1]).cuda())
+        if len(refs) == 4:
+            kw.update(ref_rhou=torch.from_numpy(np.ascontiguousarray(refs[2])).cuda(),
+                      ref_rhov=torch.from_numpy(np.ascontiguousarray(refs[3])).cuda())
     return eb.Geometry(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, ht, precision=precision, v_target_frac=vt, **kw)
 
 

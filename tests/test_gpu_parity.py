@@ -9,7 +9,7 @@ import pytest
 from paper_2604_11959_gb300 import inputs
 
 from _gpu_helpers import (FGRID, FIELDS, TOL, active_masks, make_geometry, refs_for, rel_linf, to_device, to_host,
-                          window_cut, window_oracle, worst)
+                          wind_refs, window_cut, window_oracle, worst)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -96,14 +96,16 @@ def test_geometry_and_tables_match(eb, case):
         assert info["small_cvs"][g] == int((T[g]["code"] > 0).sum())
 
 
-@pytest.mark.parametrize("precision", ["f64", "mixed"])
-def test_flux_divergence_matches(eb, case, oracle, precision):
+@pytest.mark.parametrize("precision,wind", [("f64", False), ("mixed", False), ("mixed", True)])
+def test_flux_divergence_matches(eb, case, oracle, precision, wind):
     """dU of Eqs. update-cc / update-fc.  Compared volume weighted, alpha dU
     (the flux sum the update conserves): dU itself carries 1/alpha, which
     turns the last-bit differences of two independent geometry computations
-    of a cell with alpha ~ 1e-13 into large relative differences."""
+    of a cell with alpha ~ 1e-13 into large relative differences.  With
+    ``wind`` the state holds the momenta minus the background wind
+    (eb_geom_set_wind_reference); dU is the same full derivative."""
     name, w, h, dom, G, T = case
-    refs = refs_for(w.nz, w.Lz)
+    refs = wind_refs(w, "uniform") if wind else refs_for(w.nz, w.Lz)
     U = w.state("uniform", pert=1e-2, seed=11)
     want = oracle.flux_div(dom, G, U)
     geom = make_geometry(eb, w, h, precision, refs)
@@ -129,10 +131,13 @@ def test_uniform_field_is_preserved_exactly(eb, case):
         assert torch.equal(eb.wsrd(geom32, f, c), c), (name, f)
 
 
-@pytest.mark.parametrize("precision", ["f64", "mixed"])
-def test_redistribution_matches(eb, case, oracle, precision):
+@pytest.mark.parametrize("precision,wind", [("f64", False), ("mixed", False), ("f64", True), ("mixed", True)])
+def test_redistribution_matches(eb, case, oracle, precision, wind):
+    """Redistribution of every field; with ``wind`` the momenta are stored
+    about a background profile and the redistribution adds the profile's
+    level differences back (the oracle works on full values)."""
     name, w, h, dom, G, T = case
-    refs = refs_for(w.nz, w.Lz)
+    refs = wind_refs(w, "sheltered") if wind else refs_for(w.nz, w.Lz)
     rng = np.random.default_rng(3)
     U = w.state("uniform", pert=0.05, seed=12)
     Uhat = {f: U[f] * (1.0 + 0.3 * rng.uniform(-1, 1, U[f].shape)) for f in FIELDS}
@@ -151,12 +156,17 @@ def test_redistribution_matches(eb, case, oracle, precision):
         assert np.array_equal(out.cpu().numpy()[untouched], dev[f].cpu().numpy()[untouched])
 
 
-@pytest.mark.parametrize("precision,stages,kind", [("f64", 1, "uniform"), ("mixed", 1, "uniform"),
-                                                   ("f64", 1, "sheltered"), ("mixed", 1, "sheltered"),
-                                                   ("f64", 3, "sheltered"), ("mixed", 3, "sheltered")])
-def test_steps_match(eb, case, oracle, precision, stages, kind):
+@pytest.mark.parametrize("precision,stages,kind,wind", [("f64", 1, "uniform", False), ("mixed", 1, "uniform", False),
+                                                        ("mixed", 1, "uniform", True),
+                                                        ("f64", 1, "sheltered", True), ("mixed", 1, "sheltered", True),
+                                                        ("mixed", 1, "sheltered", False),
+                                                        ("f64", 3, "sheltered", True), ("mixed", 3, "sheltered", True)])
+def test_steps_match(eb, case, oracle, precision, stages, kind, wind):
+    """Whole steps against the oracle.  ``wind``: the momenta are stored
+    about the state's background wind (the configuration the benchmark
+    runs), else as full values."""
     name, w, h, dom, G, T = case
-    refs = refs_for(w.nz, w.Lz)
+    refs = wind_refs(w, kind) if wind else refs_for(w.nz, w.Lz)
     U = w.state(kind, pert=1e-2 if kind == "uniform" else 0.0, seed=21)
     # a uniform wind into the terrain (no pressure term) piles mass up on the
     # windward side and empties the lee cut cells within a few steps; already
@@ -218,7 +228,7 @@ FULL = {"hill256": inputs.HILL_256, "grf512": inputs.GRF_512}
 def test_full_size_windows(eb, oracle, which, precision):
     w = FULL[which]
     h = w.heights()
-    refs = refs_for(w.nz, w.Lz)
+    refs = wind_refs(w, "uniform")
     U = w.state("uniform", pert=1e-2, seed=31)
     geom = make_geometry(eb, w, h, precision, refs)
     got = to_host(eb.step(geom, to_device(U, precision, refs), w.dt(), 1, 1), refs)
@@ -358,3 +368,34 @@ def test_packed_state_gives_the_same_step(eb):
     for f in FIELDS:
         assert torch.equal(want[f], oviews[f]), f
     geom.close()
+
+
+def test_wind_reference_zero_is_full_values(eb):
+    """A zero background profile (set explicitly) steps bit for bit like no
+    profile; a nonzero profile with the state shifted by it gives the same
+    full result to float rounding after one step (the two float paths round
+    differently, and on this uniform wind into the terrain their difference
+    grows past 1e-5 from the second step on, as each one's error against the
+    oracle does); the anelastic calls refuse a handle with a profile (they
+    need full momenta)."""
+    w = rough_workload()
+    refs = refs_for(w.nz, w.Lz)
+    U = w.state("uniform", pert=1e-2, seed=9)
+    g0 = make_geometry(eb, w, w.heights(), "mixed", refs)
+    want = eb.step(g0, to_device(U, "mixed", refs), w.dt(), 2)
+    zero = torch.zeros(w.nz, dtype=torch.float64, device="cuda")
+    g0.set_wind_reference(zero, zero)
+    got = eb.step(g0, to_device(U, "mixed", refs), w.dt(), 2)
+    for f in FIELDS:
+        assert torch.equal(want[f], got[f]), f
+    wr = wind_refs(w, "uniform")
+    g1 = make_geometry(eb, w, w.heights(), "mixed", wr)
+    full = to_host(eb.step(g1, to_device(U, "mixed", wr), w.dt(), 1), wr)
+    base = to_host(eb.step(g0, to_device(U, "mixed", refs), w.dt(), 1), refs)
+    for f in FIELDS:
+        assert rel_linf(full[f], base[f]) <= TOL["mixed"], f
+    with pytest.raises(eb.EbError) as e:
+        eb.project(g1, to_device(U, "mixed", wr), w.dt())
+    assert e.value.code == 6   # EB_ERR_STATE
+    g0.close()
+    g1.close()
