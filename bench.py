@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--terrains", type=int, default=48, help="warmstart: training terrains")
+    ap.add_argument("--terrains", type=int, default=250,
+                    help="warmstart: training terrains (8 samples each; 250 gives the 2000 training fields)")
     ap.add_argument("--epochs", type=int, default=12, help="warmstart: training epochs")
     ap.add_argument("--workload", choices=("hill256", "grf512", "ensemble", "anelastic", "warmstart"),
                     default="hill256",
@@ -102,13 +103,21 @@ def run_warmstart(eb, terrains, epochs):
         held.append(ws.compare(g, params, w, refs, 77 + q, scale))
         loose.append(ws.compare(g, params, w, refs, 77 + q, scale, rtol=1e-4))
         g.close()
+    # the guess's relative error on held-out samples, all modes and smooth modes
+    test_data, _ = ws.make_dataset(r, scale, first_terrain=5000, terrains=4)
+    net = eb.UNet(r.nx, r.ny, r.nz)
+    net.set_params(params)
+    delta_all, delta_smooth = ws.guess_error(net, test_data)
+    net.close()
     w = inputs.GRF_192
     refs = inputs.cell_reference(w.nz, w.Lz)
     g = eb.Geometry(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, torch.from_numpy(w.heights()).cuda(), precision="mixed",
                     ref_rho=torch.from_numpy(refs[0]).cuda(), ref_rhotheta=torch.from_numpy(refs[1]).cuda())
     big = ws.compare(g, params, w, refs, 1, scale)
+    seq_jacobi = ws.sequence(g, params, w, refs, 1, scale)
     eb.set_preconditioner(g, "mg")
     big_mg = ws.compare(g, params, w, refs, 1, scale)
+    seq_mg = ws.sequence(g, params, w, refs, 1, scale)
     g.close()
     return {"scale": scale, "samples": len(data), "mean_cold_iters_train": float(np.mean(cold_train)),
             "data_s": t_data, "train_s": t_train, "train_step_ms": ms_step,
@@ -120,7 +129,14 @@ def run_warmstart(eb, terrains, epochs):
                        "momentum_diff": big[4], "ratio": big[0] / max(1, big[1])},
             "grf192_multigrid": {"cold": big_mg[0], "warm": big_mg[1], "relres_cold": big_mg[2],
                                  "relres_warm": big_mg[3], "momentum_diff": big_mg[4],
-                                 "ratio": big_mg[0] / max(1, big_mg[1])}}
+                                 "ratio": big_mg[0] / max(1, big_mg[1])},
+            "guess_relative_error": {"all_modes": delta_all, "smooth_modes_8cubed": delta_smooth,
+                                     "samples": len(test_data), "held_out_terrains": 4},
+            "consecutive_steps_grf192": {
+                "note": "iterations to 1e-10 per projection of consecutive forward-Euler anelastic steps: "
+                        "zero start, previous step's solution, network guess",
+                "jacobi": [{"zero": a, "previous_step": b, "network": c} for a, b, c in seq_jacobi],
+                "multigrid": [{"zero": a, "previous_step": b, "network": c} for a, b, c in seq_mg]}}
 
 
 def init_ranks(world):
@@ -222,7 +238,7 @@ def run_ensemble(eb, steps, warmup, clk=None, dist=None):
     (3.8 GB) also leaves no state in L2."""
     import torch
     from paper_2604_11959_gb300 import inputs
-    geoms, states, dts, cells, fast_bytes = [], [], [], 0, 0
+    geoms, states, dts, cells = [], [], [], 0
     for b, (n, _, nz, h0, sig) in enumerate(inputs.ensemble_members()):
         w = inputs.Workload(f"hill-{b}", n, n, nz, 100, terrain="gaussian", hmax=h0, sigma=sig)
         h = w.heights()
@@ -232,7 +248,6 @@ def run_ensemble(eb, steps, warmup, clk=None, dist=None):
         states.append(eb.device_state(w.state("sheltered", seed=b), "mixed", refs))
         dts.append(w.dt())
         cells += w.cells()
-        fast_bytes += g.info()["fast_cells"] * 10 * 4
     ens = eb.Ensemble(geoms)
 
     def reload():
@@ -241,7 +256,6 @@ def run_ensemble(eb, steps, warmup, clk=None, dist=None):
 
     reload()
     slab = ens.tune(dts, reps=2)
-    prio = int(geoms[0].info()["bulk_high_priority"])
     for _ in range(warmup):
         reload()
         ens.step(dts, 1)
@@ -260,23 +274,39 @@ def run_ensemble(eb, steps, warmup, clk=None, dist=None):
     ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in evs])), dist)
     for g in geoms:
         eb.sync_status(g)
-    # the dominant kernel: each member's bulk kernel timed alone
-    bulk_ms = 0.0
-    for g, U, dt in zip(geoms, states, dts):
-        prof = [eb.step_profile(g, U, g.empty_state(), dt)[0] for _ in range(3)]
-        bulk_ms += float(np.median(prof))
+    kinfo = ens.info()
+    # the other schedule, timed the same way (reported beside the tuned one)
+    other = "branches" if kinfo["schedule"] == "persistent" else "persistent"
+    ens.set_schedule(other)
+    ot = []
+    for q in range(steps + 2):
+        reload()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ens.step(dts, 1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if q >= 2:
+            ot.append(a.elapsed_time(b))
+    for g in geoms:
+        eb.sync_status(g)
     ens.close()
     for g in geoms:
         g.close()
     hbm, kind = peaks()
-    achieved = fast_bytes / (bulk_ms * 1e-3) / 1e9
-    launches = 7 * len(geoms)   # per member and step: bulk, 3 near-EB, 3 redistribution kernels
+    # the step is one kernel: its algorithmic traffic is the whole step's, 43
+    # bytes per cell-update of the mixed path (5 fields read and written, the
+    # near-EB geometry and redistribution tables)
+    step_bytes = 43 * cells
+    achieved = step_bytes / (ms * 1e-3) / 1e9
+    per_step = 1 if kinfo["schedule"] == "persistent" else 7 * len(geoms)
     return {"value": cells / (ms * 1e-3), "ms_per_step": ms, "cells": cells, "members": len(geoms),
-            "slab_levels": slab, "bulk_high_priority": prio,
+            "slab_levels": slab, "kernel_ctas": kinfo["ctas"], "bulk_units": kinfo["units"],
+            "schedule": kinfo["schedule"], "other_schedule": {"schedule": other, "ms_per_step": float(np.mean(ot))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": None, "kernel": "k_fast_tiled (each member alone, summed)",
-                         "algorithmic_bytes_per_launch": fast_bytes, "peak_kind": kind},
-            "gpu_launches": launches * steps}
+                         "traffic": None, "kernel": "the whole ensemble step (%s schedule)" % kinfo["schedule"],
+                         "algorithmic_bytes_per_launch": step_bytes, "peak_kind": kind},
+            "gpu_launches": per_step * steps}   # persistent: one kernel per step; branches: ~7 per member
 
 
 def peaks():
@@ -445,24 +475,36 @@ def cpu_baseline(w, steps=None, warmup=0, budget_s=15.0, orc=None):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def traffic_record(kernel, workload_name, precision):
-    """DRAM bytes per launch of a kernel from a committed ncu summary, valid
-    only while the kernel source and the set-up that decides its work (the
-    first fast level of every column) are unchanged (hash recorded with it)."""
+BULK_SOURCES = ("eb_bulk.cuh", "eb_fast.cu", "eb_geom.cu")
+
+
+def bulk_source_hash():
+    """Hash of the bulk kernel's source and of the set-up that decides its
+    work (the first fast level of every column)."""
+    srcs = [os.path.join(ROOT, "paper_2604_11959_gb300", "csrc", f) for f in BULK_SOURCES]
+    return hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()[:16]
+
+
+def profile_record(kernel, workload_name, precision, key):
+    """A figure of a committed ncu summary (DRAM bytes per launch, FP64
+    operations per cell), valid only while the sources it was taken on are
+    unchanged (their hash is recorded with it); None otherwise."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}_{precision}.txt")
-    srcs = [os.path.join(ROOT, "paper_2604_11959_gb300", "csrc", f) for f in ("eb_fast.cu", "eb_geom.cu")]
     try:
-        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()[:16]
         rec = {}
         for line in open(path):
             if ":" in line:
                 k, v = line.split(":", 1)
                 rec[k.strip()] = v.strip()
-        if rec.get("source_sha256_16") != h:
+        if rec.get("source_sha256_16") != bulk_source_hash():
             return None
-        return float(rec["dram_bytes_per_launch_full_size"])
+        return float(rec[key])
     except Exception:
         return None
+
+
+def traffic_record(kernel, workload_name, precision):
+    return profile_record(kernel, workload_name, precision, "dram_bytes_per_launch_full_size")
 
 
 def make_geom(eb, w, h, precision, refs):
@@ -524,6 +566,23 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=
     fast_bytes = info["fast_cells"] * 10 * es
     hbm, kind = peaks()
     achieved = fast_bytes / (prof[0] * 1e-3) / 1e9
+    hbm_roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic_record("k_fast_tiled", w.name, precision), "kernel": "k_fast_tiled",
+                "algorithmic_bytes_per_launch": fast_bytes, "peak_kind": kind,
+                "warp_instructions_per_fast_cell": profile_record("k_fast_tiled", w.name, precision,
+                                                                  "warp_instructions_per_fast_cell")}
+    roof = hbm_roof
+    if precision == "f64":
+        # GB300's FP64 rate is low: the FP64 bulk kernel is bound by its FP64
+        # arithmetic, measured against the DFMA rate of this GPU
+        fpeak = eb.fma_peak("f64")
+        fpc = profile_record("k_fast_tiled", w.name, precision, "fp64_flops_per_fast_cell")
+        roof = {"bound": "fp64", "achieved": None, "peak": fpeak, "unit": "GFLOP/s", "frac": None,
+                "kernel": "k_fast_tiled", "peak_kind": "measured (eb_fma_peak, DFMA = 2 flops)",
+                "flops_per_fast_cell": fpc, "hbm": hbm_roof}
+        if fpc:
+            roof["achieved"] = fpc * info["fast_cells"] / (prof[0] * 1e-3) / 1e9
+            roof["frac"] = roof["achieved"] / fpeak
     # per step: static pass-through (a fresh output buffer every call), the
     # tiled bulk kernel, the two near-EB kernels (face fluxes; CVs with and
     # without a record in one launch) and the three fused redistribution passes
@@ -540,9 +599,7 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=
         "geometry": info,
         "phases_ms": {"fast": float(prof[0]), "band": float(prof[1]), "wsrd": float(prof[2]),
                       "step": float(prof[3])},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": traffic_record("k_fast_tiled", w.name, precision), "kernel": "k_fast_tiled",
-                     "algorithmic_bytes_per_launch": fast_bytes, "peak_kind": kind},
+        "roofline": roof,
         "step_gbs": step_bytes / (ms_step * 1e-3) / 1e9,
         "step_frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm,
         "gpu_launches": launches_per_step * steps,
@@ -754,11 +811,14 @@ def run_arm(args, rank, world, w, dist):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": "ensemble-64-gaussian-hills", "cells": r["cells"], "members": r["members"],
                            "precision": "mixed", "stages": 1, "tuned_slab_levels": r["slab_levels"],
-                           "tuned_bulk_high_priority": r["bulk_high_priority"],
-                           "launch": "one CUDA-graph launch per step of all members",
+                           "kernel_ctas": r["kernel_ctas"], "bulk_units": r["bulk_units"],
+                           "schedule": r["schedule"],
+                           "launch": "tuned schedule, one CUDA-graph launch per step: the persistent cooperative "
+                                     "kernel, or every member's kernels side by side",
                            "l2": "the same input states (3.8 GB, larger than L2) reloaded untimed before every "
                                  "timed step; per-step CUDA events",
                            "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+                "other_schedule": r["other_schedule"],
                 "roofline": r["roofline"], "gpu_launches": r["gpu_launches"], "clocks": clk.summary(),
                 "cpu_baseline": None, "e2e": None}))
         return 0

@@ -168,6 +168,11 @@ eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision
  *   ref_rhou, ref_rhov  device, nz doubles each, finite; NULL means zero.
  *                       Copied during the call (the stream is synchronised
  *                       and the device drained first).
+ * A profile needs the handle's reference density (eb_geom_build with
+ * ref_rho; EB_ERR_STATE otherwise): the bulk kernel advects the deviations
+ * of u and v from u_bg = ref_rhou / rho0 and v_bg = ref_rhov / rho0, as it
+ * advects theta - theta0 (Sec. 4.1 face values of a constant are the
+ * constant, so this changes rounding only).
  * The anelastic calls (eb_project, eb_anelastic_step, eb_project_sample,
  * eb_project_warm) need full momenta and return EB_ERR_STATE on a handle
  * with a nonzero profile.  Setting both to NULL (or zeros) restores full
@@ -400,12 +405,29 @@ eb_status eb_project_warm(eb_geom geom, eb_unet net, eb_state *U, double dt, dou
  * and on the current device; it does not own them (destroy the ensemble
  * first).  It owns two state buffers per member.  Every step of every member
  * is forward Euler (Eq. basic_fv_srd), exactly as eb_step(nsteps = 1,
- * stages = 1) computes it.  One step of the whole ensemble is captured once
- * as a CUDA graph, each member on its own branch so that the kernels of
- * small members run side by side; eb_ensemble_step replays it.  Calls on one
- * ensemble, and on its members' handles, must be serialised.
+ * stages = 1) computes it, bit for bit, in either of two schedules:
+ *   EB_ENSEMBLE_PERSISTENT (the default): one step of the whole ensemble is
+ *     ONE cooperative launch of a persistent kernel with as many CTAs as the
+ *     device holds at once; they take the bulk kernel's work units of all
+ *     members (longest first), then the near-EB fluxes and updates and the
+ *     redistribution of all members, phase after phase, with grid-wide
+ *     barriers between the phases.  A barrier wait is bounded (about a
+ *     second): if a CTA never arrives, the others latch EB_DEV_TIMEOUT into
+ *     every member's status word (eb_sync_status of any member reports it)
+ *     and return; the step's results are then undefined.
+ *   EB_ENSEMBLE_BRANCHES: each member's own kernels on a branch of their
+ *     own, so that the kernels of different members run side by side.
+ * Either step is captured once per step direction as a CUDA graph;
+ * eb_ensemble_step replays it.  eb_ensemble_tune times both and keeps the
+ * faster.  Calls on one ensemble, and on its members' handles, must be
+ * serialised.  EB_ERR_STATE from eb_ensemble_create when the device cannot
+ * hold one CTA of the persistent kernel.
  */
 typedef struct eb_ensemble_s *eb_ensemble;
+
+/* Schedules of an ensemble step (eb_ensemble_set_schedule). */
+#define EB_ENSEMBLE_PERSISTENT 0 /* one cooperative launch of the persistent kernel per step */
+#define EB_ENSEMBLE_BRANCHES 1   /* each member's kernels on a branch of their own */
 
 /* members: n handles (copied).  Allocates the state buffers. */
 eb_status eb_ensemble_create(const eb_geom *members, int n, eb_ensemble *out);
@@ -423,13 +445,32 @@ eb_status eb_ensemble_get_state(eb_ensemble e, int member, eb_state *U, void *st
 eb_status eb_ensemble_step(eb_ensemble e, const double *dt, int nsteps, void *stream);
 
 /* Autotuner: times 2 * reps ensemble steps for each candidate slab height
- * of the bulk kernel's tiles (automatic, 8 .. 64 levels, whole column), each
- * with every member's bulk kernel at the same and at a higher stream priority
- * (eb_geom_set_bulk_priority), and keeps the fastest pair for every member;
- * *slab_levels (if not NULL) receives the height (0 = automatic).  Results do
- * not depend on either.  The loaded states are restored afterwards.
- * Synchronises the stream; allocates a temporary copy of the states. */
+ * of the bulk kernel's tiles (automatic, 8 .. 64 levels, whole column; it
+ * sets the size of the bulk work units) with the persistent schedule and
+ * with the branches schedule (every member's bulk kernel at the same and at
+ * a higher stream priority, eb_geom_set_bulk_priority), and keeps the
+ * fastest combination; *slab_levels (if not NULL) receives the height (0 =
+ * automatic).  Results depend on none of them.  The loaded states are
+ * restored afterwards.  Synchronises the stream; allocates a temporary copy
+ * of the states. */
 eb_status eb_ensemble_tune(eb_ensemble e, const double *dt, int reps, int *slab_levels, void *stream);
+
+/* Sets the schedule (EB_ENSEMBLE_PERSISTENT or EB_ENSEMBLE_BRANCHES) of
+ * later steps; the next step captures its graphs again. */
+eb_status eb_ensemble_set_schedule(eb_ensemble e, int schedule);
+
+/* Launch figures (host array of 6): CTAs of the persistent kernel (all
+ * resident at once), its bulk work units for the current split (0 before
+ * the first step), its registers per thread, static shared and local
+ * (spill) bytes per thread, and the schedule in use. */
+eb_status eb_ensemble_info(eb_ensemble e, int out[6]);
+
+/* Failure test of the bounded barrier (no counterpart in the paper): with
+ * cta >= 0, CTA `cta` of every later step leaves before the first barrier,
+ * so the other CTAs' waits expire and EB_DEV_TIMEOUT latches (the states are
+ * then undefined: load them again); cta = -1 restores normal steps.  Waits
+ * for the device.  No device fault is involved: the kernel only counts. */
+eb_status eb_ensemble_inject_barrier_fault(eb_ensemble e, int cta);
 
 /* Waits for the device, then frees the ensemble's buffers. */
 eb_status eb_ensemble_destroy(eb_ensemble e);

@@ -18,7 +18,11 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = ["eb_api.cu", "eb_geom.cu", "eb_wsrd_setup.cu", "eb_step.cu", "eb_fast.cu", "eb_scan.cu", "eb_ensemble.cu", "eb_project.cu", "eb_unet.cu", "eb_peak.cu"]
-NO_FMA = {"eb_geom.cu", "eb_wsrd_setup.cu"}
+# Units compiled without contraction of a * b + c: the set-up (bit-exact
+# geometry), and the step units, whose device functions run both in their
+# own kernels and inlined into the persistent ensemble kernel and must round
+# the same in both (their heavy arithmetic uses explicit FMA intrinsics).
+NO_FMA = {"eb_geom.cu", "eb_wsrd_setup.cu", "eb_step.cu", "eb_fast.cu"}
 
 
 def nvcc() -> str:

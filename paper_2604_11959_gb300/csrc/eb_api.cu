@@ -36,6 +36,7 @@ eb_status eb_replan_bulk(eb_geom g, int slab_levels) {
   g->boff = nullptr;
   g->slab_levels = slab_levels;
   g->bctas = (int)off.size() - 1;
+  ++g->plan_gen;
   CUDA_TRY(g->alloc(&g->bseg, std::max<long long>(1, (long long)seg.size() / 4)), "alloc bulk split");
   CUDA_TRY(g->alloc(&g->boff, (long long)off.size()), "alloc bulk split");
   if (!seg.empty())
@@ -63,6 +64,22 @@ bool bad_desc(const eb_desc *d, std::string &why) {
   return false;
 }
 
+// A per-level profile is stored with PROFILE_PAD zero levels on both sides
+// (the pointer kept is that of level 0), so the bulk kernel reads levels
+// -PROFILE_PAD .. nz + PROFILE_PAD - 1 without bounds checks.
+constexpr int PROFILE_PAD = 4;
+
+template <typename P>
+cudaError_t alloc_profile(eb_geom g, P **p) {
+  const int n = g->D.nz + 2 * PROFILE_PAD;
+  P *base = nullptr;
+  cudaError_t e = g->alloc(&base, n);
+  if (e != cudaSuccess) return e;
+  e = cudaMemset(base, 0, sizeof(P) * n);
+  *p = base + PROFILE_PAD;
+  return e;
+}
+
 template <typename T>
 cudaError_t fill_ref(eb_geom g, const double *src, double **dd, float **ff, cudaStream_t s) {
   const int nz = g->D.nz;
@@ -75,13 +92,39 @@ cudaError_t fill_ref(eb_geom g, const double *src, double **dd, float **ff, cuda
   }
   std::vector<float> hf(nz);
   for (int k = 0; k < nz; ++k) hf[k] = (float)hv[k];
-  cudaError_t e = g->alloc(dd, nz);
+  cudaError_t e = alloc_profile(g, dd);
   if (e != cudaSuccess) return e;
-  e = g->alloc(ff, nz);
+  e = alloc_profile(g, ff);
   if (e != cudaSuccess) return e;
   e = cudaMemcpy(*dd, hv.data(), sizeof(double) * nz, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
   return cudaMemcpy(*ff, hf.data(), sizeof(float) * nz, cudaMemcpyHostToDevice);
+}
+
+// Background advected values of every level from the reference profiles
+// (device copies in g->ref_d): theta0 = ref_rt / ref_rho, u_bg = ref_u /
+// ref_rho, v_bg = ref_v / ref_rho, in double, with their float copies; zero
+// on levels whose reference density is zero (no profile given).
+cudaError_t update_background(eb_geom g) {
+  const int nz = g->D.nz;
+  std::vector<double> r[4];
+  for (int q = 0; q < 4; ++q) {
+    r[q].resize(nz);
+    cudaError_t e = cudaMemcpy(r[q].data(), g->ref_d[q], sizeof(double) * nz, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+  }
+  for (int b = 0; b < 3; ++b) {
+    std::vector<double> hd(nz);
+    std::vector<float> hf(nz);
+    for (int k = 0; k < nz; ++k) {
+      hd[k] = r[0][k] > 0.0 ? r[b + 1][k] / r[0][k] : 0.0;
+      hf[k] = (float)hd[k];
+    }
+    cudaError_t e = cudaMemcpy(g->bg_d[b], hd.data(), sizeof(double) * nz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->bg_f[b], hf.data(), sizeof(float) * nz, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, const double *ref_rt, cudaStream_t s) {
@@ -385,6 +428,11 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
   CUDA_TRY(fill_ref<double>(g, ref_rt, &g->ref_d[1], &g->ref_f[1], s), "reference");
   CUDA_TRY(fill_ref<double>(g, nullptr, &g->ref_d[2], &g->ref_f[2], s), "reference");
   CUDA_TRY(fill_ref<double>(g, nullptr, &g->ref_d[3], &g->ref_f[3], s), "reference");
+  for (int q = 0; q < 3; ++q) {
+    CUDA_TRY(alloc_profile(g, &g->bg_d[q]), "alloc background");
+    CUDA_TRY(alloc_profile(g, &g->bg_f[q]), "alloc background");
+  }
+  CUDA_TRY(update_background(g), "background");
   CUDA_TRY(g->alloc(&g->status, 1), "alloc status");
   CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(unsigned), s), "memset status");
   // host-side counts for eb_geom_info
@@ -789,6 +837,8 @@ eb_status eb_geom_set_slab_levels(eb_geom geom, int slab_levels) {
 
 eb_status eb_geom_set_wind_reference(eb_geom geom, const double *ref_rhou, const double *ref_rhov, void *stream) {
   if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  if (!geom->has_ref && (ref_rhou || ref_rhov))
+    return fail(EB_ERR_STATE, "a momentum profile needs a handle built with a reference density profile");
   const int nz = geom->D.nz;
   cudaStream_t s = as_stream(stream);
   std::vector<double> hv[2];
@@ -819,6 +869,7 @@ eb_status eb_geom_set_wind_reference(eb_geom geom, const double *ref_rhou, const
              "write momentum profile");
   }
   geom->has_wind_ref = nonzero;
+  CUDA_TRY(update_background(geom), "background");
   return EB_OK;
 }
 

@@ -84,6 +84,7 @@ struct eb_geom_s {
   int *boff = nullptr;
   int bctas = 0;
   int slab_levels = 0;    // slab height of the split (0: automatic)
+  int plan_gen = 0;       // incremented whenever the split is rebuilt (its arrays move)
   int bulk_high = 0;      // 1: the bulk kernel runs on the high-priority stream
   int wsrd_side = 0;      // 1: the redistribution runs on the side stream (see stage)
   std::vector<int> kfast_host;
@@ -95,6 +96,12 @@ struct eb_geom_s {
   // each field minus its profile
   double *ref_d[4] = {nullptr, nullptr, nullptr, nullptr};
   float *ref_f[4] = {nullptr, nullptr, nullptr, nullptr};
+  // per-level background values of the advected quantities, from the
+  // profiles: theta0 = (rho0 theta0) / rho0, u_bg = ref_rhou / rho0,
+  // v_bg = ref_rhov / rho0 (zero where rho0 is zero); the bulk kernel
+  // advects deviations from them
+  double *bg_d[3] = {nullptr, nullptr, nullptr};
+  float *bg_f[3] = {nullptr, nullptr, nullptr};
   double *zero_d = nullptr;
   float *zero_f = nullptr;
   unsigned *status = nullptr;
@@ -182,11 +189,17 @@ StepArgs<T> step_args(eb_geom g, void *const src[5], void *const base[5], void *
     A.src.ref_rt = (const T *)g->ref_d[1];
     A.src.ref_u = (const T *)g->ref_d[2];
     A.src.ref_v = (const T *)g->ref_d[3];
+    A.src.bg_t = (const T *)g->bg_d[0];
+    A.src.bg_u = (const T *)g->bg_d[1];
+    A.src.bg_v = (const T *)g->bg_d[2];
   } else {
     A.src.ref_rho = (const T *)g->ref_f[0];
     A.src.ref_rt = (const T *)g->ref_f[1];
     A.src.ref_u = (const T *)g->ref_f[2];
     A.src.ref_v = (const T *)g->ref_f[3];
+    A.src.bg_t = (const T *)g->bg_f[0];
+    A.src.bg_u = (const T *)g->bg_f[1];
+    A.src.bg_v = (const T *)g->bg_f[2];
   }
   A.dt = dt;
   A.dtT = (T)dt;
@@ -252,9 +265,9 @@ void flux_update(eb_geom g, const StepArgs<T> &A, cudaStream_t s) {
   flux_update(g, A, s, [](cudaStream_t) {});
 }
 
-// Redistribution of all five fields of a state in one pass of three kernels.
+// Arguments of the redistribution of all five fields of the state out[].
 template <typename T>
-void wsrd_all(eb_geom g, void *const out[5], cudaStream_t s) {
+WsrdSet<T> wsrd_set(eb_geom g, void *const out[5]) {
   WsrdSet<T> S;
   long long os = 0, oa = 0;
   for (int f = 0; f < 5; ++f) {
@@ -275,7 +288,13 @@ void wsrd_all(eb_geom g, void *const out[5], cudaStream_t s) {
   }
   S.off_small[5] = os;
   S.off_aff[5] = oa;
-  launch_wsrd5(S, s);
+  return S;
+}
+
+// Redistribution of all five fields of a state in one pass of three kernels.
+template <typename T>
+void wsrd_all(eb_geom g, void *const out[5], cudaStream_t s) {
+  launch_wsrd5(wsrd_set<T>(g, out), s);
 }
 
 // One stage: flux update, then redistribution.  When every CV the

@@ -187,6 +187,7 @@ struct StateIn {
   const T *f[5];             // rho, rho*theta, rho*u, rho*v, rho*w
   const T *ref_rho, *ref_rt; // per cell level, reference added back to rho and rho*theta
   const T *ref_u, *ref_v;    // per cell level, background momenta added back to rho*u and rho*v
+  const T *bg_t, *bg_u, *bg_v; // per cell level, background theta, u, v (profile ratios)
 };
 
 template <typename T>

@@ -21,6 +21,7 @@
 // Every kernel writes a disjoint set of CVs, so no atomics are needed and
 // results are deterministic.
 #include "eb_step.cuh"
+#include "eb_bulk.cuh"
 
 #include <math.h>
 
@@ -392,9 +393,9 @@ __global__ void k_face_mask(StepArgs<float> A) {
   A.G[g].fmask[d][t] = (uint16_t)face_dispatch<float, true>(A, g, d, A.G[g].flist[d][t], 0u, fm, fp);
 }
 
+// the provisional flux of listed face t (all grids and directions in turn)
 template <typename T>
-__global__ void k_face_flux(StepArgs<T> A) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ inline void face_one(const StepArgs<T> &A, long long t) {
   int g, d;
   if (!face_of(A, t, g, d)) return;
   const unsigned c = A.G[g].flist[d][t];
@@ -402,6 +403,11 @@ __global__ void k_face_flux(StepArgs<T> A) {
   face_dispatch<T, false>(A, g, d, c, A.G[g].fmask[d][t], fm, fp);
   ((T *)A.G[g].fh[d])[c] = fp;
   if (A.G[g].fhm[d]) ((T *)A.G[g].fhm[d])[c] = fm;
+}
+
+template <typename T>
+__global__ void k_face_flux(StepArgs<T> A) {
+  face_one(A, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 // Set-up: every CV of grid G a listed (G, Dd) face's stencil reads (t = -2 .. 1
@@ -454,9 +460,9 @@ __global__ void k_stage_marks(StageMarkArgs M) {
 }
 
 // Phase A0: the advected value of every staged CV, once per step.
+// the advected value of staged CV t (all grids in turn)
 template <typename T>
-__global__ void k_stage(StepArgs<T> A) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ inline void stage_one(const StepArgs<T> &A, long long t) {
   int g = 0;
   for (g = 0; g < 4; ++g) {
     if (t < A.G[g].nstage) break;
@@ -474,6 +480,11 @@ __global__ void k_stage(StepArgs<T> A) {
     default: v = cv_advected<T, 3>(A, c, i, j, k); break;
   }
   ((T *)A.G[g].pv)[c] = v;
+}
+
+template <typename T>
+__global__ void k_stage(StepArgs<T> A) {
+  stage_one(A, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 // Phase B: the divergence of every listed cut CV, from
@@ -565,9 +576,10 @@ __device__ inline void regular_cv(const StepArgs<T> &A, long long t) {
   }
 }
 
+// the divergence and update of near-EB CV t: the cut CVs' rows first, then
+// the regular near-EB CVs
 template <typename T>
-__global__ void k_band(StepArgs<T> A) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ inline void band_one(const StepArgs<T> &A, long long t) {
   const long long nrec = A.G[0].nband_rec + A.G[1].nband_rec + A.G[2].nband_rec + A.G[3].nband_rec;
   if (t >= nrec) {   // the regular CVs follow the rows in the same launch
     regular_cv(A, t - nrec);
@@ -600,6 +612,11 @@ __global__ void k_band(StepArgs<T> A) {
       write_out(A, g + 1, c, sp);
     }
   }
+}
+
+template <typename T>
+__global__ void k_band(StepArgs<T> A) {
+  band_one(A, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -829,6 +846,207 @@ __global__ void k_final5(const __grid_constant__ WsrdSet<T> S) {
   final_one(S.f[f], t - S.off_aff[f]);
 }
 
+
+// ---------------------------------------------------------------------------
+// persistent ensemble step: every phase of one step of every member in one
+// cooperative launch, separated by grid-wide barriers whose waits are
+// bounded (an expired wait latches EB_DEV_TIMEOUT in every member's status
+// word and the CTA returns)
+// ---------------------------------------------------------------------------
+
+// member m of the item with global index t: pre[m] <= t < pre[m + 1]
+__device__ inline int member_of(const long long *pre, int nm, long long t) {
+  int lo = 0, hi = nm - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__device__ inline void ens_timeout(const EnsembleArgs<T> &E) {
+  for (int q = 0; q < E.nm; ++q) atomicOr(E.m[q].A.status, EB_DEV_TIMEOUT);
+}
+
+// Grid-wide barrier: every CTA arrives once; the last one to arrive resets
+// the count and advances the generation.  A waiting CTA polls the
+// generation at most spin_limit times (about a microsecond apart) and then
+// gives up.  Returns whether every CTA arrived.
+template <typename T>
+__device__ bool ens_barrier(const EnsembleArgs<T> &E) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    volatile unsigned *gen = E.ctl + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(E.ctl, 1u) + 1u;
+    int good = 1;
+    if (arrived == gridDim.x) {
+      atomicExch(E.ctl, 0u);
+      __threadfence();
+      atomicAdd(E.ctl + 1, 1u);
+    } else {
+      unsigned polls = 0;
+      while (*gen == g) {
+        if (++polls > E.spin_limit) {
+          good = 0;
+          ens_timeout(E);
+          break;
+        }
+        __nanosleep(1000);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Items of a phase handed out in chunks of one warp: lane 0 takes the next
+// chunk from the counter, the warp walks it.
+template <typename F>
+__device__ inline void warp_chunks(unsigned *counter, long long total, F &&fn) {
+  const unsigned lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31u;
+  for (;;) {
+    unsigned c = 0;
+    if (lane == 0) c = atomicAdd(counter, 1u);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    const long long t = (long long)c * 32 + lane;
+    if ((long long)c * 32 >= total) break;
+    if (t < total) fn(t);
+  }
+}
+
+// The bulk march keeps its carried state in registers here (no tensor
+// memory): a cooperative launch may only hold as many CTAs as the driver
+// counts co-resident, and it counts a CTA that allocates tensor memory as
+// filling its SM.
+template <typename T, int V>
+__global__ void __launch_bounds__(bulk::BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1))
+    k_ensemble_step(const __grid_constant__ EnsembleArgs<T> E) {
+  using P = typename bulk::PairOf<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_bytes[];
+  __shared__ unsigned tm_slot;
+  __shared__ int s_unit;
+  if (*E.fault == (int)blockIdx.x + 1) return;   // failure test: this CTA never arrives
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const long long gtid = (long long)blockIdx.x * bulk::BulkTile<T>::NT + tid;
+  const long long nthreads = (long long)gridDim.x * bulk::BulkTile<T>::NT;
+  const int nm = E.nm;
+
+  // phase 1: the bulk kernel's units of every member, longest first, handed
+  // out one per CTA; then (float path) the face fluxes in warp chunks
+  const unsigned tbase = bulk::bulk_tmem_begin<T, false>(&tm_slot);
+  for (;;) {
+    if (tid == 0) s_unit = (int)atomicAdd(E.ctl + 2, 1u);
+    __syncthreads();
+    const int u = s_unit;
+    __syncthreads();
+    if (u >= E.nunits) break;
+    const int2 w = E.units[u];
+    const StepArgs<T> &A = E.m[w.x].A;
+    P bad = bulk::splat(T(0));
+    for (int sgi = A.boff[w.y]; sgi < A.boff[w.y + 1]; ++sgi)
+      bulk::bulk_march<T, V, false>(A, A.bseg[sgi], smem_bytes, tbase, bad);
+    if (!(isfinite(bad.x) && isfinite(bad.y))) atomicOr(A.status, EB_DEV_NUMERIC);
+  }
+  bulk::bulk_tmem_end<T, false>(&tm_slot);
+  for (long long t = gtid; t < E.pre_stage[nm]; t += nthreads) {
+    const int q = member_of(E.pre_stage, nm, t);
+    stage_one(E.m[q].A, t - E.pre_stage[q]);
+  }
+  if (E.faces_first)
+    warp_chunks(E.ctl + 3, E.pre_face[nm], [&](long long t) {
+      const int q = member_of(E.pre_face, nm, t);
+      face_one(E.m[q].A, t - E.pre_face[q]);
+    });
+  if (!ens_barrier(E)) return;
+  // phase 2 (double path): face fluxes from the staged values
+  if (!E.faces_first) {
+    for (long long t = gtid; t < E.pre_face[nm]; t += nthreads) {
+      const int q = member_of(E.pre_face, nm, t);
+      face_one(E.m[q].A, t - E.pre_face[q]);
+    }
+    if (!ens_barrier(E)) return;
+  }
+  // phase 3: near-EB divergence and update
+  for (long long t = gtid; t < E.pre_band[nm]; t += nthreads) {
+    const int q = member_of(E.pre_band, nm, t);
+    band_one(E.m[q].A, t - E.pre_band[q]);
+  }
+  if (!ens_barrier(E)) return;
+  // phases 4-6: redistribution of all five fields of every member
+  for (long long t = gtid; t < E.pre_small[nm]; t += nthreads) {
+    const int q = member_of(E.pre_small, nm, t);
+    const WsrdSet<T> &S = E.m[q].S;
+    const long long ts = t - E.pre_small[q];
+    const int f = field_of(S.off_small, ts);
+    qhat_one(S.f[f], ts - S.off_small[f]);
+  }
+  if (!ens_barrier(E)) return;
+  {
+    // 8 lanes per small CV; every lane of a warp takes part in each round
+    const long long groups = E.pre_small[nm];
+    const long long wbase = (gtid >> 5) * 4, wstep = (nthreads >> 5) * 4;
+    for (long long b = wbase; b < groups; b += wstep) {
+      const long long g = b + ((tid & 31) >> 3);
+      const bool valid = g < groups;
+      const int q = valid ? member_of(E.pre_small, nm, g) : 0;
+      const WsrdSet<T> &S = E.m[q].S;
+      const long long ts = valid ? g - E.pre_small[q] : 0;
+      const int f = valid ? field_of(S.off_small, ts) : 0;
+      sigma_one<T, 8>(S.f[f], valid ? ts - S.off_small[f] : 0, tid & 7, valid);
+    }
+  }
+  if (!ens_barrier(E)) return;
+  for (long long t = gtid; t < E.pre_aff[nm]; t += nthreads) {
+    const int q = member_of(E.pre_aff, nm, t);
+    const WsrdSet<T> &S = E.m[q].S;
+    const long long ta = t - E.pre_aff[q];
+    const int f = field_of(S.off_aff, ta);
+    final_one(S.f[f], ta - S.off_aff[f]);
+  }
+}
+
+template <typename T, int V>
+int ensemble_ctas_v(int info[3]) {
+  auto *k = k_ensemble_step<T, V>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bulk::BulkTile<T>::BYTES) !=
+      cudaSuccess)
+    return 0;
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, bulk::BulkTile<T>::NT, bulk::BulkTile<T>::BYTES) !=
+      cudaSuccess)
+    return 0;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k) == cudaSuccess) {
+    info[0] = fa.numRegs;
+    info[1] = (int)fa.sharedSizeBytes;
+    info[2] = (int)fa.localSizeBytes;
+  }
+  return per * sms;
+}
+
+template <typename T, int V>
+cudaError_t launch_ensemble_v(const EnsembleArgs<T> &E, int ctas, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas, 1, 1);
+  cfg.blockDim = dim3(bulk::BulkTile<T>::NPX, bulk::BulkTile<T>::TY, 1);
+  cfg.dynamicSmemBytes = bulk::BulkTile<T>::BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_ensemble_step<T, V>, E);
+}
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -920,3 +1138,20 @@ template void launch_flux_band<float>(const StepArgs<float> &, cudaStream_t);
 template void launch_flux_update<float>(const StepArgs<float> &, cudaStream_t);
 template void launch_wsrd<double>(const WsrdArgs<double> &, cudaStream_t);
 template void launch_wsrd<float>(const WsrdArgs<float> &, cudaStream_t);
+
+template <typename T>
+int ensemble_kernel_ctas(bool vec, int info[3]) {
+  constexpr int V = 16 / sizeof(T);
+  return vec ? ensemble_ctas_v<T, V>(info) : ensemble_ctas_v<T, 1>(info);
+}
+
+template <typename T>
+cudaError_t launch_ensemble_step(const EnsembleArgs<T> &E, bool vec, int ctas, cudaStream_t s) {
+  constexpr int V = 16 / sizeof(T);
+  return vec ? launch_ensemble_v<T, V>(E, ctas, s) : launch_ensemble_v<T, 1>(E, ctas, s);
+}
+
+template int ensemble_kernel_ctas<float>(bool, int[3]);
+template int ensemble_kernel_ctas<double>(bool, int[3]);
+template cudaError_t launch_ensemble_step<float>(const EnsembleArgs<float> &, bool, int, cudaStream_t);
+template cudaError_t launch_ensemble_step<double>(const EnsembleArgs<double> &, bool, int, cudaStream_t);

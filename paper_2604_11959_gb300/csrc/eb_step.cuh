@@ -60,3 +60,37 @@ template <typename T>
 void launch_wsrd(const WsrdArgs<T> &R, cudaStream_t s);
 template <typename T>
 void launch_wsrd5(const WsrdSet<T> &S, cudaStream_t s);
+
+// One ensemble member in one step direction: the arguments of its flux
+// update and of its five-field redistribution.
+template <typename T>
+struct EnsMember {
+  StepArgs<T> A;
+  WsrdSet<T> S;
+};
+
+// The persistent ensemble step (one cooperative launch per step).  Item
+// counts of every phase are prefix sums over the members (nm + 1 entries);
+// ctl[0..3] (zeroed before every launch) hold the barrier's arrival count and
+// generation and the next bulk unit and face chunk to hand out; *fault (set
+// only by the failure test) names a CTA + 1 that leaves before the first
+// barrier.
+template <typename T>
+struct EnsembleArgs {
+  const EnsMember<T> *m;
+  int nm;
+  const int2 *units;        // bulk work units (member, CTA group of its split), longest first
+  int nunits;
+  const long long *pre_stage, *pre_face, *pre_band, *pre_small, *pre_aff;
+  unsigned *ctl;
+  const int *fault;
+  unsigned spin_limit;      // polls of a barrier wait before it gives up
+  int faces_first;          // 1: face fluxes run in the first phase (no staged values)
+};
+
+// Launch attributes of the persistent kernel: CTAs that fit the device at
+// once (the launch is cooperative), or 0 if the kernel cannot be used.
+template <typename T>
+int ensemble_kernel_ctas(bool vec, int info[3]);   // info: registers per thread, static and local bytes
+template <typename T>
+cudaError_t launch_ensemble_step(const EnsembleArgs<T> &E, bool vec, int ctas, cudaStream_t s);

@@ -33,7 +33,8 @@ EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom
                     "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step", "eb_unet_destroy",
                     "eb_project_sample", "eb_project_warm", "eb_geom_tune",
                     "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
-                    "eb_geom_set_wind_reference", "eb_fma_peak")
+                    "eb_geom_set_wind_reference", "eb_fma_peak", "eb_ensemble_info",
+                    "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule")
 
 
 class EbError(RuntimeError):
@@ -117,6 +118,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_project_set_preconditioner.argtypes = [V, I]
     lib.eb_geom_set_wind_reference.argtypes = [V, V, V, V]
     lib.eb_fma_peak.argtypes = [I, P(D), V]
+    lib.eb_ensemble_info.argtypes = [V, P(I)]
+    lib.eb_ensemble_inject_barrier_fault.argtypes = [V, I]
+    lib.eb_ensemble_set_schedule.argtypes = [V, I]
     lib.eb_last_error.restype = ctypes.c_char_p
     lib.eb_version.restype = I
     for name in ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom_export", "eb_flux_div", "eb_wsrd",
@@ -126,7 +130,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                  "eb_unet_get_params", "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step",
                  "eb_unet_destroy", "eb_project_sample", "eb_project_warm", "eb_geom_tune",
                  "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
-                 "eb_geom_set_wind_reference", "eb_fma_peak"):
+                 "eb_geom_set_wind_reference", "eb_fma_peak", "eb_ensemble_info",
+                 "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -471,6 +476,23 @@ class Ensemble:
         best = ctypes.c_int(0)
         _check(load().eb_ensemble_tune(self.handle, self._dt(dt), int(reps), ctypes.byref(best), _stream(stream)))
         return best.value
+
+    def info(self) -> dict:
+        """Launch figures of the persistent step kernel (``eb_ensemble_info``)."""
+        v = (ctypes.c_int * 6)()
+        _check(load().eb_ensemble_info(self.handle, v))
+        return {"ctas": v[0], "units": v[1], "registers": v[2], "static_smem": v[3], "local_bytes": v[4],
+                "schedule": ("persistent", "branches")[v[5]]}
+
+    def set_schedule(self, schedule: str):
+        """"persistent" (one cooperative launch per step) or "branches" (each
+        member's kernels side by side); ``eb_ensemble_set_schedule``."""
+        _check(load().eb_ensemble_set_schedule(self.handle, {"persistent": 0, "branches": 1}[schedule]))
+
+    def inject_barrier_fault(self, cta: int):
+        """Failure test: CTA ``cta`` of later steps skips the first barrier
+        (-1 restores normal steps); ``eb_ensemble_inject_barrier_fault``."""
+        _check(load().eb_ensemble_inject_barrier_fault(self.handle, int(cta)))
 
 
 class UNet:

@@ -59,10 +59,11 @@ def workload(r: Recipe, t: int, nx=None, ny=None, nz=None) -> inputs.Workload:
                            seed=r.seed + t, hmax=r.hmax_frac * nz * r.dx)
 
 
-def geometry(w: inputs.Workload):
+def geometry(w: inputs.Workload, preconditioner: str = "jacobi"):
     refs = inputs.cell_reference(w.nz, w.Lz)
     g = eb.Geometry(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, torch.from_numpy(w.heights()).cuda(), precision="mixed",
                     ref_rho=torch.from_numpy(refs[0]).cuda(), ref_rhotheta=torch.from_numpy(refs[1]).cuda())
+    eb.set_preconditioner(g, preconditioner)
     return g, refs
 
 
@@ -85,11 +86,12 @@ def target_scale(r: Recipe) -> float:
 
 def make_dataset(r: Recipe, scale: float, first_terrain: int = 0, terrains: int | None = None):
     """Samples (input, target, mask) on the GPU and the cold-start iteration
-    count of each."""
+    count of each (multigrid-preconditioned solves: the samples are the same
+    converged solutions, found faster)."""
     data, iters = [], []
     for t in range(first_terrain, first_terrain + (terrains or r.terrains)):
         w = workload(r, t)
-        g, refs = geometry(w)
+        g, refs = geometry(w, "mg")
         for s in range(r.states_per_terrain):
             x, tt, m, it = eb.project_sample(g, state(w, refs, 1000 * t + s), w.dt(), scale, rtol=r.rtol)
             data.append((x, tt, m))
@@ -136,3 +138,54 @@ def compare(geom, net_params, w, refs, seed, scale, rtol=1e-10):
     diff = max(float((A[f] - B[f]).abs().max()) for f in ("rhou", "rhov", "rhow")) / ms
     net.close()
     return it_c, it_w, res_c, res_w, diff
+
+
+def guess_error(net: eb.UNet, data, block: int = 8):
+    """Relative error of the network's guess on samples (input, target, mask):
+    over all fluid cells, and on the smooth part (means over blocks of
+    block^3 cells, the modes conjugate gradients converge on last), as the
+    median over the samples.  Measurement only: the guess itself comes from
+    the library's forward pass."""
+    fine, smooth = [], []
+    pool = torch.nn.functional.avg_pool3d
+    for x, t, m in data:
+        y = net.forward(x)
+        e, tm = (y - t) * m, t * m
+        fine.append(float(e.norm() / tm.norm()))
+        es = pool(e[None, None], block, ceil_mode=True)
+        ts = pool(tm[None, None], block, ceil_mode=True)
+        smooth.append(float(es.norm() / ts.norm()))
+    return float(np.median(fine)), float(np.median(smooth))
+
+
+def sequence(geom, net_params, w, refs, seed, scale, nsteps=4, rtol=1e-10):
+    """Projections of consecutive forward-Euler anelastic steps (provisional
+    momenta from eb_step with the density at the reference, then the
+    projection) from a projected initial state, each solved from a zero
+    start, from the previous step's solution and from the network's guess.
+    Returns one (zero, previous, network) iteration triple per step (previous
+    is None on the first).  The converged projections agree to the solver's
+    tolerance; the zero-start one advances the sequence."""
+    net = eb.UNet(w.nx, w.ny, w.nz)
+    net.set_params(net_params)
+    dt = w.dt()
+    S = state(w, refs, seed)
+    eb.project(geom, S, dt, rtol=rtol)
+    phi_prev = None
+    rows = []
+    for _ in range(nsteps):
+        P = eb.step(geom, S, dt, 1)
+        P["rho"].zero_()   # the anelastic density is the reference
+        A = {f: P[f].clone() for f in P}
+        phi = torch.empty(geom.shape(0), dtype=torch.float64, device="cuda")
+        it0, _ = eb.project(geom, A, dt, rtol=rtol, phi=phi)
+        itp = None
+        if phi_prev is not None:
+            B = {f: P[f].clone() for f in P}
+            itp, _ = eb.project(geom, B, dt, rtol=rtol, phi0=phi_prev)
+        C = {f: P[f].clone() for f in P}
+        itw, _ = eb.project_warm(geom, net, C, dt, scale, rtol=rtol)
+        rows.append((it0, itp, itw))
+        phi_prev, S = phi, A
+    net.close()
+    return rows

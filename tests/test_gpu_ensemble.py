@@ -1,13 +1,16 @@
 """Ensembles (eb_ensemble_*): members of uneven sizes advanced together by
-graph replay must give exactly what eb_step gives for each member alone
-(same kernels, same arithmetic; the work split and the tuned slab heights
-change only who computes what), in both precisions."""
+one persistent cooperative launch per step must give exactly what eb_step
+gives for each member alone (same device functions, same arithmetic; the
+work split and the tuned slab heights change only who computes what), in
+both precisions; a member must match the oracle; and a CTA that never
+arrives at the kernel's grid barrier must end the step with EB_ERR_TIMEOUT,
+not a hang."""
 import numpy as np
 import pytest
 
 from paper_2604_11959_gb300 import inputs
 
-from _gpu_helpers import FIELDS, make_geometry, refs_for, to_device
+from _gpu_helpers import FGRID, FIELDS, TOL, active_masks, make_geometry, refs_for, rel_linf, to_device, to_host
 
 torch = pytest.importorskip("torch")
 
@@ -33,9 +36,14 @@ def members():
     ]
 
 
-@pytest.mark.parametrize("precision", ["f64", "mixed"])
-def test_ensemble_equals_each_member_alone(eb, precision):
-    ws = members()
+@pytest.mark.parametrize("schedule", ["persistent", "branches"])
+@pytest.mark.parametrize("precision,ragged", [("f64", True), ("mixed", True), ("mixed", False)])
+def test_ensemble_equals_each_member_alone(eb, precision, ragged, schedule):
+    """ragged: a member whose rows do not suit 16-byte copies makes the whole
+    ensemble use the element-wise variant of the persistent kernel; without
+    it the vector variant runs.  The tuner's choice (either schedule) gives
+    the same results again."""
+    ws = members() if ragged else [w for w in members() if w.nx % 4 == 0]
     geoms, states, dts, refs = [], [], [], []
     for q, w in enumerate(ws):
         r = refs_for(w.nz, w.Lz)
@@ -46,9 +54,12 @@ def test_ensemble_equals_each_member_alone(eb, precision):
     nsteps = 3
     want = [eb.step(g, U, dt, nsteps) for g, U, dt in zip(geoms, states, dts)]
     ens = eb.Ensemble(geoms)
+    ens.set_schedule(schedule)
     for q, U in enumerate(states):
         ens.set_state(q, U)
     ens.step(dts, nsteps)
+    info = ens.info()
+    assert info["ctas"] > 0 and info["units"] > 0 and info["schedule"] == schedule
     for q in range(len(ws)):
         got = ens.get_state(q)
         for f in FIELDS:
@@ -100,4 +111,69 @@ def test_ensemble_argument_errors(eb):
         ens.step([-1.0], 1)
     with pytest.raises(ValueError):
         ens.step([1e-3, 1e-3], 1)
+    ens.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_ensemble_member_matches_the_oracle(eb, oracle, precision):
+    """Two members (a hill and a ragged random terrain) three steps in the
+    ensemble against the FP64 oracle run on each member alone."""
+    ws = [members()[0], members()[3]]
+    geoms, states, dts, refs = [], [], [], []
+    for q, w in enumerate(ws):
+        r = refs_for(w.nz, w.Lz)
+        refs.append(r)
+        geoms.append(make_geometry(eb, w, w.heights(), precision, r))
+        states.append(w.state("sheltered", seed=40 + q))
+        dts.append(w.dt())
+    ens = eb.Ensemble(geoms)
+    for q in range(len(ws)):
+        ens.set_state(q, to_device(states[q], precision, refs[q]))
+    ens.step(dts, 3)
+    for q, w in enumerate(ws):
+        dom = oracle.Domain(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, w.heights())
+        G = oracle.geometry(dom)
+        want = oracle.step(dom, G, oracle.wsrd_setup(dom, G), states[q], dts[q], 3)
+        got = to_host(ens.get_state(q), refs[q])
+        act = active_masks(G, w.nz)
+        for f in FIELDS:
+            err = rel_linf(got[f], want[f], act[FGRID[f]])
+            assert err <= TOL[precision], (precision, w.name, f, err)
+    for g in geoms:
+        eb.sync_status(g)
+    ens.close()
+
+
+def test_barrier_wait_expires_when_a_cta_never_arrives(eb):
+    """CTA 0 of the persistent kernel skips the first grid barrier (the
+    failure test's switch): every other CTA's bounded wait expires, the step
+    returns and every member reports EB_ERR_TIMEOUT.  With the switch off
+    again the next steps are exact (the barrier's counters are reset before
+    every launch)."""
+    ws = members()[:2]
+    geoms = [make_geometry(eb, w, w.heights(), "mixed", refs_for(w.nz, w.Lz)) for w in ws]
+    states = [to_device(w.state("sheltered", seed=3 + q), "mixed", refs_for(w.nz, w.Lz)) for q, w in enumerate(ws)]
+    dts = [w.dt() for w in ws]
+    want = [eb.step(g, U, dt, 2) for g, U, dt in zip(geoms, states, dts)]
+    ens = eb.Ensemble(geoms)
+    for q, U in enumerate(states):
+        ens.set_state(q, U)
+    ens.inject_barrier_fault(0)
+    ens.step(dts, 1)
+    for g in geoms:
+        with pytest.raises(eb.EbError) as e:
+            eb.sync_status(g)
+        assert e.value.code == 5   # EB_ERR_TIMEOUT
+    ens.inject_barrier_fault(-1)
+    for q, U in enumerate(states):
+        ens.set_state(q, U)
+    ens.step(dts, 2)
+    for q in range(len(ws)):
+        got = ens.get_state(q)
+        for f in FIELDS:
+            assert torch.equal(got[f], want[q][f]), (ws[q].name, f)
+    for g in geoms:
+        eb.sync_status(g)
+    with pytest.raises(eb.EbError):
+        ens.inject_barrier_fault(ens.info()["ctas"])
     ens.close()
