@@ -45,10 +45,11 @@ def parse():
     ap.add_argument("--terrains", type=int, default=250,
                     help="warmstart: training terrains (8 samples each; 250 gives the 2000 training fields)")
     ap.add_argument("--epochs", type=int, default=12, help="warmstart: training epochs")
-    ap.add_argument("--workload", choices=("hill256", "grf512", "ensemble", "anelastic", "warmstart"),
+    ap.add_argument("--workload", choices=("hill256", "grf512", "ensemble", "anelastic", "warmstart", "slabs"),
                     default="hill256",
                     help="ensemble: 64 uneven Gaussian-hill instances advanced together (mixed path); "
-                         "anelastic: 192x192x96 random terrain, anelastic steps with the projection")
+                         "anelastic: 192x192x96 random terrain, anelastic steps with the projection; "
+                         "slabs: the 256x256x128 hill cut into one x-slab per rank (halo exchange each step)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--precision", choices=("both", "mixed", "f64"), default="both",
                     help="arms to run (profiling runs pick one)")
@@ -307,6 +308,46 @@ def run_ensemble(eb, steps, warmup, clk=None, dist=None):
                          "traffic": None, "kernel": "the whole ensemble step (%s schedule)" % kinfo["schedule"],
                          "algorithmic_bytes_per_launch": step_bytes, "peak_kind": kind},
             "gpu_launches": per_step * steps}   # persistent: one kernel per step; branches: ~7 per member
+
+
+def run_slabs(eb, steps, warmup, world, rank, dist, clk=None):
+    """The 256x256x128 hill (mixed path, forward Euler) cut into one x-slab
+    per rank: each rank holds its owned columns plus a 12-column halo, and
+    every step exchanges the halos (NCCL point-to-point) and advances the
+    slab with eb_step.  Strong scaling: the whole job is the one domain."""
+    import torch
+    from paper_2604_11959_gb300 import inputs, slabs as S
+    w = inputs.HILL_256
+    h = w.heights()
+    refs = w.references("sheltered")
+    U = w.state("sheltered")
+    sl = S.Slabs(w.nx, world, rank, S.HALO_EULER)
+    ws = inputs.Workload("slab", sl.ext, w.ny, w.nz, 1, Lx=sl.ext * w.Lx / w.nx, Ly=w.Ly, Lz=w.Lz)
+    geom = make_geom(eb, ws, sl.heights(h), "mixed", refs)
+    held0 = eb.device_state({f: np.ascontiguousarray(sl.scatter(U[f])) for f in S.FIELDS}, "mixed", refs)
+    dt = w.dt()
+
+    def step_one(Uq):
+        return eb.step(geom, Uq, dt, 1)
+
+    A = {f: held0[f].clone() for f in S.FIELDS}
+    S.advance(sl, A, warmup, step_one, dist)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    A = {f: held0[f].clone() for f in S.FIELDS}
+    barrier(dist)
+    torch.cuda.synchronize()
+    with clk or contextlib.nullcontext():
+        a.record(stream)
+        A = S.advance(sl, A, steps, step_one, dist)
+        b.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms = max_over_ranks(a.elapsed_time(b) / steps, dist)
+    eb.sync_status(geom)
+    geom.close()
+    return {"value": w.cells() / (ms * 1e-3), "ms_per_step": ms, "cells": w.cells(), "halo": sl.halo,
+            "held_columns": sl.ext, "owned_columns": sl.width}
 
 
 def peaks():
@@ -797,6 +838,24 @@ def run_arm(args, rank, world, w, dist):
                 "iters_per_solve": r["iters_per_solve"], "projection": r["projection"],
                 "roofline": r["projection"]["mg"]["roofline"], "clocks": clk.summary(),
                 "cpu_baseline": None, "e2e": None}))
+        return 0
+    if args.workload == "slabs":
+        from paper_2604_11959_gb300 import build as libbuild, eb
+        libbuild.build()
+        eb.load()
+        clk = ClockSampler(torch.cuda.current_device())
+        r = run_slabs(eb, args.steps, max(3, args.warmup), world, rank, dist, clk)
+        if rank == 0:
+            print(json.dumps({
+                "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "gaussian-hill-256x256x128 in x-slabs", "cells": r["cells"],
+                           "precision": "mixed", "stages": 1, "halo": r["halo"],
+                           "held_columns_per_rank": r["held_columns"], "owned_columns_per_rank": r["owned_columns"],
+                           "parallelism": f"{world} x-slabs, halo exchange every step"},
+                "roofline": None, "clocks": clk.summary(), "cpu_baseline": None, "e2e": None,
+                "gpu_launches": 7 * args.steps}))   # per step: pass-through, bulk, 2 near-EB, 3 redistribution
         return 0
     if args.workload == "ensemble":
         from paper_2604_11959_gb300 import build as libbuild, eb
