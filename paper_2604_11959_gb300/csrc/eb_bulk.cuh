@@ -405,8 +405,11 @@ __device__ __forceinline__ void bulk_march(const StepArgs<T> &A, const int4 sg, 
     request(p + 2 <= p1 ? p + 2 : -1);
 
     // ---- phase 2a: own window; x / y faces of level p
+    // (on the tensor-memory path the own values of level p stay in registers
+    // for the z step: after the barrier below, other warps may already be
+    // writing the primitive plane of level p + 1)
+    P a0 = zero, a1 = zero, a2 = zero, a3 = zero;   // above the top: zeros (w wall level nz)
     if constexpr (TM) {
-      P a0 = zero, a1 = zero, a2 = zero, a3 = zero;   // above the top: zeros (w wall level nz)
       if (p < nz) {   // full values: the z fluxes cross levels of different backgrounds
         const T *Q = prim + TL::qi(2 * tx, ty);
         a0 = padd(ld2(Q), splat(bt_p));
@@ -596,15 +599,10 @@ __device__ __forceinline__ void bulk_march(const StepArgs<T> &A, const int4 sg, 
         zu = w2(o, 36);
         zv = w2(o, 38);
         zw = w2(o, 40);
-        if (p < nz) {
-          const T *Q = prim + TL::qi(2 * tx, ty);
-          th[3] = padd(ld2(Q), splat(bt_p));
-          uu[3] = padd(ld2(Q + NQ), splat(bu_p));
-          vv[3] = padd(ld2(Q + 2 * NQ), splat(bv_p));
-          ww[3] = ld2(Q + 3 * NQ);
-        } else {
-          th[3] = uu[3] = vv[3] = ww[3] = zero;
-        }
+        th[3] = a0;
+        uu[3] = a1;
+        vv[3] = a2;
+        ww[3] = a3;
       }
       if (k + 2 <= nz - 1) zstep(std::true_type());
       else zstep(std::false_type());

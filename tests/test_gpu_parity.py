@@ -328,6 +328,31 @@ def test_tuning_changes_no_result(eb, precision):
 
 
 @pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_every_slab_height_gives_the_same_steps(eb, precision):
+    """The bulk kernel's slab heights (eb_geom_set_slab_levels: automatic,
+    a few levels, whole columns) change which CTA marches which levels, never
+    a cell's arithmetic: the steps agree bit for bit, and a negative height is
+    rejected."""
+    w = rough_workload()
+    refs = refs_for(w.nz, w.Lz)
+    U = w.state("uniform", pert=1e-2, seed=6)
+    geom = make_geometry(eb, w, w.heights(), precision, refs)
+    A = to_device(U, precision, refs)
+    eb.set_slab_levels(geom, 0)
+    want = eb.step(geom, A, w.dt(), 3)
+    for split in (1, 5, w.nz + 7):
+        eb.set_slab_levels(geom, split)
+        assert geom.info()["slab_levels"] == split
+        got = eb.step(geom, A, w.dt(), 3)
+        for f in FIELDS:
+            assert torch.equal(got[f], want[f]), (precision, split, f)
+    with pytest.raises(eb.EbError):
+        eb.set_slab_levels(geom, -1)
+    eb.sync_status(geom)
+    geom.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
 def test_bulk_priority_changes_no_result(eb, precision):
     """The bulk kernel on the high-priority stream or on the caller's stream
     (eb_geom_set_bulk_priority) only changes the schedule: the steps agree
