@@ -350,6 +350,30 @@ def run_slabs(eb, steps, warmup, world, rank, dist, clk=None):
             "held_columns": sl.ext, "owned_columns": sl.width}
 
 
+def other_configs(eb, world, dist, warmup, steps=10):
+    """The other timed configurations, measured in the default run beside
+    the headline: the 512x512x256 random terrain (mixed path, tuned, per-step
+    events with the L2 flushed, bulk kernel against HBM) and the 64-member
+    ensemble (tuned schedule).  The warm-start training (about two minutes)
+    runs only as its own workload."""
+    import torch
+    w = workload("grf512")
+    h = w.heights()
+    refs = w.references("sheltered")
+    geom, r = run_precision(eb, w, h, w.state("sheltered"), refs, "mixed", steps, warmup, world, dist)
+    geom.close()
+    torch.cuda.empty_cache()
+    out = {"grf512": {"workload": w.name, "cells": w.cells(), "value": r["value"], "ms_per_step": r["ms_per_step"],
+                      "steps": r["steps"], "phases_ms": r["phases_ms"], "roofline_frac": r["roofline"]["frac"],
+                      "tuned_slab_levels": r["tuned_slab_levels"], "bulk_high_priority": r["bulk_high_priority"]}}
+    e = run_ensemble(eb, steps, warmup, None, dist)
+    torch.cuda.empty_cache()
+    out["ensemble"] = {"workload": "ensemble-64-gaussian-hills", "cells": e["cells"], "value": e["value"] * world,
+                       "ms_per_step": e["ms_per_step"], "steps": steps, "schedule": e["schedule"],
+                       "other_schedule": e["other_schedule"], "step_hbm_frac": e["roofline"]["frac"]}
+    return out
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -900,6 +924,9 @@ def run_arm(args, rank, world, w, dist):
         geom64, f64 = run_precision(eb, w, h, U, refs, "f64", max(10, args.steps // 10), args.warmup, world, dist,
                                     None if mixed else clk, args.slab_levels)
         geom64.close()
+    others = None
+    if args.precision == "both" and args.workload == "hill256":
+        others = other_configs(eb, world, dist, max(3, args.warmup))
     acc = cb = orc = None
     if rank == 0 and world == 1 and not args.no_cpu:
         orc = oracle_domain(w)   # after every timed region: the oracle loads all host cores
@@ -931,6 +958,8 @@ def run_arm(args, rank, world, w, dist):
     }
     if acc:
         line["accuracy"] = acc
+    if others:
+        line["other_configs"] = others
     if mixed and f64:
         line["fp64"] = {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "roofline": f64["roofline"],
                         "step_hbm_frac": f64["step_frac"], "phases_ms": f64["phases_ms"], "steps": f64["steps"]}
