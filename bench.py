@@ -350,6 +350,45 @@ def run_slabs(eb, steps, warmup, world, rank, dist, clk=None):
             "held_columns": sl.ext, "owned_columns": sl.width}
 
 
+def compressible_cost(eb, world, dist, warmup, steps):
+    """The hill's mixed step with the sources of the compressible system
+    switched on (eb_geom_set_sources: pressure gradient and buoyancy), timed
+    like the headline (L2 flushed before every step, per-step events), beside
+    the same handle's advection-only step.  The sources run as their own
+    pass after the flux update, and the redistribution then follows them
+    instead of running beside the bulk kernel."""
+    import torch
+    w = workload("hill256")
+    h = w.heights()
+    refs = w.references("sheltered")
+    geom = make_geom(eb, w, h, "mixed", refs)
+    eb.tune(geom, eb.device_state(w.state("sheltered"), "mixed", refs), w.dt(), reps=3)
+    A = eb.device_state(w.state("sheltered"), "mixed", refs)
+    out = geom.empty_state()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for on in (False, True):
+        geom.set_sources(on, on)
+        for _ in range(warmup):
+            eb.step(geom, A, w.dt(), 1, out=out)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            eb.step(geom, A, w.dt(), 1, out=out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        res["with_sources" if on else "advection_only"] = max_over_ranks(float(np.mean(ms)), dist)
+    eb.sync_status(geom)
+    geom.close()
+    return {"workload": w.name, "cells": w.cells(), "value": world * w.cells() / (res["with_sources"] * 1e-3),
+            "ms_per_step": res["with_sources"], "ms_per_step_advection_only": res["advection_only"],
+            "steps": steps, "sources": "pressure gradient (equation of state) and buoyancy"}
+
+
 def other_configs(eb, world, dist, warmup, steps=10):
     """The other timed configurations, measured in the default run beside
     the headline: the 512x512x256 random terrain (mixed path, tuned, per-step
@@ -366,6 +405,7 @@ def other_configs(eb, world, dist, warmup, steps=10):
     out = {"grf512": {"workload": w.name, "cells": w.cells(), "value": r["value"], "ms_per_step": r["ms_per_step"],
                       "steps": r["steps"], "phases_ms": r["phases_ms"], "roofline_frac": r["roofline"]["frac"],
                       "tuned_slab_levels": r["tuned_slab_levels"], "bulk_high_priority": r["bulk_high_priority"]}}
+    out["hill256_compressible"] = compressible_cost(eb, world, dist, warmup, steps)
     e = run_ensemble(eb, steps, warmup, None, dist)
     torch.cuda.empty_cache()
     out["ensemble"] = {"workload": "ensemble-64-gaussian-hills", "cells": e["cells"], "value": e["value"] * world,

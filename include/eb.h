@@ -180,6 +180,35 @@ eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision
  */
 eb_status eb_geom_set_wind_reference(eb_geom geom, const double *ref_rhou, const double *ref_rhov, void *stream);
 
+/*
+ * Sources of the compressible system (Sec. 2.1, Eq. mom-comp) that eb_step
+ * adds to the flux divergence of every stage, before the redistribution:
+ *   EB_SOURCE_PRESSURE  -grad p' on rho*u, rho*v, rho*w: p' = p - p0(z), p from
+ *                       the equation of state p = P00 (R rho theta / P00)^gamma
+ *                       and p0 from the reference rho0 theta0 of each level;
+ *   EB_SOURCE_BUOYANCY  B = -rho' g on rho*w.
+ * Pressure and density live at cell centres: the source of a momentum CV is
+ * -(p'_b - p'_a) / dx_d across its two cells a (one step back along its
+ * staggering axis d) and b (same index), on w also -g (rho'_a + rho'_b) / 2;
+ * a covered cell takes the other cell's value.  Constants: P00 = 1e5 Pa (the
+ * paper's), R = 287 J/(kg K), cp = 1004.5 J/(kg K), gamma = cp / (cp - R),
+ * g = 9.81 m/s^2 (EB_P00, EB_RD, EB_CP, EB_GRAV).  The time step must then
+ * resolve sound waves: eb_step does not check it.
+ *   flags  a combination of EB_SOURCE_*; 0 switches them off (default).
+ * Needs the handle's reference profiles (eb_geom_build with ref_rho and
+ * ref_rhotheta): EB_ERR_STATE otherwise.  eb_flux_div, eb_wsrd and
+ * eb_step_profile never add sources; the anelastic calls and
+ * eb_ensemble_create return EB_ERR_STATE on a handle with sources;
+ * EB_ERR_INVALID_ARG for other flag bits.
+ */
+#define EB_SOURCE_PRESSURE 1
+#define EB_SOURCE_BUOYANCY 2
+#define EB_P00 1.0e5
+#define EB_RD 287.0
+#define EB_CP 1004.5
+#define EB_GRAV 9.81
+eb_status eb_geom_set_sources(eb_geom geom, int flags);
+
 /* Free everything the handle owns (synchronises the device).  NULL is OK. */
 eb_status eb_geom_destroy(eb_geom geom);
 

@@ -20,7 +20,10 @@
  *      flux interpolation to the face centroid);
  *   3. weighted state redistribution (Sec. 5.1, Eqs. kappa, omega, nbhd_vol,
  *      centroid, qhat_omega, qrecon, final_update_omega);
- *   4. the step of Algorithm 1 (stages = 1: forward Euler of Eq. FV-discrete;
+ *   4. the sources of the compressible system (Sec. 2.1, Eq. mom-comp): the
+ *      perturbation pressure gradient from the equation of state and the
+ *      buoyancy, added to the flux divergence of every stage when asked for;
+ *   5. the step of Algorithm 1 (stages = 1: forward Euler of Eq. FV-discrete;
  *      stages = 3: the three-stage Runge-Kutta of Sec. 5.2 with WSRD after
  *      every stage).
  *
@@ -1107,13 +1110,105 @@ int orc_wsrd_apply(const OrcDomain *D, int g, const OrcGeom *Gg, const OrcWsrd *
 }
 
 /* ------------------------------------------------------------------------- */
-/* 4. The step (Algorithm 1 with S = 0)                                       */
+/* 4. Sources of the compressible system (Sec. 2.1, Eq. mom-comp)            */
 /* ------------------------------------------------------------------------- */
-/* One stage: Uout = R[ Ubase + dt * dU(Usrc) ] on all four grids.  scratch
- * holds 5 arrays of the field sizes. */
+/* The momentum equation of the compressible system carries -grad p' and the
+ * buoyancy B = -rho' g (g pointing down: a force -rho' |g| on rho*w), with
+ * p' = p - p0(z), rho' = rho - rho0(z) and p from the equation of state
+ * p = P00 (R rho theta / P00)^gamma; the reference state satisfies it,
+ * p0 = P00 (R rho0 theta0 / P00)^gamma.  P00 = 1e5 Pa is the paper's; the gas
+ * constant and specific heat of dry air and the gravitational acceleration
+ * are not printed there: R = 287 J/(kg K), cp = 1004.5 J/(kg K),
+ * gamma = cp / (cp - R), g = 9.81 m/s^2.
+ *
+ * On the staggered mesh the pressure and the density live at cell centres
+ * and every momentum CV sits between two cells along its staggering axis d
+ * (the cell below, e_d back, and the cell of the same index): the source of
+ * the CV is the difference of p' across it over dx_d, and on w the mean of
+ * rho' of the two cells.  The source enters dU of the CV as it stands (the
+ * integral of a source over the CV over its volume).  A cell that is covered
+ * (or outside the window) takes the value of the other cell: no pressure
+ * force across a wall side, the buoyancy of the fluid cell. */
+#define ORC_P00 1.0e5
+#define ORC_RD 287.0
+#define ORC_CP 1004.5
+
+typedef struct {
+  const double *rho0;   /* nz  reference density of every level              */
+  const double *rt0;    /* nz  reference rho0*theta0 of every level          */
+  double grav;          /* gravitational acceleration (buoyancy), m/s^2      */
+  int pressure;         /* add -grad p'                                     */
+  int buoyancy;         /* add -rho' g to rho*w                              */
+} OrcSources;
+
+/* p from the equation of state */
+double orc_eos_pressure(double rt) {
+  double gamma = ORC_CP / (ORC_CP - ORC_RD);
+  return ORC_P00 * pow(ORC_RD * rt / ORC_P00, gamma);
+}
+
+/* p' = p(rt) - p(rt0) of a cell with rho*theta = rt on a level with
+ * reference rt0.  Written as p(rt0) [(1 + x)^gamma - 1], x = (rt - rt0) / rt0,
+ * the same quantity without subtracting two values near 1e5 Pa (which
+ * would leave an error near 1e-11 Pa in p'); rt - rt0 is exact in FP64 for
+ * rt within a factor two of rt0. */
+static double pressure_perturbation(double rt, double rt0) {
+  double gamma = ORC_CP / (ORC_CP - ORC_RD);
+  return orc_eos_pressure(rt0) * expm1(gamma * log1p((rt - rt0) / rt0));
+}
+
+/* Adds the sources of state U to dU (rho*u, rho*v, rho*w; every prognostic
+ * non-covered CV of the window). */
+int orc_sources(const OrcDomain *D, const OrcGeom *G, const OrcState *U, const OrcSources *S, OrcState *dU) {
+  const double inv[3] = {1.0 / D->dx, 1.0 / D->dy, 1.0 / D->dz};
+  for (int g = GU; g <= GW; g++) {
+    int d = g - 1, di = d == 0, dj = d == 1, dk = d == 2;
+    int nzg = nzg_of(D, g);
+    double *out = dU->f[g + 1];
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nzg; k++) {
+      if (!prognostic(D, g, k)) continue;
+      for (int wj = 0; wj < D->WY; wj++)
+        for (int wi = 0; wi < D->WX; wi++) {
+          int gi = D->x0 + wi, gj = D->y0 + wj;
+          long id = avail(D, G, g, gi, gj, k);
+          if (id < 0) continue;
+          long a = avail(D, G, GC, gi - di, gj - dj, k - dk);   /* the cell below along d */
+          long b = avail(D, G, GC, gi, gj, k);                    /* the cell of the same index */
+          if (a < 0 && b < 0) continue;
+          int ka = k - dk;
+          double s = 0.0;
+          if (S->pressure) {
+            double pa = a >= 0 ? pressure_perturbation(U->f[1][a], S->rt0[ka]) : 0.0;
+            double pb = b >= 0 ? pressure_perturbation(U->f[1][b], S->rt0[k]) : 0.0;
+            if (a < 0) pa = pb;
+            if (b < 0) pb = pa;
+            s -= (pb - pa) * inv[d];
+          }
+          if (S->buoyancy && g == GW) {
+            double ra = a >= 0 ? U->f[0][a] - S->rho0[ka] : 0.0;
+            double rb = b >= 0 ? U->f[0][b] - S->rho0[k] : 0.0;
+            if (a < 0) ra = rb;
+            if (b < 0) rb = ra;
+            s -= S->grav * 0.5 * (ra + rb);
+          }
+          out[id] += s;
+        }
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 5. The step (Algorithm 1)                                                   */
+/* ------------------------------------------------------------------------- */
+/* One stage: Uout = R[ Ubase + dt * (dU(Usrc) + S(Usrc)) ] on all four grids,
+ * S the sources of section 4 (none when S is NULL).  scratch holds 5 arrays
+ * of the field sizes. */
 int orc_stage(const OrcDomain *D, const OrcGeom *G, const OrcWsrd *W, const OrcState *Usrc, const OrcState *Ubase,
-              double dt, OrcState *Uout, OrcState *scratch) {
+              double dt, OrcState *Uout, OrcState *scratch, const OrcSources *S) {
   orc_flux_div(D, G, Usrc, scratch);
+  if (S) orc_sources(D, G, Usrc, S, scratch);
   for (int f = 0; f < 5; f++) {
     int g = FIELD_GRID[f];
     long n = ncv(D, g);

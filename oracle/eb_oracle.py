@@ -8,10 +8,12 @@ Arrays are numpy, shaped ``(nz_g, WY, WX)`` (x fastest) for a grid with
 ``nz_g`` levels (``nz`` for the c, u and v grids, ``nz + 1`` for w).  Vector
 fields carry a leading axis of 3 (or 6 for face centroids).
 
-The step follows Algorithm 1 of the paper with S = 0: ``stages=1`` is the
-forward-Euler update of Eq. FV-discrete, ``stages=3`` the three-stage
-Runge-Kutta of Sec. 5.2 (U1 = U + dt/3 L(U), U2 = U + dt/2 L(U1),
-U' = U + dt L(U2)) with redistribution after every stage.
+The step follows Algorithm 1 of the paper: ``stages=1`` is the forward-Euler
+update of Eq. FV-discrete, ``stages=3`` the three-stage Runge-Kutta of Sec.
+5.2 (U1 = U + dt/3 L(U), U2 = U + dt/2 L(U1), U' = U + dt L(U2)) with
+redistribution after every stage; L is the flux divergence, plus the sources
+of the compressible system (Sec. 2.1: the perturbation pressure gradient from
+the equation of state and the buoyancy) when a ``Sources`` is given.
 """
 from __future__ import annotations
 
@@ -71,6 +73,11 @@ class _State(ctypes.Structure):
     _fields_ = [("f", ctypes.c_void_p * 5)]
 
 
+class _Sources(ctypes.Structure):
+    _fields_ = [("rho0", ctypes.c_void_p), ("rt0", ctypes.c_void_p), ("grav", ctypes.c_double),
+                ("pressure", ctypes.c_int), ("buoyancy", ctypes.c_int)]
+
+
 def _load():
     global _lib
     with _lock:
@@ -83,7 +90,10 @@ def _load():
             lib.orc_wsrd_apply.argtypes = [P(_Domain), ctypes.c_int, P(_Geom), P(_Wsrd), ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_stage.argtypes = [P(_Domain), P(_Geom), P(_Wsrd), P(_State), P(_State), ctypes.c_double,
-                                      P(_State), P(_State)]
+                                      P(_State), P(_State), P(_Sources)]
+            lib.orc_sources.argtypes = [P(_Domain), P(_Geom), P(_State), P(_Sources), P(_State)]
+            lib.orc_eos_pressure.argtypes = [ctypes.c_double]
+            lib.orc_eos_pressure.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -212,8 +222,40 @@ def wsrd(dom: Domain, geom: dict, tabs: dict, g: int, Uhat: np.ndarray, diag: bo
     return out
 
 
-def stage(dom, geom, tabs, Usrc, Ubase, dt):
-    """Uout = R[Ubase + dt * dU(Usrc)] on all four grids."""
+class Sources:
+    """The sources of the compressible system (Sec. 2.1, Eq. mom-comp) for a
+    reference state given per level: rho0 and rho0*theta0 (nz values each);
+    ``pressure``: -grad p' with p from the equation of state, ``buoyancy``:
+    -rho' g on rho*w."""
+
+    def __init__(self, rho0, rt0, pressure=True, buoyancy=True, grav=9.81):
+        self.rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+        self.rt0 = np.ascontiguousarray(rt0, dtype=np.float64)
+        self.pressure, self.buoyancy, self.grav = bool(pressure), bool(buoyancy), float(grav)
+
+    def _c(self):
+        return _Sources(_ptr(self.rho0), _ptr(self.rt0), self.grav, int(self.pressure), int(self.buoyancy))
+
+
+def eos_pressure(rt: float) -> float:
+    """p of the equation of state for rho*theta = rt (Sec. 2.1)."""
+    return float(_load().orc_eos_pressure(float(rt)))
+
+
+def sources(dom: Domain, geom: dict, U: dict, S: Sources) -> dict:
+    """The sources of state U alone, as a dU (zero on the c grid)."""
+    _check_state(dom, U)
+    assert S.rho0.shape == (dom.nz,) and S.rt0.shape == (dom.nz,)
+    dU = empty_state(dom)
+    cs = S._c()
+    _load().orc_sources(ctypes.byref(dom._c), _cgeom(geom), ctypes.byref(_cstate(U)), ctypes.byref(cs),
+                        ctypes.byref(_cstate(dU)))
+    return dU
+
+
+def stage(dom, geom, tabs, Usrc, Ubase, dt, src: Sources | None = None):
+    """Uout = R[Ubase + dt * (dU(Usrc) + S(Usrc))] on all four grids (S: the
+    sources, none when src is None)."""
     lib = _load()
     _check_state(dom, Usrc)
     _check_state(dom, Ubase)
@@ -223,21 +265,27 @@ def stage(dom, geom, tabs, Usrc, Ubase, dt):
     for g in range(4):
         T = tabs[g]
         cw[g] = _Wsrd(*(_ptr(T[k]) for k in ("code", "nnb", "kappa", "omega", "vhat", "xhat")))
+    cs = None
+    if src is not None:
+        assert src.rho0.shape == (dom.nz,) and src.rt0.shape == (dom.nz,)
+        cs = src._c()
     lib.orc_stage(ctypes.byref(dom._c), _cgeom(geom), cw, ctypes.byref(_cstate(Usrc)), ctypes.byref(_cstate(Ubase)),
-                  float(dt), ctypes.byref(_cstate(out)), ctypes.byref(_cstate(scratch)))
+                  float(dt), ctypes.byref(_cstate(out)), ctypes.byref(_cstate(scratch)),
+                  ctypes.byref(cs) if cs is not None else None)
     return out
 
 
-def step(dom, geom, tabs, U, dt, nsteps=1, stages=1):
-    """nsteps steps of Algorithm 1 (stages = 1 or 3)."""
+def step(dom, geom, tabs, U, dt, nsteps=1, stages=1, src: Sources | None = None):
+    """nsteps steps of Algorithm 1 (stages = 1 or 3), with the sources src
+    when given."""
     U = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in U.items()}
     for _ in range(int(nsteps)):
         if stages == 1:
-            U = stage(dom, geom, tabs, U, U, dt)
+            U = stage(dom, geom, tabs, U, U, dt, src)
         elif stages == 3:
-            U1 = stage(dom, geom, tabs, U, U, dt / 3.0)
-            U2 = stage(dom, geom, tabs, U1, U, dt / 2.0)
-            U = stage(dom, geom, tabs, U2, U, dt)
+            U1 = stage(dom, geom, tabs, U, U, dt / 3.0, src)
+            U2 = stage(dom, geom, tabs, U1, U, dt / 2.0, src)
+            U = stage(dom, geom, tabs, U2, U, dt, src)
         else:
             raise ValueError("stages must be 1 or 3")
     return U

@@ -873,6 +873,36 @@ eb_status eb_geom_set_wind_reference(eb_geom geom, const double *ref_rhou, const
   return EB_OK;
 }
 
+eb_status eb_geom_set_sources(eb_geom geom, int flags) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  if (flags & ~(EB_SOURCE_PRESSURE | EB_SOURCE_BUOYANCY)) return fail(EB_ERR_INVALID_ARG, "unknown source flags");
+  if (flags && !geom->has_ref)
+    return fail(EB_ERR_STATE, "the sources need a handle built with the reference profiles rho0 and rho0*theta0");
+  if (flags && !geom->src_d[0]) {
+    // per-level tables from the reference: p0 (equation of state of rho0
+    // theta0) and 1 / (rho0 theta0), in double and in float
+    const int nz = geom->D.nz;
+    std::vector<double> rt(nz), td[2];
+    CUDA_TRY(cudaMemcpy(rt.data(), geom->ref_d[1], sizeof(double) * nz, cudaMemcpyDeviceToHost), "read profile");
+    const double gamma = EB_CP / (EB_CP - EB_RD);
+    for (int q = 0; q < 2; ++q) td[q].resize(nz);
+    for (int k = 0; k < nz; ++k) {
+      if (!(rt[k] > 0.0)) return fail(EB_ERR_STATE, "the reference rho0*theta0 must be positive for the sources");
+      td[0][k] = EB_P00 * pow(EB_RD * rt[k] / EB_P00, gamma);
+      td[1][k] = 1.0 / rt[k];
+    }
+    for (int q = 0; q < 2; ++q) {
+      std::vector<float> tf(td[q].begin(), td[q].end());
+      CUDA_TRY(geom->alloc(&geom->src_d[q], nz), "alloc source tables");
+      CUDA_TRY(geom->alloc(&geom->src_f[q], nz), "alloc source tables");
+      CUDA_TRY(cudaMemcpy(geom->src_d[q], td[q].data(), sizeof(double) * nz, cudaMemcpyHostToDevice), "tables");
+      CUDA_TRY(cudaMemcpy(geom->src_f[q], tf.data(), sizeof(float) * nz, cudaMemcpyHostToDevice), "tables");
+    }
+  }
+  geom->src_flags = flags;
+  return EB_OK;
+}
+
 eb_status eb_geom_set_bulk_priority(eb_geom geom, int high) {
   if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
   if (high != 0 && high != 1) return fail(EB_ERR_INVALID_ARG, "high must be 0 or 1");

@@ -258,8 +258,11 @@ eb_status eb_ensemble_create(const eb_geom *members, int n, eb_ensemble *out) {
   if (!out) return fail(EB_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!members || n < 1) return fail(EB_ERR_INVALID_ARG, "members is NULL or n < 1");
-  for (int q = 0; q < n; ++q)
+  for (int q = 0; q < n; ++q) {
     if (!members[q]) return fail(EB_ERR_INVALID_ARG, "a member handle is NULL");
+    if (members[q]->src_flags)
+      return fail(EB_ERR_STATE, "ensembles take no compressible sources: a member has them switched on");
+  }
   for (int q = 1; q < n; ++q) {
     if (members[q]->prec != members[0]->prec) return fail(EB_ERR_INVALID_ARG, "members differ in precision");
     if (members[q]->device != members[0]->device) return fail(EB_ERR_INVALID_ARG, "members are on different devices");

@@ -121,6 +121,11 @@ struct eb_geom_s {
   eb_geom_info_t info;
   bool has_ref = false;        // built with a reference profile
   bool has_wind_ref = false;   // a nonzero background momentum profile was set
+  // sources of the compressible system (EB_SOURCE_* flags) and their
+  // per-level tables: p0 = EOS of rho0 theta0, 1 / (rho0 theta0)
+  int src_flags = 0;
+  double *src_d[2] = {nullptr, nullptr};
+  float *src_f[2] = {nullptr, nullptr};
   ProjWork pw;
 
   template <typename P>
@@ -307,7 +312,13 @@ template <typename T>
 void stage(eb_geom g, void *const src[5], void *const base[5], void *const out[5], double dt, int copy,
            cudaStream_t s, bool wsrd_beside = true) {
   const StepArgs<T> A = step_args<T>(g, src, base, out, dt, copy);
-  if (g->wsrd_side && wsrd_beside) {
+  if (g->src_flags) {   // the sources follow the whole flux update; the redistribution follows them
+    flux_update(g, A, s);
+    const bool f64 = sizeof(T) == sizeof(double);
+    launch_sources<T>(A, g->src_flags, f64 ? (const T *)g->src_d[0] : (const T *)g->src_f[0],
+                      f64 ? (const T *)g->src_d[1] : (const T *)g->src_f[1], s);
+    wsrd_all<T>(g, out, s);
+  } else if (g->wsrd_side && wsrd_beside) {
     flux_update(g, A, s, [&](cudaStream_t side) { wsrd_all<T>(g, out, side); });
   } else {
     flux_update(g, A, s);

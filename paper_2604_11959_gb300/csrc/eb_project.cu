@@ -698,6 +698,8 @@ void launch_correct(eb_geom g, void *const mom[3], double dt, cudaStream_t s) {
 eb_status eb_project_rhs(eb_geom g, void *const mom[3], double dt, double *rms, cudaStream_t s) {
   if (g->has_wind_ref)
     return fail(EB_ERR_STATE, "the projection needs full momenta: this handle has a background momentum profile");
+  if (g->src_flags)
+    return fail(EB_ERR_STATE, "the anelastic calls take no compressible sources: this handle has them switched on");
   eb_status st = setup(g, s);
   if (st != EB_OK) return st;
   ProjWork &w = g->pw;
@@ -716,6 +718,8 @@ eb_status eb_project_impl(eb_geom g, void *const mom[3], double dt, double rtol,
                           double *phi_out, int *iters, double *relres, cudaStream_t s, bool correct) {
   if (g->has_wind_ref)
     return fail(EB_ERR_STATE, "the projection needs full momenta: this handle has a background momentum profile");
+  if (g->src_flags)
+    return fail(EB_ERR_STATE, "the anelastic calls take no compressible sources: this handle has them switched on");
   eb_status st = setup(g, s);
   if (st != EB_OK) return st;
   ProjWork &w = g->pw;
@@ -818,6 +822,8 @@ eb_status eb_anelastic_step(eb_geom geom, const eb_state *Un, eb_state *Unp1, do
                             int maxit, int *iters, void *stream) {
   if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
   if (!geom->has_ref) return fail(EB_ERR_STATE, "the anelastic step needs a handle built with a reference profile");
+  if (geom->src_flags)
+    return fail(EB_ERR_STATE, "the anelastic calls take no compressible sources: this handle has them switched on");
   const size_t es = geom->prec == EB_F64 ? 8 : 4;
   if (!state_ok(Un, es) || !state_ok(Unp1, es)) return fail(EB_ERR_INVALID_ARG, "state pointer NULL or misaligned");
   if (!(dt > 0.0) || !isfinite(dt)) return fail(EB_ERR_INVALID_ARG, "dt must be finite and > 0");

@@ -60,6 +60,10 @@ template <typename T>
 void launch_wsrd(const WsrdArgs<T> &R, cudaStream_t s);
 template <typename T>
 void launch_wsrd5(const WsrdSet<T> &S, cudaStream_t s);
+// sources of the compressible system (eb_sources.cu): flags EB_SOURCE_*,
+// per-level tables p0 and 1 / (rho0 theta0)
+template <typename T>
+void launch_sources(const StepArgs<T> &A, int flags, const T *p0, const T *irt0, cudaStream_t s);
 
 // One ensemble member in one step direction: the arguments of its flux
 // update and of its five-field redistribution.

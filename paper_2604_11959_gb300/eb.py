@@ -34,7 +34,7 @@ EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom
                     "eb_project_sample", "eb_project_warm", "eb_geom_tune",
                     "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
                     "eb_geom_set_wind_reference", "eb_fma_peak", "eb_ensemble_info",
-                    "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule")
+                    "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule", "eb_geom_set_sources")
 
 
 class EbError(RuntimeError):
@@ -117,6 +117,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_geom_set_bulk_priority.argtypes = [V, I]
     lib.eb_project_set_preconditioner.argtypes = [V, I]
     lib.eb_geom_set_wind_reference.argtypes = [V, V, V, V]
+    lib.eb_geom_set_sources.argtypes = [V, I]
     lib.eb_fma_peak.argtypes = [I, P(D), V]
     lib.eb_ensemble_info.argtypes = [V, P(I)]
     lib.eb_ensemble_inject_barrier_fault.argtypes = [V, I]
@@ -131,7 +132,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                  "eb_unet_destroy", "eb_project_sample", "eb_project_warm", "eb_geom_tune",
                  "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
                  "eb_geom_set_wind_reference", "eb_fma_peak", "eb_ensemble_info",
-                 "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule"):
+                 "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule", "eb_geom_set_sources"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -199,6 +200,12 @@ class Geometry:
                                                  ref_rhov.data_ptr() if ref_rhov is not None else None,
                                                  _stream(stream)))
         self._wind = (ref_rhou, ref_rhov)
+
+    def set_sources(self, pressure: bool = True, buoyancy: bool = True):
+        """Sources of the compressible system that eb_step adds to every stage
+        (``eb_geom_set_sources``): the perturbation pressure gradient from the
+        equation of state and the buoyancy; both False switches them off."""
+        _check(load().eb_geom_set_sources(self.handle, (1 if pressure else 0) | (2 if buoyancy else 0)))
 
     def close(self):
         if getattr(self, "_h", None):
