@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--precision", choices=("both", "mixed", "f64"), default="both",
                     help="arms to run (profiling runs pick one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--ensemble-schedule", choices=("tuned", "persistent", "branches"), default="tuned",
+                    help="ensemble: the autotuner's schedule, or one forced after tuning the slab heights")
     ap.add_argument("--slab-levels", type=int, default=None,
                     help="bulk kernel slab height (0 = automatic); default: chosen by the autotuner")
     return ap.parse_args()
@@ -229,7 +231,7 @@ def run_anelastic(eb, steps, warmup, clk=None, dist=None):
             "projection": proj, "workload": w.name}
 
 
-def run_ensemble(eb, steps, warmup, clk=None, dist=None):
+def run_ensemble(eb, steps, warmup, clk=None, dist=None, schedule="tuned"):
     """64 uneven Gaussian-hill instances (64x64x32 .. 256x256x64, 94,371,840
     cells), mixed path, advanced together: one CUDA-graph launch per step,
     slab heights chosen by the autotuner.  Like the single-domain line, every
@@ -257,6 +259,8 @@ def run_ensemble(eb, steps, warmup, clk=None, dist=None):
 
     reload()
     slab = ens.tune(dts, reps=2)
+    if schedule != "tuned":
+        ens.set_schedule(schedule)
     for _ in range(warmup):
         reload()
         ens.step(dts, 1)
@@ -926,7 +930,7 @@ def run_arm(args, rank, world, w, dist):
         libbuild.build()
         eb.load()
         clk = ClockSampler(torch.cuda.current_device())
-        r = run_ensemble(eb, args.steps, max(3, args.warmup), clk, dist)
+        r = run_ensemble(eb, args.steps, max(3, args.warmup), clk, dist, args.ensemble_schedule)
         if rank == 0:
             print(json.dumps({
                 "metric": METRIC, "value": r["value"] * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
