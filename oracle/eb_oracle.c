@@ -25,7 +25,10 @@
  *      buoyancy, added to the flux divergence of every stage when asked for;
  *   5. the step of Algorithm 1 (stages = 1: forward Euler of Eq. FV-discrete;
  *      stages = 3: the three-stage Runge-Kutta of Sec. 5.2 with WSRD after
- *      every stage).
+ *      every stage);
+ *   6. two-level static refinement (Sec. 4.3): the geometry of the coarse
+ *      level merged from the fine level's cells, and the restriction of a
+ *      fine state (volume- and area-weighted averages).
  *
  * Units: inside the geometry every length is in grid units (x / dx, y / dy,
  * z / dz).  Volume fractions are relative to dx*dy*dz, face fractions to the
@@ -1216,6 +1219,172 @@ int orc_stage(const OrcDomain *D, const OrcGeom *G, const OrcWsrd *W, const OrcS
     for (long c = 0; c < n; c++) hat[c] = Ubase->f[f][c] + dt * hat[c];
     /* covered and non-prognostic CVs keep their value: dU is zero there */
     orc_wsrd_apply(D, g, &G[g], &W[g], hat, Uout->f[f], NULL, NULL, NULL);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 6. Two-level static refinement (Sec. 4.3)                                  */
+/* ------------------------------------------------------------------------- */
+/* Refinement ratio 2 in every direction: the fine level has 2NX x 2NY x 2nz
+ * cells over the same domain as the coarse one.  The coarse geometry is
+ * built from the fine cells by merging, so that coarse volumes, face areas
+ * and EB areas are sums of fine ones.  A coarse CV of any grid is a block of
+ * 2x2x2 fine cells of the fine c grid: cells 2I, 2I+1 along x for the c grid,
+ * 2I-1, 2I for the u grid (the right half of coarse cell I-1 and the left
+ * half of cell I), likewise along y for v and along z for w; fine cells
+ * below the bottom or above the top of the domain hold no fluid.
+ *   volume fraction   the mean of the 8 fine ones;
+ *   volume centroid   their volume-weighted mean position;
+ *   face fraction     the mean of the 4 fine faces on the coarse low face,
+ *                     its centroid their area-weighted mean position;
+ *   EB area           the sum of the fine ones (a quarter of it in units of
+ *                     the coarse dx dy), its centroid their area-weighted mean;
+ *   EB normal         the direction of the area-weighted sum of the fine EB
+ *                     normals, which (the boundary of a fluid region being
+ *                     closed) is sum_d (open area of the high d-face - open
+ *                     area of the low d-face) e_d over the coarse CV's faces;
+ *   class             covered (all its fine cells inside the domain
+ *                     covered), regular (all of them regular) or cut.
+ * Positions are offsets from the CV (or face) centre in grid units of its
+ * level: a fine cell's centre sits at -1/2 or +1/2 fine units from the
+ * coarse CV centre along each axis, and a fine unit is half a coarse one. */
+
+/* the fine c-grid cell (i, j, k) of the whole periodic fine domain; id < 0
+ * outside the domain in z (no fluid) */
+static long fine_id(const OrcDomain *Df, int i, int j, int k) {
+  if (k < 0 || k >= Df->nz) return -1;
+  return loc(Df, GC, imod(i, Df->NX), imod(j, Df->NY), k);
+}
+
+int orc_coarsen(const OrcDomain *Df, const OrcGeom *Gf, const OrcDomain *Dc, int g, OrcGeom *Gc) {
+  if (Df->WX != Df->NX || Df->WY != Df->NY || Dc->WX != Dc->NX || Dc->WY != Dc->NY) return 1;
+  if (Df->NX != 2 * Dc->NX || Df->NY != 2 * Dc->NY || Df->nz != 2 * Dc->nz) return 1;
+  const OrcGeom *F = &Gf[GC];
+  long nf = ncv(Df, GC), nc = ncv(Dc, g);
+  int nzg = nzg_of(Dc, g);
+  int sx = g == GU, sy = g == GV, sz = g == GW;
+  double Af[3] = {Df->dy * Df->dz, Df->dx * Df->dz, Df->dx * Df->dy};
+#pragma omp parallel for schedule(static)
+  for (int K = 0; K < nzg; K++)
+    for (int J = 0; J < Dc->NY; J++)
+      for (int I = 0; I < Dc->NX; I++) {
+        long id = loc(Dc, g, I, J, K);
+        int f0[3] = {2 * I - sx, 2 * J - sy, 2 * K - sz};
+        double vol = 0, m[3] = {0, 0, 0}, eba = 0, eb[3] = {0, 0, 0}, ebv[3] = {0, 0, 0};
+        double fa[3] = {0, 0, 0}, f1[3] = {0, 0, 0}, f2[3] = {0, 0, 0}, fh[3] = {0, 0, 0};
+        int nin = 0, ncov = 0, nreg = 0;
+        for (int c = 0; c < 2; c++)
+          for (int b = 0; b < 2; b++)
+            for (int a = 0; a < 2; a++) {
+              int q[3] = {a, b, c};
+              double o[3] = {a - 0.5, b - 0.5, c - 0.5};
+              long f = fine_id(Df, f0[0] + a, f0[1] + b, f0[2] + c);
+              if (f < 0) continue;   /* outside the domain: no fluid, and no part of the class */
+              nin++;
+              if (F->flag[f] == ORC_COVERED) ncov++;
+              if (F->flag[f] == ORC_REGULAR) nreg++;
+              double al = F->alpha[f], ae = F->aeb[f];
+              vol += al;
+              eba += ae;
+              for (int d = 0; d < 3; d++) {
+                m[d] += al * (o[d] + F->cent[d * nf + f]);
+                eb[d] += ae * (o[d] + F->ebc[d * nf + f]);
+                ebv[d] += F->ebv[d * nf + f];
+              }
+              for (int d = 0; d < 3; d++) {
+                if (q[d] != 0) continue;   /* the fine cells on the coarse low d-face */
+                int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+                double be = F->beta[d * nf + f];
+                fa[d] += be;
+                f1[d] += be * (o[t1] + F->fcent[(2 * d) * nf + f]);
+                f2[d] += be * (o[t2] + F->fcent[(2 * d + 1) * nf + f]);
+              }
+            }
+        /* open areas of the coarse high faces: the low faces of the fine cells
+         * two beyond the block's first; the lid above the top is open */
+        for (int d = 0; d < 3; d++)
+          for (int u = 0; u < 2; u++)
+            for (int v = 0; v < 2; v++) {
+              int ii = f0[0], jj = f0[1], kk = f0[2];
+              int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+              int *pd = d == 0 ? &ii : d == 1 ? &jj : &kk;
+              int *p1 = t1 == 0 ? &ii : &jj;
+              int *p2 = t2 == 1 ? &jj : &kk;
+              *pd += 2;
+              *p1 += u;
+              *p2 += v;
+              long f = fine_id(Df, ii, jj, kk);
+              if (f >= 0) fh[d] += F->beta[d * nf + f];
+              else if (d == 2 && kk >= Df->nz) fh[d] += 1.0;
+            }
+        Gc->flag[id] = (uint8_t)(ncov == nin ? ORC_COVERED : nreg == nin ? ORC_REGULAR : ORC_CUT);
+        Gc->alpha[id] = vol / 8.0;
+        Gc->aeb[id] = eba / 4.0;
+        double nv[3], nn = 0;
+        for (int d = 0; d < 3; d++) {
+          Gc->cent[d * nc + id] = vol > 0 ? 0.5 * m[d] / vol : 0.0;
+          Gc->beta[d * nc + id] = fa[d] / 4.0;
+          Gc->fcent[(2 * d) * nc + id] = fa[d] > 0 ? 0.5 * f1[d] / fa[d] : 0.0;
+          Gc->fcent[(2 * d + 1) * nc + id] = fa[d] > 0 ? 0.5 * f2[d] / fa[d] : 0.0;
+          Gc->ebc[d * nc + id] = eba > 0 ? 0.5 * eb[d] / eba : 0.0;
+          Gc->ebv[d * nc + id] = ebv[d] / 4.0;
+          nv[d] = (fh[d] - fa[d]) * Af[d];
+          nn += nv[d] * nv[d];
+        }
+        nn = sqrt(nn);
+        for (int d = 0; d < 3; d++) Gc->nrm[d * nc + id] = (eba > 0 && nn > 0) ? nv[d] / nn : 0.0;
+      }
+  return 0;
+}
+
+/* Restriction of a fine state to the coarse level (Sec. 4.3): a coarse
+ * cell-centred value is the volume-weighted mean of its 8 fine cells (weights
+ * the fine volume fractions), so that the coarse cell holds the fine cells'
+ * total; a coarse face value is the area-weighted mean of the 4 fine values
+ * on its face (weights the fine face fractions), so that the flux integral
+ * over the coarse face is kept.  Coarse CVs whose fine parts hold no fluid or
+ * no open area keep their values (Uc is read and written). */
+int orc_restrict(const OrcDomain *Df, const OrcGeom *Gf, const OrcState *Uf, const OrcDomain *Dc, OrcState *Uc) {
+  if (Df->NX != 2 * Dc->NX || Df->NY != 2 * Dc->NY || Df->nz != 2 * Dc->nz) return 1;
+  const OrcGeom *F = &Gf[GC];
+  long nf = ncv(Df, GC);
+  for (int fld = 0; fld < 5; fld++) {
+    int g = FIELD_GRID[fld];
+    int nzg = nzg_of(Dc, g);
+    int d = g - 1;
+#pragma omp parallel for schedule(static)
+    for (int K = 0; K < nzg; K++)
+      for (int J = 0; J < Dc->NY; J++)
+        for (int I = 0; I < Dc->NX; I++) {
+          long id = loc(Dc, g, I, J, K);
+          double w = 0, s = 0;
+          if (g == GC) {
+            for (int c = 0; c < 2; c++)
+              for (int b = 0; b < 2; b++)
+                for (int a = 0; a < 2; a++) {
+                  long f = fine_id(Df, 2 * I + a, 2 * J + b, 2 * K + c);
+                  w += F->alpha[f];
+                  s += F->alpha[f] * Uf->f[fld][f];
+                }
+          } else {
+            /* the 4 fine faces of grid g at fine index 2I (2J, 2K) along d */
+            for (int v = 0; v < 2; v++)
+              for (int u = 0; u < 2; u++) {
+                int ii = 2 * I, jj = 2 * J, kk = 2 * K;
+                if (d == 0) { jj += u; kk += v; }
+                else if (d == 1) { ii += u; kk += v; }
+                else { ii += u; jj += v; }
+                long f = fine_id(Df, ii, jj, kk);          /* the fine cell whose low d-face it is */
+                if (f < 0) continue;                        /* the top lid of w: a wall */
+                long fu = loc(Df, g, imod(ii, Df->NX), imod(jj, Df->NY), kk);
+                double be = F->beta[d * nf + f];
+                w += be;
+                s += be * Uf->f[fld][fu];
+              }
+          }
+          if (w > 0) Uc->f[fld][id] = s / w;
+        }
   }
   return 0;
 }

@@ -92,6 +92,8 @@ def _load():
             lib.orc_stage.argtypes = [P(_Domain), P(_Geom), P(_Wsrd), P(_State), P(_State), ctypes.c_double,
                                       P(_State), P(_State), P(_Sources)]
             lib.orc_sources.argtypes = [P(_Domain), P(_Geom), P(_State), P(_Sources), P(_State)]
+            lib.orc_coarsen.argtypes = [P(_Domain), P(_Geom), P(_Domain), ctypes.c_int, P(_Geom)]
+            lib.orc_restrict.argtypes = [P(_Domain), P(_Geom), P(_State), P(_Domain), P(_State)]
             lib.orc_eos_pressure.argtypes = [ctypes.c_double]
             lib.orc_eos_pressure.restype = ctypes.c_double
             _lib = lib
@@ -289,6 +291,47 @@ def step(dom, geom, tabs, U, dt, nsteps=1, stages=1, src: Sources | None = None)
         else:
             raise ValueError("stages must be 1 or 3")
     return U
+
+
+def coarse_domain(fine: Domain, h_coarse=None) -> Domain:
+    """The coarse level of a refinement ratio 2 over the same domain (Sec.
+    4.3): NX/2 x NY/2 x nz/2 cells; its nodal heights default to every other
+    fine node (they serve only as a record: the coarse geometry comes from
+    ``coarsen``)."""
+    assert fine.NX % 2 == 0 and fine.NY % 2 == 0 and fine.nz % 2 == 0
+    h = fine.h[::2, ::2] if h_coarse is None else h_coarse
+    return Domain(fine.NX // 2, fine.NY // 2, fine.nz // 2, fine.Lx, fine.Ly, fine.Lz, np.ascontiguousarray(h))
+
+
+def coarsen(fine: Domain, geom: dict, coarse: Domain) -> dict:
+    """Geometry of the four grids of the coarse level, merged from the fine
+    level's cells (Sec. 4.3; section 6 of eb_oracle.c)."""
+    lib = _load()
+    fg = _cgeom(geom)
+    out = {}
+    for g in range(4):
+        s = coarse.shape(g)
+        G = dict(alpha=np.zeros(s), cent=np.zeros((3,) + s), beta=np.zeros((3,) + s),
+                 fcent=np.zeros((6,) + s), aeb=np.zeros(s), nrm=np.zeros((3,) + s),
+                 ebc=np.zeros((3,) + s), ebv=np.zeros((3,) + s), flag=np.zeros(s, np.uint8))
+        cg = _Geom(*(_ptr(G[k]) for k in ("alpha", "cent", "beta", "fcent", "aeb", "nrm", "ebc", "ebv", "flag")))
+        if lib.orc_coarsen(ctypes.byref(fine._c), fg, ctypes.byref(coarse._c), g, ctypes.byref(cg)) != 0:
+            raise ValueError("coarsen: the coarse level must halve every fine dimension over the whole domain")
+        out[g] = G
+    return out
+
+
+def restrict(fine: Domain, geom: dict, Uf: dict, coarse: Domain, Uc: dict) -> dict:
+    """The fine state restricted to the coarse level (Sec. 4.3): volume-
+    weighted cell-centred fields, area-weighted face fields; coarse CVs with
+    no fine fluid or open area keep their values from Uc."""
+    _check_state(fine, Uf)
+    _check_state(coarse, Uc)
+    out = {k: np.ascontiguousarray(Uc[k], dtype=np.float64).copy() for k in FIELDS}
+    if _load().orc_restrict(ctypes.byref(fine._c), _cgeom(geom), ctypes.byref(_cstate(Uf)), ctypes.byref(coarse._c),
+                            ctypes.byref(_cstate(out))) != 0:
+        raise ValueError("restrict: the coarse level must halve every fine dimension")
+    return out
 
 
 def set_threads(n: int) -> None:
