@@ -393,6 +393,51 @@ def compressible_cost(eb, world, dist, warmup, steps):
             "steps": steps, "sources": "pressure gradient (equation of state) and buoyancy"}
 
 
+def restriction_cost(eb, dist, warmup, steps):
+    """Two-level refinement on the hill: the 128x128x64 coarse level built
+    from the 256x256x128 handle by merging its cells (eb_geom_build_coarse,
+    timed once on the host clock), and the restriction of a mixed state onto
+    it (eb_restrict, per-call events with the L2 flushed before each).  The
+    restriction's algorithmic traffic: the fine state (5 fields, 4 B) read
+    once, the coarse state written once."""
+    import torch
+    w = workload("hill256")
+    h = w.heights()
+    refs = w.references("sheltered")
+    fine = make_geom(eb, w, h, "mixed", refs)
+    from paper_2604_11959_gb300 import inputs
+    rc = inputs.cell_reference(w.nz // 2, w.Lz)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    coarse = fine.coarse(ref_rho=torch.from_numpy(rc[0]).cuda(), ref_rhotheta=torch.from_numpy(rc[1]).cuda())
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Uf = eb.device_state(w.state("sheltered"), "mixed", refs)
+    Uc = coarse.empty_state()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        eb.restrict(fine, coarse, Uf, Uc)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        eb.restrict(fine, coarse, Uf, Uc)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = max_over_ranks(float(np.mean(ms)), dist)
+    fine_bytes = sum(int(np.prod(fine.shape(f))) for f in eb.FIELDS) * 4
+    coarse_bytes = sum(int(np.prod(coarse.shape(f))) for f in eb.FIELDS) * 4
+    hbm, kind = peaks()
+    gbs = (fine_bytes + coarse_bytes) / (t * 1e-3) / 1e9
+    coarse.close()
+    fine.close()
+    return {"workload": f"{w.name} -> 128x128x64", "coarse_build_s": build_s, "restrict_ms": t,
+            "restrict_gbs": gbs, "restrict_hbm_frac": gbs / hbm, "algorithmic_bytes": fine_bytes + coarse_bytes}
+
+
 def other_configs(eb, world, dist, warmup, steps=10):
     """The other timed configurations, measured in the default run beside
     the headline: the 512x512x256 random terrain (mixed path, tuned, per-step
@@ -410,6 +455,7 @@ def other_configs(eb, world, dist, warmup, steps=10):
                       "steps": r["steps"], "phases_ms": r["phases_ms"], "roofline_frac": r["roofline"]["frac"],
                       "tuned_slab_levels": r["tuned_slab_levels"], "bulk_high_priority": r["bulk_high_priority"]}}
     out["hill256_compressible"] = compressible_cost(eb, world, dist, warmup, steps)
+    out["hill256_restriction"] = restriction_cost(eb, dist, warmup, steps)
     e = run_ensemble(eb, steps, warmup, None, dist)
     torch.cuda.empty_cache()
     out["ensemble"] = {"workload": "ensemble-64-gaussian-hills", "cells": e["cells"], "value": e["value"] * world,

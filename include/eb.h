@@ -154,6 +154,53 @@ eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision
                         const double *ref_rhotheta, void *stream, eb_geom *out);
 
 /*
+ * Two-level static refinement (Sec. 4.3), refinement ratio 2 in every
+ * direction over the same domain.
+ *
+ * eb_geom_build_coarse: a handle of the coarse level (nx/2 x ny/2 x nz/2
+ * cells, the fine handle's lengths, small-cell threshold and precision)
+ * whose geometry is merged from the fine handle's cells, so that coarse
+ * volumes, face areas and EB areas are sums of fine ones.  A coarse CV of
+ * any grid is a block of 2x2x2 fine c-grid cells (cells 2I, 2I+1 along x for
+ * the c grid, 2I-1, 2I for u: the right half of coarse cell I-1 and the left
+ * half of cell I; likewise along y for v and z for w; fine cells outside the
+ * domain hold no fluid).  Volume fraction: the mean of the 8; face fraction:
+ * the mean of the 4 fine faces on the coarse face; EB area: the sum; volume,
+ * face and EB centroids: weighted mean positions; EB normal: the direction of
+ * sum_d (open area of the high d-face - of the low d-face) e_d; class:
+ * covered / regular when all fine cells inside the domain are, else cut.  The
+ * redistribution tables, lists and everything else then follow from that
+ * geometry as in eb_geom_build, and the handle takes every call a handle
+ * built from heights takes.
+ *   fine              a handle with even nx, ny, nz (nx/2 etc. must pass the
+ *                     eb_geom_build checks); it is only read, and may be
+ *                     destroyed afterwards.
+ *   ref_rho, ref_rhotheta  device, nz/2 doubles each, or both NULL: the coarse
+ *                     level's reference profiles, as for eb_geom_build.
+ * The coarse handle's nodal heights (eb_geom_export's wall values) are every
+ * other fine node.  EB_ERR_INVALID_ARG for odd dimensions or another current
+ * device; the eb_geom_build errors otherwise.
+ *
+ * eb_restrict: the fine state restricted to the coarse level: every coarse
+ * cell-centred value is the mean of its 8 fine cells weighted by their volume
+ * fractions (the coarse cell holds the fine cells' total), every coarse face
+ * value the mean of the 4 fine values on its face (the fine faces 2I, 2I+1 of
+ * the fine grid at index 2I for u, and so on) weighted by their area fractions
+ * (the flux integral over the coarse face is kept).  Sums in double.  States
+ * hold values minus each handle's own per-level profiles, which the
+ * restriction accounts for.  Coarse CVs whose fine parts hold no fluid (or no
+ * open area) keep the value Uc has.
+ *   fine, coarse      coarse must halve every dimension of fine; same
+ *                     precision.
+ *   Uf, Uc            device states of the fine and the coarse handle.
+ * Asynchronous on stream.  EB_ERR_INVALID_ARG on mismatched handles or
+ * NULL / misaligned pointers.
+ */
+eb_status eb_geom_build_coarse(eb_geom fine, const double *ref_rho, const double *ref_rhotheta, void *stream,
+                               eb_geom *out);
+eb_status eb_restrict(eb_geom fine, eb_geom coarse, const eb_state *Uf, eb_state *Uc, void *stream);
+
+/*
  * Background momentum profile of the state (Sec. 2: the reference /
  * perturbation split of the governing equations, carried over to the
  * horizontal momenta of a prescribed background wind).  After this call the

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["eb_api.cu", "eb_geom.cu", "eb_wsrd_setup.cu", "eb_step.cu", "eb_fast.cu", "eb_scan.cu", "eb_ensemble.cu", "eb_project.cu", "eb_unet.cu", "eb_peak.cu", "eb_sources.cu"]
+UNITS = ["eb_api.cu", "eb_geom.cu", "eb_wsrd_setup.cu", "eb_step.cu", "eb_fast.cu", "eb_scan.cu", "eb_ensemble.cu", "eb_project.cu", "eb_unet.cu", "eb_peak.cu", "eb_sources.cu", "eb_amr.cu"]
 # Units compiled without contraction of a * b + c: the set-up (bit-exact
 # geometry), and the step units, whose device functions run both in their
 # own kernels and inlined into the persistent ensemble kernel and must round

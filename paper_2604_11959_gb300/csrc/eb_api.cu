@@ -127,13 +127,19 @@ cudaError_t update_background(eb_geom g) {
   return cudaSuccess;
 }
 
-eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, const double *ref_rt, cudaStream_t s) {
+// Builds the handle's geometry, tables and lists: from the nodal heights, or
+// (fine != nullptr) as the coarse level of the fine handle, merged from its
+// cells (eb_amr.cu; the heights then are every other fine node, kept as a
+// record of the terrain).
+eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, const double *ref_rt, cudaStream_t s,
+                     eb_geom fine = nullptr) {
   g->has_ref = ref_rho != nullptr;
   const Dims &D = g->D;
   const long long ncol = (long long)D.nx * D.ny;
   const long long nh = (long long)(D.nx + 1) * (D.ny + 1);
   CUDA_TRY(g->alloc(&g->h, nh), "alloc heights");
-  CUDA_TRY(cudaMemcpyAsync(g->h, h_nodes, sizeof(double) * nh, cudaMemcpyDeviceToDevice, s), "copy heights");
+  if (fine) launch_subsample_heights(fine->h, fine->D, g->h, D, s);
+  else CUDA_TRY(cudaMemcpyAsync(g->h, h_nodes, sizeof(double) * nh, cudaMemcpyDeviceToDevice, s), "copy heights");
   long long *counts = nullptr;
   long long scan_room = 2 * (ncol + 2) + 8;
   CUDA_TRY(g->alloc(&counts, scan_room), "alloc counts");
@@ -143,7 +149,8 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
     CUDA_TRY(g->alloc(&g->kreg[q], ncol), "alloc kreg");
     CUDA_TRY(g->alloc(&g->kxt[q], ncol), "alloc kxt");
     CUDA_TRY(g->alloc(&g->roff[q], ncol + 1), "alloc roff");
-    launch_band_bounds(g->h, D, q, g->kcov[q], g->kreg[q], s);
+    if (fine) launch_coarse_bounds(fine->D, fine->G[0], D, q, g->kcov[q], g->kreg[q], s);
+    else launch_band_bounds(g->h, D, q, g->kcov[q], g->kreg[q], s);
   }
   for (int q = 0; q < 4; ++q) {
     const int nzg = nzg_of(D, q);
@@ -181,7 +188,8 @@ eb_status build_impl(eb_geom g, const double *h_nodes, const double *ref_rho, co
     CUDA_TRY(g->alloc(&G.omega, n), "alloc tables");
     CUDA_TRY(g->alloc(&G.vhat, n), "alloc tables");
     CUDA_TRY(g->alloc(&G.xhat, 3 * n), "alloc tables");
-    launch_band_geometry(g->h, D, q, G, s);
+    if (fine) launch_coarse_geometry(fine->D, fine->G[0], D, q, G, s);
+    else launch_band_geometry(g->h, D, q, G, s);
     tmp_need = std::max(tmp_need, 2 * (n + 1) + 1 + (n + 1) / 256 + 8);
   }
   CUDA_TRY(cudaGetLastError(), "geometry kernels");
@@ -580,16 +588,8 @@ void wsrd_field_scratch(eb_geom g, int field, T *u, char *scratch, cudaStream_t 
 
 extern "C" {
 
-eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision prec, const double *ref_rho,
-                        const double *ref_rhotheta, void *stream, eb_geom *out) {
-  std::string why;
-  if (!out) return fail(EB_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  if (bad_desc(desc, why)) return fail(EB_ERR_INVALID_ARG, "%s", why.c_str());
-  if (!h_nodes || ((uintptr_t)h_nodes % 8)) return fail(EB_ERR_INVALID_ARG, "h_nodes is NULL or misaligned");
-  if (prec != EB_F64 && prec != EB_MIXED) return fail(EB_ERR_INVALID_ARG, "unknown precision");
-  if ((ref_rho == nullptr) != (ref_rhotheta == nullptr))
-    return fail(EB_ERR_INVALID_ARG, "ref_rho and ref_rhotheta must both be given or both be NULL");
+static eb_status build_common(const eb_desc *desc, const double *h_nodes, eb_precision prec, const double *ref_rho,
+                              const double *ref_rhotheta, void *stream, eb_geom *out, eb_geom fine) {
   eb_geom g = new eb_geom_s();
   memset(&g->info, 0, sizeof(g->info));
   g->desc = *desc;
@@ -616,7 +616,7 @@ eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision
   g->D.idx = 1.0 / g->D.dx;
   g->D.idy = 1.0 / g->D.dy;
   g->D.idz = 1.0 / g->D.dz;
-  eb_status st = build_impl(g, h_nodes, ref_rho, ref_rhotheta, as_stream(stream));
+  eb_status st = build_impl(g, h_nodes, ref_rho, ref_rhotheta, as_stream(stream), fine);
   if (st != EB_OK) {
     cudaStreamSynchronize(as_stream(stream));
     g->release();
@@ -626,6 +626,40 @@ eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision
   *out = g;
   g_last_error.clear();
   return EB_OK;
+}
+
+eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision prec, const double *ref_rho,
+                        const double *ref_rhotheta, void *stream, eb_geom *out) {
+  std::string why;
+  if (!out) return fail(EB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (bad_desc(desc, why)) return fail(EB_ERR_INVALID_ARG, "%s", why.c_str());
+  if (!h_nodes || ((uintptr_t)h_nodes % 8)) return fail(EB_ERR_INVALID_ARG, "h_nodes is NULL or misaligned");
+  if (prec != EB_F64 && prec != EB_MIXED) return fail(EB_ERR_INVALID_ARG, "unknown precision");
+  if ((ref_rho == nullptr) != (ref_rhotheta == nullptr))
+    return fail(EB_ERR_INVALID_ARG, "ref_rho and ref_rhotheta must both be given or both be NULL");
+  return build_common(desc, h_nodes, prec, ref_rho, ref_rhotheta, stream, out, nullptr);
+}
+
+eb_status eb_geom_build_coarse(eb_geom fine, const double *ref_rho, const double *ref_rhotheta, void *stream,
+                               eb_geom *out) {
+  std::string why;
+  if (!out) return fail(EB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!fine) return fail(EB_ERR_INVALID_ARG, "NULL fine handle");
+  if (fine->D.nx % 2 || fine->D.ny % 2 || fine->D.nz % 2)
+    return fail(EB_ERR_INVALID_ARG, "the fine level needs even nx, ny and nz");
+  eb_desc desc = fine->desc;
+  desc.nx /= 2;
+  desc.ny /= 2;
+  desc.nz /= 2;
+  if (bad_desc(&desc, why)) return fail(EB_ERR_INVALID_ARG, "%s", why.c_str());
+  if ((ref_rho == nullptr) != (ref_rhotheta == nullptr))
+    return fail(EB_ERR_INVALID_ARG, "ref_rho and ref_rhotheta must both be given or both be NULL");
+  int cur = -1;
+  CUDA_TRY(cudaGetDevice(&cur), "current device");
+  if (cur != fine->device) return fail(EB_ERR_INVALID_ARG, "the current device is not the fine handle's device");
+  return build_common(&desc, nullptr, fine->prec, ref_rho, ref_rhotheta, stream, out, fine);
 }
 
 eb_status eb_geom_destroy(eb_geom geom) {

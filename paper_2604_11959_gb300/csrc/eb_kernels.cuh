@@ -45,6 +45,14 @@ void launch_fluid_level(const Dims &D, const GridDev &G, int *kflu, cudaStream_t
 void launch_fast_level(const Dims &D, const int *const kreg[4], const int *const kflu[4], int *kfast,
                        cudaStream_t s);
 void launch_band_geometry(const double *h, const Dims &D, int g, const GridDev &G, cudaStream_t s);
+// two-level refinement (eb_amr.cu): band bounds and geometry records of a
+// coarse level (Dc) merged from the c grid of the fine level (Df, Gf), and
+// its nodal heights as every other fine node
+void launch_coarse_bounds(const Dims &Df, const GridDev &Gf, const Dims &Dc, int g, int *kcov, int *kreg,
+                          cudaStream_t s);
+void launch_coarse_geometry(const Dims &Df, const GridDev &Gf, const Dims &Dc, int g, const GridDev &Gc,
+                            cudaStream_t s);
+void launch_subsample_heights(const double *hf, const Dims &Df, double *hc, const Dims &Dc, cudaStream_t s);
 void launch_dense_flags(const Dims &D, int g, const GridDev &G, cudaStream_t s);
 void launch_band_marks(const Dims &D, int g, const int *kcov, const int *kfast, int kmax, long long *mark,
                        cudaStream_t s);

@@ -34,7 +34,8 @@ EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom
                     "eb_project_sample", "eb_project_warm", "eb_geom_tune",
                     "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
                     "eb_geom_set_wind_reference", "eb_fma_peak", "eb_ensemble_info",
-                    "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule", "eb_geom_set_sources")
+                    "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule", "eb_geom_set_sources",
+                    "eb_geom_build_coarse", "eb_restrict")
 
 
 class EbError(RuntimeError):
@@ -118,6 +119,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_project_set_preconditioner.argtypes = [V, I]
     lib.eb_geom_set_wind_reference.argtypes = [V, V, V, V]
     lib.eb_geom_set_sources.argtypes = [V, I]
+    lib.eb_geom_build_coarse.argtypes = [V, V, V, V, V]
+    lib.eb_restrict.argtypes = [V, V, V, V, V]
     lib.eb_fma_peak.argtypes = [I, P(D), V]
     lib.eb_ensemble_info.argtypes = [V, P(I)]
     lib.eb_ensemble_inject_barrier_fault.argtypes = [V, I]
@@ -132,7 +135,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                  "eb_unet_destroy", "eb_project_sample", "eb_project_warm", "eb_geom_tune",
                  "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
                  "eb_geom_set_wind_reference", "eb_fma_peak", "eb_ensemble_info",
-                 "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule", "eb_geom_set_sources"):
+                 "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule", "eb_geom_set_sources",
+                 "eb_geom_build_coarse", "eb_restrict"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -206,6 +210,27 @@ class Geometry:
         (``eb_geom_set_sources``): the perturbation pressure gradient from the
         equation of state and the buoyancy; both False switches them off."""
         _check(load().eb_geom_set_sources(self.handle, (1 if pressure else 0) | (2 if buoyancy else 0)))
+
+    def coarse(self, ref_rho=None, ref_rhotheta=None, stream=None) -> "Geometry":
+        """The coarse level of a refinement ratio 2 (``eb_geom_build_coarse``):
+        nx/2 x ny/2 x nz/2 cells, geometry merged from this handle's cells;
+        reference profiles of nz/2 levels (CUDA float64) or None."""
+        refs = [None, None]
+        for q, r in enumerate((ref_rho, ref_rhotheta)):
+            if r is not None:
+                _require_cuda(r, torch.float64, (self.nz // 2,), "reference profile")
+                refs[q] = r
+        handle = ctypes.c_void_p()
+        _check(load().eb_geom_build_coarse(self.handle, refs[0].data_ptr() if refs[0] is not None else None,
+                                           refs[1].data_ptr() if refs[1] is not None else None, _stream(stream),
+                                           ctypes.byref(handle)))
+        g = Geometry.__new__(Geometry)
+        g.nx, g.ny, g.nz = self.nx // 2, self.ny // 2, self.nz // 2
+        g.Lx, g.Ly, g.Lz = self.Lx, self.Ly, self.Lz
+        g.precision, g.dtype = self.precision, self.dtype
+        g._keep = (None, refs)
+        g._h = handle
+        return g
 
     def close(self):
         if getattr(self, "_h", None):
@@ -370,6 +395,18 @@ def set_bulk_priority(geom: Geometry, high: bool) -> None:
 def set_slab_levels(geom: Geometry, levels: int) -> None:
     """Set the bulk kernel's slab height (``eb_geom_set_slab_levels``)."""
     _check(load().eb_geom_set_slab_levels(geom.handle, int(levels)))
+
+
+def restrict(fine: Geometry, coarse: Geometry, Uf: dict, Uc: dict, stream=None) -> dict:
+    """The fine state restricted onto the coarse level in place of Uc
+    (``eb_restrict``): volume-weighted cell-centred fields, area-weighted face
+    fields; coarse CVs without fine fluid keep their values.  Returns Uc."""
+    for U, gm in ((Uf, fine), (Uc, coarse)):
+        for f in FIELDS:
+            _require_cuda(U[f], gm.dtype, gm.shape(f), f)
+    _check(load().eb_restrict(fine.handle, coarse.handle, ctypes.byref(fine._cstate(Uf)),
+                              ctypes.byref(coarse._cstate(Uc)), _stream(stream)))
+    return Uc
 
 
 def fma_peak(kind: str, stream=None) -> float:

@@ -120,3 +120,19 @@ def window_cut(a, x0, y0, W, nx, ny):
     ii = (x0 + np.arange(W)) % nx
     jj = (y0 + np.arange(W)) % ny
     return a[..., jj[:, None], ii[None, :]]
+
+
+def oracle_export(G, T, g, name):
+    """The oracle's value of eb_geom_export field ``name`` of grid g
+    (geometry G, redistribution tables T)."""
+    if name == "alpha" or name == "aeb" or name == "flag":
+        return G[g][name].astype(np.float64)
+    if name.startswith("cent_") or name.startswith("nrm_") or name.startswith("ebc_") or name.startswith("beta_"):
+        key, ax = name.split("_")
+        return G[g][key]["xyz".index(ax)]
+    if name.startswith("fcent_"):
+        ax, t = name[6], int(name[7]) - 1
+        return G[g]["fcent"][2 * "xyz".index(ax) + t]
+    if name.startswith("xhat_"):
+        return T[g]["xhat"]["xyz".index(name[5])]
+    return T[g][name].astype(np.float64)

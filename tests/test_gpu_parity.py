@@ -8,8 +8,8 @@ import pytest
 
 from paper_2604_11959_gb300 import inputs
 
-from _gpu_helpers import (FGRID, FIELDS, TOL, active_masks, make_geometry, refs_for, rel_linf, to_device, to_host,
-                          wind_refs, window_cut, window_oracle, worst)
+from _gpu_helpers import (FGRID, FIELDS, TOL, active_masks, make_geometry, oracle_export, refs_for, rel_linf, to_device,
+                          to_host, wind_refs, window_cut, window_oracle, worst)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -61,20 +61,6 @@ def case(request, oracle):
     G = oracle.geometry(dom)
     T = oracle.wsrd_setup(dom, G)
     return request.param, w, h, dom, G, T
-
-
-def oracle_export(G, T, g, name):
-    if name == "alpha" or name == "aeb" or name == "flag":
-        return G[g][name].astype(np.float64)
-    if name.startswith("cent_") or name.startswith("nrm_") or name.startswith("ebc_") or name.startswith("beta_"):
-        key, ax = name.split("_")
-        return G[g][key]["xyz".index(ax)]
-    if name.startswith("fcent_"):
-        ax, t = name[6], int(name[7]) - 1
-        return G[g]["fcent"][2 * "xyz".index(ax) + t]
-    if name.startswith("xhat_"):
-        return T[g]["xhat"]["xyz".index(name[5])]
-    return T[g][name].astype(np.float64)
 
 
 def test_geometry_and_tables_match(eb, case):
