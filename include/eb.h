@@ -181,24 +181,40 @@ eb_status eb_geom_build(const eb_desc *desc, const double *h_nodes, eb_precision
  * other fine node.  EB_ERR_INVALID_ARG for odd dimensions or another current
  * device; the eb_geom_build errors otherwise.
  *
- * eb_restrict: the fine state restricted to the coarse level: every coarse
+ * eb_restrict: a fine state restricted to the coarse level: every coarse
  * cell-centred value is the mean of its 8 fine cells weighted by their volume
  * fractions (the coarse cell holds the fine cells' total), every coarse face
- * value the mean of the 4 fine values on its face (the fine faces 2I, 2I+1 of
- * the fine grid at index 2I for u, and so on) weighted by their area fractions
- * (the flux integral over the coarse face is kept).  Sums in double.  States
- * hold values minus each handle's own per-level profiles, which the
- * restriction accounts for.  Coarse CVs whose fine parts hold no fluid (or no
- * open area) keep the value Uc has.
- *   fine, coarse      coarse must halve every dimension of fine; same
- *                     precision.
+ * value the mean of the 4 fine values on its face weighted by their area
+ * fractions (the flux integral over the coarse face is kept).  Sums in
+ * double.  States hold values minus each handle's own per-level profiles,
+ * which both calls account for.  Coarse CVs whose fine parts hold no fluid
+ * (or no open area) keep the value Uc has.
+ *
+ * eb_prolong: the boundary values a refined patch takes from the coarse level
+ * (Sec. 4.3): every fine CV outside the fine handle's columns [lo, hi) takes
+ * the value of the coarse CV it lies in; a fine face of a face grid on a
+ * coarse face takes that face's value, one halfway between two coarse faces
+ * (odd fine index along the face's axis) the mean of the two.  Covered CVs
+ * included (the step passes them through).
+ *
+ * For both: the fine handle is the coarse handle's fine level over all of y
+ * and z and an x-window of it: fine column q of the handle is global fine
+ * column fine_x0 + q (mod 2 nx_c); the whole level is fine_x0 = 0,
+ * nx = 2 nx_c (e.g. the handle eb_geom_build_coarse was built from).
+ *   lo, hi            local fine columns: eb_restrict restricts the coarse
+ *                     columns over [lo, hi) (lo, hi and fine_x0 even),
+ *                     eb_prolong fills every column outside [lo, hi).
  *   Uf, Uc            device states of the fine and the coarse handle.
- * Asynchronous on stream.  EB_ERR_INVALID_ARG on mismatched handles or
- * NULL / misaligned pointers.
+ * Asynchronous on stream.  EB_ERR_INVALID_ARG on handles that are not two
+ * levels of one grid (ny, nz halved, cells twice as large, nx_f <= 2 nx_c,
+ * same precision), on a bad column range, or NULL / misaligned pointers.
  */
 eb_status eb_geom_build_coarse(eb_geom fine, const double *ref_rho, const double *ref_rhotheta, void *stream,
                                eb_geom *out);
-eb_status eb_restrict(eb_geom fine, eb_geom coarse, const eb_state *Uf, eb_state *Uc, void *stream);
+eb_status eb_restrict(eb_geom fine, eb_geom coarse, const eb_state *Uf, eb_state *Uc, int fine_x0, int lo, int hi,
+                      void *stream);
+eb_status eb_prolong(eb_geom coarse, const eb_state *Uc, eb_geom fine, eb_state *Uf, int fine_x0, int lo, int hi,
+                     void *stream);
 
 /*
  * Background momentum profile of the state (Sec. 2: the reference /

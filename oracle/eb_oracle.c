@@ -1343,10 +1343,15 @@ int orc_coarsen(const OrcDomain *Df, const OrcGeom *Gf, const OrcDomain *Dc, int
  * the fine volume fractions), so that the coarse cell holds the fine cells'
  * total; a coarse face value is the area-weighted mean of the 4 fine values
  * on its face (weights the fine face fractions), so that the flux integral
- * over the coarse face is kept.  Coarse CVs whose fine parts hold no fluid or
- * no open area keep their values (Uc is read and written). */
-int orc_restrict(const OrcDomain *Df, const OrcGeom *Gf, const OrcState *Uf, const OrcDomain *Dc, OrcState *Uc) {
+ * over the coarse face is kept.  Only the coarse columns over the fine
+ * columns [x_lo, x_hi) (global fine indices, both even, periodic) are
+ * restricted; the fine domain may be a window holding them.  Coarse CVs whose
+ * fine parts hold no fluid or no open area keep their values (Uc is read and
+ * written). */
+int orc_restrict(const OrcDomain *Df, const OrcGeom *Gf, const OrcState *Uf, const OrcDomain *Dc, OrcState *Uc,
+                 int x_lo, int x_hi) {
   if (Df->NX != 2 * Dc->NX || Df->NY != 2 * Dc->NY || Df->nz != 2 * Dc->nz) return 1;
+  if (x_lo % 2 || x_hi % 2 || x_hi <= x_lo || x_hi - x_lo > Df->NX) return 1;
   const OrcGeom *F = &Gf[GC];
   long nf = ncv(Df, GC);
   for (int fld = 0; fld < 5; fld++) {
@@ -1356,7 +1361,8 @@ int orc_restrict(const OrcDomain *Df, const OrcGeom *Gf, const OrcState *Uf, con
 #pragma omp parallel for schedule(static)
     for (int K = 0; K < nzg; K++)
       for (int J = 0; J < Dc->NY; J++)
-        for (int I = 0; I < Dc->NX; I++) {
+        for (int Ix = x_lo / 2; Ix < x_hi / 2; Ix++) {
+          int I = imod(Ix, Dc->NX);
           long id = loc(Dc, g, I, J, K);
           double w = 0, s = 0;
           if (g == GC) {
@@ -1384,6 +1390,45 @@ int orc_restrict(const OrcDomain *Df, const OrcGeom *Gf, const OrcState *Uf, con
               }
           }
           if (w > 0) Uc->f[fld][id] = s / w;
+        }
+  }
+  return 0;
+}
+
+/* Prolongation of a coarse state onto a fine window (the boundary values a
+ * refined patch takes from the coarse level, Sec. 4.3): every fine CV of the
+ * window outside the columns [x_lo, x_hi) (global fine indices, periodic)
+ * takes the value of the coarse CV it lies in; a fine face of a face grid
+ * that lies on a coarse face takes that face's value, one halfway between two
+ * coarse faces (the odd fine index along the face's axis) their mean.  Covered
+ * CVs included: the step passes them through. */
+int orc_prolong(const OrcDomain *Dc, const OrcState *Uc, const OrcDomain *Df, OrcState *Uf, int x_lo, int x_hi) {
+  if (Df->NX != 2 * Dc->NX || Df->NY != 2 * Dc->NY || Df->nz != 2 * Dc->nz) return 1;
+  for (int fld = 0; fld < 5; fld++) {
+    int g = FIELD_GRID[fld];
+    int nzg = nzg_of(Df, g);
+    int d = g - 1;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nzg; k++)
+      for (int wj = 0; wj < Df->WY; wj++)
+        for (int wi = 0; wi < Df->WX; wi++) {
+          int gi = Df->x0 + wi, gj = Df->y0 + wj;
+          int rel = imod(gi - x_lo, Df->NX);
+          if (rel < x_hi - x_lo) continue;   /* an owned column */
+          int c[3] = {imod(gi, Df->NX) / 2, imod(gj, Df->NY) / 2, k / 2};
+          int f[3] = {imod(gi, Df->NX), imod(gj, Df->NY), k};
+          long id = loc(Df, g, gi, gj, k);
+          double v;
+          long a = loc(Dc, g, c[0], c[1], c[2]);
+          if (g == GC || f[d] % 2 == 0) {
+            v = Uc->f[fld][a];
+          } else {
+            int c2[3] = {c[0], c[1], c[2]};
+            c2[d] += 1;
+            if (d < 2) c2[d] = imod(c2[d], d == 0 ? Dc->NX : Dc->NY);
+            v = 0.5 * (Uc->f[fld][a] + Uc->f[fld][loc(Dc, g, c2[0], c2[1], c2[2])]);
+          }
+          Uf->f[fld][id] = v;
         }
   }
   return 0;

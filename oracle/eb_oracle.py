@@ -93,7 +93,9 @@ def _load():
                                       P(_State), P(_State), P(_Sources)]
             lib.orc_sources.argtypes = [P(_Domain), P(_Geom), P(_State), P(_Sources), P(_State)]
             lib.orc_coarsen.argtypes = [P(_Domain), P(_Geom), P(_Domain), ctypes.c_int, P(_Geom)]
-            lib.orc_restrict.argtypes = [P(_Domain), P(_Geom), P(_State), P(_Domain), P(_State)]
+            lib.orc_restrict.argtypes = [P(_Domain), P(_Geom), P(_State), P(_Domain), P(_State), ctypes.c_int,
+                                         ctypes.c_int]
+            lib.orc_prolong.argtypes = [P(_Domain), P(_State), P(_Domain), P(_State), ctypes.c_int, ctypes.c_int]
             lib.orc_eos_pressure.argtypes = [ctypes.c_double]
             lib.orc_eos_pressure.restype = ctypes.c_double
             _lib = lib
@@ -321,16 +323,32 @@ def coarsen(fine: Domain, geom: dict, coarse: Domain) -> dict:
     return out
 
 
-def restrict(fine: Domain, geom: dict, Uf: dict, coarse: Domain, Uc: dict) -> dict:
+def restrict(fine: Domain, geom: dict, Uf: dict, coarse: Domain, Uc: dict, cols=None) -> dict:
     """The fine state restricted to the coarse level (Sec. 4.3): volume-
     weighted cell-centred fields, area-weighted face fields; coarse CVs with
-    no fine fluid or open area keep their values from Uc."""
+    no fine fluid or open area keep their values from Uc.  ``cols``: the
+    global fine columns (x_lo, x_hi), both even, whose coarse columns are
+    restricted (default all); the fine domain may be a window holding them."""
     _check_state(fine, Uf)
     _check_state(coarse, Uc)
+    lo, hi = (0, fine.NX) if cols is None else (int(cols[0]), int(cols[1]))
     out = {k: np.ascontiguousarray(Uc[k], dtype=np.float64).copy() for k in FIELDS}
     if _load().orc_restrict(ctypes.byref(fine._c), _cgeom(geom), ctypes.byref(_cstate(Uf)), ctypes.byref(coarse._c),
-                            ctypes.byref(_cstate(out))) != 0:
-        raise ValueError("restrict: the coarse level must halve every fine dimension")
+                            ctypes.byref(_cstate(out)), lo, hi) != 0:
+        raise ValueError("restrict: the coarse level must halve every fine dimension, cols even")
+    return out
+
+
+def prolong(coarse: Domain, Uc: dict, fine: Domain, Uf: dict, owned) -> dict:
+    """The coarse state prolonged onto the fine window outside its owned
+    global fine columns (x_lo, x_hi) (Sec. 4.3: boundary values of a refined
+    patch); returns a copy of Uf with those columns filled."""
+    _check_state(coarse, Uc)
+    _check_state(fine, Uf)
+    out = {k: np.ascontiguousarray(Uf[k], dtype=np.float64).copy() for k in FIELDS}
+    if _load().orc_prolong(ctypes.byref(coarse._c), ctypes.byref(_cstate(Uc)), ctypes.byref(fine._c),
+                           ctypes.byref(_cstate(out)), int(owned[0]), int(owned[1])) != 0:
+        raise ValueError("prolong: the coarse level must halve every fine dimension")
     return out
 
 

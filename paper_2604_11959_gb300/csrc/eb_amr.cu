@@ -63,6 +63,18 @@ __device__ inline int fine_cell(const FineC &F, int i, int j, int k, double v[20
   return F.G.flag[r];
 }
 
+// the volume fraction (q = 0) or the low q-1 face fraction (q = 1..3) of
+// fine cell (i, j, k) alone: 0 outside the domain or covered, 1 regular
+__device__ inline double fine_frac(const FineC &F, int i, int j, int k, int q) {
+  if (k < 0 || k >= F.D.nz) return 0.0;
+  const int col = wrapi(i, F.D.nx) + F.D.nx * wrapi(j, F.D.ny);
+  const int kc = F.G.kcov[col], kx = F.G.kxt[col];
+  if (k < kc) return 0.0;
+  if (k >= kx) return 1.0;
+  const long long r = F.G.roff[col] + (k - kc);
+  return q == 0 ? F.G.alpha[r] : F.G.beta[(q - 1) * F.G.nrec + r];
+}
+
 // open fraction of the low d-face of fine cell (i, j, k); the lid above the
 // top is open, the floor below the bottom closed
 __device__ inline double fine_low_face(const FineC &F, int i, int j, int k, int d) {
@@ -204,7 +216,10 @@ __global__ void k_subsample_heights(const double *hf, Dims Df, double *hc, Dims 
 // 4 fine faces on the coarse face (face grids), in double; the states hold
 // perturbations about per-level profiles of their own level (pf fine, pc
 // coarse; zeros where none), so the profiles' weighted mean minus the coarse
-// profile is added.  CVs without fine fluid or open area keep their value.
+// profile is added.  The fine handle may be an x-window of the fine level:
+// its local column q is global fine column fx0 + q (mod nxg); coarse columns
+// I0 .. I0 + ncols - 1 (mod the coarse nx) are restricted.  CVs without fine
+// fluid or open area keep their value.
 template <typename T>
 struct RestrictArgs {
   FineC F;
@@ -212,28 +227,31 @@ struct RestrictArgs {
   const T *uf[5];
   T *uc[5];
   const double *pf[5], *pc[5];   // per-level profiles (nullptr: none)
+  int fx0, nxg, I0, ncols;
 };
 
 template <typename T>
 __global__ void k_restrict(const __grid_constant__ RestrictArgs<T> R, int f) {
   const Dims &Dc = R.Dc;
   const int g = f <= 1 ? 0 : f - 1;
-  const long long n = Dc.nxy * (long long)nzg_of(Dc, g);
+  const long long plane = (long long)R.ncols * Dc.ny;
+  const long long n = plane * nzg_of(Dc, g);
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const int K = (int)(t / Dc.nxy);
-  const long long c2 = t - (long long)K * Dc.nxy;
-  const int J = (int)(c2 / Dc.nx), I = (int)(c2 - (long long)J * Dc.nx);
+  const int K = (int)(t / plane);
+  const long long c2 = t - (long long)K * plane;
+  const int J = (int)(c2 / R.ncols), It = (int)(c2 - (long long)J * R.ncols);
+  const int I = wrapi(R.I0 + It, Dc.nx);
+  const long long tc = I + (long long)Dc.nx * J + Dc.nxy * K;
   const Dims &Df = R.F.D;
+  auto local = [&](int gx) { return wrapi(gx - R.fx0, R.nxg); };   // fine global column -> the handle's column
   double w = 0.0, s = 0.0, sp = 0.0;
-  double v[20];
   if (g == 0) {
     for (int c = 0; c < 2; ++c)
       for (int b = 0; b < 2; ++b)
         for (int a = 0; a < 2; ++a) {
-          const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
-          fine_cell<true>(R.F, i, j, k, v);
-          const double al = v[0];
+          const int i = local(2 * I + a), j = 2 * J + b, k = 2 * K + c;
+          const double al = fine_frac(R.F, i, j, k, 0);
           const long long q = i + (long long)Df.nx * j + Df.nxy * k;
           w += al;
           s += al * (double)R.uf[f][q];
@@ -248,8 +266,8 @@ __global__ void k_restrict(const __grid_constant__ RestrictArgs<T> R, int f) {
         p[t1] += x;
         p[t2] += y;
         if (p[2] >= Df.nz) continue;   // the lid above the top: a wall of w
-        fine_cell<true>(R.F, p[0], p[1], p[2], v);
-        const double be = v[4 + d];
+        p[0] = local(p[0]);
+        const double be = fine_frac(R.F, p[0], p[1], p[2], 1 + d);
         const long long q = p[0] + (long long)Df.nx * p[1] + Df.nxy * p[2];
         w += be;
         s += be * (double)R.uf[f][q];
@@ -260,8 +278,55 @@ __global__ void k_restrict(const __grid_constant__ RestrictArgs<T> R, int f) {
     double val = s / w;
     if (R.pf[f]) val += sp / w;
     if (R.pc[f]) val -= R.pc[f][K];
-    R.uc[f][t] = (T)val;
+    R.uc[f][tc] = (T)val;
   }
+}
+
+// Prolongation onto the fine handle's columns outside [lo, hi) (local
+// indices): every fine CV takes the value of the coarse CV it lies in; a fine
+// face of a face grid on a coarse face takes that face's value, one halfway
+// between two coarse faces (odd fine index along the face's axis) their mean;
+// full values (state plus profile) are interpolated, in double.
+template <typename T>
+struct ProlongArgs {
+  Dims Df, Dc;
+  const T *uc[5];
+  T *uf[5];
+  const double *pf[5], *pc[5];
+  int fx0, nxg, lo, hi;
+};
+
+template <typename T>
+__global__ void k_prolong(const __grid_constant__ ProlongArgs<T> P, int f) {
+  const Dims &Df = P.Df, &Dc = P.Dc;
+  const int g = f <= 1 ? 0 : f - 1;
+  const long long n = Df.nxy * (long long)nzg_of(Df, g);
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int k = (int)(t / Df.nxy);
+  const long long c2 = t - (long long)k * Df.nxy;
+  const int j = (int)(c2 / Df.nx), i = (int)(c2 - (long long)j * Df.nx);
+  if (i >= P.lo && i < P.hi) return;   // an owned column
+  const int gi = wrapi(P.fx0 + i, P.nxg);
+  int c[3] = {gi / 2, j / 2, k / 2};
+  const int fc[3] = {gi, j, k};
+  auto full = [&](int I, int J, int K) -> double {
+    const double u = (double)P.uc[f][I + (long long)Dc.nx * J + Dc.nxy * K];
+    return P.pc[f] ? u + P.pc[f][K] : u;
+  };
+  double val;
+  const int d = g - 1;
+  if (g == 0 || fc[d] % 2 == 0) {
+    val = full(c[0], c[1], c[2]);
+  } else {
+    int e[3] = {c[0], c[1], c[2]};
+    e[d] += 1;
+    if (d == 0) e[0] = wrapi(e[0], Dc.nx);
+    if (d == 1) e[1] = wrapi(e[1], Dc.ny);
+    val = 0.5 * (full(c[0], c[1], c[2]) + full(e[0], e[1], e[2]));
+  }
+  if (P.pf[f]) val -= P.pf[f][k];
+  P.uf[f][t] = (T)val;
 }
 
 }  // namespace
@@ -284,10 +349,15 @@ void launch_subsample_heights(const double *hf, const Dims &Df, double *hc, cons
 }
 
 template <typename T>
-static void restrict_t(eb_geom fine, eb_geom coarse, const eb_state *Uf, eb_state *Uc, cudaStream_t s) {
+static void restrict_t(eb_geom fine, eb_geom coarse, const eb_state *Uf, eb_state *Uc, int fx0, int lo, int hi,
+                       cudaStream_t s) {
   RestrictArgs<T> R;
   R.F = FineC{fine->D, fine->G[0]};
   R.Dc = coarse->D;
+  R.nxg = 2 * coarse->D.nx;
+  R.fx0 = wrapi(fx0, R.nxg);
+  R.I0 = wrapi(R.fx0 + lo, R.nxg) / 2;
+  R.ncols = (hi - lo) / 2;
   void **uf = state_ptrs(Uf), **uc = state_ptrs(Uc);
   for (int f = 0; f < 5; ++f) {
     R.uf[f] = (const T *)uf[f];
@@ -297,22 +367,72 @@ static void restrict_t(eb_geom fine, eb_geom coarse, const eb_state *Uf, eb_stat
   }
   for (int f = 0; f < 5; ++f) {
     const int g = f <= 1 ? 0 : f - 1;
-    const long long n = coarse->D.nxy * (long long)nzg_of(coarse->D, g);
-    k_restrict<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(R, f);
+    const long long n = (long long)R.ncols * coarse->D.ny * nzg_of(coarse->D, g);
+    if (n > 0) k_restrict<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(R, f);
   }
 }
 
-eb_status eb_restrict(eb_geom fine, eb_geom coarse, const eb_state *Uf, eb_state *Uc, void *stream) {
+template <typename T>
+static void prolong_t(eb_geom coarse, const eb_state *Uc, eb_geom fine, eb_state *Uf, int fx0, int lo, int hi,
+                      cudaStream_t s) {
+  ProlongArgs<T> P;
+  P.Df = fine->D;
+  P.Dc = coarse->D;
+  P.nxg = 2 * coarse->D.nx;
+  P.fx0 = wrapi(fx0, P.nxg);
+  P.lo = lo;
+  P.hi = hi;
+  void **uf = state_ptrs(Uf), **uc = state_ptrs(Uc);
+  for (int f = 0; f < 5; ++f) {
+    P.uc[f] = (const T *)uc[f];
+    P.uf[f] = (T *)uf[f];
+    P.pf[f] = f <= 3 ? fine->ref_d[f] : nullptr;
+    P.pc[f] = f <= 3 ? coarse->ref_d[f] : nullptr;
+  }
+  for (int f = 0; f < 5; ++f) {
+    const int g = f <= 1 ? 0 : f - 1;
+    const long long n = fine->D.nxy * (long long)nzg_of(fine->D, g);
+    k_prolong<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, f);
+  }
+}
+
+// the fine handle is the coarse level's fine level over fine columns fx0 ..
+// fx0 + nx - 1 (mod 2 nx_c), full y and z
+static eb_status check_levels(eb_geom fine, eb_geom coarse, const eb_state *Uf, const eb_state *Uc, int lo, int hi) {
   if (!fine || !coarse) return fail(EB_ERR_INVALID_ARG, "NULL handle");
-  if (fine->D.nx != 2 * coarse->D.nx || fine->D.ny != 2 * coarse->D.ny || fine->D.nz != 2 * coarse->D.nz)
-    return fail(EB_ERR_INVALID_ARG, "the coarse handle must halve every dimension of the fine one");
+  if (fine->D.ny != 2 * coarse->D.ny || fine->D.nz != 2 * coarse->D.nz || fine->D.nx > 2 * coarse->D.nx)
+    return fail(EB_ERR_INVALID_ARG, "the fine handle must be an x-window of the coarse handle's fine level");
+  if (fabs(2.0 * fine->D.dx - coarse->D.dx) > 1e-12 * coarse->D.dx ||
+      fabs(2.0 * fine->D.dy - coarse->D.dy) > 1e-12 * coarse->D.dy ||
+      fabs(2.0 * fine->D.dz - coarse->D.dz) > 1e-12 * coarse->D.dz)
+    return fail(EB_ERR_INVALID_ARG, "the fine cells must be half the coarse ones");
   if (fine->prec != coarse->prec) return fail(EB_ERR_INVALID_ARG, "the handles differ in precision");
+  if (lo < 0 || hi > fine->D.nx || lo > hi) return fail(EB_ERR_INVALID_ARG, "column range outside the fine handle");
   const size_t es = fine->prec == EB_F64 ? 8 : 4;
-  if (!state_ok(Uf, es) || !state_ok(Uc, es))
-    return fail(EB_ERR_INVALID_ARG, "state pointer NULL or misaligned");
+  if (!state_ok(Uf, es) || !state_ok(Uc, es)) return fail(EB_ERR_INVALID_ARG, "state pointer NULL or misaligned");
+  return EB_OK;
+}
+
+eb_status eb_restrict(eb_geom fine, eb_geom coarse, const eb_state *Uf, eb_state *Uc, int fine_x0, int lo, int hi,
+                      void *stream) {
+  eb_status st = check_levels(fine, coarse, Uf, Uc, lo, hi);
+  if (st != EB_OK) return st;
+  if ((lo % 2) || (hi % 2) || ((fine_x0 % 2 + 2) % 2))
+    return fail(EB_ERR_INVALID_ARG, "restriction columns must start on even fine columns");
   cudaStream_t s = as_stream(stream);
-  if (fine->prec == EB_F64) restrict_t<double>(fine, coarse, Uf, Uc, s);
-  else restrict_t<float>(fine, coarse, Uf, Uc, s);
+  if (fine->prec == EB_F64) restrict_t<double>(fine, coarse, Uf, Uc, fine_x0, lo, hi, s);
+  else restrict_t<float>(fine, coarse, Uf, Uc, fine_x0, lo, hi, s);
   CUDA_TRY(cudaGetLastError(), "restriction");
+  return EB_OK;
+}
+
+eb_status eb_prolong(eb_geom coarse, const eb_state *Uc, eb_geom fine, eb_state *Uf, int fine_x0, int lo, int hi,
+                     void *stream) {
+  eb_status st = check_levels(fine, coarse, Uf, Uc, lo, hi);
+  if (st != EB_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  if (fine->prec == EB_F64) prolong_t<double>(coarse, Uc, fine, Uf, fine_x0, lo, hi, s);
+  else prolong_t<float>(coarse, Uc, fine, Uf, fine_x0, lo, hi, s);
+  CUDA_TRY(cudaGetLastError(), "prolongation");
   return EB_OK;
 }

@@ -35,7 +35,7 @@ EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom
                     "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
                     "eb_geom_set_wind_reference", "eb_fma_peak", "eb_ensemble_info",
                     "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule", "eb_geom_set_sources",
-                    "eb_geom_build_coarse", "eb_restrict")
+                    "eb_geom_build_coarse", "eb_restrict", "eb_prolong")
 
 
 class EbError(RuntimeError):
@@ -120,7 +120,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_geom_set_wind_reference.argtypes = [V, V, V, V]
     lib.eb_geom_set_sources.argtypes = [V, I]
     lib.eb_geom_build_coarse.argtypes = [V, V, V, V, V]
-    lib.eb_restrict.argtypes = [V, V, V, V, V]
+    lib.eb_restrict.argtypes = [V, V, V, V, I, I, I, V]
+    lib.eb_prolong.argtypes = [V, V, V, V, I, I, I, V]
     lib.eb_fma_peak.argtypes = [I, P(D), V]
     lib.eb_ensemble_info.argtypes = [V, P(I)]
     lib.eb_ensemble_inject_barrier_fault.argtypes = [V, I]
@@ -136,7 +137,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                  "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
                  "eb_geom_set_wind_reference", "eb_fma_peak", "eb_ensemble_info",
                  "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule", "eb_geom_set_sources",
-                 "eb_geom_build_coarse", "eb_restrict"):
+                 "eb_geom_build_coarse", "eb_restrict", "eb_prolong"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -397,16 +398,28 @@ def set_slab_levels(geom: Geometry, levels: int) -> None:
     _check(load().eb_geom_set_slab_levels(geom.handle, int(levels)))
 
 
-def restrict(fine: Geometry, coarse: Geometry, Uf: dict, Uc: dict, stream=None) -> dict:
-    """The fine state restricted onto the coarse level in place of Uc
+def restrict(fine: Geometry, coarse: Geometry, Uf: dict, Uc: dict, fine_x0: int = 0, cols=None, stream=None) -> dict:
+    """A fine state restricted onto the coarse level in place of Uc
     (``eb_restrict``): volume-weighted cell-centred fields, area-weighted face
-    fields; coarse CVs without fine fluid keep their values.  Returns Uc."""
-    for U, gm in ((Uf, fine), (Uc, coarse)):
-        for f in FIELDS:
-            _require_cuda(U[f], gm.dtype, gm.shape(f), f)
+    fields; coarse CVs without fine fluid keep their values.  The fine handle
+    may be an x-window of the fine level starting at global fine column
+    fine_x0; ``cols`` = (lo, hi) local fine columns to restrict (default
+    all).  Returns Uc."""
+    lo, hi = (0, fine.nx) if cols is None else (int(cols[0]), int(cols[1]))
     _check(load().eb_restrict(fine.handle, coarse.handle, ctypes.byref(fine._cstate(Uf)),
-                              ctypes.byref(coarse._cstate(Uc)), _stream(stream)))
+                              ctypes.byref(coarse._cstate(Uc)), int(fine_x0), lo, hi, _stream(stream)))
     return Uc
+
+
+def prolong(coarse: Geometry, Uc: dict, fine: Geometry, Uf: dict, fine_x0: int = 0, owned=(0, 0),
+            stream=None) -> dict:
+    """The coarse state prolonged onto every column of the fine handle
+    outside its local columns ``owned`` = (lo, hi) (``eb_prolong``: boundary
+    values of a refined patch), in place of Uf.  Returns Uf."""
+    _check(load().eb_prolong(coarse.handle, ctypes.byref(coarse._cstate(Uc)), fine.handle,
+                             ctypes.byref(fine._cstate(Uf)), int(fine_x0), int(owned[0]), int(owned[1]),
+                             _stream(stream)))
+    return Uf
 
 
 def fma_peak(kind: str, stream=None) -> float:

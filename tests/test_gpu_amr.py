@@ -188,3 +188,59 @@ def test_coarse_handle_argument_errors(eb):
         g.coarse()
     assert e.value.code == 1
     g.close()
+
+
+@pytest.mark.parametrize("precision,stages", [("f64", 1), ("mixed", 1), ("f64", 3), ("mixed", 3)])
+def test_two_level_steps_match(eb, oracle, precision, stages):
+    """The coupled two-level step (paper_2604_11959_gb300/amr.py) against the
+    same sequence in the oracle: a rough terrain with planted tiny cells,
+    fine level 80x32x16, coarse level merged from it, one refined x-patch of
+    16 fine columns; every step the patch's halo takes the coarse state, both
+    levels advance with the fine time step, and the patch's owned columns are
+    restricted onto the coarse level.  The whole coarse state and the patch's
+    owned columns after three forward-Euler / two three-stage steps, both
+    precisions, to 1e-12 / 1e-5."""
+    from paper_2604_11959_gb300 import amr
+    w = inputs.Workload("grf-80x32x16", 80, 32, 16, 1, terrain="grf", seed=9, hmax=0.2, tiny=2)
+    wc = inputs.Workload("grf-40x16x8", 40, 16, 8, 1, Lx=w.Lx, Ly=w.Ly, Lz=w.Lz, terrain="grf", hmax=0.2)
+    h = w.heights()
+    H = amr.HALO_EULER if stages == 1 else amr.HALO_RK3
+    x_lo, x_hi = 28, 44
+    rf, rc = w.references("sheltered"), wc.references("sheltered")
+    dt = w.dt()
+    nsteps = 3 if stages == 1 else 2
+    # oracle
+    df = oracle.Domain(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, h)
+    dc = oracle.coarse_domain(df)
+    Gc = oracle.coarsen(df, oracle.geometry(df), dc)
+    Tc = oracle.wsrd_setup(dc, Gc)
+    dw = oracle.Domain(w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, h, window=((x_lo - H) % w.nx, 0, x_hi - x_lo + 2 * H, w.ny))
+    Gw = oracle.geometry(dw)
+    Tw = oracle.wsrd_setup(dw, Gw)
+    Uc = wc.state("sheltered", seed=3)
+    grid = {"rho": 0, "rhotheta": 0, "rhou": 1, "rhov": 2, "rhow": 3}
+    Uw = oracle.prolong(dc, Uc, dw, {f: np.zeros(dw.shape(grid[f])) for f in FIELDS}, (0, 0))
+    # the library
+    two = amr.TwoLevel(eb, w.nx, w.ny, w.nz, w.Lx, w.Ly, w.Lz, h, x_lo, x_hi, H, precision, rf, rc)
+    Cd = to_device(Uc, precision, rc)
+    Fd = two.fill(Cd, two.patch.empty_state())
+    for _ in range(nsteps):
+        Uw = oracle.prolong(dc, Uc, dw, Uw, (x_lo, x_hi))
+        Uc1 = oracle.step(dc, Gc, Tc, Uc, dt, 1, stages)
+        Uw = oracle.step(dw, Gw, Tw, Uw, dt, 1, stages)
+        Uc = oracle.restrict(dw, Gw, Uw, dc, Uc1, (x_lo, x_hi))
+        Cd, Fd = two.step(Cd, Fd, dt, stages)
+    eb.sync_status(two.coarse)
+    eb.sync_status(two.patch)
+    gc, gf = to_host(Cd, rc), to_host(Fd, rf)
+    actc = active_masks(Gc, dc.nz)
+    actw = active_masks(Gw, dw.nz)
+    own = slice(H, H + x_hi - x_lo)
+    for f in FIELDS:
+        g = FGRID[f]
+        err = rel_linf(gc[f], Uc[f], actc[g])
+        assert err <= TOL[precision], ("coarse", precision, stages, f, err, worst(gc[f], Uc[f], actc[g]))
+        a, b, m = gf[f][..., own], Uw[f][..., own], actw[g][..., own]
+        err = rel_linf(a, b, m)
+        assert err <= TOL[precision], ("patch", precision, stages, f, err, worst(a, b, m))
+    two.close()

@@ -131,3 +131,40 @@ def test_restriction_keeps_totals_and_uniform_states(oracle):
     for f in FIELDS:
         m = R1[f] != -7.0
         assert m.any() and np.abs(R1[f][m] - 2.5).max() <= 1e-15, f
+
+
+def test_prolongation_then_restriction_is_the_identity(oracle):
+    """Prolonging a coarse state onto a fine window (every column not owned)
+    and restricting it back gives the coarse state on every coarse CV with fine
+    fluid: injected cell values and face values on coarse faces are kept by
+    the weighted means.  A face field linear along its axis is prolonged
+    exactly (the odd fine faces take the mean of their two coarse faces), and
+    owned columns are left alone.  Fails if the odd faces take one neighbour,
+    if cells take a neighbouring coarse cell, or if owned columns are
+    overwritten."""
+    df = _rough(oracle)
+    dc = oracle.coarse_domain(df)
+    Gf = oracle.geometry(df)
+    rng = np.random.default_rng(5)
+    grid = {"rho": 0, "rhotheta": 0, "rhou": 1, "rhov": 2, "rhow": 3}
+    Uc = {f: 1.0 + rng.random(dc.shape(grid[f])) for f in FIELDS}
+    Uc["rhou"] = np.broadcast_to(0.3 * np.arange(dc.NX)[None, None, :], dc.shape(1)).copy() + 1.0
+    win = oracle.Domain(df.NX, df.NY, df.nz, df.Lx, df.Ly, df.Lz, df.h, window=(8, 0, 20, df.NY))
+    U0 = {f: np.full(win.shape(grid[f]), -3.0) for f in FIELDS}
+    owned = (12, 24)                               # global fine columns 12 .. 23 of the window 8 .. 27
+    P = oracle.prolong(dc, Uc, win, U0, owned)
+    for f in FIELDS:
+        assert (P[f][..., 4:16] == -3.0).all(), f  # owned columns untouched
+        assert (P[f][..., :4] != -3.0).all() and (P[f][..., 16:] != -3.0).all(), f
+    # rho*u linear in the coarse face index: fine face 2I + 1 sits halfway
+    xi = 8 + np.arange(20)
+    want = 1.0 + 0.3 * (xi / 2.0)
+    halo = np.r_[0:4, 16:20]
+    assert np.abs(P["rhou"][..., halo] - want[halo]).max() <= 1e-14
+    full = {f: oracle.prolong(dc, Uc, df, {k: np.zeros(df.shape(grid[k])) for k in FIELDS}, (0, 0))[f]
+            for f in FIELDS}
+    back = oracle.restrict(df, Gf, full, dc, {f: np.full(dc.shape(grid[f]), -9.0) for f in FIELDS})
+    for f in FIELDS:
+        m = back[f] != -9.0
+        assert m.sum() > 0.5 * m.size, f
+        assert np.abs(back[f][m] - Uc[f][m]).max() <= 1e-14 * np.abs(Uc[f]).max(), f
