@@ -303,9 +303,8 @@ __global__ void k_prolong(const __grid_constant__ ProlongArgs<T> P, int f) {
   const long long n = Df.nxy * (long long)nzg_of(Df, g);
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const int k = (int)(t / Df.nxy);
-  const long long c2 = t - (long long)k * Df.nxy;
-  const int j = (int)(c2 / Df.nx), i = (int)(c2 - (long long)j * Df.nx);
+  int i, j, k;
+  split_index(Df, (unsigned)t, i, j, k);
   if (i >= P.lo && i < P.hi) return;   // an owned column
   const int gi = wrapi(P.fx0 + i, P.nxg);
   int c[3] = {gi / 2, j / 2, k / 2};

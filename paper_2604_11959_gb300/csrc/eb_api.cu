@@ -933,6 +933,12 @@ eb_status eb_geom_set_sources(eb_geom geom, int flags) {
       CUDA_TRY(cudaMemcpy(geom->src_f[q], tf.data(), sizeof(float) * nz, cudaMemcpyHostToDevice), "tables");
     }
   }
+  if (flags && !geom->src_pp) {
+    const size_t es = geom->prec == EB_F64 ? sizeof(double) : sizeof(float);
+    double *pp = nullptr;   // one cell field in the state's precision
+    CUDA_TRY(geom->alloc(&pp, (long long)((geom->D.nxy * geom->D.nz * es + 7) / 8)), "alloc source scratch");
+    geom->src_pp = pp;
+  }
   geom->src_flags = flags;
   return EB_OK;
 }

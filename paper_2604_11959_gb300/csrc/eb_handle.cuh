@@ -126,6 +126,7 @@ struct eb_geom_s {
   int src_flags = 0;
   double *src_d[2] = {nullptr, nullptr};
   float *src_f[2] = {nullptr, nullptr};
+  void *src_pp = nullptr;   // p' of every cell, scratch of the source pass
   ProjWork pw;
 
   template <typename P>
@@ -316,7 +317,7 @@ void stage(eb_geom g, void *const src[5], void *const base[5], void *const out[5
     flux_update(g, A, s);
     const bool f64 = sizeof(T) == sizeof(double);
     launch_sources<T>(A, g->src_flags, f64 ? (const T *)g->src_d[0] : (const T *)g->src_f[0],
-                      f64 ? (const T *)g->src_d[1] : (const T *)g->src_f[1], s);
+                      f64 ? (const T *)g->src_d[1] : (const T *)g->src_f[1], (T *)g->src_pp, s);
     wsrd_all<T>(g, out, s);
   } else if (g->wsrd_side && wsrd_beside) {
     flux_update(g, A, s, [&](cudaStream_t side) { wsrd_all<T>(g, out, side); });

@@ -15,7 +15,8 @@
 //   p' = p0(k) * expm1(gamma * log1p((rho theta)' / (rho0 theta0)(k)))
 // (the deviation form of p - p0: the float path rounds p', not p ~ 1e5 Pa);
 // p0(k) and 1 / (rho0 theta0)(k) are per-level tables built in double when
-// the sources are switched on.
+// the sources are switched on.  A first pass writes p' of every fluid cell
+// (k_pressure), the second forms the sources (k_sources).
 #include "eb_step.cuh"
 
 namespace {
@@ -28,6 +29,7 @@ struct SourceArgs {
   const T *rho, *rt;         // rho', (rho theta)' of the stage's source state
   T *out[3];                 // rho*u, rho*v, rho*w of the stage's output
   const T *p0, *irt0;        // per level: p0, 1 / (rho0 theta0)
+  T *pp;                     // p' of every fluid cell (written by k_pressure)
   T dt, gamma, grav, inv[3];
   int pressure, buoyancy;
   unsigned *status;
@@ -38,6 +40,18 @@ __device__ inline double log1p_t(double x) { return log1p(x); }
 __device__ inline float expm1_t(float x) { return expm1f(x); }
 __device__ inline double expm1_t(double x) { return expm1(x); }
 
+// p' of every cell that holds fluid, once per stage (the source pass reads
+// each cell's value for up to six faces)
+template <typename T>
+__global__ void k_pressure(const __grid_constant__ SourceArgs<T> S) {
+  const Dims &D = S.D;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= D.nxy * (long long)D.nz) return;
+  if (!(S.cflag[t] & 1)) return;
+  const int k = (int)D.fnxy.div((unsigned)t);
+  S.pp[t] = S.p0[k] * expm1_t(S.gamma * log1p_t(S.rt[t] * S.irt0[k]));
+}
+
 // one thread per (i, j, k) position: the u and v CVs of level k (k < nz) and
 // the w CV of face level k (0 < k < nz)
 template <typename T>
@@ -45,12 +59,9 @@ __global__ void k_sources(const __grid_constant__ SourceArgs<T> S) {
   const Dims &D = S.D;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= D.nxy * (long long)(D.nz + 1)) return;
-  const int k = (int)(t / D.nxy);
-  const long long c2 = t - (long long)k * D.nxy;
-  const int j = (int)(c2 / D.nx), i = (int)(c2 - (long long)j * D.nx);
-  auto pprime = [&](long long c, int kk) -> T {
-    return S.p0[kk] * expm1_t(S.gamma * log1p_t(S.rt[c] * S.irt0[kk]));
-  };
+  int i, j, k;
+  split_index(D, (unsigned)t, i, j, k);   // below 2^32 (checked when the handle is built)
+  auto pprime = [&](long long c, int) -> T { return S.pp[c]; };
   const bool own = k < D.nz && (S.cflag[t] & 1);
   T p_own = T(0);
   if (own && S.pressure) p_own = pprime(t, k);
@@ -90,7 +101,7 @@ __global__ void k_sources(const __grid_constant__ SourceArgs<T> S) {
 }  // namespace
 
 template <typename T>
-void launch_sources(const StepArgs<T> &A, int flags, const T *p0, const T *irt0, cudaStream_t s) {
+void launch_sources(const StepArgs<T> &A, int flags, const T *p0, const T *irt0, T *pp, cudaStream_t s) {
   SourceArgs<T> S;
   S.D = A.D;
   S.cflag = A.G[0].dflag;
@@ -102,6 +113,7 @@ void launch_sources(const StepArgs<T> &A, int flags, const T *p0, const T *irt0,
   S.rt = A.src.f[1];
   S.p0 = p0;
   S.irt0 = irt0;
+  S.pp = pp;
   S.dt = A.dtT;
   S.gamma = (T)(EB_CP / (EB_CP - EB_RD));
   S.grav = (T)EB_GRAV;
@@ -111,9 +123,15 @@ void launch_sources(const StepArgs<T> &A, int flags, const T *p0, const T *irt0,
   S.pressure = (flags & EB_SOURCE_PRESSURE) ? 1 : 0;
   S.buoyancy = (flags & EB_SOURCE_BUOYANCY) ? 1 : 0;
   S.status = A.status;
+  if (S.pressure) {
+    const long long nc = A.D.nxy * (long long)A.D.nz;
+    k_pressure<T><<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(S);
+  }
   const long long n = A.D.nxy * (long long)(A.D.nz + 1);
   k_sources<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S);
 }
 
-template void launch_sources<float>(const StepArgs<float> &, int, const float *, const float *, cudaStream_t);
-template void launch_sources<double>(const StepArgs<double> &, int, const double *, const double *, cudaStream_t);
+template void launch_sources<float>(const StepArgs<float> &, int, const float *, const float *, float *,
+                                    cudaStream_t);
+template void launch_sources<double>(const StepArgs<double> &, int, const double *, const double *, double *,
+                                     cudaStream_t);

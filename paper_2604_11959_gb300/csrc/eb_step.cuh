@@ -61,9 +61,9 @@ void launch_wsrd(const WsrdArgs<T> &R, cudaStream_t s);
 template <typename T>
 void launch_wsrd5(const WsrdSet<T> &S, cudaStream_t s);
 // sources of the compressible system (eb_sources.cu): flags EB_SOURCE_*,
-// per-level tables p0 and 1 / (rho0 theta0)
+// per-level tables p0 and 1 / (rho0 theta0), scratch pp of one cell field
 template <typename T>
-void launch_sources(const StepArgs<T> &A, int flags, const T *p0, const T *irt0, cudaStream_t s);
+void launch_sources(const StepArgs<T> &A, int flags, const T *p0, const T *irt0, T *pp, cudaStream_t s);
 
 // One ensemble member in one step direction: the arguments of its flux
 // update and of its five-field redistribution.
