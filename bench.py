@@ -330,6 +330,7 @@ def run_slabs(eb, steps, warmup, world, rank, dist, clk=None):
     geom = make_geom(eb, ws, sl.heights(h), "mixed", refs)
     held0 = eb.device_state({f: np.ascontiguousarray(sl.scatter(U[f])) for f in S.FIELDS}, "mixed", refs)
     dt = w.dt()
+    slab_levels = eb.tune(geom, held0, dt, reps=3)   # the bulk kernel's split for the slab's columns
 
     def step_one(Uq):
         return eb.step(geom, Uq, dt, 1)
@@ -351,7 +352,7 @@ def run_slabs(eb, steps, warmup, world, rank, dist, clk=None):
     eb.sync_status(geom)
     geom.close()
     return {"value": w.cells() / (ms * 1e-3), "ms_per_step": ms, "cells": w.cells(), "halo": sl.halo,
-            "held_columns": sl.ext, "owned_columns": sl.width}
+            "held_columns": sl.ext, "owned_columns": sl.width, "tuned_slab_levels": slab_levels}
 
 
 def compressible_cost(eb, world, dist, warmup, steps):
@@ -967,6 +968,7 @@ def run_arm(args, rank, world, w, dist):
                 "config": {"workload": "gaussian-hill-256x256x128 in x-slabs", "cells": r["cells"],
                            "precision": "mixed", "stages": 1, "halo": r["halo"],
                            "held_columns_per_rank": r["held_columns"], "owned_columns_per_rank": r["owned_columns"],
+                           "tuned_slab_levels": r["tuned_slab_levels"],
                            "parallelism": f"{world} x-slabs, halo exchange every step"},
                 "roofline": None, "clocks": clk.summary(), "cpu_baseline": None, "e2e": None,
                 "gpu_launches": 7 * args.steps}))   # per step: pass-through, bulk, 2 near-EB, 3 redistribution
