@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--ensemble-schedule", choices=("tuned", "persistent", "branches"), default="tuned",
                     help="ensemble: the autotuner's schedule, or one forced after tuning the slab heights")
+    ap.add_argument("--tile-rows", type=int, choices=(16, 14), default=None,
+                    help="bulk kernel tile rows (with --slab-levels); default: chosen by the autotuner")
     ap.add_argument("--slab-levels", type=int, default=None,
                     help="bulk kernel slab height (0 = automatic); default: chosen by the autotuner")
     return ap.parse_args()
@@ -675,7 +677,8 @@ def make_geom(eb, w, h, precision, refs):
                        ref_rho=torch.from_numpy(refs[0]).cuda(), ref_rhotheta=torch.from_numpy(refs[1]).cuda(), **kw)
 
 
-def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=None, slab_levels=None):
+def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=None, slab_levels=None,
+                  tile_rows=None):
     import torch
     geom = make_geom(eb, w, h, precision, refs)
     info = geom.info()
@@ -688,6 +691,8 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=
         slab = eb.tune(geom, A, w.dt(), reps=5)   # autotuned slab height of the bulk kernel's tiles
     else:
         slab = slab_levels
+        if tile_rows is not None and precision == "mixed":
+            eb.set_tile_rows(geom, tile_rows)
         eb.set_slab_levels(geom, slab)
     outs = [geom.empty_state(), geom.empty_state()]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -728,6 +733,31 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=
                 "warp_instructions_per_fast_cell": profile_record("k_fast_tiled", w.name, precision,
                                                                   "warp_instructions_per_fast_cell")}
     roof = hbm_roof
+    if precision == "mixed":
+        # the other tile height, timed the same way: the bulk kernel alone and
+        # the whole step (the tuner keeps the faster step)
+        tuned_rows = int(geom.info()["tile_rows"])
+        other = 14 if tuned_rows == 16 else 16
+        eb.set_tile_rows(geom, other)
+        alt = []
+        for q in range(max(5, min(steps, 20))):
+            flush.zero_()
+            alt.append(eb.step_profile(geom, A, outs[q % 2], dt))
+        alt = np.median(np.array(alt), axis=0)
+        st_ms = []
+        for q in range(max(5, min(steps, 20))):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            eb.step(geom, A, dt, 1, out=outs[q % 2])
+            b.record(stream)
+            torch.cuda.synchronize()
+            st_ms.append(a.elapsed_time(b))
+        eb.set_tile_rows(geom, tuned_rows)
+        hbm_roof["other_tile_rows"] = {
+            "tile_rows": other, "bulk_ms": float(alt[0]),
+            "frac": fast_bytes / (float(alt[0]) * 1e-3) / 1e9 / hbm, "step_ms": float(np.mean(st_ms)),
+            "note": "the tuner keeps the tile height of the faster whole step"}
     if precision == "f64":
         # GB300's FP64 rate is low: the FP64 bulk kernel is bound by its FP64
         # arithmetic, measured against the DFMA rate of this GPU
@@ -762,6 +792,7 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=
         "steps": steps,
         "tuned_slab_levels": slab,
         "bulk_high_priority": int(geom.info()["bulk_high_priority"]),
+        "tile_rows": int(geom.info()["tile_rows"]),
     }
     return geom, res
 
@@ -1008,7 +1039,7 @@ def run_arm(args, rank, world, w, dist):
     clk = ClockSampler(dev_index)
     if args.precision in ("both", "mixed"):
         geom, mixed = run_precision(eb, w, h, U, refs, "mixed", args.steps, args.warmup, world, dist, clk,
-                                    args.slab_levels)
+                                    args.slab_levels, args.tile_rows)
         if rank == 0 and not args.no_e2e:
             e2e_res = e2e(eb, geom, w, U, refs, "mixed", min(args.steps, 20))
         geom.close()
@@ -1037,6 +1068,7 @@ def run_arm(args, rank, world, w, dist):
                    "l2": "512 MiB buffer written before every timed step (untimed); per-step CUDA events",
                    "tuned_slab_levels": head.get("tuned_slab_levels"),
                    "tuned_bulk_high_priority": head.get("bulk_high_priority"),
+                   "tuned_tile_rows": head.get("tile_rows"),
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "roofline": head["roofline"],
         "step_hbm_frac": head["step_frac"],

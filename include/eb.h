@@ -130,6 +130,7 @@ typedef struct {
                                is a near-EB CV, so eb_step runs it right after
                                the near-EB kernels, beside the bulk kernel
                                (ensembles keep it after the bulk kernel)      */
+  int64_t tile_rows;        /* rows of the bulk kernel's tiles (16, or 14)    */
 } eb_geom_info_t;
 
 /*
@@ -571,9 +572,10 @@ eb_status eb_ensemble_destroy(eb_ensemble e);
  * stages = 1) from U (read only; the results go to a temporary state) for each
  * candidate slab height of the bulk kernel's tiles (automatic, 12 .. 64
  * levels, whole column), each with the bulk kernel at the same and at a
- * higher stream priority than the near-EB kernels (eb_geom_set_bulk_priority),
- * and keeps the fastest pair; *slab_levels (NULL allowed) receives the height
- * (0 = automatic), eb_geom_info the pair.  Results of later steps do not
+ * higher stream priority than the near-EB kernels (eb_geom_set_bulk_priority)
+ * and, on the mixed path, with tiles of 16 and of 14 rows
+ * (eb_geom_set_tile_rows), and keeps the fastest combination; *slab_levels
+ * (NULL allowed) receives the height (0 = automatic), eb_geom_info the rest.  Results of later steps do not
  * depend on either.  Synchronises the stream; allocates and frees the
  * temporary state. */
 eb_status eb_geom_tune(eb_geom geom, const eb_state *U, double dt, int reps, int *slab_levels, void *stream);
@@ -593,6 +595,14 @@ eb_status eb_geom_set_bulk_priority(eb_geom geom, int high);
  * nz mean whole columns), e.g. to re-apply a height eb_geom_tune chose
  * earlier.  Waits for the device to be idle (the old plan may be in use). */
 eb_status eb_geom_set_slab_levels(eb_geom geom, int slab_levels);
+
+/* Rows of the bulk kernel's tiles of 32 columns: 16 (default) or, on the
+ * mixed path, 14 (a 256-row domain then cuts into 19 tile rows, and two slabs
+ * of its 152 tiles fill every SM with two CTAs).  Scheduling only: every
+ * cell's arithmetic is the same.  eb_geom_tune tries both on the mixed path;
+ * ensembles keep 16 for their members.  Waits for the device to be idle.
+ * EB_ERR_INVALID_ARG for other values, or 14 on an FP64 handle. */
+eb_status eb_geom_set_tile_rows(eb_geom geom, int rows);
 
 /* Synchronise the stream, then return (and clear) the first device-side
  * error latched since the last call: EB_ERR_NUMERIC or EB_ERR_TIMEOUT. */

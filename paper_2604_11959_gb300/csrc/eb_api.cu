@@ -21,7 +21,8 @@ std::string &eb_error_slot() { return g_last_error; }
 
 eb_status eb_replan_bulk(eb_geom g, int slab_levels) {
   std::vector<int> seg, off;
-  CUDA_TRY(bulk_plan(g->D, g->kfast_host.data(), g->prec == EB_F64, slab_levels, seg, off), "bulk work split");
+  CUDA_TRY(bulk_plan(g->D, g->kfast_host.data(), g->prec == EB_F64, slab_levels, g->tile_rows, seg, off),
+           "bulk work split");
   // the split arrays are small: the old ones are released right away
   for (void *p : {(void *)g->bseg, (void *)g->boff}) {
     if (!p) continue;
@@ -676,6 +677,7 @@ eb_status eb_geom_info(eb_geom geom, eb_geom_info_t *info) {
   info->slab_levels = geom->slab_levels;
   info->bulk_high_priority = geom->bulk_high;
   info->wsrd_beside_bulk = geom->wsrd_side;
+  info->tile_rows = geom->tile_rows;
   return EB_OK;
 }
 
@@ -862,6 +864,15 @@ eb_status eb_step_profile(eb_geom geom, const eb_state *Un, eb_state *Unp1, doub
   return EB_OK;
 }
 
+eb_status eb_geom_set_tile_rows(eb_geom geom, int rows) {
+  if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
+  if (rows != 16 && rows != 14) return fail(EB_ERR_INVALID_ARG, "rows must be 16 or 14");
+  if (rows == 14 && geom->prec == EB_F64) return fail(EB_ERR_INVALID_ARG, "14-row tiles are for the mixed path");
+  CUDA_TRY(cudaDeviceSynchronize(), "drain before re-planning");
+  geom->tile_rows = rows;
+  return eb_replan_bulk(geom, geom->slab_levels);
+}
+
 eb_status eb_geom_set_slab_levels(eb_geom geom, int slab_levels) {
   if (!geom) return fail(EB_ERR_INVALID_ARG, "NULL handle");
   if (slab_levels < 0) return fail(EB_ERR_INVALID_ARG, "slab_levels must be >= 0");
@@ -975,10 +986,14 @@ eb_status eb_geom_tune(eb_geom geom, const eb_state *U, double dt, int reps, int
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
   float best = 0.f;
-  int best_c = 0, best_h = 0;
+  int best_c = 0, best_h = 0, best_r = 16;
   bool first = true;
   eb_status st = EB_OK;
+  const int rows_cand[2] = {16, 14};
+  const int nrows = geom->prec == EB_F64 ? 1 : 2;
+  for (int ri = 0; ri < nrows && st == EB_OK; ++ri)
   for (int c : cand) {
+    geom->tile_rows = rows_cand[ri];
     if ((st = eb_replan_bulk(geom, c)) != EB_OK) break;
     for (int hp = 0; hp < 2 && st == EB_OK; ++hp) {
       geom->bulk_high = hp;
@@ -998,12 +1013,14 @@ eb_status eb_geom_tune(eb_geom geom, const eb_state *U, double dt, int reps, int
         best = ms;
         best_c = c;
         best_h = hp;
+        best_r = rows_cand[ri];
         first = false;
       }
     }
     if (st != EB_OK) break;
   }
   geom->bulk_high = best_h;
+  geom->tile_rows = best_r;
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   cudaStreamSynchronize(s);

@@ -178,9 +178,12 @@ __device__ inline P flux6(P m, P a, P b, P c, P d, bool has_d = true) {
   return pmul(m, psel_pos(m, vp, vn));
 }
 
-template <typename T>
+// Tile of the bulk march: TX x TY columns (TY = 16, or 14 so that a 256-row
+// domain cuts into 19 tile rows and two slabs of 152 tiles fill every SM
+// with two CTAs).
+template <typename T, int TY_ = 16>
 struct BulkTile {
-  static constexpr int TX = 32, TY = 16;     // columns and rows of a tile
+  static constexpr int TX = 32, TY = TY_;    // columns and rows of a tile
   static constexpr int NPX = TX / 2;         // column pairs per row (threads per row)
   static constexpr int NT = NPX * TY;        // threads
   static constexpr int HX = 4;               // raw halo in x on both sides (16-byte aligned rows)
@@ -211,7 +214,7 @@ struct BulkTile {
 // co-residency check counts a CTA that allocates tensor memory as filling
 // its SM).  The arithmetic is the same either way.
 template <typename T>
-constexpr bool bulk_tmem_default() {
+__host__ __device__ constexpr bool bulk_tmem_default() {
   return sizeof(T) == sizeof(float);
 }
 
@@ -246,14 +249,15 @@ __device__ inline void bulk_tmem_end(unsigned *slot) {
   }
 }
 
-// One march of the CTA over the levels [sg.y, sg.z) of tile sg.x.  smem_bytes
-// holds BulkTile<T>::BYTES of dynamic shared memory, tbase is this thread's
+// One march of the CTA over the levels [sg.y, sg.z) of tile sg.x (tiles of
+// TYV rows).  smem_bytes holds BulkTile<T, TYV>::BYTES of dynamic shared
+// memory, tbase is this thread's
 // tensor-memory base (bulk_tmem_begin), and bad turns NaN when a written
 // value is not finite.  Every thread of the CTA calls it.
-template <typename T, int V, bool TM = bulk_tmem_default<T>()>
+template <typename T, int V, bool TM = bulk_tmem_default<T>(), int TYV = 16>
 __device__ __forceinline__ void bulk_march(const StepArgs<T> &A, const int4 sg, unsigned char *smem_bytes,
                                            const unsigned tbase, typename PairOf<T>::type &bad) {
-  using TL = BulkTile<T>;
+  using TL = BulkTile<T, TYV>;
   using P = typename PairOf<T>::type;
   constexpr int TX = TL::TX, TY = TL::TY, NPX = TL::NPX, NT = TL::NT, PX = TL::PX, NP = TL::NP, QX = TL::QX,
                 NQ = TL::NQ;
@@ -462,7 +466,7 @@ __device__ __forceinline__ void bulk_march(const StepArgs<T> &A, const int4 sg, 
         const P fB = flux6(mB, ld2(Q - 2 * QX), ld2(Q - QX), ld2(Q), ld2(Q + QX));
         st2(FY + G0 * TL::NFY + TY * TX + 2 * tx, fA);
         st2(FY + (G0 + 1) * TL::NFY + TY * TX + 2 * tx, fB);
-      } else if (ty >= TY - 2) {   // faces on the high x edge of the tile (row tx): two grids per row
+      } else if (ty >= TY - 2 && tx < TY) {   // faces on the high x edge of the tile (row tx): two grids per row
         const int hi = ty - (TY - 2), G0 = 2 * hi;
         const int c = TL::ri(TX, tx);
         const T *U = Rk + 2 * NP;

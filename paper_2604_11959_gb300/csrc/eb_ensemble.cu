@@ -127,7 +127,7 @@ eb_status build_tables(eb_ensemble e, EnsembleArgs<T> E[2]) {
   for (int q = 0; q < n; ++q) {
     eb_geom g = e->m[q];
     std::vector<int> seg, off;
-    CUDA_TRY(bulk_plan(g->D, g->kfast_host.data(), g->prec == EB_F64, g->slab_levels, seg, off), "work split");
+    CUDA_TRY(bulk_plan(g->D, g->kfast_host.data(), g->prec == EB_F64, g->slab_levels, 16, seg, off), "work split");
     if ((int)off.size() - 1 != g->bctas)
       return fail(EB_ERR_STATE, "a member's work split changed outside the ensemble; tune it again");
     for (int u = 0; u + 1 < (int)off.size(); ++u) {
@@ -263,6 +263,13 @@ eb_status eb_ensemble_create(const eb_geom *members, int n, eb_ensemble *out) {
     if (members[q]->src_flags)
       return fail(EB_ERR_STATE, "ensembles take no compressible sources: a member has them switched on");
   }
+  // the persistent kernel marches tiles of 16 rows: members keep that height
+  for (int q = 0; q < n; ++q)
+    if (members[q]->tile_rows != 16) {
+      members[q]->tile_rows = 16;
+      const eb_status st = eb_replan_bulk(members[q], members[q]->slab_levels);
+      if (st != EB_OK) return st;
+    }
   for (int q = 1; q < n; ++q) {
     if (members[q]->prec != members[0]->prec) return fail(EB_ERR_INVALID_ARG, "members differ in precision");
     if (members[q]->device != members[0]->device) return fail(EB_ERR_INVALID_ARG, "members are on different devices");

@@ -10,16 +10,17 @@ namespace {
 
 using namespace bulk;
 
-// One CTA marches the pieces boff[b] .. boff[b+1]-1 of the work split.
-template <typename T, int V>
-__global__ void __launch_bounds__(BulkTile<T>::NT, (sizeof(T) == 4 ? 2 : 1)) k_fast_tiled(StepArgs<T> A) {
+// One CTA marches the pieces boff[b] .. boff[b+1]-1 of the work split
+// (tiles of TYV rows).
+template <typename T, int V, int TYV>
+__global__ void __launch_bounds__(BulkTile<T, TYV>::NT, (sizeof(T) == 4 ? 2 : 1)) k_fast_tiled(StepArgs<T> A) {
   using P = typename PairOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   __shared__ unsigned tm_slot;
   const unsigned tbase = bulk_tmem_begin<T>(&tm_slot);
   P bad = splat(T(0));   // becomes NaN once any written value is not finite
   for (int sgi = A.boff[blockIdx.x]; sgi < A.boff[blockIdx.x + 1]; ++sgi)
-    bulk_march<T, V>(A, A.bseg[sgi], smem_bytes, tbase, bad);
+    bulk_march<T, V, bulk_tmem_default<T>(), TYV>(A, A.bseg[sgi], smem_bytes, tbase, bad);
   bulk_tmem_end<T>(&tm_slot);
   if (!(isfinite(bad.x) && isfinite(bad.y))) atomicOr(A.status, EB_DEV_NUMERIC);
 }
@@ -59,32 +60,36 @@ __global__ void k_static(StepArgs<T> A, StaticBlocks SB) {
   }
 }
 
-template <typename T, int V>
+template <typename T, int V, int TYV>
 void set_smem_attr() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_fast_tiled<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)BulkTile<T>::BYTES);
+    cudaFuncSetAttribute(k_fast_tiled<T, V, TYV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)BulkTile<T, TYV>::BYTES);
     done = true;
   }
 }
 
-template <typename T, int V>
+template <typename T, int V, int TYV>
 void launch_bulk(const StepArgs<T> &A, cudaStream_t s) {
-  using TL = BulkTile<T>;
+  using TL = BulkTile<T, TYV>;
   if (A.bctas < 1) return;
-  set_smem_attr<T, V>();
-  k_fast_tiled<T, V><<<A.bctas, dim3(TL::NPX, TL::TY, 1), TL::BYTES, s>>>(A);
+  set_smem_attr<T, V, TYV>();
+  k_fast_tiled<T, V, TYV><<<A.bctas, dim3(TL::NPX, TL::TY, 1), TL::BYTES, s>>>(A);
 }
 
 template <typename T>
 int resident_ctas_per_sm() {
   constexpr int V = 16 / sizeof(T);
-  set_smem_attr<T, V>();
-  set_smem_attr<T, 1>();   // both variants set here, outside any graph capture
+  set_smem_attr<T, V, 16>();   // every variant set here, outside any graph capture
+  set_smem_attr<T, 1, 16>();
+  if constexpr (sizeof(T) == sizeof(float)) {
+    set_smem_attr<T, V, 14>();
+    set_smem_attr<T, 1, 14>();
+  }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast_tiled<T, V>, BulkTile<T>::NT, BulkTile<T>::BYTES) !=
-          cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fast_tiled<T, V, 16>, BulkTile<T>::NT,
+                                                    BulkTile<T>::BYTES) != cudaSuccess ||
       n < 1)
     n = 1;
   return n;
@@ -92,9 +97,9 @@ int resident_ctas_per_sm() {
 
 }  // namespace
 
-cudaError_t bulk_plan(const Dims &D, const int *kfast_host, bool f64, int slab_levels, std::vector<int> &seg,
-                      std::vector<int> &off) {
-  const int TX = BulkTile<float>::TX, TY = BulkTile<float>::TY;
+cudaError_t bulk_plan(const Dims &D, const int *kfast_host, bool f64, int slab_levels, int tile_rows,
+                      std::vector<int> &seg, std::vector<int> &off) {
+  const int TX = BulkTile<float>::TX, TY = tile_rows;
   const int tx = (D.nx + TX - 1) / TX, ty = (D.ny + TY - 1) / TY;
   const long long ntile = (long long)tx * ty;
   std::vector<int> kb(ntile, D.nz);
@@ -170,8 +175,15 @@ void launch_flux_bulk(const StepArgs<T> &A, cudaStream_t s) {
     vec = vec && ((uintptr_t)A.src.f[f] % 16 == 0) && ((uintptr_t)A.out[f] % 16 == 0);
     if (A.base[0]) vec = vec && ((uintptr_t)A.base[f] % 16 == 0);
   }
-  if (vec) launch_bulk<T, V>(A, s);
-  else launch_bulk<T, 1>(A, s);
+  if constexpr (sizeof(T) == sizeof(float)) {   // 14-row tiles on the float path only
+    if (A.tile_rows == 14) {
+      if (vec) launch_bulk<T, V, 14>(A, s);
+      else launch_bulk<T, 1, 14>(A, s);
+      return;
+    }
+  }
+  if (vec) launch_bulk<T, V, 16>(A, s);
+  else launch_bulk<T, 1, 16>(A, s);
 }
 
 template void launch_flux_fast<double>(const StepArgs<double> &, cudaStream_t);

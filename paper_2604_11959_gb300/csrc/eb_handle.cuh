@@ -86,6 +86,7 @@ struct eb_geom_s {
   int slab_levels = 0;    // slab height of the split (0: automatic)
   int plan_gen = 0;       // incremented whenever the split is rebuilt (its arrays move)
   int bulk_high = 0;      // 1: the bulk kernel runs on the high-priority stream
+  int tile_rows = 16;     // rows of the bulk kernel's tiles (16, or 14 on the float path)
   int wsrd_side = 0;      // 1: the redistribution runs on the side stream (see stage)
   std::vector<int> kfast_host;
   int kcov_max = 0;
@@ -216,6 +217,7 @@ StepArgs<T> step_args(eb_geom g, void *const src[5], void *const base[5], void *
   for (int q = 0; q < 4; ++q) A.G[q] = g->G[q];
   A.status = g->status;
   A.copy_static = copy;
+  A.tile_rows = g->tile_rows;
   A.kcov_max = g->kcov_max;
   return A;
 }

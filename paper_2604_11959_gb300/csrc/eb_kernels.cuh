@@ -80,8 +80,8 @@ void launch_stage_marks(const Dims &D, const GridDev G[4], uint8_t *const marks[
 // slabs of slab_levels levels (0: chosen from the GPU's size); seg holds
 // (tile, first level, end level, 0) per piece, off[b] .. off[b+1] the pieces
 // of CTA b
-cudaError_t bulk_plan(const Dims &D, const int *kfast_host, bool f64, int slab_levels, std::vector<int> &seg,
-                      std::vector<int> &off);
+cudaError_t bulk_plan(const Dims &D, const int *kfast_host, bool f64, int slab_levels, int tile_rows,
+                      std::vector<int> &seg, std::vector<int> &off);
 
 // eb_scan.cu: in-place exclusive scan of n values; total written to *total (device)
 void scan_exclusive(long long *data, long long n, long long *total, cudaStream_t s);

@@ -15,6 +15,7 @@ struct StepArgs {
   GridDev G[4];
   unsigned *status;
   int copy_static;     // also write covered CVs and the w wall levels
+  int tile_rows;       // rows of the bulk kernel's tiles (16, or 14 on the float path)
   int kcov_max;        // highest covered level + 1 over every grid and column
   // work split of the bulk kernel: CTA b marches the pieces boff[b] .. boff[b+1]-1
   // of bseg, each (tile, first level, end level, 0)

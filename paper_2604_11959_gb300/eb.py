@@ -35,7 +35,7 @@ EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom
                     "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
                     "eb_geom_set_wind_reference", "eb_fma_peak", "eb_ensemble_info",
                     "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule", "eb_geom_set_sources",
-                    "eb_geom_build_coarse", "eb_restrict", "eb_prolong")
+                    "eb_geom_build_coarse", "eb_restrict", "eb_prolong", "eb_geom_set_tile_rows")
 
 
 class EbError(RuntimeError):
@@ -60,7 +60,8 @@ class GeomInfo(ctypes.Structure):
                 ("tiny_cvs", ctypes.c_int64 * 4), ("fast_cells", ctypes.c_int64),
                 ("min_alpha", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("slab_levels", ctypes.c_int64),
-                ("bulk_high_priority", ctypes.c_int64), ("wsrd_beside_bulk", ctypes.c_int64)]
+                ("bulk_high_priority", ctypes.c_int64), ("wsrd_beside_bulk", ctypes.c_int64),
+                ("tile_rows", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -119,6 +120,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_project_set_preconditioner.argtypes = [V, I]
     lib.eb_geom_set_wind_reference.argtypes = [V, V, V, V]
     lib.eb_geom_set_sources.argtypes = [V, I]
+    lib.eb_geom_set_tile_rows.argtypes = [V, I]
     lib.eb_geom_build_coarse.argtypes = [V, V, V, V, V]
     lib.eb_restrict.argtypes = [V, V, V, V, I, I, I, V]
     lib.eb_prolong.argtypes = [V, V, V, V, I, I, I, V]
@@ -137,7 +139,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                  "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
                  "eb_geom_set_wind_reference", "eb_fma_peak", "eb_ensemble_info",
                  "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule", "eb_geom_set_sources",
-                 "eb_geom_build_coarse", "eb_restrict", "eb_prolong"):
+                 "eb_geom_build_coarse", "eb_restrict", "eb_prolong", "eb_geom_set_tile_rows"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -391,6 +393,12 @@ def set_bulk_priority(geom: Geometry, high: bool) -> None:
     """Run the bulk kernel on a high-priority stream beside the near-EB
     kernels, or on the caller's stream (``eb_geom_set_bulk_priority``)."""
     _check(load().eb_geom_set_bulk_priority(geom.handle, 1 if high else 0))
+
+
+def set_tile_rows(geom: Geometry, rows: int) -> None:
+    """Rows of the bulk kernel's tiles, 16 or (mixed path) 14
+    (``eb_geom_set_tile_rows``)."""
+    _check(load().eb_geom_set_tile_rows(geom.handle, int(rows)))
 
 
 def set_slab_levels(geom: Geometry, levels: int) -> None:

@@ -316,9 +316,10 @@ def test_tuning_changes_no_result(eb, precision):
 @pytest.mark.parametrize("precision", ["f64", "mixed"])
 def test_every_slab_height_gives_the_same_steps(eb, precision):
     """The bulk kernel's slab heights (eb_geom_set_slab_levels: automatic,
-    a few levels, whole columns) change which CTA marches which levels, never
-    a cell's arithmetic: the steps agree bit for bit, and a negative height is
-    rejected."""
+    a few levels, whole columns) and tile heights (eb_geom_set_tile_rows: 16,
+    or 14 on the mixed path) change which CTA marches which columns and
+    levels, never a cell's arithmetic: the steps agree bit for bit, and other
+    values are rejected."""
     w = rough_workload()
     refs = refs_for(w.nz, w.Lz)
     U = w.state("uniform", pert=1e-2, seed=6)
@@ -326,14 +327,22 @@ def test_every_slab_height_gives_the_same_steps(eb, precision):
     A = to_device(U, precision, refs)
     eb.set_slab_levels(geom, 0)
     want = eb.step(geom, A, w.dt(), 3)
-    for split in (1, 5, w.nz + 7):
-        eb.set_slab_levels(geom, split)
-        assert geom.info()["slab_levels"] == split
-        got = eb.step(geom, A, w.dt(), 3)
-        for f in FIELDS:
-            assert torch.equal(got[f], want[f]), (precision, split, f)
+    for rows in ((16, 14) if precision == "mixed" else (16,)):
+        eb.set_tile_rows(geom, rows)
+        assert geom.info()["tile_rows"] == rows
+        for split in (0, 1, 5, w.nz + 7):
+            eb.set_slab_levels(geom, split)
+            assert geom.info()["slab_levels"] == split
+            got = eb.step(geom, A, w.dt(), 3)
+            for f in FIELDS:
+                assert torch.equal(got[f], want[f]), (precision, rows, split, f)
     with pytest.raises(eb.EbError):
         eb.set_slab_levels(geom, -1)
+    with pytest.raises(eb.EbError):
+        eb.set_tile_rows(geom, 15)
+    if precision == "f64":
+        with pytest.raises(eb.EbError):
+            eb.set_tile_rows(geom, 14)
     eb.sync_status(geom)
     geom.close()
 
