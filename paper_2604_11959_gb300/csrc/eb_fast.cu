@@ -11,9 +11,16 @@ namespace {
 using namespace bulk;
 
 // One CTA marches the pieces boff[b] .. boff[b+1]-1 of the work split
-// (tiles of TYV rows).
+// (tiles of TYV rows).  The float path is held to EB_BULK_MAXNREG registers
+// per thread (96: the fewest without spills), so that beside its two CTAs per
+// SM (2 x 256 x 96 of the 65536 registers) the near-EB kernels' blocks still
+// find registers on the same SM and run beside the march.
+#ifndef EB_BULK_MAXNREG
+#define EB_BULK_MAXNREG 96
+#endif
 template <typename T, int V, int TYV>
-__global__ void __launch_bounds__(BulkTile<T, TYV>::NT, (sizeof(T) == 4 ? 2 : 1)) k_fast_tiled(StepArgs<T> A) {
+__global__ void __launch_bounds__(BulkTile<T, TYV>::NT, (sizeof(T) == 4 ? 2 : 1))
+    __maxnreg__(sizeof(T) == 4 ? EB_BULK_MAXNREG : 255) k_fast_tiled(StepArgs<T> A) {
   using P = typename PairOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_bytes[];
   __shared__ unsigned tm_slot;
