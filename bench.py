@@ -643,11 +643,13 @@ def bulk_source_hash():
     return hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()[:16]
 
 
-def profile_record(kernel, workload_name, precision, key):
+def profile_record(kernel, workload_name, precision, key, tile_rows=16):
     """A figure of a committed ncu summary (DRAM bytes per launch, FP64
     operations per cell), valid only while the sources it was taken on are
-    unchanged (their hash is recorded with it); None otherwise."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}_{precision}.txt")
+    unchanged (their hash is recorded with it) and for the tile height it was
+    taken at; None otherwise."""
+    rows = "" if int(tile_rows) == 16 else f"_rows{int(tile_rows)}"
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}_{precision}{rows}.txt")
     try:
         rec = {}
         for line in open(path):
@@ -656,13 +658,15 @@ def profile_record(kernel, workload_name, precision, key):
                 rec[k.strip()] = v.strip()
         if rec.get("source_sha256_16") != bulk_source_hash():
             return None
+        if int(rec.get("tile_rows", "16")) != int(tile_rows):
+            return None
         return float(rec[key])
     except Exception:
         return None
 
 
-def traffic_record(kernel, workload_name, precision):
-    return profile_record(kernel, workload_name, precision, "dram_bytes_per_launch_full_size")
+def traffic_record(kernel, workload_name, precision, tile_rows=16):
+    return profile_record(kernel, workload_name, precision, "dram_bytes_per_launch_full_size", tile_rows)
 
 
 def make_geom(eb, w, h, precision, refs):
@@ -727,16 +731,19 @@ def run_precision(eb, w, h, U, refs, precision, steps, warmup, world, dist, clk=
     fast_bytes = info["fast_cells"] * 10 * es
     hbm, kind = peaks()
     achieved = fast_bytes / (prof[0] * 1e-3) / 1e9
+    rows_now = int(geom.info()["tile_rows"])
     hbm_roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic_record("k_fast_tiled", w.name, precision), "kernel": "k_fast_tiled",
+                "traffic": traffic_record("k_fast_tiled", w.name, precision, rows_now),
+                "kernel": "k_fast_tiled", "tile_rows": rows_now,
                 "algorithmic_bytes_per_launch": fast_bytes, "peak_kind": kind,
                 "warp_instructions_per_fast_cell": profile_record("k_fast_tiled", w.name, precision,
-                                                                  "warp_instructions_per_fast_cell")}
+                                                                  "warp_instructions_per_fast_cell",
+                                                                  rows_now)}
     roof = hbm_roof
     if precision == "mixed":
         # the other tile height, timed the same way: the bulk kernel alone and
         # the whole step (the tuner keeps the faster step)
-        tuned_rows = int(geom.info()["tile_rows"])
+        tuned_rows = rows_now
         other = 14 if tuned_rows == 16 else 16
         eb.set_tile_rows(geom, other)
         alt = []
