@@ -472,6 +472,12 @@ eb_status eb_unet_train_step(eb_unet net, const float *in, const float *target, 
 /* Waits for the device, then frees the network. */
 eb_status eb_unet_destroy(eb_unet net);
 
+/* Waits for the device; EB_ERR_TIMEOUT when a convolution's bounded wait
+ * for its tensor-core products (about one second) expired since the last
+ * check (eb_unet_gradient with a loss or gradient requested and
+ * eb_unet_get_params check too), EB_OK otherwise.  The flag is cleared. */
+eb_status eb_unet_sync_status(eb_unet net);
+
 /* A training sample for the network from the face momenta of U (not
  * modified): in (2*N floats) = [rhs / rms, alpha] with rhs the projection's
  * mean-free right-hand side and rms its RMS over the cells in the solve;

@@ -8,19 +8,21 @@
 // Parameters are one flat vector: per layer, weights [cout][cin][k^3] then
 // biases [cout].  Activations are [channels][nz][ny][nx].
 //
-// Convolutions run on the tensor cores (mma.sync, BF16 operands, FP32
-// accumulation) as implicit GEMMs, with the FP32 activations split into BF16
-// hi + lo so that the products keep FP32-level accuracy: the forward pass
-// (rows = voxels, columns = output channels, K = input channels x taps), the
-// input gradient (the same kernel on the output gradient with the weights
-// transposed and flipped) and the weight gradient (rows = output channels,
-// columns = input channels, K = voxels, per tap; tiles add their sums
-// atomically).
+// Convolutions run on the fifth-generation tensor cores (tcgen05.mma, BF16
+// operands in shared memory, FP32 accumulators in tensor memory) as implicit
+// GEMMs, with FP32 activations and gradients split into BF16 hi + lo so that
+// the products keep FP32-level accuracy: the forward pass and the input
+// gradient (the same convolution on the output gradient with the weights
+// transposed and flipped; rows = voxels, columns = output channels, K =
+// input channels x taps) and the weight gradient (rows = taps x input
+// channels, columns = output channels, K = voxels).
 #include "eb_handle.cuh"
+#include "eb_umma.cuh"
 
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 using namespace ebh;
@@ -45,120 +47,200 @@ struct Vol {
   __host__ __device__ long long n() const { return (long long)nx * ny * nz; }
 };
 
-constexpr int TX = 16, TY = 8, TZ = 2;   // voxel tile of the weight gradient
-constexpr int HXn = TX + 2, HYn = TY + 2, HZn = TZ + 2, HN = HXn * HYn * HZn;
 
 // ---- tensor-core convolution (forward and input gradient) ------------------
-// The same convolution as an implicit GEMM on the tensor cores (mma.sync,
-// BF16 operands, FP32 accumulation): rows = 16 voxels along x (one warp per
-// row; a CTA covers 16 x 8 x 1 voxels), columns = 32 output channels (four
-// 8-wide tiles), K = 16 input channels per tap, 27 taps.  The FP32 inputs
-// are split into BF16 hi + lo (v = hi + lo to about 2^-17 relative) and both
-// parts are multiplied by the BF16 weights, so the products keep FP32-level
-// accuracy.  Shared memory holds the 16-channel halo (channels fastest, a
-// pitch of 24 halfwords: conflict-free 32-bit fragment loads) and the chunk's
-// weights [tap][output channel][input channel].
-constexpr int TC_CH = 16, TC_P = 24, TC_RZ = 2;   // channels per K chunk, channel pitch, z rows per warp
-constexpr int TC_HX = 18, TC_HY = 10, TC_HZ = TC_RZ + 2, TC_HN = TC_HX * TC_HY * TC_HZ;
-template <int NT>
-constexpr size_t tc_smem() {
-  return (size_t)(2 * TC_HN * TC_P + 27 * NT * 8 * TC_P) * sizeof(__nv_bfloat16);
+// The convolution as an implicit GEMM on the fifth-generation tensor cores
+// (tcgen05.mma, BF16 operands, FP32 accumulators in tensor memory).  A CTA
+// owns 8 x 16 voxels (x, y) on TZ consecutive z-levels.  Per z-level the
+// GEMM has M = 128 rows (row m = voxel (m % 8, m / 8) of the tile), N = the
+// output channels (NP: 16 ... 96) and K = the input channels, 16 per chunk;
+// the 27 taps add 27 products into the same accumulator.  Each tap's A
+// operand is read in place from the chunk's halo: the halo holds, per group
+// of 8 channels, one 16-byte row per voxel (x fastest), so the 8 voxels of a
+// core matrix are 8 consecutive rows wherever the tap puts them, the next y
+// row is 10 rows (160 bytes) on and the second group of 8 channels one plane
+// on.  The FP32 inputs are split into BF16 hi + lo (v = hi + lo to about
+// 2^-17 relative) and both parts are multiplied by the BF16 weights, so the
+// products keep FP32-level accuracy.  The weights come prepacked per chunk
+// as [tap][channel group][output channel][8 channels] (k_pack_w), one
+// contiguous copy.  One thread issues the 54 TZ products of a chunk and
+// commits them to an mbarrier; every thread waits (bounded) before the
+// chunk's shared memory is refilled and before the accumulators are read.
+template <int NP, int TZ>
+struct ConvTile {
+  static constexpr int HX = 10, HY = 18, HZ = TZ + 2;   // halo of the 8 x 16 x TZ tile
+  static constexpr int HV = HX * HY * HZ;
+  static constexpr int PLANE = HV * 16;                // bytes of one 8-channel group
+  static constexpr int ACT = 2 * PLANE;                // hi (or lo) of a 16-channel chunk
+  static constexpr int WB = 27 * 2 * NP * 16;          // the chunk's weights
+  static constexpr int SMEM = 2 * ACT + WB;
+  static constexpr int COLS = TZ * NP;
+  static constexpr uint32_t TCOLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
+  static_assert(NP % 16 == 0 && NP >= 16 && NP <= 256, "M = 128 products need N a multiple of 16 up to 256");
+  static_assert(TZ % 2 == 0 && COLS <= 256, "two warp quads share the z-levels; two CTAs per SM share TMEM");
+};
+
+constexpr long long kWaitCycles = 2000000000LL;   // about one second at the maximum SM clock
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-__device__ inline void mma_bf16(float c[4], const unsigned a[4], const unsigned b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// NT 8-wide tiles of output channels per CTA (8 NT channels); a CTA covers
-// 16 x 8 x TC_RZ voxels, warp w the rows y0 + w, z0 .. z0 + TC_RZ - 1
-template <int NT>
-__global__ void __launch_bounds__(256) k_conv3_tc(const float *in, int cin, const __nv_bfloat16 *W, const float *bias,
-                                                  float *out, int cout, Vol V, int relu) {
-  constexpr int NCO = NT * 8;
-  extern __shared__ __align__(16) unsigned char tc_smem[];
-  __nv_bfloat16 *s_hi = reinterpret_cast<__nv_bfloat16 *>(tc_smem);
-  __nv_bfloat16 *s_lo = s_hi + TC_HN * TC_P;
-  __nv_bfloat16 *s_w = s_lo + TC_HN * TC_P;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int ntx = (V.nx + 15) / 16, nty = (V.ny + 7) / 8;
-  const int tile = blockIdx.x;
-  const int x0 = (tile % ntx) * 16, y0 = ((tile / ntx) % nty) * 8, z0 = (tile / (ntx * nty)) * TC_RZ;
-  const int co0 = blockIdx.y * NCO;
+template <int NP, int TZ>
+__global__ void __launch_bounds__(256, 2) k_conv3_umma(const float *in, int cin, const __nv_bfloat16 *Wp,
+                                                       const float *bias, float *out, int cout, Vol V, int relu,
+                                                       int *err) {
+  using G = ConvTile<NP, TZ>;
+  extern __shared__ __align__(16) unsigned char cv_smem[];
+  __shared__ uint32_t tbase;
+  __shared__ __align__(8) uint64_t mbar;
+  unsigned char *s_hi = cv_smem, *s_lo = cv_smem + G::ACT, *s_w = cv_smem + 2 * G::ACT;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntx = (V.nx + 7) / 8, nty = (V.ny + 15) / 16, ntz = (V.nz + TZ - 1) / TZ;
+  const int ntiles = ntx * nty * ntz, nch = (cin + 15) / 16;
   const long long N = V.n();
-  float acc[TC_RZ][NT][4];
+  if (warp == 0) umma::alloc(&tbase, G::TCOLS);
+  if (tid == 0) umma::bar_init(&mbar, 1);
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  const uint32_t tm = tbase;
+  // The CTA walks the (tile, chunk) steps i of its tiles blockIdx.x,
+  // blockIdx.x + gridDim.x, ..., chunks innermost.  A thread owns the halo
+  // items q = tid + 256 k (8 channels of one halo voxel each); their values
+  // for step i + 1 are loaded into registers right after step i's products
+  // are issued and stored (as hi and lo rows) once those products are done.
+  constexpr int ITEMS = 2 * G::HV, IS = (ITEMS + 255) / 256;
+  const int mine = ((int)blockIdx.x < ntiles) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nsteps = mine * nch;
+  float pv[IS][8];
+  auto tile_of = [&](int i) { return (int)blockIdx.x + (i / nch) * (int)gridDim.x; };
+  auto load_step = [&](int i) {
+    const int tile = tile_of(i), c0 = (i % nch) * 16;
+    const int x0 = (tile % ntx) * 8, y0 = ((tile / ntx) % nty) * 16, z0 = (tile / (ntx * nty)) * TZ;
 #pragma unroll
-  for (int rz = 0; rz < TC_RZ; ++rz)
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[rz][nt][e] = 0.f;
-  for (int c0 = 0; c0 < cin; c0 += TC_CH) {
-    __syncthreads();
-    for (int q = threadIdx.x; q < TC_CH * TC_HN; q += blockDim.x) {
-      const int c = q / TC_HN, h = q % TC_HN;
-      const int hx = h % TC_HX, hy = (h / TC_HX) % TC_HY, hz = h / (TC_HX * TC_HY);
+    for (int k = 0; k < IS; ++k) {
+      const int q = tid + 256 * k;
+      const int kg = q / G::HV, h = q - kg * G::HV;
+      const int hx = h % G::HX, hy = (h / G::HX) % G::HY, hz = h / (G::HX * G::HY);
       const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
-      float v = 0.f;
-      if (c0 + c < cin && x >= 0 && x < V.nx && y >= 0 && y < V.ny && z >= 0 && z < V.nz)
-        v = in[(long long)(c0 + c) * N + ((long long)z * V.ny + y) * V.nx + x];
-      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-      s_hi[h * TC_P + c] = hi;
-      s_lo[h * TC_P + c] = __float2bfloat16_rn(v - __bfloat162float(hi));
-    }
-    for (int q = threadIdx.x; q < 27 * NCO * TC_CH; q += blockDim.x) {
-      const int a = q % 27, r = q / 27, c = r % TC_CH, co = r / TC_CH;   // consecutive threads: consecutive taps
-      __nv_bfloat16 w = __float2bfloat16_rn(0.f);
-      if (co0 + co < cout && c0 + c < cin) w = W[((long long)(co0 + co) * cin + c0 + c) * 27 + a];
-      s_w[(a * NCO + co) * TC_P + c] = w;
-    }
-    __syncthreads();
-    for (int a = 0; a < 27; ++a) {
-      const int dz = a / 9, dy = (a / 3) % 3, dx = a % 3;
-      unsigned b[NT][2];
+      const bool inside = q < ITEMS && x >= 0 && x < V.nx && y >= 0 && y < V.ny && z >= 0 && z < V.nz;
+      const float *src = in + ((long long)z * V.ny + y) * V.nx + x;
 #pragma unroll
-      for (int nt = 0; nt < NT; ++nt) {
-        const unsigned *pb = reinterpret_cast<const unsigned *>(s_w + (a * NCO + nt * 8 + g) * TC_P + 2 * t);
-        b[nt][0] = pb[0];
-        b[nt][1] = pb[4];
+      for (int j = 0; j < 8; ++j) {
+        const int c = c0 + kg * 8 + j;
+        pv[k][j] = inside && c < cin ? src[(long long)c * N] : 0.f;
       }
+    }
+  };
+  auto store_step = [&]() {
 #pragma unroll
-      for (int rz = 0; rz < TC_RZ; ++rz) {
-        const int h0 = ((rz + dz) * TC_HY + (warp + dy)) * TC_HX + dx;   // halo voxel of row 0
-        const unsigned *ph = reinterpret_cast<const unsigned *>(s_hi + (h0 + g) * TC_P + 2 * t);
-        const unsigned *ph8 = reinterpret_cast<const unsigned *>(s_hi + (h0 + g + 8) * TC_P + 2 * t);
-        const unsigned *pl = reinterpret_cast<const unsigned *>(s_lo + (h0 + g) * TC_P + 2 * t);
-        const unsigned *pl8 = reinterpret_cast<const unsigned *>(s_lo + (h0 + g + 8) * TC_P + 2 * t);
-        const unsigned ahi[4] = {ph[0], ph8[0], ph[4], ph8[4]};
-        const unsigned alo[4] = {pl[0], pl8[0], pl[4], pl8[4]};
+    for (int k = 0; k < IS; ++k) {
+      const int q = tid + 256 * k;
+      if (q >= ITEMS) break;
+      const int kg = q / G::HV, h = q - kg * G::HV;
+      uint32_t hw[4], lw[4];
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          mma_bf16(acc[rz][nt], ahi, b[nt]);
-          mma_bf16(acc[rz][nt], alo, b[nt]);
+      for (int j = 0; j < 8; j += 2) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(pv[k][j]), h1 = __float2bfloat16_rn(pv[k][j + 1]);
+        hw[j / 2] = pack_bf16(h0, h1);
+        lw[j / 2] = pack_bf16(__float2bfloat16_rn(pv[k][j] - __bfloat162float(h0)),
+                              __float2bfloat16_rn(pv[k][j + 1] - __bfloat162float(h1)));
+      }
+      *reinterpret_cast<uint4 *>(s_hi + kg * G::PLANE + h * 16) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4 *>(s_lo + kg * G::PLANE + h * 16) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+  };
+  // the accumulators of a finished tile: warps w and w + 4 read TMEM lanes
+  // 32 (w % 4) ... (row m = this lane), one half of the z-levels each
+  auto epilogue = [&](int tile) {
+    const int x0 = (tile % ntx) * 8, y0 = ((tile / ntx) % nty) * 16, z0 = (tile / (ntx * nty)) * TZ;
+    const int quad = warp & 3, half = warp >> 2;
+    const int m = 32 * quad + lane;
+    const int x = x0 + (m & 7), y = y0 + (m >> 3);
+    const bool xy = x < V.nx && y < V.ny;
+#pragma unroll
+    for (int r = 0; r < TZ / 2; ++r) {
+      const int rz = half * (TZ / 2) + r, z = z0 + rz;
+      float *dst = out + ((long long)z * V.ny + y) * V.nx + x;
+#pragma unroll
+      for (int cc = 0; cc < NP; cc += 16) {
+        float v[16];
+        umma::ld16(tm + ((uint32_t)(32 * quad) << 16) + (uint32_t)(rz * NP + cc), v);
+        if (xy && z < V.nz) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int co = cc + j;
+            if (co < cout) {
+              float o = v[j] + (bias ? bias[co] : 0.f);
+              if (relu) o = fmaxf(o, 0.f);
+              dst[(long long)co * N] = o;
+            }
+          }
         }
       }
     }
-  }
-  const int y = y0 + warp;
-  if (y >= V.ny) return;
-#pragma unroll
-  for (int rz = 0; rz < TC_RZ; ++rz) {
-    const int z = z0 + rz;
-    if (z >= V.nz) break;
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int x = x0 + g + (e >= 2 ? 8 : 0), co = co0 + nt * 8 + 2 * t + (e & 1);
-        if (x >= V.nx || co >= cout) continue;
-        float r = acc[rz][nt][e] + (bias ? bias[co] : 0.f);
-        if (relu) r = fmaxf(r, 0.f);
-        out[(long long)co * N + ((long long)z * V.ny + y) * V.nx + x] = r;
+  };
+  bool ok = true;
+  int i = 0;
+  if (nsteps > 0) load_step(0);
+  for (; i < nsteps; ++i) {
+    const int ch = i % nch;
+    if (i > 0) {   // step i - 1's products read the buffers refilled below
+      ok = umma::bar_wait(&mbar, (uint32_t)((i - 1) & 1), kWaitCycles);
+      ok = __syncthreads_and(ok) != 0;
+      if (!ok) break;
+      umma::fence_after();
+      if (ch == 0) {   // step i - 1 finished a tile
+        epilogue(tile_of(i - 1));
+        umma::fence_before();
       }
+    }
+    store_step();
+    if (nch > 1 || i == 0) {   // the chunk's weights (once, when there is one chunk)
+      const uint4 *wsrc = reinterpret_cast<const uint4 *>(Wp) + (long long)ch * (G::WB / 16);
+      for (int q = tid; q < G::WB / 16; q += 256) reinterpret_cast<uint4 *>(s_w)[q] = wsrc[q];
+    }
+    umma::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      // the start address sits in the low bits of a descriptor (shared
+      // addresses / 16 < 2^14, so no carry): each tap adds its offset / 16
+      umma::fence_after();
+      constexpr uint32_t idesc = umma::idesc_bf16(128, NP);
+      const uint64_t ahi = umma::sdesc(umma::smem_u32(s_hi), G::PLANE, G::HX * 16);
+      const uint64_t alo = umma::sdesc(umma::smem_u32(s_lo), G::PLANE, G::HX * 16);
+      const uint64_t bw = umma::sdesc(umma::smem_u32(s_w), NP * 16, 128);
+#pragma unroll
+      for (int rz = 0; rz < TZ; ++rz)
+#pragma unroll
+        for (int a = 0; a < 27; ++a) {
+          const int dz = a / 9, dy = (a / 3) % 3, dx = a % 3;
+          const uint64_t off = (uint64_t)(((rz + dz) * G::HY + dy) * G::HX + dx);   // 16-byte rows
+          const uint64_t bo = (uint64_t)(a * 2 * NP);
+          const uint32_t d = tm + (uint32_t)(rz * NP);
+          umma::mma_bf16(d, ahi + off, bw + bo, idesc, (ch > 0 || a > 0) ? 1u : 0u);
+          umma::mma_bf16(d, alo + off, bw + bo, idesc, 1u);
+        }
+      umma::commit(&mbar);
+    }
+    if (i + 1 < nsteps) load_step(i + 1);
   }
+  if (ok && nsteps > 0) {
+    ok = umma::bar_wait(&mbar, (uint32_t)((nsteps - 1) & 1), kWaitCycles);
+    ok = __syncthreads_and(ok) != 0;
+    umma::fence_after();
+    if (ok) epilogue(tile_of(nsteps - 1));
+  }
+  if (!ok) {
+    // the last products may still be running: give them another bounded
+    // wait before the tensor memory is released
+    umma::bar_wait(&mbar, (uint32_t)((i - 1) & 1), kWaitCycles);
+    if (tid == 0) atomicExch(err, 1);
+  }
+  umma::fence_before();
+  __syncthreads();
+  if (warp == 0) umma::dealloc(tm, G::TCOLS);
 }
 
 // 1x1 head: out[v] = b + sum_ci W[ci] in[ci][v]
@@ -195,116 +277,225 @@ __global__ void k_chan_dot(const float *a, const float *b, int C, long long N, f
   }
 }
 
-// W' = transposed and flipped W: W'[ci][co][26 - a] = W[co][ci][a]
-__global__ void k_flip(const __nv_bfloat16 *W, int cout, int cin, __nv_bfloat16 *Wt) {
+// The weights of a convolution prepacked for k_conv3_umma: Wp[chunk][tap]
+// [group][n][j] = the weight from input channel 16 chunk + 8 group + j to
+// output channel n at that tap, zero beyond the channel counts.  flip = 0:
+// the layer itself (n = output channel, W[n][c][a]); flip = 1: its input
+// gradient, the convolution with transposed and flipped weights (n = the
+// layer's input channel, c its output channel: W[c][n][26 - a]).
+__global__ void k_pack_w(const __nv_bfloat16 *W, int cout, int cin, int flip, int NP, __nv_bfloat16 *Wp,
+                         long long total) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= (long long)cout * cin * 27) return;
-  const int a = q % 27, ci = (q / 27) % cin, co = q / (27LL * cin);
-  Wt[((long long)ci * cout + co) * 27 + (26 - a)] = W[q];
+  if (q >= total) return;
+  const int j = (int)(q % 8), n = (int)((q / 8) % NP), kg = (int)((q / (8 * NP)) % 2);
+  const int a = (int)((q / (16LL * NP)) % 27), chunk = (int)(q / (16LL * NP * 27));
+  const int c = chunk * 16 + kg * 8 + j;
+  __nv_bfloat16 w = __float2bfloat16_rn(0.f);
+  if (!flip) {
+    if (n < cout && c < cin) w = W[((long long)n * cin + c) * 27 + a];
+  } else {
+    if (n < cin && c < cout) w = W[((long long)c * cin + n) * 27 + (26 - a)];
+  }
+  Wp[q] = w;
 }
 
-// Weight gradient on the tensor cores: per tap a, dW[co][ci][a] += sum over
-// the tile's voxels of dOut[co][v] in[ci][v + a] -- a GEMM with rows = 16
-// output channels, columns = 16 input channels (two 8-wide tiles), K = the
-// 16 x 8 x 2 voxels of a tile (16 per step, one x-row).  Both operands are
-// split into BF16 hi + lo and multiplied as hi.hi + hi.lo + lo.hi (relative
-// error about 2^-16).  Warp w takes taps w, w + 8, w + 16, w + 24.  The input
-// halo is held twice, the second copy shifted by one voxel along x, so that
-// the voxel pairs of the x-shift dx = 1 start on a 32-bit boundary.  Row
-// pitches (264 and 728 halfwords) keep the fragment loads conflict-free.
-// Each tile adds its sums atomically.
-constexpr int WG_DP = 264, WG_IP = 728, WG_C = 16;
-constexpr size_t WG_SMEM = (size_t)(2 * WG_C * WG_DP + 4 * WG_C * WG_IP) * sizeof(__nv_bfloat16);
+// Weight gradient on the fifth-generation tensor cores.  For a chunk of 16
+// input channels and one tap offset dz, dW[co][ci][a] = sum over voxels v of
+// in[ci][v + a] dout[co][v] is a GEMM with rows m = (dy, dx, ci) (9 x 16 = 144
+// rows, two M = 128 products), columns = the output channels (NP) and K = the
+// voxels, 16 per product (two x-rows of 8).  The halo of a tile of 8 x 8 x 2
+// voxels is held as rows of 8 x-voxels, ordered [z][y][dx copy][channel], the
+// copy dx starting dx - 1 voxels from the tile: along one (z, y) the 48 rows
+// (dx, ci) follow each other and the next y row continues them, so the rows
+// (dy, dx, ci) of every tap of a dz are one run of 16-byte rows at a constant
+// 128-byte stride per 8 rows, and the second x-row of a product is 48 rows
+// (768 bytes) on.  The output gradient is held as rows of 8 x-voxels ordered
+// [z][y][output channel].  Both operands are split into BF16 hi + lo and
+// multiplied as hi.hi + hi.lo + lo.hi (relative error about 2^-16).  A CTA
+// walks tiles blockIdx.x, blockIdx.x + gridDim.x, ..., adds every tile into
+// its tensor-memory accumulators (DZN offsets dz x 2 row blocks x NP
+// columns) and adds them to dW once, atomically, at the end.
+template <int NP>
+struct WgTile {
+  static constexpr int TX = 8, TY = 8, TZ = 2, HY = TY + 2, HZ = TZ + 2, CI = 16;
+  static constexpr int DZN = NP >= 64 ? 1 : 3;         // dz offsets per CTA (tensor-memory columns)
+  static constexpr int ROWS = 9 * CI, NM = 2;          // used rows, M = 128 blocks
+  static constexpr int PAD = NM * 128 - ROWS;          // rows the second block reads past the taps
+  static constexpr int IN_ROWS = HZ * HY * 3 * CI + PAD;
+  static constexpr int IN_B = IN_ROWS * 16;            // hi (or lo) of the input halo
+  static constexpr int DO_B = TZ * TY * NP * 16;       // hi (or lo) of the output gradient
+  static constexpr int SMEM = 2 * IN_B + 2 * DO_B;
+  static constexpr int COLS = DZN * NM * NP;
+  static constexpr uint32_t TCOLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
+  static constexpr int STEPS = TZ * TY / 2;            // K = 16 products per tile
+  static_assert(COLS <= 256, "two CTAs per SM share the tensor memory");
+};
 
-__global__ void __launch_bounds__(256) k_conv3_wgrad_tc(const float *in, int cin, const float *dout, int cout,
-                                                        Vol V, float *dW) {
+template <int NP>
+__global__ void __launch_bounds__(256, 2) k_conv3_wgrad_umma(const float *in, int cin, const float *dout, int cout,
+                                                          Vol V, float *dW, int *err) {
+  using G = WgTile<NP>;
   extern __shared__ __align__(16) unsigned char wg_smem[];
-  __nv_bfloat16 *d_hi = reinterpret_cast<__nv_bfloat16 *>(wg_smem);
-  __nv_bfloat16 *d_lo = d_hi + WG_C * WG_DP;
-  __nv_bfloat16 *i0h = d_lo + WG_C * WG_DP, *i0l = i0h + WG_C * WG_IP;
-  __nv_bfloat16 *i1h = i0l + WG_C * WG_IP, *i1l = i1h + WG_C * WG_IP;
-  const int ntx = (V.nx + TX - 1) / TX, nty = (V.ny + TY - 1) / TY;
-  const int tile = blockIdx.x;
-  const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY, z0 = (tile / (ntx * nty)) * TZ;
-  const int co0 = blockIdx.y * WG_C, ci0 = blockIdx.z * WG_C;
+  __shared__ uint32_t tbase;
+  __shared__ __align__(8) uint64_t mbar;
+  unsigned char *i_hi = wg_smem, *i_lo = wg_smem + G::IN_B;
+  unsigned char *d_hi = wg_smem + 2 * G::IN_B, *d_lo = d_hi + G::DO_B;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntx = (V.nx + G::TX - 1) / G::TX, nty = (V.ny + G::TY - 1) / G::TY, ntz = (V.nz + G::TZ - 1) / G::TZ;
+  const int ntiles = ntx * nty * ntz;
+  const int dz0 = blockIdx.y * G::DZN, c0 = blockIdx.z * G::CI;
   const long long N = V.n();
-  constexpr int NV = TX * TY * TZ;   // 256 voxels
-  for (int q = threadIdx.x; q < WG_C * HN; q += blockDim.x) {
-    const int c = q / HN, h = q % HN;
-    const int hx = h % HXn, hy = (h / HXn) % HYn, hz = h / (HXn * HYn);
-    const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
-    float v = 0.f;
-    if (ci0 + c < cin && x >= 0 && x < V.nx && y >= 0 && y < V.ny && z >= 0 && z < V.nz)
-      v = in[(long long)(ci0 + c) * N + ((long long)z * V.ny + y) * V.nx + x];
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v), lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    i0h[c * WG_IP + h] = hi;
-    i0l[c * WG_IP + h] = lo;
-    if (h >= 1) {   // shifted copy: i1[h - 1] = i0[h]
-      i1h[c * WG_IP + h - 1] = hi;
-      i1l[c * WG_IP + h - 1] = lo;
-    }
-    if (h == HN - 1) {
-      i1h[c * WG_IP + h] = __float2bfloat16_rn(0.f);
-      i1l[c * WG_IP + h] = __float2bfloat16_rn(0.f);
-    }
-  }
-  for (int q = threadIdx.x; q < WG_C * NV; q += blockDim.x) {
-    const int co = q / NV, r = q % NV;
-    const int x = x0 + r % TX, y = y0 + (r / TX) % TY, z = z0 + r / (TX * TY);
-    float v = 0.f;
-    if (co0 + co < cout && x < V.nx && y < V.ny && z < V.nz)
-      v = dout[(long long)(co0 + co) * N + ((long long)z * V.ny + y) * V.nx + x];
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    d_hi[co * WG_DP + r] = hi;
-    d_lo[co * WG_DP + r] = __float2bfloat16_rn(v - __bfloat162float(hi));
-  }
+  if (warp == 0) umma::alloc(&tbase, G::TCOLS);
+  if (tid == 0) umma::bar_init(&mbar, 1);
+  umma::fence_before();
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float acc[4][2][4];
+  umma::fence_after();
+  const uint32_t tm = tbase;
+  // Each thread owns up to IS input rows (q = tid + 256 k) and DS output-
+  // gradient rows of every tile.  Their values are loaded into registers for
+  // the next tile right after the current tile's products are issued, so
+  // that the loads run while the tensor core works; they are converted and
+  // stored once those products have finished reading the buffers.
+  constexpr int IT = G::HZ * G::HY * G::CI, IS = (IT + 255) / 256;
+  constexpr int DI = G::TZ * G::TY * NP, DS = DI / 256;
+  static_assert(DI % 256 == 0, "whole output-gradient rows per thread");
+  float pin[IS][10], pdo[DS][8];
+  auto load_tile = [&](int tile) {
+    const int x0 = (tile % ntx) * G::TX, y0 = ((tile / ntx) % nty) * G::TY, z0 = (tile / (ntx * nty)) * G::TZ;
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+    for (int k = 0; k < IS; ++k) {
+      const int q = tid + 256 * k;
+      const int ci = q % G::CI, hy = (q / G::CI) % G::HY, hz = q / (G::CI * G::HY);
+      const int y = y0 + hy - 1, z = z0 + hz - 1, c = c0 + ci;
+      const bool row = q < IT && c < cin && y >= 0 && y < V.ny && z >= 0 && z < V.nz;
+      const float *src = in + (long long)c * N + ((long long)z * V.ny + y) * V.nx;
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[j][nt][e] = 0.f;
-  auto u32 = [](const __nv_bfloat16 *p) { return *reinterpret_cast<const unsigned *>(p); };
-  for (int row = 0; row < TY * TZ; ++row) {   // K steps: one x-row of 16 voxels each
-    const int ty = row % TY, tz = row / TY, kb = row * TX;
-    const unsigned ahi[4] = {u32(d_hi + g * WG_DP + kb + 2 * t), u32(d_hi + (g + 8) * WG_DP + kb + 2 * t),
-                             u32(d_hi + g * WG_DP + kb + 2 * t + 8), u32(d_hi + (g + 8) * WG_DP + kb + 2 * t + 8)};
-    const unsigned alo[4] = {u32(d_lo + g * WG_DP + kb + 2 * t), u32(d_lo + (g + 8) * WG_DP + kb + 2 * t),
-                             u32(d_lo + g * WG_DP + kb + 2 * t + 8), u32(d_lo + (g + 8) * WG_DP + kb + 2 * t + 8)};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int a = warp + 8 * j;
-      if (a >= 27) break;
-      const int dz = a / 9, dy = (a / 3) % 3, dx = a % 3;
-      const int base = ((tz + dz) * HYn + (ty + dy)) * HXn;
-      const __nv_bfloat16 *bh = dx == 1 ? i1h : i0h, *bl = dx == 1 ? i1l : i0l;
-      const int off = base + 2 * t + (dx == 2 ? 2 : 0);
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        const int ci = nt * 8 + g;
-        const unsigned bhi[2] = {u32(bh + ci * WG_IP + off), u32(bh + ci * WG_IP + off + 8)};
-        const unsigned blo[2] = {u32(bl + ci * WG_IP + off), u32(bl + ci * WG_IP + off + 8)};
-        mma_bf16(acc[j][nt], ahi, bhi);
-        mma_bf16(acc[j][nt], ahi, blo);
-        mma_bf16(acc[j][nt], alo, bhi);
+      for (int e = 0; e < 10; ++e) {
+        const int x = x0 - 1 + e;
+        pin[k][e] = row && x >= 0 && x < V.nx ? src[x] : 0.f;
       }
     }
-  }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int a = warp + 8 * j;
-    if (a >= 27) break;
+    for (int k = 0; k < DS; ++k) {
+      const int q = tid + 256 * k;
+      const int co = q % NP, vy = (q / NP) % G::TY, vz = q / (NP * G::TY);
+      const int y = y0 + vy, z = z0 + vz;
+      const bool row = co < cout && y < V.ny && z < V.nz;
+      const float *src = dout + (long long)co * N + ((long long)z * V.ny + y) * V.nx;
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
+      for (int e = 0; e < 8; ++e) pdo[k][e] = row && x0 + e < V.nx ? src[x0 + e] : 0.f;
+    }
+  };
+  auto store_tile = [&]() {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int co = co0 + g + (e >= 2 ? 8 : 0), ci = ci0 + nt * 8 + 2 * t + (e & 1);
-        if (co < cout && ci < cin) atomicAdd(dW + ((long long)co * cin + ci) * 27 + a, acc[j][nt][e]);
+    for (int k = 0; k < IS; ++k) {
+      const int q = tid + 256 * k;
+      if (q >= IT) break;
+      const int ci = q % G::CI, hzy = q / G::CI;   // hz * HY + hy
+      __nv_bfloat16 h[10], l[10];
+#pragma unroll
+      for (int e = 0; e < 10; ++e) {
+        h[e] = __float2bfloat16_rn(pin[k][e]);
+        l[e] = __float2bfloat16_rn(pin[k][e] - __bfloat162float(h[e]));
       }
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {   // the copy dx starts dx - 1 voxels from the tile
+        const int r = (hzy * 3 + dx) * G::CI + ci;
+        *reinterpret_cast<uint4 *>(i_hi + r * 16) =
+            make_uint4(pack_bf16(h[dx], h[dx + 1]), pack_bf16(h[dx + 2], h[dx + 3]),
+                       pack_bf16(h[dx + 4], h[dx + 5]), pack_bf16(h[dx + 6], h[dx + 7]));
+        *reinterpret_cast<uint4 *>(i_lo + r * 16) =
+            make_uint4(pack_bf16(l[dx], l[dx + 1]), pack_bf16(l[dx + 2], l[dx + 3]),
+                       pack_bf16(l[dx + 4], l[dx + 5]), pack_bf16(l[dx + 6], l[dx + 7]));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < DS; ++k) {
+      const int q = tid + 256 * k;
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(pdo[k][e]), h1 = __float2bfloat16_rn(pdo[k][e + 1]);
+        hw[e / 2] = pack_bf16(h0, h1);
+        lw[e / 2] = pack_bf16(__float2bfloat16_rn(pdo[k][e] - __bfloat162float(h0)),
+                              __float2bfloat16_rn(pdo[k][e + 1] - __bfloat162float(h1)));
+      }
+      *reinterpret_cast<uint4 *>(d_hi + q * 16) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4 *>(d_lo + q * 16) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+  };
+  bool ok = true;
+  int it = 0;
+  if ((int)blockIdx.x < ntiles) load_tile(blockIdx.x);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    if (it > 0) {   // the previous tile's products read the buffers refilled below
+      ok = umma::bar_wait(&mbar, (uint32_t)((it - 1) & 1), kWaitCycles);
+      ok = __syncthreads_and(ok) != 0;
+      if (!ok) break;
+    }
+    store_tile();
+    umma::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      // descriptors advance by their start address / 16 (one 16-byte row)
+      umma::fence_after();
+      constexpr uint32_t idesc = umma::idesc_bf16(128, NP);
+      const uint64_t arow0 = (uint64_t)(dz0 * G::HY * 3 * G::CI);
+      const uint64_t ah = umma::sdesc(umma::smem_u32(i_hi), 3 * G::CI * 16, 128) + arow0;
+      const uint64_t al = umma::sdesc(umma::smem_u32(i_lo), 3 * G::CI * 16, 128) + arow0;
+      const uint64_t bh = umma::sdesc(umma::smem_u32(d_hi), NP * 16, 128);
+      const uint64_t bl = umma::sdesc(umma::smem_u32(d_lo), NP * 16, 128);
+#pragma unroll
+      for (int s = 0; s < G::STEPS; ++s) {
+        const int vz = s / (G::TY / 2), vy = 2 * (s % (G::TY / 2));
+        const uint64_t bo = (uint64_t)((vz * G::TY + vy) * NP);
+#pragma unroll
+        for (int dzi = 0; dzi < G::DZN; ++dzi)
+#pragma unroll
+          for (int j = 0; j < G::NM; ++j) {
+            const uint64_t ao = (uint64_t)(((vz + dzi) * G::HY + vy) * 3 * G::CI + j * 128);
+            const uint32_t d = tm + (uint32_t)((dzi * G::NM + j) * NP);
+            umma::mma_bf16(d, ah + ao, bh + bo, idesc, (it > 0 || s > 0) ? 1u : 0u);
+            umma::mma_bf16(d, ah + ao, bl + bo, idesc, 1u);
+            umma::mma_bf16(d, al + ao, bh + bo, idesc, 1u);
+          }
+      }
+      umma::commit(&mbar);
+    }
+    if (tile + (int)gridDim.x < ntiles) load_tile(tile + gridDim.x);
   }
+  if (ok && it > 0) {
+    ok = umma::bar_wait(&mbar, (uint32_t)((it - 1) & 1), kWaitCycles);
+    ok = __syncthreads_and(ok) != 0;
+  }
+  umma::fence_after();
+  if (ok && it > 0) {
+    // warps w and w + 4 read TMEM lanes 32 (w % 4) ...; the two warp quads
+    // take alternate accumulators
+    const int quad = warp & 3, half = warp >> 2, m = 32 * quad + lane;
+    for (int acc = half; acc < G::DZN * G::NM; acc += 2) {
+      const int dzi = acc / G::NM, j = acc % G::NM, r = j * 128 + m;
+      const int dy = r / (3 * G::CI), dx = (r / G::CI) % 3, ci = c0 + r % G::CI;
+      const bool live = r < G::ROWS && ci < cin;
+      const int a = (dz0 + dzi) * 9 + dy * 3 + dx;
+#pragma unroll
+      for (int cc = 0; cc < NP; cc += 16) {
+        float v[16];
+        umma::ld16(tm + ((uint32_t)(32 * quad) << 16) + (uint32_t)(acc * NP + cc), v);
+        if (live) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (cc + q < cout) atomicAdd(dW + ((long long)(cc + q) * cin + ci) * 27 + a, v[q]);
+        }
+      }
+    }
+  } else if (!ok) {
+    umma::bar_wait(&mbar, (uint32_t)((it - 1) & 1), kWaitCycles);
+    if (tid == 0) atomicExch(err, 1);
+  }
+  umma::fence_before();
+  __syncthreads();
+  if (warp == 0) umma::dealloc(tm, G::TCOLS);
 }
 
 __global__ void k_relu_mask(float *d, const float *post, long long n) {
@@ -407,7 +598,8 @@ struct eb_unet_s {
   Vol V[3];
   long long np = 0;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
-  __nv_bfloat16 *pb = nullptr, *wt = nullptr;   // working weights, transposed scratch
+  __nv_bfloat16 *pb = nullptr, *wp = nullptr;   // working weights, one convolution's packed weights
+  int *err = nullptr;                            // set when a bounded device wait expired
   long long off_w[11], off_b[11];
   // activations (forward) and their gradients
   float *e1a, *e1, *p1, *e2a, *e2, *p2, *ba, *bt, *c2, *d2a, *d2, *c1, *d1a, *d1, *y;
@@ -430,50 +622,82 @@ struct eb_unet_s {
 
 namespace {
 
-// the tensor-core convolution on a volume: 16 x 8 x 4 voxel tiles, 8 NT output
-// channels per CTA with NT = 1, 2 or 4 from the number of output channels
-template <int NT>
-void conv3_tc_nt(const float *in, int cin, const __nv_bfloat16 *W, const float *bias, float *out, int cout,
-                 const Vol &V, bool relu, cudaStream_t s) {
+// packed weights of one convolution: chunks x 27 taps x 2 groups x NP x 8
+long long packed_size(int cin, int cout) { return (long long)((cin + 15) / 16) * 27 * 2 * ((cout + 15) / 16 * 16) * 8; }
+
+template <int NP, int TZ>
+void conv3_umma_launch(const float *in, int cin, const __nv_bfloat16 *Wp, const float *bias, float *out, int cout,
+                       const Vol &V, bool relu, int *err, cudaStream_t s) {
+  using G = ConvTile<NP, TZ>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_conv3_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<NT>());
+    cudaFuncSetAttribute(k_conv3_umma<NP, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     attr = true;
   }
-  const unsigned tiles = (unsigned)(((V.nx + 15) / 16) * ((V.ny + 7) / 8) * ((V.nz + TC_RZ - 1) / TC_RZ));
-  k_conv3_tc<NT><<<dim3(tiles, (cout + NT * 8 - 1) / (NT * 8)), 256, tc_smem<NT>(), s>>>(in, cin, W, bias, out,
-                                                                                        cout, V, relu ? 1 : 0);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sms = std::max(sms, 1);
+  }
+  const int tiles = ((V.nx + 7) / 8) * ((V.ny + 15) / 16) * ((V.nz + TZ - 1) / TZ);
+  const int grid = std::max(1, std::min(tiles, 2 * sms));   // persistent: two CTAs per SM walk the tiles
+  k_conv3_umma<NP, TZ><<<grid, 256, G::SMEM, s>>>(in, cin, Wp, bias, out, cout, V, relu ? 1 : 0, err);
 }
 
-void conv3_tc(const float *in, int cin, const __nv_bfloat16 *W, const float *bias, float *out, int cout,
-              const Vol &V, bool relu, cudaStream_t s) {
-  if (cout <= 8) conv3_tc_nt<1>(in, cin, W, bias, out, cout, V, relu, s);
-  else if (cout <= 16) conv3_tc_nt<2>(in, cin, W, bias, out, cout, V, relu, s);
-  else conv3_tc_nt<4>(in, cin, W, bias, out, cout, V, relu, s);
+// out (cout, V) = conv of in (cin, V) with the weights W [cout][cin][27]
+// (flip = 0) or, for an input gradient, with the layer W [cin][cout][27]
+// transposed and flipped (flip = 1)
+void conv3_tc(eb_unet u, const float *in, int cin, const __nv_bfloat16 *W, int flip, const float *bias, float *out,
+              int cout, const Vol &V, bool relu, cudaStream_t s) {
+  const int NP = (cout + 15) / 16 * 16;
+  const long long np = packed_size(cin, cout);
+  k_pack_w<<<nblk(np), 256, 0, s>>>(W, flip ? cin : cout, flip ? cout : cin, flip, NP, u->wp, np);
+  switch (NP) {
+    case 16: conv3_umma_launch<16, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, s); break;
+    case 32: conv3_umma_launch<32, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, s); break;
+    case 48: conv3_umma_launch<48, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, s); break;
+    case 64: conv3_umma_launch<64, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, s); break;
+    default: conv3_umma_launch<96, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, s); break;
+  }
 }
 
 void conv3(eb_unet u, int l, const float *in, float *out, const Vol &V, bool relu, cudaStream_t s) {
   const LayerSpec &L = kLayers[l];
-  conv3_tc(in, L.cin, u->pb + u->off_w[l], u->p + u->off_b[l], out, L.cout, V, relu, s);
+  conv3_tc(u, in, L.cin, u->pb + u->off_w[l], 0, u->p + u->off_b[l], out, L.cout, V, relu, s);
 }
 
 // input gradient of layer l: din = conv of dout with flipped, transposed W
 void conv3_dgrad(eb_unet u, int l, const float *dout, float *din, const Vol &V, cudaStream_t s) {
   const LayerSpec &L = kLayers[l];
-  k_flip<<<nblk(layer_w(l)), 256, 0, s>>>(u->pb + u->off_w[l], L.cout, L.cin, u->wt);
-  conv3_tc(dout, L.cout, u->wt, nullptr, din, L.cin, V, false, s);
+  conv3_tc(u, dout, L.cout, u->pb + u->off_w[l], 1, nullptr, din, L.cin, V, false, s);
+}
+
+template <int NP>
+void conv3_wgrad_launch(const float *in, int cin, const float *dout, int cout, const Vol &V, float *dW, int *err,
+                        cudaStream_t s) {
+  using G = WgTile<NP>;
+  static int sms = 0;
+  if (!sms) {
+    cudaFuncSetAttribute(k_conv3_wgrad_umma<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sms = std::max(sms, 1);
+  }
+  const int ntiles = ((V.nx + G::TX - 1) / G::TX) * ((V.ny + G::TY - 1) / G::TY) * ((V.nz + G::TZ - 1) / G::TZ);
+  const int gy = 3 / G::DZN, gz = (cin + G::CI - 1) / G::CI;
+  const int gx = std::max(1, std::min(ntiles, 2 * sms / (gy * gz)));   // two CTAs per SM, each over many tiles
+  k_conv3_wgrad_umma<NP><<<dim3(gx, gy, gz), 256, G::SMEM, s>>>(in, cin, dout, cout, V, dW, err);
 }
 
 void conv3_wgrad(eb_unet u, int l, const float *in, const float *dout, const Vol &V, cudaStream_t s) {
   const LayerSpec &L = kLayers[l];
-  const unsigned tiles = (unsigned)(((V.nx + TX - 1) / TX) * ((V.ny + TY - 1) / TY) * ((V.nz + TZ - 1) / TZ));
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_conv3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WG_SMEM);
-    attr = true;
-  }
-  k_conv3_wgrad_tc<<<dim3(tiles, (L.cout + WG_C - 1) / WG_C, (L.cin + WG_C - 1) / WG_C), 256, WG_SMEM, s>>>(
-      in, L.cin, dout, L.cout, V, u->g + u->off_w[l]);
+  float *dW = u->g + u->off_w[l];
+  if (L.cout <= 16) conv3_wgrad_launch<16>(in, L.cin, dout, L.cout, V, dW, u->err, s);
+  else if (L.cout <= 32) conv3_wgrad_launch<32>(in, L.cin, dout, L.cout, V, dW, u->err, s);
+  else conv3_wgrad_launch<64>(in, L.cin, dout, L.cout, V, dW, u->err, s);
   k_chan_dot<<<dim3(64, L.cout), 256, 0, s>>>(dout, nullptr, L.cout, V.n(), u->g + u->off_b[l]);
 }
 
@@ -581,11 +805,27 @@ eb_status loss_and_backward(eb_unet u, const float *x, const float *target, cons
   return EB_OK;
 }
 
+// after the device has finished: EB_ERR_TIMEOUT (and the flag cleared) when
+// a convolution gave up waiting for its tensor-core products
+eb_status take_error(eb_unet u) {
+  int h = 0;
+  CUDA_TRY(cudaMemcpy(&h, u->err, sizeof(int), cudaMemcpyDeviceToHost), "network status");
+  if (!h) return EB_OK;
+  CUDA_TRY(cudaMemset(u->err, 0, sizeof(int)), "network status");
+  return fail(EB_ERR_TIMEOUT, "a convolution's bounded wait for its tensor-core products expired");
+}
+
 }  // namespace
 
 extern "C" {
 
 int64_t eb_unet_num_params(void) { return total_params(); }
+
+eb_status eb_unet_sync_status(eb_unet u) {
+  if (!u) return fail(EB_ERR_INVALID_ARG, "NULL network");
+  CUDA_TRY(cudaDeviceSynchronize(), "network status");
+  return take_error(u);
+}
 
 eb_status eb_unet_create(int nx, int ny, int nz, eb_unet *out) {
   if (!out) return fail(EB_ERR_INVALID_ARG, "out is NULL");
@@ -598,13 +838,15 @@ eb_status eb_unet_create(int nx, int ny, int nz, eb_unet *out) {
   u->V[2] = {nx / 4, ny / 4, nz / 4};
   u->np = total_params();
   long long o = 0;
-  long long wmax = 0;
+  long long wpmax = 0;
   for (int l = 0; l < 11; ++l) {
     u->off_w[l] = o;
     o += layer_w(l);
     u->off_b[l] = o;
     o += kLayers[l].cout;
-    wmax = std::max(wmax, layer_w(l));
+    if (kLayers[l].k == 3)
+      wpmax = std::max({wpmax, packed_size(kLayers[l].cin, kLayers[l].cout),
+                        packed_size(kLayers[l].cout, kLayers[l].cin)});
   }
   const long long n0 = u->V[0].n(), n1 = u->V[1].n(), n2 = u->V[2].n();
   struct {
@@ -618,7 +860,9 @@ eb_status eb_unet_create(int nx, int ny, int nz, eb_unet *out) {
     if (e == cudaSuccess) e = u->alloc(x.q, x.n);
   if (e == cudaSuccess) e = u->alloc(&u->p, u->np);
   if (e == cudaSuccess) e = u->alloc(&u->pb, u->np);
-  if (e == cudaSuccess) e = u->alloc(&u->wt, wmax);
+  if (e == cudaSuccess) e = u->alloc(&u->wp, wpmax);
+  if (e == cudaSuccess) e = u->alloc(&u->err, 1);
+  if (e == cudaSuccess) e = cudaMemset(u->err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(u->p, 0, sizeof(float) * u->np);
   if (e == cudaSuccess) e = cudaMemset(u->pb, 0, sizeof(__nv_bfloat16) * u->np);
   if (e != cudaSuccess) {
@@ -657,7 +901,7 @@ eb_status eb_unet_get_params(eb_unet u, float *host, int64_t n) {
   if (!u || !host) return fail(EB_ERR_INVALID_ARG, "NULL network or parameters");
   if (n != u->np) return fail(EB_ERR_INVALID_ARG, "wrong parameter count");
   CUDA_TRY(cudaMemcpy(host, u->p, sizeof(float) * n, cudaMemcpyDeviceToHost), "get parameters");
-  return EB_OK;
+  return take_error(u);
 }
 
 eb_status eb_unet_forward(eb_unet u, const float *in, float *out, void *stream) {
@@ -680,6 +924,7 @@ eb_status eb_unet_gradient(eb_unet u, const float *in, const float *target, cons
     CUDA_TRY(cudaStreamSynchronize(s), "gradient");
   }
   CUDA_TRY(cudaGetLastError(), "network gradient");
+  if (loss || grad_host) return take_error(u);
   return EB_OK;
 }
 

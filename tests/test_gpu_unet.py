@@ -167,3 +167,28 @@ def test_trained_network_saves_iterations(eb):
         g.close()
     assert np.mean(warm_l) < np.mean(cold_l), (cold_l, warm_l)
     assert np.mean(warm_t) <= np.mean(cold_t) + 5, (cold_t, warm_t)
+
+
+def test_many_tiles_per_cta_match_oracle(eb, un):
+    """A 64 x 64 x 32 grid: the persistent convolution kernels then walk
+    several tiles per CTA (the forward 512 tiles of 8 x 16 x 2 voxels over
+    at most two CTAs per SM; the weight gradient 1024 tiles of 8 x 8 x 2 over
+    about 100 to 300 CTAs per layer), carrying halo prefetches and tensor-
+    memory accumulators from tile to tile.  Forward pass and gradient against
+    the oracle with the tolerances above."""
+    shape = (32, 64, 64)
+    p, x, t, mask = _problem(un, shape, 4)
+    net = eb.UNet(shape[2], shape[1], shape[0])
+    net.set_params(p)
+    xs = torch.from_numpy(x).float().cuda()
+    y = net.forward(xs).double().cpu().numpy()
+    pw = bf16_weights(un, p)
+    want, a = un.forward(pw, x.astype(np.float32).astype(np.float64))
+    assert np.max(np.abs(y - want[0])) <= 1e-4 * np.max(np.abs(want))
+    loss, g = net.gradient(xs, torch.from_numpy(t[0]).float().cuda(), torch.from_numpy(mask[0]).float().cuda())
+    L, dy = un.loss(want, t.astype(np.float32).astype(np.float64), mask)
+    gw, _ = un.backward(pw, a, dy)
+    assert abs(loss - L) <= 1e-4 * L
+    assert np.linalg.norm(g - gw) <= 1e-3 * np.linalg.norm(gw)
+    net.sync_status()
+    net.close()
