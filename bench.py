@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--terrains", type=int, default=250,
                     help="warmstart: training terrains (8 samples each; 250 gives the 2000 training fields)")
     ap.add_argument("--epochs", type=int, default=12, help="warmstart: training epochs")
-    ap.add_argument("--workload", choices=("hill256", "grf512", "ensemble", "anelastic", "warmstart", "slabs"),
+    ap.add_argument("--workload", choices=("hill256", "grf512", "ensemble", "anelastic", "warmstart", "slabs",
+                                           "network"),
                     default="hill256",
                     help="ensemble: 64 uneven Gaussian-hill instances advanced together (mixed path); "
                          "anelastic: 192x192x96 random terrain, anelastic steps with the projection; "
@@ -441,6 +442,59 @@ def restriction_cost(eb, dist, warmup, steps):
             "restrict_gbs": gbs, "restrict_hbm_frac": gbs / hbm, "algorithmic_bytes": fine_bytes + coarse_bytes}
 
 
+def unet_cost(eb, warmup, steps=10):
+    """The warm-start network's kernels on the 96x96x48 grid of its training
+    samples, with seeded random parameters, inputs and targets: one forward
+    pass and one training step (forward, input and weight gradients, Adam),
+    timed with CUDA events.  The arithmetic counts 2 cin cout 27 per voxel and
+    convolution pass (three passes per step); the BF16 hi + lo split of the
+    FP32 activations doubles the tensor-core products and is not counted.
+    Against the measured BF16 tensor peak (burst: the kernels are timed
+    alone)."""
+    import torch
+    from paper_2604_11959_gb300 import warmstart as ws
+    nx, ny, nz = 96, 96, 48
+    net = eb.UNet(nx, ny, nz)
+    net.set_params(ws.init_params(11))
+    rng = np.random.default_rng(12)
+    x = torch.from_numpy(rng.standard_normal((2, nz, ny, nx)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal((nz, ny, nx)).astype(np.float32)).cuda()
+    m = torch.ones((nz, ny, nx), dtype=torch.float32, device="cuda")
+    out = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        for _ in range(max(3, warmup)):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    f_ms = timed(lambda: net.forward(x, out))
+    s_ms = timed(lambda: net.train_step(x, t, m, 1e-6))
+    net.sync_status()
+    net.close()
+    vox = nx * ny * nz
+    fwd = sum(2 * ci * co * k ** 3 * vox / 8 ** lv for (ci, co, k), lv in
+              zip(ws.LAYERS, (0, 0, 1, 1, 2, 2, 1, 1, 0, 0, 0)))
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, kind = float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    return {"workload": "warm-start network 96x96x48 (16/32/64 channels)", "forward_ms": f_ms,
+            "forward_tflops": fwd / (f_ms * 1e-3) / 1e12, "train_step_ms": s_ms,
+            "train_step_tflops": 3 * fwd / (s_ms * 1e-3) / 1e12,
+            "bf16_peak_tflops": peak, "peak_kind": kind,
+            "forward_frac": fwd / (f_ms * 1e-3) / 1e12 / peak,
+            "train_step_frac": 3 * fwd / (s_ms * 1e-3) / 1e12 / peak,
+            "kernels": "tcgen05.mma implicit GEMMs, FP32 activations as BF16 hi + lo, TMEM accumulators"}
+
+
 def other_configs(eb, world, dist, warmup, steps=10):
     """The other timed configurations, measured in the default run beside
     the headline: the 512x512x256 random terrain (mixed path, tuned, per-step
@@ -459,6 +513,8 @@ def other_configs(eb, world, dist, warmup, steps=10):
                       "tuned_slab_levels": r["tuned_slab_levels"], "bulk_high_priority": r["bulk_high_priority"]}}
     out["hill256_compressible"] = compressible_cost(eb, world, dist, warmup, steps)
     out["hill256_restriction"] = restriction_cost(eb, dist, warmup, steps)
+    out["warmstart_network"] = unet_cost(eb, warmup, steps)
+    torch.cuda.empty_cache()
     e = run_ensemble(eb, steps, warmup, None, dist)
     torch.cuda.empty_cache()
     out["ensemble"] = {"workload": "ensemble-64-gaussian-hills", "cells": e["cells"], "value": e["value"] * world,
@@ -972,6 +1028,16 @@ def run_arm(args, rank, world, w, dist):
             print(json.dumps({"workload": "warmstart", "metric": "PCG iterations to relative residual 1e-10, "
                               "zero start / network start", "value": r["grf192"]["ratio"], "unit": "x",
                               "higher_is_better": True, "data": "synthetic", **r}))
+        return 0
+    if args.workload == "network":
+        from paper_2604_11959_gb300 import build as libbuild, eb
+        libbuild.build()
+        eb.load()
+        r = unet_cost(eb, args.warmup, args.steps)
+        if rank == 0:
+            print(json.dumps({"metric": "warm-start network training step, useful TFLOP/s", "unit": "TFLOP/s",
+                              "value": r["train_step_tflops"], "higher_is_better": True, "data": "synthetic",
+                              "steps": args.steps, "warmup": max(3, args.warmup), **r}))
         return 0
     if args.workload == "anelastic":
         from paper_2604_11959_gb300 import build as libbuild, eb

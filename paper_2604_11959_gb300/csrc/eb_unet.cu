@@ -503,50 +503,56 @@ __global__ void k_relu_mask(float *d, const float *post, long long n) {
   if (q < n && !(post[q] > 0.f)) d[q] = 0.f;
 }
 
+// The pooling and upsampling kernels take one channel per blockIdx.y and a
+// voxel of it per thread, with 32-bit index arithmetic (a network's volumes
+// hold fewer than 2^31 values per channel; eb_unet_create checks).
+
 // 2x2x2 average pool: out (C, V/2) from in (C, V)
-__global__ void k_pool(const float *in, Vol V, int C, float *out) {
-  const Vol H{V.nx / 2, V.ny / 2, V.nz / 2};
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= (long long)C * H.n()) return;
-  const long long c = q / H.n(), r = q % H.n();
-  const int x = r % H.nx, y = (r / H.nx) % H.ny, z = r / ((long long)H.nx * H.ny);
+__global__ void k_pool(const float *in, Vol V, float *out) {
+  const unsigned hx = V.nx / 2, hy = V.ny / 2, hn = hx * hy * (unsigned)(V.nz / 2);
+  const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= hn) return;
+  const unsigned x = r % hx, t = r / hx, y = t % hy, z = t / hy;
+  const unsigned nx = V.nx, nxy = nx * V.ny;
+  const float *src = in + (size_t)blockIdx.y * nxy * V.nz + (2 * z) * nxy + (2 * y) * nx + 2 * x;
   float s = 0.f;
-  for (int a = 0; a < 8; ++a)
-    s += in[c * V.n() + ((long long)(2 * z + (a >> 2)) * V.ny + 2 * y + ((a >> 1) & 1)) * V.nx + 2 * x + (a & 1)];
-  out[q] = s * 0.125f;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) s += src[(a >> 2) * nxy + ((a >> 1) & 1) * nx + (a & 1)];
+  out[(size_t)blockIdx.y * hn + r] = s * 0.125f;
 }
 
 // din (C, V) += pool backward of dout (C, V/2)
-__global__ void k_pool_bwd_add(const float *dout, Vol V, int C, float *din) {
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= (long long)C * V.n()) return;
-  const long long c = q / V.n(), r = q % V.n();
-  const int x = r % V.nx, y = (r / V.nx) % V.ny, z = r / ((long long)V.nx * V.ny);
-  const Vol H{V.nx / 2, V.ny / 2, V.nz / 2};
-  din[q] += 0.125f * dout[c * H.n() + ((long long)(z / 2) * H.ny + y / 2) * H.nx + x / 2];
+__global__ void k_pool_bwd_add(const float *dout, Vol V, float *din) {
+  const unsigned n = (unsigned)V.nx * V.ny * V.nz;
+  const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const unsigned x = r % V.nx, t = r / V.nx, y = t % V.ny, z = t / V.ny;
+  const unsigned hx = V.nx / 2, hy = V.ny / 2, hn = hx * hy * (unsigned)(V.nz / 2);
+  din[(size_t)blockIdx.y * n + r] += 0.125f * dout[(size_t)blockIdx.y * hn + ((z / 2) * hy + y / 2) * hx + x / 2];
 }
 
-// out (C, V) = nearest upsampling of in (C, V/2), written at channel offset
-__global__ void k_up(const float *in, Vol V, int C, float *out) {
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= (long long)C * V.n()) return;
-  const long long c = q / V.n(), r = q % V.n();
-  const int x = r % V.nx, y = (r / V.nx) % V.ny, z = r / ((long long)V.nx * V.ny);
-  const Vol H{V.nx / 2, V.ny / 2, V.nz / 2};
-  out[q] = in[c * H.n() + ((long long)(z / 2) * H.ny + y / 2) * H.nx + x / 2];
+// out (C, V) = nearest upsampling of in (C, V/2)
+__global__ void k_up(const float *in, Vol V, float *out) {
+  const unsigned n = (unsigned)V.nx * V.ny * V.nz;
+  const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const unsigned x = r % V.nx, t = r / V.nx, y = t % V.ny, z = t / V.ny;
+  const unsigned hx = V.nx / 2, hy = V.ny / 2, hn = hx * hy * (unsigned)(V.nz / 2);
+  out[(size_t)blockIdx.y * n + r] = in[(size_t)blockIdx.y * hn + ((z / 2) * hy + y / 2) * hx + x / 2];
 }
 
 // din (C, V/2) = upsampling backward of dout (C, V): sum of the 8 children
-__global__ void k_up_bwd(const float *dout, Vol V, int C, float *din) {
-  const Vol H{V.nx / 2, V.ny / 2, V.nz / 2};
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= (long long)C * H.n()) return;
-  const long long c = q / H.n(), r = q % H.n();
-  const int x = r % H.nx, y = (r / H.nx) % H.ny, z = r / ((long long)H.nx * H.ny);
+__global__ void k_up_bwd(const float *dout, Vol V, float *din) {
+  const unsigned hx = V.nx / 2, hy = V.ny / 2, hn = hx * hy * (unsigned)(V.nz / 2);
+  const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= hn) return;
+  const unsigned x = r % hx, t = r / hx, y = t % hy, z = t / hy;
+  const unsigned nx = V.nx, nxy = nx * V.ny;
+  const float *src = dout + (size_t)blockIdx.y * nxy * V.nz + (2 * z) * nxy + (2 * y) * nx + 2 * x;
   float s = 0.f;
-  for (int a = 0; a < 8; ++a)
-    s += dout[c * V.n() + ((long long)(2 * z + (a >> 2)) * V.ny + 2 * y + ((a >> 1) & 1)) * V.nx + 2 * x + (a & 1)];
-  din[q] = s;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) s += src[(a >> 2) * nxy + ((a >> 1) & 1) * nx + (a & 1)];
+  din[(size_t)blockIdx.y * hn + r] = s;
 }
 
 // masked half mean-square loss: dy = mask (y - t) / sum(mask); loss sums
@@ -705,17 +711,17 @@ void forward(eb_unet u, const float *x, cudaStream_t s) {
   const Vol &V0 = u->V[0], &V1 = u->V[1], &V2 = u->V[2];
   conv3(u, 0, x, u->e1a, V0, true, s);
   conv3(u, 1, u->e1a, u->e1, V0, true, s);
-  k_pool<<<nblk(16 * V1.n()), 256, 0, s>>>(u->e1, V0, 16, u->p1);
+  k_pool<<<dim3(nblk(V1.n()), 16), 256, 0, s>>>(u->e1, V0, u->p1);
   conv3(u, 2, u->p1, u->e2a, V1, true, s);
   conv3(u, 3, u->e2a, u->e2, V1, true, s);
-  k_pool<<<nblk(32 * V2.n()), 256, 0, s>>>(u->e2, V1, 32, u->p2);
+  k_pool<<<dim3(nblk(V2.n()), 32), 256, 0, s>>>(u->e2, V1, u->p2);
   conv3(u, 4, u->p2, u->ba, V2, true, s);
   conv3(u, 5, u->ba, u->bt, V2, true, s);
-  k_up<<<nblk(64 * V1.n()), 256, 0, s>>>(u->bt, V1, 64, u->c2);
+  k_up<<<dim3(nblk(V1.n()), 64), 256, 0, s>>>(u->bt, V1, u->c2);
   cudaMemcpyAsync(u->c2 + 64 * V1.n(), u->e2, sizeof(float) * 32 * V1.n(), cudaMemcpyDeviceToDevice, s);
   conv3(u, 6, u->c2, u->d2a, V1, true, s);
   conv3(u, 7, u->d2a, u->d2, V1, true, s);
-  k_up<<<nblk(32 * V0.n()), 256, 0, s>>>(u->d2, V0, 32, u->c1);
+  k_up<<<dim3(nblk(V0.n()), 32), 256, 0, s>>>(u->d2, V0, u->c1);
   cudaMemcpyAsync(u->c1 + 32 * V0.n(), u->e1, sizeof(float) * 16 * V0.n(), cudaMemcpyDeviceToDevice, s);
   conv3(u, 8, u->c1, u->d1a, V0, true, s);
   conv3(u, 9, u->d1a, u->d1, V0, true, s);
@@ -737,7 +743,7 @@ void backward(eb_unet u, const float *x, cudaStream_t s) {
   k_relu_mask<<<nblk(16 * n0), 256, 0, s>>>(u->gd1a, u->d1a, 16 * n0);
   conv3_wgrad(u, 8, u->c1, u->gd1a, V0, s);
   conv3_dgrad(u, 8, u->gd1a, u->gc1, V0, s);
-  k_up_bwd<<<nblk(32 * n1), 256, 0, s>>>(u->gc1, V0, 32, u->gd2);
+  k_up_bwd<<<dim3(nblk(n1), 32), 256, 0, s>>>(u->gc1, V0, u->gd2);
   cudaMemcpyAsync(u->ge1, u->gc1 + 32 * n0, sizeof(float) * 16 * n0, cudaMemcpyDeviceToDevice, s);
   k_relu_mask<<<nblk(32 * n1), 256, 0, s>>>(u->gd2, u->d2, 32 * n1);
   conv3_wgrad(u, 7, u->d2a, u->gd2, V1, s);
@@ -745,7 +751,7 @@ void backward(eb_unet u, const float *x, cudaStream_t s) {
   k_relu_mask<<<nblk(32 * n1), 256, 0, s>>>(u->gd2a, u->d2a, 32 * n1);
   conv3_wgrad(u, 6, u->c2, u->gd2a, V1, s);
   conv3_dgrad(u, 6, u->gd2a, u->gc2, V1, s);
-  k_up_bwd<<<nblk(64 * n2), 256, 0, s>>>(u->gc2, V1, 64, u->gbt);
+  k_up_bwd<<<dim3(nblk(n2), 64), 256, 0, s>>>(u->gc2, V1, u->gbt);
   cudaMemcpyAsync(u->ge2, u->gc2 + 64 * n1, sizeof(float) * 32 * n1, cudaMemcpyDeviceToDevice, s);
   k_relu_mask<<<nblk(64 * n2), 256, 0, s>>>(u->gbt, u->bt, 64 * n2);
   conv3_wgrad(u, 5, u->ba, u->gbt, V2, s);
@@ -753,14 +759,14 @@ void backward(eb_unet u, const float *x, cudaStream_t s) {
   k_relu_mask<<<nblk(64 * n2), 256, 0, s>>>(u->gba, u->ba, 64 * n2);
   conv3_wgrad(u, 4, u->p2, u->gba, V2, s);
   conv3_dgrad(u, 4, u->gba, u->gp2, V2, s);
-  k_pool_bwd_add<<<nblk(32 * n1), 256, 0, s>>>(u->gp2, V1, 32, u->ge2);
+  k_pool_bwd_add<<<dim3(nblk(n1), 32), 256, 0, s>>>(u->gp2, V1, u->ge2);
   k_relu_mask<<<nblk(32 * n1), 256, 0, s>>>(u->ge2, u->e2, 32 * n1);
   conv3_wgrad(u, 3, u->e2a, u->ge2, V1, s);
   conv3_dgrad(u, 3, u->ge2, u->ge2a, V1, s);
   k_relu_mask<<<nblk(32 * n1), 256, 0, s>>>(u->ge2a, u->e2a, 32 * n1);
   conv3_wgrad(u, 2, u->p1, u->ge2a, V1, s);
   conv3_dgrad(u, 2, u->ge2a, u->gp1, V1, s);
-  k_pool_bwd_add<<<nblk(16 * n0), 256, 0, s>>>(u->gp1, V0, 16, u->ge1);
+  k_pool_bwd_add<<<dim3(nblk(n0), 16), 256, 0, s>>>(u->gp1, V0, u->ge1);
   k_relu_mask<<<nblk(16 * n0), 256, 0, s>>>(u->ge1, u->e1, 16 * n0);
   conv3_wgrad(u, 1, u->e1a, u->ge1, V0, s);
   conv3_dgrad(u, 1, u->ge1, u->ge1a, V0, s);
@@ -832,6 +838,7 @@ eb_status eb_unet_create(int nx, int ny, int nz, eb_unet *out) {
   *out = nullptr;
   if (nx < 4 || ny < 4 || nz < 4 || nx % 4 || ny % 4 || nz % 4)
     return fail(EB_ERR_INVALID_ARG, "nx, ny, nz must be multiples of 4 (two 2x poolings), at least 4");
+  if ((long long)nx * ny * nz >= (1LL << 31)) return fail(EB_ERR_INVALID_ARG, "grid too large: 2^31 voxels or more");
   eb_unet u = new eb_unet_s();
   u->V[0] = {nx, ny, nz};
   u->V[1] = {nx / 2, ny / 2, nz / 2};
