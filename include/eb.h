@@ -478,6 +478,14 @@ eb_status eb_unet_destroy(eb_unet net);
  * eb_unet_get_params check too), EB_OK otherwise.  The flag is cleared. */
 eb_status eb_unet_sync_status(eb_unet net);
 
+/* Failure test of the bounded waits (no counterpart in the paper): the next
+ * convolution launch of this network issues its first products without
+ * signalling their completion, so every CTA's wait runs out (about one
+ * second, twice), the CTAs release their tensor memory and return, the
+ * launch's output is left unwritten, and the next eb_unet_sync_status
+ * reports EB_ERR_TIMEOUT.  Later launches are normal. */
+eb_status eb_unet_inject_wait_fault(eb_unet net);
+
 /* A training sample for the network from the face momenta of U (not
  * modified): in (2*N floats) = [rhs / rms, alpha] with rhs the projection's
  * mean-free right-hand side and rms its RMS over the cells in the solve;

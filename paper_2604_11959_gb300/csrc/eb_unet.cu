@@ -89,7 +89,7 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) 
 template <int NP, int TZ>
 __global__ void __launch_bounds__(256, 2) k_conv3_umma(const float *in, int cin, const __nv_bfloat16 *Wp,
                                                        const float *bias, float *out, int cout, Vol V, int relu,
-                                                       int *err) {
+                                                       int *err, int skip_commit) {
   using G = ConvTile<NP, TZ>;
   extern __shared__ __align__(16) unsigned char cv_smem[];
   __shared__ uint32_t tbase;
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256, 2) k_conv3_umma(const float *in, int cin,
           umma::mma_bf16(d, ahi + off, bw + bo, idesc, (ch > 0 || a > 0) ? 1u : 0u);
           umma::mma_bf16(d, alo + off, bw + bo, idesc, 1u);
         }
-      umma::commit(&mbar);
+      if (!(skip_commit && i == 0)) umma::commit(&mbar);   // skipped only by the failure test
     }
     if (i + 1 < nsteps) load_step(i + 1);
   }
@@ -606,6 +606,7 @@ struct eb_unet_s {
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   __nv_bfloat16 *pb = nullptr, *wp = nullptr;   // working weights, one convolution's packed weights
   int *err = nullptr;                            // set when a bounded device wait expired
+  int fault = 0;                                 // failure test: the next convolution skips its commit
   long long off_w[11], off_b[11];
   // activations (forward) and their gradients
   float *e1a, *e1, *p1, *e2a, *e2, *p2, *ba, *bt, *c2, *d2a, *d2, *c1, *d1a, *d1, *y;
@@ -633,7 +634,7 @@ long long packed_size(int cin, int cout) { return (long long)((cin + 15) / 16) *
 
 template <int NP, int TZ>
 void conv3_umma_launch(const float *in, int cin, const __nv_bfloat16 *Wp, const float *bias, float *out, int cout,
-                       const Vol &V, bool relu, int *err, cudaStream_t s) {
+                       const Vol &V, bool relu, int *err, int skip_commit, cudaStream_t s) {
   using G = ConvTile<NP, TZ>;
   static bool attr = false;
   if (!attr) {
@@ -649,7 +650,7 @@ void conv3_umma_launch(const float *in, int cin, const __nv_bfloat16 *Wp, const 
   }
   const int tiles = ((V.nx + 7) / 8) * ((V.ny + 15) / 16) * ((V.nz + TZ - 1) / TZ);
   const int grid = std::max(1, std::min(tiles, 2 * sms));   // persistent: two CTAs per SM walk the tiles
-  k_conv3_umma<NP, TZ><<<grid, 256, G::SMEM, s>>>(in, cin, Wp, bias, out, cout, V, relu ? 1 : 0, err);
+  k_conv3_umma<NP, TZ><<<grid, 256, G::SMEM, s>>>(in, cin, Wp, bias, out, cout, V, relu ? 1 : 0, err, skip_commit);
 }
 
 // out (cout, V) = conv of in (cin, V) with the weights W [cout][cin][27]
@@ -660,12 +661,14 @@ void conv3_tc(eb_unet u, const float *in, int cin, const __nv_bfloat16 *W, int f
   const int NP = (cout + 15) / 16 * 16;
   const long long np = packed_size(cin, cout);
   k_pack_w<<<nblk(np), 256, 0, s>>>(W, flip ? cin : cout, flip ? cout : cin, flip, NP, u->wp, np);
+  const int skip = u->fault;   // the failure test: one launch never signals its products' completion
+  u->fault = 0;
   switch (NP) {
-    case 16: conv3_umma_launch<16, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, s); break;
-    case 32: conv3_umma_launch<32, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, s); break;
-    case 48: conv3_umma_launch<48, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, s); break;
-    case 64: conv3_umma_launch<64, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, s); break;
-    default: conv3_umma_launch<96, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, s); break;
+    case 16: conv3_umma_launch<16, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, skip, s); break;
+    case 32: conv3_umma_launch<32, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, skip, s); break;
+    case 48: conv3_umma_launch<48, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, skip, s); break;
+    case 64: conv3_umma_launch<64, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, skip, s); break;
+    default: conv3_umma_launch<96, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, skip, s); break;
   }
 }
 
@@ -826,6 +829,12 @@ eb_status take_error(eb_unet u) {
 extern "C" {
 
 int64_t eb_unet_num_params(void) { return total_params(); }
+
+eb_status eb_unet_inject_wait_fault(eb_unet u) {
+  if (!u) return fail(EB_ERR_INVALID_ARG, "NULL network");
+  u->fault = 1;
+  return EB_OK;
+}
 
 eb_status eb_unet_sync_status(eb_unet u) {
   if (!u) return fail(EB_ERR_INVALID_ARG, "NULL network");

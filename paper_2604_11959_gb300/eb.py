@@ -31,7 +31,8 @@ EXPORTED_SYMBOLS = ("eb_geom_build", "eb_geom_destroy", "eb_geom_info", "eb_geom
                     "eb_ensemble_tune", "eb_ensemble_destroy", "eb_project", "eb_anelastic_step",
                     "eb_unet_num_params", "eb_unet_create", "eb_unet_set_params", "eb_unet_get_params",
                     "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step", "eb_unet_destroy",
-                    "eb_unet_sync_status", "eb_project_sample", "eb_project_warm", "eb_geom_tune",
+                    "eb_unet_sync_status", "eb_unet_inject_wait_fault", "eb_project_sample", "eb_project_warm",
+                    "eb_geom_tune",
                     "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
                     "eb_geom_set_wind_reference", "eb_fma_peak", "eb_ensemble_info",
                     "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule", "eb_geom_set_sources",
@@ -113,6 +114,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.eb_unet_train_step.argtypes = [V, V, V, V, F, P(F), V]
     lib.eb_unet_destroy.argtypes = [V]
     lib.eb_unet_sync_status.argtypes = [V]
+    lib.eb_unet_inject_wait_fault.argtypes = [V]
     lib.eb_project_sample.argtypes = [V, P(_State), D, D, I, D, V, V, V, P(I), V]
     lib.eb_project_warm.argtypes = [V, V, P(_State), D, D, I, D, P(I), P(D), V]
     lib.eb_geom_tune.argtypes = [V, P(_State), D, I, P(I), V]
@@ -136,7 +138,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                  "eb_ensemble_set_state", "eb_ensemble_get_state", "eb_ensemble_step", "eb_ensemble_tune",
                  "eb_ensemble_destroy", "eb_project", "eb_anelastic_step", "eb_unet_create", "eb_unet_set_params",
                  "eb_unet_get_params", "eb_unet_forward", "eb_unet_gradient", "eb_unet_train_step",
-                 "eb_unet_destroy", "eb_unet_sync_status", "eb_project_sample", "eb_project_warm", "eb_geom_tune",
+                 "eb_unet_destroy", "eb_unet_sync_status", "eb_unet_inject_wait_fault", "eb_project_sample",
+                 "eb_project_warm", "eb_geom_tune",
                  "eb_geom_set_slab_levels", "eb_geom_set_bulk_priority", "eb_project_set_preconditioner",
                  "eb_geom_set_wind_reference", "eb_fma_peak", "eb_ensemble_info",
                  "eb_ensemble_inject_barrier_fault", "eb_ensemble_set_schedule", "eb_geom_set_sources",
@@ -628,6 +631,11 @@ class UNet:
         """Raise EbError (EB_ERR_TIMEOUT) if a convolution's bounded wait
         expired since the last check."""
         _check(load().eb_unet_sync_status(self.handle))
+
+    def inject_wait_fault(self):
+        """The failure test: the next convolution never signals its products'
+        completion (``eb_unet_inject_wait_fault``)."""
+        _check(load().eb_unet_inject_wait_fault(self.handle))
 
     def train_step(self, x, target, mask, lr: float, want_loss: bool = False, stream=None):
         for t, ch, nm in ((x, 2, "input"), (target, 1, "target"), (mask, 1, "mask")):

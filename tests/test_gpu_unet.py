@@ -192,3 +192,26 @@ def test_many_tiles_per_cta_match_oracle(eb, un):
     assert np.linalg.norm(g - gw) <= 1e-3 * np.linalg.norm(gw)
     net.sync_status()
     net.close()
+
+
+def test_a_wait_that_runs_out_reports_a_timeout(eb, un):
+    """The bounded waits of the convolution kernels, tested without a GPU
+    fault: one convolution launch issues its products without signalling
+    their completion, every CTA's wait runs out (about one second, twice) and
+    the CTAs return; eb_unet_sync_status reports EB_ERR_TIMEOUT once, and the
+    next forward pass on the same context matches the oracle."""
+    shape = (8, 16, 16)
+    p, x, _, _ = _problem(un, shape, 5)
+    net = eb.UNet(shape[2], shape[1], shape[0])
+    net.set_params(p)
+    xs = torch.from_numpy(x).float().cuda()
+    net.inject_wait_fault()
+    net.forward(xs)
+    with pytest.raises(eb.EbError) as e:
+        net.sync_status()
+    assert e.value.code == 5
+    net.sync_status()   # reported once
+    y = net.forward(xs).double().cpu().numpy()
+    want, _ = un.forward(bf16_weights(un, p), x.astype(np.float32).astype(np.float64))
+    assert np.max(np.abs(y - want[0])) <= 1e-4 * np.max(np.abs(want))
+    net.close()
