@@ -62,7 +62,7 @@ struct Vol {
 // on.  The FP32 inputs are split into BF16 hi + lo (v = hi + lo to about
 // 2^-17 relative) and both parts are multiplied by the BF16 weights, so the
 // products keep FP32-level accuracy.  The weights come prepacked per chunk
-// as [tap][channel group][output channel][8 channels] (k_pack_w), one
+// as [tap][channel group][output channel][8 channels] (k_pack_all), one
 // contiguous copy.  One thread issues the 54 TZ products of a chunk and
 // commits them to an mbarrier; every thread waits (bounded) before the
 // chunk's shared memory is refilled and before the accumulators are read.
@@ -86,10 +86,10 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) 
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-template <int NP, int TZ>
+template <int NP, int TZ, bool MASK>
 __global__ void __launch_bounds__(256, 2) k_conv3_umma(const float *in, int cin, const __nv_bfloat16 *Wp,
                                                        const float *bias, float *out, int cout, Vol V, int relu,
-                                                       int *err, int skip_commit) {
+                                                       const float *mask, int *err, int skip_commit) {
   using G = ConvTile<NP, TZ>;
   extern __shared__ __align__(16) unsigned char cv_smem[];
   __shared__ uint32_t tbase;
@@ -162,19 +162,26 @@ __global__ void __launch_bounds__(256, 2) k_conv3_umma(const float *in, int cin,
 #pragma unroll
     for (int r = 0; r < TZ / 2; ++r) {
       const int rz = half * (TZ / 2) + r, z = z0 + rz;
-      float *dst = out + ((long long)z * V.ny + y) * V.nx + x;
+      const long long vox = ((long long)z * V.ny + y) * V.nx + x;
+      const bool live = xy && z < V.nz;
 #pragma unroll
       for (int cc = 0; cc < NP; cc += 16) {
+        // the mask values first (all 16 loads in flight), then the accumulators
+        float mk[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          mk[j] = MASK && live && cc + j < cout ? __ldg(mask + (long long)(cc + j) * N + vox) : 1.f;
         float v[16];
         umma::ld16(tm + ((uint32_t)(32 * quad) << 16) + (uint32_t)(rz * NP + cc), v);
-        if (xy && z < V.nz) {
+        if (live) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int co = cc + j;
             if (co < cout) {
               float o = v[j] + (bias ? bias[co] : 0.f);
               if (relu) o = fmaxf(o, 0.f);
-              dst[(long long)co * N] = o;
+              if (MASK && !(mk[j] > 0.f)) o = 0.f;   // ReLU backward of the input
+              out[(long long)co * N + vox] = o;
             }
           }
         }
@@ -252,12 +259,13 @@ __global__ void k_head(const float *in, int cin, const __nv_bfloat16 *W, const f
   out[v] = a;
 }
 
-// head backward: dIn[ci][v] = W[ci] dy[v]
-__global__ void k_head_bwd(const float *dy, const __nv_bfloat16 *W, int cin, float *din, long long N) {
+// head backward: dIn[ci][v] = W[ci] dy[v] where the head's (ReLU) input post[ci][v] > 0, else 0
+__global__ void k_head_bwd(const float *dy, const __nv_bfloat16 *W, int cin, const float *post, float *din,
+                           long long N) {
   const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (v >= N) return;
   const float g = dy[v];
-  for (int c = 0; c < cin; ++c) din[c * N + v] = __bfloat162float(W[c]) * g;
+  for (int c = 0; c < cin; ++c) din[c * N + v] = post[c * N + v] > 0.f ? __bfloat162float(W[c]) * g : 0.f;
 }
 
 // sum over voxels of a[c][v] * b[v] (b may be NULL: plain sum) into out[c]
@@ -283,10 +291,8 @@ __global__ void k_chan_dot(const float *a, const float *b, int C, long long N, f
 // the layer itself (n = output channel, W[n][c][a]); flip = 1: its input
 // gradient, the convolution with transposed and flipped weights (n = the
 // layer's input channel, c its output channel: W[c][n][26 - a]).
-__global__ void k_pack_w(const __nv_bfloat16 *W, int cout, int cin, int flip, int NP, __nv_bfloat16 *Wp,
-                         long long total) {
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= total) return;
+__device__ inline void pack_elem(const __nv_bfloat16 *W, int cout, int cin, int flip, int NP, __nv_bfloat16 *Wp,
+                                 long long q) {
   const int j = (int)(q % 8), n = (int)((q / 8) % NP), kg = (int)((q / (8 * NP)) % 2);
   const int a = (int)((q / (16LL * NP)) % 27), chunk = (int)(q / (16LL * NP * 27));
   const int c = chunk * 16 + kg * 8 + j;
@@ -297,6 +303,23 @@ __global__ void k_pack_w(const __nv_bfloat16 *W, int cout, int cin, int flip, in
     if (n < cin && c < cout) w = W[((long long)c * cin + n) * 27 + (26 - a)];
   }
   Wp[q] = w;
+}
+
+// Every convolution's packed weights in one launch (after each change of
+// the weights): job j packs the layer at w_off[j] into dst_off[j], its
+// elements numbered start[j] ... start[j + 1] - 1 of the launch.
+struct PackJobs {
+  int n;
+  long long start[20], w_off[19], dst_off[19];
+  int cout[19], cin[19], flip[19], NP[19];
+};
+
+__global__ void k_pack_all(const __nv_bfloat16 *pb, __nv_bfloat16 *wp, PackJobs J) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= J.start[J.n]) return;
+  int j = 0;
+  while (q >= J.start[j + 1]) ++j;
+  pack_elem(pb + J.w_off[j], J.cout[j], J.cin[j], J.flip[j], J.NP[j], wp + J.dst_off[j], q - J.start[j]);
 }
 
 // Weight gradient on the fifth-generation tensor cores.  For a chunk of 16
@@ -498,11 +521,6 @@ __global__ void __launch_bounds__(256, 2) k_conv3_wgrad_umma(const float *in, in
   if (warp == 0) umma::dealloc(tm, G::TCOLS);
 }
 
-__global__ void k_relu_mask(float *d, const float *post, long long n) {
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q < n && !(post[q] > 0.f)) d[q] = 0.f;
-}
-
 // The pooling and upsampling kernels take one channel per blockIdx.y and a
 // voxel of it per thread, with 32-bit index arithmetic (a network's volumes
 // hold fewer than 2^31 values per channel; eb_unet_create checks).
@@ -521,14 +539,17 @@ __global__ void k_pool(const float *in, Vol V, float *out) {
   out[(size_t)blockIdx.y * hn + r] = s * 0.125f;
 }
 
-// din (C, V) += pool backward of dout (C, V/2)
-__global__ void k_pool_bwd_add(const float *dout, Vol V, float *din) {
+// din (C, V) += pool backward of dout (C, V/2), then zeroed where post (C, V)
+// (the ReLU output the gradient belongs to) is not positive
+__global__ void k_pool_bwd_add(const float *dout, Vol V, const float *post, float *din) {
   const unsigned n = (unsigned)V.nx * V.ny * V.nz;
   const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const unsigned x = r % V.nx, t = r / V.nx, y = t % V.ny, z = t / V.ny;
   const unsigned hx = V.nx / 2, hy = V.ny / 2, hn = hx * hy * (unsigned)(V.nz / 2);
-  din[(size_t)blockIdx.y * n + r] += 0.125f * dout[(size_t)blockIdx.y * hn + ((z / 2) * hy + y / 2) * hx + x / 2];
+  const size_t q = (size_t)blockIdx.y * n + r;
+  const float g = din[q] + 0.125f * dout[(size_t)blockIdx.y * hn + ((z / 2) * hy + y / 2) * hx + x / 2];
+  din[q] = post[q] > 0.f ? g : 0.f;
 }
 
 // out (C, V) = nearest upsampling of in (C, V/2)
@@ -541,8 +562,9 @@ __global__ void k_up(const float *in, Vol V, float *out) {
   out[(size_t)blockIdx.y * n + r] = in[(size_t)blockIdx.y * hn + ((z / 2) * hy + y / 2) * hx + x / 2];
 }
 
-// din (C, V/2) = upsampling backward of dout (C, V): sum of the 8 children
-__global__ void k_up_bwd(const float *dout, Vol V, float *din) {
+// din (C, V/2) = upsampling backward of dout (C, V): sum of the 8 children,
+// zeroed where post (C, V/2) (the ReLU output upsampled) is not positive
+__global__ void k_up_bwd(const float *dout, Vol V, const float *post, float *din) {
   const unsigned hx = V.nx / 2, hy = V.ny / 2, hn = hx * hy * (unsigned)(V.nz / 2);
   const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= hn) return;
@@ -552,7 +574,8 @@ __global__ void k_up_bwd(const float *dout, Vol V, float *din) {
   float s = 0.f;
 #pragma unroll
   for (int a = 0; a < 8; ++a) s += src[(a >> 2) * nxy + ((a >> 1) & 1) * nx + (a & 1)];
-  din[(size_t)blockIdx.y * hn + r] = s;
+  const size_t q = (size_t)blockIdx.y * hn + r;
+  din[q] = post[q] > 0.f ? s : 0.f;
 }
 
 // masked half mean-square loss: dy = mask (y - t) / sum(mask); loss sums
@@ -607,6 +630,7 @@ struct eb_unet_s {
   __nv_bfloat16 *pb = nullptr, *wp = nullptr;   // working weights, one convolution's packed weights
   int *err = nullptr;                            // set when a bounded device wait expired
   int fault = 0;                                 // failure test: the next convolution skips its commit
+  long long wp_off[10][2];                       // packed weights: forward, input gradient
   long long off_w[11], off_b[11];
   // activations (forward) and their gradients
   float *e1a, *e1, *p1, *e2a, *e2, *p2, *ba, *bt, *c2, *d2a, *d2, *c1, *d1a, *d1, *y;
@@ -632,13 +656,13 @@ namespace {
 // packed weights of one convolution: chunks x 27 taps x 2 groups x NP x 8
 long long packed_size(int cin, int cout) { return (long long)((cin + 15) / 16) * 27 * 2 * ((cout + 15) / 16 * 16) * 8; }
 
-template <int NP, int TZ>
+template <int NP, int TZ, bool MASK>
 void conv3_umma_launch(const float *in, int cin, const __nv_bfloat16 *Wp, const float *bias, float *out, int cout,
-                       const Vol &V, bool relu, int *err, int skip_commit, cudaStream_t s) {
+                       const Vol &V, bool relu, const float *mask, int *err, int skip_commit, cudaStream_t s) {
   using G = ConvTile<NP, TZ>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_conv3_umma<NP, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    cudaFuncSetAttribute(k_conv3_umma<NP, TZ, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     attr = true;
   }
   static int sms = 0;
@@ -650,37 +674,72 @@ void conv3_umma_launch(const float *in, int cin, const __nv_bfloat16 *Wp, const 
   }
   const int tiles = ((V.nx + 7) / 8) * ((V.ny + 15) / 16) * ((V.nz + TZ - 1) / TZ);
   const int grid = std::max(1, std::min(tiles, 2 * sms));   // persistent: two CTAs per SM walk the tiles
-  k_conv3_umma<NP, TZ><<<grid, 256, G::SMEM, s>>>(in, cin, Wp, bias, out, cout, V, relu ? 1 : 0, err, skip_commit);
+  k_conv3_umma<NP, TZ, MASK><<<grid, 256, G::SMEM, s>>>(in, cin, Wp, bias, out, cout, V, relu ? 1 : 0, mask, err,
+                                                    skip_commit);
 }
 
-// out (cout, V) = conv of in (cin, V) with the weights W [cout][cin][27]
-// (flip = 0) or, for an input gradient, with the layer W [cin][cout][27]
-// transposed and flipped (flip = 1)
-void conv3_tc(eb_unet u, const float *in, int cin, const __nv_bfloat16 *W, int flip, const float *bias, float *out,
-              int cout, const Vol &V, bool relu, cudaStream_t s) {
+// out (cout, V) = conv of in (cin, V) with the packed weights Wp (a layer's
+// own, or its transposed and flipped ones for an input gradient); mask:
+// where not NULL, out is zeroed wherever mask (cout, V) is not positive (the
+// ReLU backward of the layer below)
+void conv3_tc(eb_unet u, const float *in, int cin, const __nv_bfloat16 *Wp, const float *bias, float *out, int cout,
+              const Vol &V, bool relu, const float *mask, cudaStream_t s) {
   const int NP = (cout + 15) / 16 * 16;
-  const long long np = packed_size(cin, cout);
-  k_pack_w<<<nblk(np), 256, 0, s>>>(W, flip ? cin : cout, flip ? cout : cin, flip, NP, u->wp, np);
   const int skip = u->fault;   // the failure test: one launch never signals its products' completion
   u->fault = 0;
-  switch (NP) {
-    case 16: conv3_umma_launch<16, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, skip, s); break;
-    case 32: conv3_umma_launch<32, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, skip, s); break;
-    case 48: conv3_umma_launch<48, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, skip, s); break;
-    case 64: conv3_umma_launch<64, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, skip, s); break;
-    default: conv3_umma_launch<96, 2>(in, cin, u->wp, bias, out, cout, V, relu, u->err, skip, s); break;
+  // the combinations the network uses: forward passes without a mask, input
+  // gradients with one where a ReLU lies below the layer
+  if (mask) {
+    switch (NP) {
+      case 16: conv3_umma_launch<16, 2, true>(in, cin, Wp, bias, out, cout, V, relu, mask, u->err, skip, s); break;
+      case 32: conv3_umma_launch<32, 2, true>(in, cin, Wp, bias, out, cout, V, relu, mask, u->err, skip, s); break;
+      default: conv3_umma_launch<64, 2, true>(in, cin, Wp, bias, out, cout, V, relu, mask, u->err, skip, s); break;
+    }
+  } else {
+    switch (NP) {
+      case 16: conv3_umma_launch<16, 2, false>(in, cin, Wp, bias, out, cout, V, relu, mask, u->err, skip, s); break;
+      case 32: conv3_umma_launch<32, 2, false>(in, cin, Wp, bias, out, cout, V, relu, mask, u->err, skip, s); break;
+      case 48: conv3_umma_launch<48, 2, false>(in, cin, Wp, bias, out, cout, V, relu, mask, u->err, skip, s); break;
+      case 64: conv3_umma_launch<64, 2, false>(in, cin, Wp, bias, out, cout, V, relu, mask, u->err, skip, s); break;
+      default: conv3_umma_launch<96, 2, false>(in, cin, Wp, bias, out, cout, V, relu, mask, u->err, skip, s); break;
+    }
   }
 }
 
 void conv3(eb_unet u, int l, const float *in, float *out, const Vol &V, bool relu, cudaStream_t s) {
   const LayerSpec &L = kLayers[l];
-  conv3_tc(u, in, L.cin, u->pb + u->off_w[l], 0, u->p + u->off_b[l], out, L.cout, V, relu, s);
+  conv3_tc(u, in, L.cin, u->wp + u->wp_off[l][0], u->p + u->off_b[l], out, L.cout, V, relu, nullptr, s);
 }
 
-// input gradient of layer l: din = conv of dout with flipped, transposed W
-void conv3_dgrad(eb_unet u, int l, const float *dout, float *din, const Vol &V, cudaStream_t s) {
+// the input gradients that carry a ReLU mask (layers 1, 3, 5, 7, 9) have 16,
+// 32 or 64 output channels: the masked kernels instantiated above
+static_assert(kLayers[1].cin == 16 && kLayers[3].cin == 32 && kLayers[5].cin == 64 && kLayers[7].cin == 32 &&
+                  kLayers[9].cin == 16,
+              "masked input gradients need 16, 32 or 64 channels");
+
+// input gradient of layer l: din = conv of dout with flipped, transposed W,
+// zeroed where mask (the layer's ReLU input, when there is one) is not positive
+void conv3_dgrad(eb_unet u, int l, const float *dout, float *din, const float *mask, const Vol &V, cudaStream_t s) {
   const LayerSpec &L = kLayers[l];
-  conv3_tc(u, dout, L.cout, u->pb + u->off_w[l], 1, nullptr, din, L.cin, V, false, s);
+  conv3_tc(u, dout, L.cout, u->wp + u->wp_off[l][1], nullptr, din, L.cin, V, false, mask, s);
+}
+
+// every convolution's packed weights from the BF16 working weights
+void pack_weights(eb_unet u, cudaStream_t s) {
+  PackJobs J{};
+  for (int l = 0; l < 10; ++l)
+    for (int dir = 0; dir < (l == 0 ? 1 : 2); ++dir) {
+      const LayerSpec &L = kLayers[l];
+      const int j = J.n++;
+      J.w_off[j] = u->off_w[l];
+      J.dst_off[j] = u->wp_off[l][dir];
+      J.cout[j] = L.cout;
+      J.cin[j] = L.cin;
+      J.flip[j] = dir;
+      J.NP[j] = ((dir ? L.cin : L.cout) + 15) / 16 * 16;
+      J.start[j + 1] = J.start[j] + (dir ? packed_size(L.cout, L.cin) : packed_size(L.cin, L.cout));
+    }
+  k_pack_all<<<nblk(J.start[J.n]), 256, 0, s>>>(u->pb, u->wp, J);
 }
 
 template <int NP>
@@ -739,41 +798,31 @@ void backward(eb_unet u, const float *x, cudaStream_t s) {
   // head
   k_chan_dot<<<dim3(64, 16), 256, 0, s>>>(u->d1, u->gy, 16, n0, u->g + u->off_w[10]);
   k_chan_dot<<<dim3(64, 1), 256, 0, s>>>(u->gy, nullptr, 1, n0, u->g + u->off_b[10]);
-  k_head_bwd<<<nblk(n0), 256, 0, s>>>(u->gy, u->pb + u->off_w[10], 16, u->gd1, n0);
-  k_relu_mask<<<nblk(16 * n0), 256, 0, s>>>(u->gd1, u->d1, 16 * n0);
+  k_head_bwd<<<nblk(n0), 256, 0, s>>>(u->gy, u->pb + u->off_w[10], 16, u->d1, u->gd1, n0);
   conv3_wgrad(u, 9, u->d1a, u->gd1, V0, s);
-  conv3_dgrad(u, 9, u->gd1, u->gd1a, V0, s);
-  k_relu_mask<<<nblk(16 * n0), 256, 0, s>>>(u->gd1a, u->d1a, 16 * n0);
+  conv3_dgrad(u, 9, u->gd1, u->gd1a, u->d1a, V0, s);
   conv3_wgrad(u, 8, u->c1, u->gd1a, V0, s);
-  conv3_dgrad(u, 8, u->gd1a, u->gc1, V0, s);
-  k_up_bwd<<<dim3(nblk(n1), 32), 256, 0, s>>>(u->gc1, V0, u->gd2);
+  conv3_dgrad(u, 8, u->gd1a, u->gc1, nullptr, V0, s);
+  k_up_bwd<<<dim3(nblk(n1), 32), 256, 0, s>>>(u->gc1, V0, u->d2, u->gd2);
   cudaMemcpyAsync(u->ge1, u->gc1 + 32 * n0, sizeof(float) * 16 * n0, cudaMemcpyDeviceToDevice, s);
-  k_relu_mask<<<nblk(32 * n1), 256, 0, s>>>(u->gd2, u->d2, 32 * n1);
   conv3_wgrad(u, 7, u->d2a, u->gd2, V1, s);
-  conv3_dgrad(u, 7, u->gd2, u->gd2a, V1, s);
-  k_relu_mask<<<nblk(32 * n1), 256, 0, s>>>(u->gd2a, u->d2a, 32 * n1);
+  conv3_dgrad(u, 7, u->gd2, u->gd2a, u->d2a, V1, s);
   conv3_wgrad(u, 6, u->c2, u->gd2a, V1, s);
-  conv3_dgrad(u, 6, u->gd2a, u->gc2, V1, s);
-  k_up_bwd<<<dim3(nblk(n2), 64), 256, 0, s>>>(u->gc2, V1, u->gbt);
+  conv3_dgrad(u, 6, u->gd2a, u->gc2, nullptr, V1, s);
+  k_up_bwd<<<dim3(nblk(n2), 64), 256, 0, s>>>(u->gc2, V1, u->bt, u->gbt);
   cudaMemcpyAsync(u->ge2, u->gc2 + 64 * n1, sizeof(float) * 32 * n1, cudaMemcpyDeviceToDevice, s);
-  k_relu_mask<<<nblk(64 * n2), 256, 0, s>>>(u->gbt, u->bt, 64 * n2);
   conv3_wgrad(u, 5, u->ba, u->gbt, V2, s);
-  conv3_dgrad(u, 5, u->gbt, u->gba, V2, s);
-  k_relu_mask<<<nblk(64 * n2), 256, 0, s>>>(u->gba, u->ba, 64 * n2);
+  conv3_dgrad(u, 5, u->gbt, u->gba, u->ba, V2, s);
   conv3_wgrad(u, 4, u->p2, u->gba, V2, s);
-  conv3_dgrad(u, 4, u->gba, u->gp2, V2, s);
-  k_pool_bwd_add<<<dim3(nblk(n1), 32), 256, 0, s>>>(u->gp2, V1, u->ge2);
-  k_relu_mask<<<nblk(32 * n1), 256, 0, s>>>(u->ge2, u->e2, 32 * n1);
+  conv3_dgrad(u, 4, u->gba, u->gp2, nullptr, V2, s);
+  k_pool_bwd_add<<<dim3(nblk(n1), 32), 256, 0, s>>>(u->gp2, V1, u->e2, u->ge2);
   conv3_wgrad(u, 3, u->e2a, u->ge2, V1, s);
-  conv3_dgrad(u, 3, u->ge2, u->ge2a, V1, s);
-  k_relu_mask<<<nblk(32 * n1), 256, 0, s>>>(u->ge2a, u->e2a, 32 * n1);
+  conv3_dgrad(u, 3, u->ge2, u->ge2a, u->e2a, V1, s);
   conv3_wgrad(u, 2, u->p1, u->ge2a, V1, s);
-  conv3_dgrad(u, 2, u->ge2a, u->gp1, V1, s);
-  k_pool_bwd_add<<<dim3(nblk(n0), 16), 256, 0, s>>>(u->gp1, V0, u->ge1);
-  k_relu_mask<<<nblk(16 * n0), 256, 0, s>>>(u->ge1, u->e1, 16 * n0);
+  conv3_dgrad(u, 2, u->ge2a, u->gp1, nullptr, V1, s);
+  k_pool_bwd_add<<<dim3(nblk(n0), 16), 256, 0, s>>>(u->gp1, V0, u->e1, u->ge1);
   conv3_wgrad(u, 1, u->e1a, u->ge1, V0, s);
-  conv3_dgrad(u, 1, u->ge1, u->ge1a, V0, s);
-  k_relu_mask<<<nblk(16 * n0), 256, 0, s>>>(u->ge1a, u->e1a, 16 * n0);
+  conv3_dgrad(u, 1, u->ge1, u->ge1a, u->e1a, V0, s);
   conv3_wgrad(u, 0, x, u->ge1a, V0, s);
 }
 
@@ -854,15 +903,18 @@ eb_status eb_unet_create(int nx, int ny, int nz, eb_unet *out) {
   u->V[2] = {nx / 4, ny / 4, nz / 4};
   u->np = total_params();
   long long o = 0;
-  long long wpmax = 0;
+  long long wpn = 0;
   for (int l = 0; l < 11; ++l) {
     u->off_w[l] = o;
     o += layer_w(l);
     u->off_b[l] = o;
     o += kLayers[l].cout;
-    if (kLayers[l].k == 3)
-      wpmax = std::max({wpmax, packed_size(kLayers[l].cin, kLayers[l].cout),
-                        packed_size(kLayers[l].cout, kLayers[l].cin)});
+    if (kLayers[l].k == 3) {
+      u->wp_off[l][0] = wpn;
+      wpn += packed_size(kLayers[l].cin, kLayers[l].cout);
+      u->wp_off[l][1] = wpn;
+      wpn += packed_size(kLayers[l].cout, kLayers[l].cin);
+    }
   }
   const long long n0 = u->V[0].n(), n1 = u->V[1].n(), n2 = u->V[2].n();
   struct {
@@ -876,7 +928,8 @@ eb_status eb_unet_create(int nx, int ny, int nz, eb_unet *out) {
     if (e == cudaSuccess) e = u->alloc(x.q, x.n);
   if (e == cudaSuccess) e = u->alloc(&u->p, u->np);
   if (e == cudaSuccess) e = u->alloc(&u->pb, u->np);
-  if (e == cudaSuccess) e = u->alloc(&u->wp, wpmax);
+  if (e == cudaSuccess) e = u->alloc(&u->wp, wpn);
+  if (e == cudaSuccess) e = cudaMemset(u->wp, 0, sizeof(__nv_bfloat16) * wpn);   // the packed zero weights
   if (e == cudaSuccess) e = u->alloc(&u->err, 1);
   if (e == cudaSuccess) e = cudaMemset(u->err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(u->p, 0, sizeof(float) * u->np);
@@ -903,6 +956,7 @@ eb_status eb_unet_set_params(eb_unet u, const float *host, int64_t n) {
   if (n != u->np) return fail(EB_ERR_INVALID_ARG, "wrong parameter count");
   CUDA_TRY(cudaMemcpy(u->p, host, sizeof(float) * n, cudaMemcpyHostToDevice), "set parameters");
   k_to_bf16<<<nblk(n), 256>>>(u->p, u->pb, n);
+  pack_weights(u, 0);
   CUDA_TRY(cudaGetLastError(), "set parameters");
   if (u->grads) {
     CUDA_TRY(cudaMemset(u->m, 0, sizeof(float) * n), "optimiser state");
@@ -954,6 +1008,7 @@ eb_status eb_unet_train_step(eb_unet u, const float *in, const float *target, co
   u->t += 1;
   const float c1 = (float)(1.0 / (1.0 - pow(0.9, u->t))), c2 = (float)(1.0 / (1.0 - pow(0.999, u->t)));
   k_adam<<<nblk(u->np), 256, 0, s>>>(u->p, u->m, u->v, u->g, u->pb, u->np, lr, c1, c2);
+  pack_weights(u, s);
   CUDA_TRY(cudaGetLastError(), "network update");
   return EB_OK;
 }
