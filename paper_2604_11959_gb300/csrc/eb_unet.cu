@@ -356,7 +356,7 @@ struct WgTile {
 
 template <int NP>
 __global__ void __launch_bounds__(256, 2) k_conv3_wgrad_umma(const float *in, int cin, const float *dout, int cout,
-                                                          Vol V, float *dW, int *err) {
+                                                             Vol V, float *dW, int *err, int vec) {
   using G = WgTile<NP>;
   extern __shared__ __align__(16) unsigned char wg_smem[];
   __shared__ uint32_t tbase;
@@ -392,10 +392,23 @@ __global__ void __launch_bounds__(256, 2) k_conv3_wgrad_umma(const float *in, in
       const int y = y0 + hy - 1, z = z0 + hz - 1, c = c0 + ci;
       const bool row = q < IT && c < cin && y >= 0 && y < V.ny && z >= 0 && z < V.nz;
       const float *src = in + (long long)c * N + ((long long)z * V.ny + y) * V.nx;
+      if (vec) {   // rows of a multiple of 4 values, 16-byte aligned: x0 - 4 ... x0 + 11 in four float4
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 *s4 = reinterpret_cast<const float4 *>(src + x0);
+        const float4 a = row && x0 >= 4 ? __ldg(s4 - 1) : z4;
+        const float4 b = row ? __ldg(s4) : z4;
+        const float4 c4 = row && x0 + 4 < V.nx ? __ldg(s4 + 1) : z4;
+        const float4 d = row && x0 + 8 < V.nx ? __ldg(s4 + 2) : z4;
+        pin[k][0] = a.w;
+        pin[k][1] = b.x, pin[k][2] = b.y, pin[k][3] = b.z, pin[k][4] = b.w;
+        pin[k][5] = c4.x, pin[k][6] = c4.y, pin[k][7] = c4.z, pin[k][8] = c4.w;
+        pin[k][9] = d.x;
+      } else {
 #pragma unroll
-      for (int e = 0; e < 10; ++e) {
-        const int x = x0 - 1 + e;
-        pin[k][e] = row && x >= 0 && x < V.nx ? src[x] : 0.f;
+        for (int e = 0; e < 10; ++e) {
+          const int x = x0 - 1 + e;
+          pin[k][e] = row && x >= 0 && x < V.nx ? src[x] : 0.f;
+        }
       }
     }
 #pragma unroll
@@ -405,8 +418,17 @@ __global__ void __launch_bounds__(256, 2) k_conv3_wgrad_umma(const float *in, in
       const int y = y0 + vy, z = z0 + vz;
       const bool row = co < cout && y < V.ny && z < V.nz;
       const float *src = dout + (long long)co * N + ((long long)z * V.ny + y) * V.nx;
+      if (vec) {
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 *s4 = reinterpret_cast<const float4 *>(src + x0);
+        const float4 b = row ? __ldg(s4) : z4;
+        const float4 c4 = row && x0 + 4 < V.nx ? __ldg(s4 + 1) : z4;
+        pdo[k][0] = b.x, pdo[k][1] = b.y, pdo[k][2] = b.z, pdo[k][3] = b.w;
+        pdo[k][4] = c4.x, pdo[k][5] = c4.y, pdo[k][6] = c4.z, pdo[k][7] = c4.w;
+      } else {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) pdo[k][e] = row && x0 + e < V.nx ? src[x0 + e] : 0.f;
+        for (int e = 0; e < 8; ++e) pdo[k][e] = row && x0 + e < V.nx ? src[x0 + e] : 0.f;
+      }
     }
   };
   auto store_tile = [&]() {
@@ -757,7 +779,9 @@ void conv3_wgrad_launch(const float *in, int cin, const float *dout, int cout, c
   const int ntiles = ((V.nx + G::TX - 1) / G::TX) * ((V.ny + G::TY - 1) / G::TY) * ((V.nz + G::TZ - 1) / G::TZ);
   const int gy = 3 / G::DZN, gz = (cin + G::CI - 1) / G::CI;
   const int gx = std::max(1, std::min(ntiles, 2 * sms / (gy * gz)));   // two CTAs per SM, each over many tiles
-  k_conv3_wgrad_umma<NP><<<dim3(gx, gy, gz), 256, G::SMEM, s>>>(in, cin, dout, cout, V, dW, err);
+  // float4 loads where every row starts on a 16-byte boundary
+  const int vec = V.nx % 4 == 0 && (uintptr_t)in % 16 == 0 && (uintptr_t)dout % 16 == 0;
+  k_conv3_wgrad_umma<NP><<<dim3(gx, gy, gz), 256, G::SMEM, s>>>(in, cin, dout, cout, V, dW, err, vec);
 }
 
 void conv3_wgrad(eb_unet u, int l, const float *in, const float *dout, const Vol &V, cudaStream_t s) {
