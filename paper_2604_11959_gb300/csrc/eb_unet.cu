@@ -356,7 +356,7 @@ struct WgTile {
 
 template <int NP>
 __global__ void __launch_bounds__(256, 2) k_conv3_wgrad_umma(const float *in, int cin, const float *dout, int cout,
-                                                             Vol V, float *dW, int *err, int vec) {
+                                                             Vol V, float *dW, float *dB, int *err, int vec) {
   using G = WgTile<NP>;
   extern __shared__ __align__(16) unsigned char wg_smem[];
   __shared__ uint32_t tbase;
@@ -382,7 +382,9 @@ __global__ void __launch_bounds__(256, 2) k_conv3_wgrad_umma(const float *in, in
   constexpr int IT = G::HZ * G::HY * G::CI, IS = (IT + 255) / 256;
   constexpr int DI = G::TZ * G::TY * NP, DS = DI / 256;
   static_assert(DI % 256 == 0, "whole output-gradient rows per thread");
-  float pin[IS][10], pdo[DS][8];
+  float pin[IS][10], pdo[DS][8], bsum[DS];
+#pragma unroll
+  for (int k = 0; k < DS; ++k) bsum[k] = 0.f;
   auto load_tile = [&](int tile) {
     const int x0 = (tile % ntx) * G::TX, y0 = ((tile / ntx) % nty) * G::TY, z0 = (tile / (ntx * nty)) * G::TZ;
 #pragma unroll
@@ -457,6 +459,12 @@ __global__ void __launch_bounds__(256, 2) k_conv3_wgrad_umma(const float *in, in
 #pragma unroll
     for (int k = 0; k < DS; ++k) {
       const int q = tid + 256 * k;
+      if (dB && blockIdx.y == 0 && blockIdx.z == 0) {   // bias gradient: once per tile (first dz set, chunk)
+        float r = 0.f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r += pdo[k][e];
+        bsum[k] += r;
+      }
       uint32_t hw[4], lw[4];
 #pragma unroll
       for (int e = 0; e < 8; e += 2) {
@@ -537,6 +545,13 @@ __global__ void __launch_bounds__(256, 2) k_conv3_wgrad_umma(const float *in, in
   } else if (!ok) {
     umma::bar_wait(&mbar, (uint32_t)((it - 1) & 1), kWaitCycles);
     if (tid == 0) atomicExch(err, 1);
+  }
+  if (dB && blockIdx.y == 0 && blockIdx.z == 0) {
+#pragma unroll
+    for (int k = 0; k < DS; ++k) {
+      const int co = (tid + 256 * k) % NP;
+      if (co < cout) atomicAdd(dB + co, bsum[k]);
+    }
   }
   umma::fence_before();
   __syncthreads();
@@ -765,8 +780,8 @@ void pack_weights(eb_unet u, cudaStream_t s) {
 }
 
 template <int NP>
-void conv3_wgrad_launch(const float *in, int cin, const float *dout, int cout, const Vol &V, float *dW, int *err,
-                        cudaStream_t s) {
+void conv3_wgrad_launch(const float *in, int cin, const float *dout, int cout, const Vol &V, float *dW, float *dB,
+                        int *err, cudaStream_t s) {
   using G = WgTile<NP>;
   static int sms = 0;
   if (!sms) {
@@ -781,16 +796,15 @@ void conv3_wgrad_launch(const float *in, int cin, const float *dout, int cout, c
   const int gx = std::max(1, std::min(ntiles, 2 * sms / (gy * gz)));   // two CTAs per SM, each over many tiles
   // float4 loads where every row starts on a 16-byte boundary
   const int vec = V.nx % 4 == 0 && (uintptr_t)in % 16 == 0 && (uintptr_t)dout % 16 == 0;
-  k_conv3_wgrad_umma<NP><<<dim3(gx, gy, gz), 256, G::SMEM, s>>>(in, cin, dout, cout, V, dW, err, vec);
+  k_conv3_wgrad_umma<NP><<<dim3(gx, gy, gz), 256, G::SMEM, s>>>(in, cin, dout, cout, V, dW, dB, err, vec);
 }
 
 void conv3_wgrad(eb_unet u, int l, const float *in, const float *dout, const Vol &V, cudaStream_t s) {
   const LayerSpec &L = kLayers[l];
-  float *dW = u->g + u->off_w[l];
-  if (L.cout <= 16) conv3_wgrad_launch<16>(in, L.cin, dout, L.cout, V, dW, u->err, s);
-  else if (L.cout <= 32) conv3_wgrad_launch<32>(in, L.cin, dout, L.cout, V, dW, u->err, s);
-  else conv3_wgrad_launch<64>(in, L.cin, dout, L.cout, V, dW, u->err, s);
-  k_chan_dot<<<dim3(64, L.cout), 256, 0, s>>>(dout, nullptr, L.cout, V.n(), u->g + u->off_b[l]);
+  float *dW = u->g + u->off_w[l], *dB = u->g + u->off_b[l];   // the bias gradient rides along
+  if (L.cout <= 16) conv3_wgrad_launch<16>(in, L.cin, dout, L.cout, V, dW, dB, u->err, s);
+  else if (L.cout <= 32) conv3_wgrad_launch<32>(in, L.cin, dout, L.cout, V, dW, dB, u->err, s);
+  else conv3_wgrad_launch<64>(in, L.cin, dout, L.cout, V, dW, dB, u->err, s);
 }
 
 void forward(eb_unet u, const float *x, cudaStream_t s) {
