@@ -69,12 +69,8 @@ __global__ void k_static(StepArgs<T> A, StaticBlocks SB) {
 
 template <typename T, int V, int TYV>
 void set_smem_attr() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(k_fast_tiled<T, V, TYV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)BulkTile<T, TYV>::BYTES);
-    done = true;
-  }
+  static unsigned long long done = 0;
+  ebk_smem_limit(k_fast_tiled<T, V, TYV>, (int)BulkTile<T, TYV>::BYTES, done);
 }
 
 template <typename T, int V, int TYV>

@@ -17,6 +17,32 @@
 
 #include "../../include/eb.h"
 
+// A kernel's dynamic shared-memory limit belongs to a device's context: it
+// is set once per device (done: one bit per device index).
+template <typename K>
+inline void ebk_smem_limit(K *kernel, int bytes, unsigned long long &done) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(done & bit)) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    done |= bit;
+  }
+}
+
+// SM count of the current device, queried once per device.
+inline int ebk_sm_count() {
+  static int count[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int &c = count[dev & 63];
+  if (c < 1) {
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    if (c < 1) c = 1;
+  }
+  return c;
+}
+
 #define EBK_COVERED 0
 #define EBK_REGULAR 1
 #define EBK_CUT 2

@@ -697,18 +697,9 @@ template <int NP, int TZ, bool MASK>
 void conv3_umma_launch(const float *in, int cin, const __nv_bfloat16 *Wp, const float *bias, float *out, int cout,
                        const Vol &V, bool relu, const float *mask, int *err, int skip_commit, cudaStream_t s) {
   using G = ConvTile<NP, TZ>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_conv3_umma<NP, TZ, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-    attr = true;
-  }
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    sms = std::max(sms, 1);
-  }
+  static unsigned long long attr = 0;
+  ebk_smem_limit(k_conv3_umma<NP, TZ, MASK>, G::SMEM, attr);
+  const int sms = ebk_sm_count();
   const int tiles = ((V.nx + 7) / 8) * ((V.ny + 15) / 16) * ((V.nz + TZ - 1) / TZ);
   const int grid = std::max(1, std::min(tiles, 2 * sms));   // persistent: two CTAs per SM walk the tiles
   k_conv3_umma<NP, TZ, MASK><<<grid, 256, G::SMEM, s>>>(in, cin, Wp, bias, out, cout, V, relu ? 1 : 0, mask, err,
@@ -783,14 +774,9 @@ template <int NP>
 void conv3_wgrad_launch(const float *in, int cin, const float *dout, int cout, const Vol &V, float *dW, float *dB,
                         int *err, cudaStream_t s) {
   using G = WgTile<NP>;
-  static int sms = 0;
-  if (!sms) {
-    cudaFuncSetAttribute(k_conv3_wgrad_umma<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    sms = std::max(sms, 1);
-  }
+  static unsigned long long attr = 0;
+  ebk_smem_limit(k_conv3_wgrad_umma<NP>, G::SMEM, attr);
+  const int sms = ebk_sm_count();
   const int ntiles = ((V.nx + G::TX - 1) / G::TX) * ((V.ny + G::TY - 1) / G::TY) * ((V.nz + G::TZ - 1) / G::TZ);
   const int gy = 3 / G::DZN, gz = (cin + G::CI - 1) / G::CI;
   const int gx = std::max(1, std::min(ntiles, 2 * sms / (gy * gz)));   // two CTAs per SM, each over many tiles
